@@ -1,0 +1,288 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Every check compares the oracle with something other than itself: closed forms,
+scipy's matrix exponential, dense numpy Kronecker products, hand-derived values of
+the paper's Listing 4, invariants, parameter shift and finite differences.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import oracle as O
+from paper_2406_19212_gb300 import inputs as I
+from tests.dense_ref import PAULI, embed, pauli_operator
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def op(name, qubits, param=-1, fixed=(), data=None):
+    return I.Op(name, tuple(qubits), param, tuple(fixed), data)
+
+
+# ----------------------------------------------------------------- gate matrices
+
+@pytest.mark.parametrize("t", [0.0, 0.3, 1.7, -2.9, 5.5])
+def test_rotations_are_pauli_exponentials(t):
+    # Sec. II.B: Rx, Ry, Rz == exp(-i t P / 2) (Ry and Rz per the readings of the garbles)
+    for name, P in (("RX", "X"), ("RY", "Y"), ("RZ", "Z")):
+        M = O.gate_matrix(op(name, (0,), fixed=(t,)))
+        np.testing.assert_allclose(M, scipy.linalg.expm(-0.5j * t * PAULI[P]), atol=1e-15)
+
+
+@pytest.mark.parametrize("t", [0.0, 0.4, 2.2, 4.0])
+def test_rotation_expectation_closed_forms(t):
+    z0 = O.zero_state(1)
+    Z = [(1.0, ((0, "Z"),))]
+    X = [(1.0, ((0, "X"),))]
+    c = I.Circuit(1, [op("RX", (0,), fixed=(t,))], 0)
+    assert O.expect(Z, O.apply_circuit(c, []), 1) == pytest.approx(math.cos(t), abs=1e-15)
+    c = I.Circuit(1, [op("RY", (0,), fixed=(t,))], 0)
+    psi = O.apply_circuit(c, [])
+    assert O.expect(Z, psi, 1) == pytest.approx(math.cos(t), abs=1e-15)
+    assert O.expect(X, psi, 1) == pytest.approx(math.sin(t), abs=1e-15)
+    c = I.Circuit(1, [op("H", (0,)), op("RZ", (0,), fixed=(t,))], 0)
+    assert O.expect(X, O.apply_circuit(c, []), 1) == pytest.approx(math.cos(t), abs=1e-15)
+    assert z0[0] == 1
+
+
+def test_fixed_gates_textbook():
+    r = 1 / math.sqrt(2)
+    np.testing.assert_allclose(O.gate_matrix(op("H", (0,))), [[r, r], [r, -r]], atol=1e-16)
+    np.testing.assert_allclose(O.gate_matrix(op("S", (0,))), [[1, 0], [0, 1j]], atol=1e-16)
+    np.testing.assert_allclose(O.gate_matrix(op("T", (0,))),
+                               [[1, 0], [0, np.exp(1j * np.pi / 4)]], atol=1e-16)
+    for name in "XYZ":
+        np.testing.assert_allclose(O.gate_matrix(op(name, (0,))), PAULI[name], atol=0)
+    W = (PAULI["X"] + PAULI["Y"]) / math.sqrt(2)
+    for name, G in (("SX", PAULI["X"]), ("SY", PAULI["Y"]), ("SW", W)):
+        M = O.gate_matrix(op(name, (0,)))
+        np.testing.assert_allclose(M @ M, G, atol=1e-15)          # square root
+        np.testing.assert_allclose(M, scipy.linalg.sqrtm(G), atol=1e-12)  # principal root
+        np.testing.assert_allclose(M.conj().T @ M, np.eye(2), atol=1e-15)
+
+
+def _basis_map(name, n=2):
+    """Gate action on computational basis states |b0 b1> (index b0 + 2 b1)."""
+    M = O.gate_matrix(op(name, (0, 1)))
+    return {c: {r: M[r, c] for r in range(4) if M[r, c] != 0} for c in range(4)}
+
+
+def test_two_qubit_gate_semantics():
+    # CNOT(control q0, target q1): flips q1 when q0 = 1
+    m = _basis_map("CNOT")
+    assert m == {0: {0: 1}, 1: {3: 1}, 2: {2: 1}, 3: {1: 1}}
+    assert _basis_map("CZ") == {0: {0: 1}, 1: {1: 1}, 2: {2: 1}, 3: {3: -1}}
+    assert _basis_map("SWAP") == {0: {0: 1}, 1: {2: 1}, 2: {1: 1}, 3: {3: 1}}
+    assert _basis_map("ISWAP") == {0: {0: 1}, 1: {2: 1j}, 2: {1: 1j}, 3: {3: 1}}
+    # CONTROL with X as the target block is CNOT
+    ctl = O.gate_matrix(op("CONTROL", (0, 1), data=PAULI["X"]))
+    np.testing.assert_allclose(ctl, O.gate_matrix(op("CNOT", (0, 1))), atol=0)
+
+
+def test_fsim_special_cases():
+    # Eq. (FSIM): fsim(pi/2, 0) = iSWAP^dag; fsim(0, phi) = diag(1, 1, 1, e^{-i phi})
+    F = O.gate_matrix(op("FSIM", (0, 1), fixed=(math.pi / 2, 0.0)))
+    iswap = O.gate_matrix(op("ISWAP", (0, 1)))
+    np.testing.assert_allclose(F, iswap.conj().T, atol=1e-15)
+    F = O.gate_matrix(op("FSIM", (0, 1), fixed=(0.0, 0.7)))
+    np.testing.assert_allclose(F, np.diag([1, 1, 1, np.exp(-0.7j)]), atol=1e-15)
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        F = O.gate_matrix(op("FSIM", (0, 1), fixed=tuple(rng.uniform(-3, 3, 5))))
+        np.testing.assert_allclose(F.conj().T @ F, np.eye(4), atol=1e-14)
+    # theta, phi part is exp(-i theta (XX+YY)/2) followed by the |11> phase
+    th = 0.83
+    XXYY = np.kron(PAULI["X"], PAULI["X"]) + np.kron(PAULI["Y"], PAULI["Y"])
+    F = O.gate_matrix(op("FSIM", (0, 1), fixed=(th, 0.0)))
+    np.testing.assert_allclose(F, scipy.linalg.expm(-0.5j * th * XXYY), atol=1e-14)
+
+
+@pytest.mark.parametrize("name,strength", [("DEPOL", 0.13), ("AMPDAMP", 0.21),
+                                           ("PHASEDAMP", 0.4)])
+def test_kraus_completeness(name, strength):
+    ks = O.kraus(op(name, (0,), fixed=(strength,)))
+    np.testing.assert_allclose(sum(k.conj().T @ k for k in ks), np.eye(2), atol=1e-15)
+
+
+# ------------------------------------------------------------- state evolution
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (3, 2), (4, 3), (5, 4), (6, 5)])
+def test_circuit_matches_dense_kronecker(n, seed):
+    w = I.random_circuit(n, 40, seed)
+    U = np.eye(1 << n, dtype=complex)
+    for o in w.circuit.ops:
+        U = embed(O.gate_matrix(o, w.theta), o.qubits, n) @ U
+    psi = O.apply_circuit(w.circuit, w.theta)
+    np.testing.assert_allclose(psi, U[:, 0], atol=1e-13)
+    start = I.random_state(n, seed + 100)
+    np.testing.assert_allclose(O.apply_circuit(w.circuit, w.theta, start), U @ start, atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 12])
+def test_ghz_closed_form(n):
+    ops = [op("H", (0,))] + [op("CNOT", (i, i + 1)) for i in range(n - 1)]
+    psi = O.apply_circuit(I.Circuit(n, ops, 0), [])
+    ref = np.zeros(1 << n, dtype=complex)
+    ref[0] = ref[-1] = 1 / math.sqrt(2)
+    np.testing.assert_allclose(psi, ref, atol=1e-15)
+
+
+def qft_ops(n):
+    ops = []
+    for i in range(1, n + 1):
+        t = n - i
+        ops.append(op("H", (t,)))
+        for j in range(i + 1, n + 1):
+            ang = 2 * math.pi / 2 ** (j - i + 1)
+            ops.append(op("CONTROL", (n - j, t), data=np.diag([1, np.exp(1j * ang)])))
+    for i in range(1, n // 2 + 1):
+        ops.append(op("SWAP", (n - i, i - 1)))
+    return ops
+
+
+@pytest.mark.parametrize("n,x", [(3, 5), (5, 19), (8, 201)])
+def test_qft_closed_form(n, x):
+    psi0 = np.zeros(1 << n, dtype=complex)
+    psi0[x] = 1
+    psi = O.apply_circuit(I.Circuit(n, qft_ops(n), 0), [], psi0)
+    y = np.arange(1 << n)
+    np.testing.assert_allclose(psi, np.exp(2j * np.pi * x * y / 2 ** n) / 2 ** (n / 2), atol=1e-13)
+
+
+def _golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, expr = line.split(None, 1)
+                vals[k] = eval(expr, {"math": math})
+    return vals
+
+
+def test_listing4_golden():
+    g = _golden("listing4.txt")
+    c = I.Circuit(2, [op("H", (0,)), op("RY", (0,), fixed=(math.pi / 4,)),
+                      op("CNOT", (0, 1))], 0)
+    psi = O.apply_circuit(c, [])
+    for i in range(4):
+        assert psi[i].real == pytest.approx(g[f"amp_re_{i}"], abs=1e-15)
+        assert psi[i].imag == pytest.approx(g[f"amp_im_{i}"], abs=1e-15)
+    p0 = abs(psi[0]) ** 2 + abs(psi[1]) ** 2
+    assert p0 == pytest.approx(g["prob_q1_0"], abs=1e-15)
+    assert 1 - p0 == pytest.approx(g["prob_q1_1"], abs=1e-15)
+
+
+def test_norm_preserved_and_inverse():
+    w = I.random_circuit(10, 200, 7)
+    psi = O.apply_circuit(w.circuit, w.theta)
+    assert np.linalg.norm(psi) == pytest.approx(1.0, abs=1e-13)
+
+
+# ----------------------------------------------------------------- expectation
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (3, 1), (5, 2), (6, 3)])
+def test_expectation_matches_dense(n, seed):
+    w = I.random_circuit(n, 10, seed)
+    terms = w.observable + I.heisenberg_1d(n) if n > 1 else w.observable
+    psi = I.random_state(n, seed)
+    H = pauli_operator(terms, n)
+    e, im = O.expect(terms, psi, n, return_imag=True)
+    assert e == pytest.approx((psi.conj() @ H @ psi).real, abs=1e-13)
+    assert abs(im) < 1e-13
+    np.testing.assert_allclose(O.apply_hamiltonian(terms, psi, n), H @ psi, atol=1e-13)
+
+
+# -------------------------------------------------------------------- gradients
+
+@pytest.mark.parametrize("n,seed,share", [(3, 11, False), (5, 12, True), (6, 13, False)])
+def test_adjoint_matches_parameter_shift(n, seed, share):
+    w = I.random_circuit(n, 60, seed, param_share=share)
+    e, g = O.adjoint_grad(w.circuit, w.theta, w.observable)
+    assert e == pytest.approx(O.energy(w.circuit, w.theta, w.observable), abs=1e-13)
+    ps = O.parameter_shift_grad(w.circuit, w.theta, w.observable)
+    np.testing.assert_allclose(g, ps, atol=1e-12)
+
+
+def test_adjoint_matches_finite_difference_plain10():
+    w = I.plain_10q()
+    e, g = O.adjoint_grad(w.circuit, w.theta, w.observable)
+    idx = [0, 13, 57, 119]
+    fd = O.finite_difference_grad(w.circuit, w.theta, w.observable, idx, h=1e-5)
+    np.testing.assert_allclose(g[idx], fd, atol=1e-8)
+
+
+# --------------------------------------------------------------------- density
+
+def test_single_qubit_channel_closed_forms():
+    rng = np.random.default_rng(3)
+    rho = I.random_density(1, 9).reshape(2, 2, order="F")
+    vec = rho.reshape(-1, order="F")
+    p, g = 0.23, 0.31
+    out = O.rho_apply_circuit(I.Circuit(1, [op("DEPOL", (0,), fixed=(p,))], 0, True), [], vec)
+    np.testing.assert_allclose(out.reshape(2, 2, order="F"),
+                               (1 - p) * rho + p * np.trace(rho) * np.eye(2) / 2, atol=1e-15)
+    one = np.array([0, 0, 0, 1], dtype=complex)          # |1><1|
+    out = O.rho_apply_circuit(I.Circuit(1, [op("AMPDAMP", (0,), fixed=(g,))], 0, True), [], one)
+    np.testing.assert_allclose(out, [g, 0, 0, 1 - g], atol=1e-15)
+    out = O.rho_apply_circuit(I.Circuit(1, [op("PHASEDAMP", (0,), fixed=(g,))], 0, True), [], vec)
+    r = out.reshape(2, 2, order="F")
+    np.testing.assert_allclose(np.diag(r), np.diag(rho), atol=1e-15)
+    np.testing.assert_allclose(r[0, 1], rho[0, 1] * math.sqrt(1 - g), atol=1e-15)
+    assert rng is not None
+
+
+@pytest.mark.parametrize("n,seed", [(1, 1), (2, 2), (3, 3)])
+def test_density_matches_dense_matrices(n, seed):
+    w = I.random_circuit(n, 25, seed, density=True, with_channels=True)
+    rho = I.random_density(n, seed).reshape(1 << n, 1 << n, order="F")
+    ref = rho.copy()
+    for o in w.circuit.ops:
+        if o.name in I.CHANNELS:
+            ks = [embed(k, o.qubits, n) for k in O.kraus(o)]
+            ref = sum(k @ ref @ k.conj().T for k in ks)
+        else:
+            U = embed(O.gate_matrix(o, w.theta), o.qubits, n)
+            ref = U @ ref @ U.conj().T
+    out = O.rho_apply_circuit(w.circuit, w.theta, rho.reshape(-1, order="F"))
+    np.testing.assert_allclose(out, ref.reshape(-1, order="F"), atol=1e-13)
+    vec = O.vec_apply_circuit(w.circuit, w.theta, rho.reshape(-1, order="F"))
+    np.testing.assert_allclose(vec, ref.reshape(-1, order="F"), atol=1e-13)
+    H = pauli_operator(w.observable, n)
+    e, im = O.rho_expect(w.observable, out, n, return_imag=True)
+    assert e == pytest.approx(np.trace(H @ ref).real, abs=1e-13)
+    assert abs(im) < 1e-13
+
+
+def test_unitary_density_equals_pure_projector():
+    w = I.random_circuit(4, 50, 21)
+    psi = O.apply_circuit(w.circuit, w.theta)
+    rho = O.rho_apply_circuit(I.Circuit(4, w.circuit.ops, w.circuit.n_params, True), w.theta)
+    np.testing.assert_allclose(rho, np.outer(psi, psi.conj()).reshape(-1, order="F"), atol=1e-14)
+
+
+def test_noisy_trace_hermitian_positive():
+    w = I.noisy_hea(4, 3, 5)
+    rho = O.rho_apply_circuit(w.circuit, w.theta).reshape(16, 16, order="F")
+    assert np.trace(rho).real == pytest.approx(1.0, abs=1e-14)
+    np.testing.assert_allclose(rho, rho.conj().T, atol=1e-15)
+    assert np.linalg.eigvalsh(rho).min() > -1e-14
+
+
+@pytest.mark.parametrize("n,seed", [(2, 31), (3, 32)])
+def test_noisy_adjoint_matches_parameter_shift(n, seed):
+    w = I.random_circuit(n, 30, seed, density=True, with_channels=True)
+    e, g = O.noisy_adjoint_grad(w.circuit, w.theta, w.observable)
+    assert e == pytest.approx(O.energy(w.circuit, w.theta, w.observable), abs=1e-13)
+    ps = O.parameter_shift_grad(w.circuit, w.theta, w.observable)
+    np.testing.assert_allclose(g, ps, atol=1e-12)
+
+
+def test_noisy_hea_adjoint_matches_shift():
+    w = I.noisy_hea(3, 2, 8, p1=0.05, p2=0.1, gamma=0.07)
+    e, g = O.noisy_adjoint_grad(w.circuit, w.theta, w.observable)
+    ps = O.parameter_shift_grad(w.circuit, w.theta, w.observable)
+    np.testing.assert_allclose(g, ps, atol=1e-12)
