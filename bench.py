@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark: gradient evaluations per second of the 20-qubit VQE workload on GB300.
+
+One step = one energy + full gradient evaluation (800 parameters) of the 20-qubit,
+20-layer Ry.Rz + CZ-brick ansatz with the 39-term transverse-field Ising Hamiltonian:
+gate materialisation, state initialisation, fused forward tile passes, expectation
+fused with the adjoint seed, fused reverse passes (Algorithm 2) and the gradient
+reduction, in complex64 with FP64 reductions.  Inputs (parameters) are resident on
+the device; L2 (129 MB) is flushed by writing a 256 MiB buffer between timed steps.
+
+Also reported: the end-to-end rate through the host-pointer C-ABI call, the plain
+per-gate complex128 path on the same workload, the gate-sweep HBM bandwidth of the
+28-qubit random circuit (fused tile passes vs one launch per gate), the dominant
+kernel's roofline, clocks sampled during the timed region, and the FP64 CPU oracle.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank runs an independent replica (the single-state path
+does not shard); value = evaluations of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gradient evals/s (20q VQE) and gate-sweep HBM GB/s vs plain per-gate path"
+UNIT = "gradient evals/s"
+WORKLOAD = ("vqe_20q_hea20: 20 qubits, 20 layers of Ry.Rz on every qubit + CZ brick, "
+            "800 angles U[0,2pi), H = sum Z_iZ_i+1 + sum X_i (39 terms), energy + full gradient")
+FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_tflops(sm_mhz: float) -> float:
+    """FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x SM clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def traffic_for(kernel: str, src_file: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        with open(src_file, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        for r in rec.get("kernels", []):
+            if r.get("kernel") == kernel and r.get("src_sha") == sha:
+                return r.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------- oracle legs
+
+def oracle_grad_rate(budget_s: float):
+    """FP64 CPU oracle on the same workload: a full gradient evaluation if it fits the
+    budget, else the first L layers (cost is linear in layers) extrapolated."""
+    from oracle import oracle as O
+    from paper_2406_19212_gb300 import inputs as I
+    w = I.diff_20q()
+    w1 = I.hea_ry_rz_cz(20, 1, 2, 1.0)
+    t0 = time.perf_counter()
+    O.adjoint_grad(w1.circuit, w1.theta, w1.observable)
+    t_layer = time.perf_counter() - t0
+    layers = int(max(1, min(20, budget_s // max(t_layer, 1e-9))))
+    if layers >= 20:
+        t0 = time.perf_counter()
+        O.adjoint_grad(w.circuit, w.theta, w.observable)
+        dt = time.perf_counter() - t0
+        sample = "1 full gradient evaluation (20 layers, 800 parameters)"
+        return 1.0 / dt, sample, O.num_threads()
+    ws = I.hea_ry_rz_cz(20, layers, 2, 1.0)
+    t0 = time.perf_counter()
+    O.adjoint_grad(ws.circuit, ws.theta, ws.observable)
+    dt = time.perf_counter() - t0
+    sample = (f"gradient of the first {layers} of 20 layers (same 20 qubits and H), "
+              f"extrapolated linearly in layers to one full evaluation")
+    return (layers / 20.0) / dt, sample, O.num_threads()
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    O.build()
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_grad_rate(budget)
+    rates = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, sample, cores = oracle_grad_rate(budget)
+        rates.append(r)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(rates)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (plain C, OpenMP)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------ our arm
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2406_19212_gb300 as gb
+    from paper_2406_19212_gb300 import build as gbuild
+    from paper_2406_19212_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    gbuild.build()
+    pk, pk_kind = peaks()
+    w = I.diff_20q()
+    circ = gb.circuit_create(w.circuit)
+    obs = gb.obs_create(w.observable, w.circuit.n_qubits)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    theta = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+    e_out = torch.empty(1, dtype=torch.float64, device=dev)
+    g_out = torch.empty(w.circuit.n_params, dtype=torch.float64, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        gb.grad(circ, theta, obs, gb.C64, gb.FUSED, stream=stream, out=(e_out, g_out))
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # kernel-level profile of one evaluation (CUDA events on the launching stream)
+    prof = gb.grad_profile(circ, w.theta, obs, gb.C64, gb.FUSED, stream=stream)
+    launches_per_step = sum(v[0] for v in prof.values())
+
+    # timed region: per-step events, L2 flushed between steps outside the events
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = max_over_ranks(world, sum(step_ms) / 1e3)
+    value = args.steps * world / total_s
+    ms_per_step = 1e3 * total_s / args.steps
+
+    # end to end through the host-pointer C-ABI call (H2D theta, D2H energy + gradient)
+    n_e2e = max(5, min(args.steps, 200))
+    theta_host = np.ascontiguousarray(w.theta)
+    gb.grad(circ, theta_host, obs, gb.C64, gb.FUSED)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        gb.grad(circ, theta_host, obs, gb.C64, gb.FUSED)
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e = {"value": n_e2e * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * w.circuit.n_params,
+           "d2h_bytes_per_step": 8 * (1 + w.circuit.n_params)}
+
+    out = {}
+    if rank == 0:
+        # dominant kernel roofline
+        name, (nl, ms, fl, by) = max(prof.items(), key=lambda kv: kv[1][1])
+        avg_s = ms / nl / 1e3
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        alu = alu_peak_tflops(sm_mhz)
+        hbm = pk["hbm_gbs"]
+        intensity = fl / by if by else 0.0
+        ridge = alu * 1e12 / (hbm * 1e9)
+        src = os.path.join(ROOT, "paper_2406_19212_gb300", "csrc", "kernels_fused.cu")
+        traffic = traffic_for(name, src)
+        if intensity > ridge:
+            roof = {"bound": "alu", "achieved": fl / nl / avg_s / 1e12, "peak": alu,
+                    "unit": "TFLOP/s"}
+            roof["peak_note"] = (f"FP32 CUDA cores: 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz "
+                                 f"(derived; HBM {hbm:.0f} GB/s {pk_kind})")
+        else:
+            roof = {"bound": "hbm", "achieved": by / nl / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
+                    "peak_note": f"{pk_kind} copy bandwidth"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["traffic"] = traffic
+        roof["kernel"] = name
+        roof["launches_per_step"] = nl
+        roof["avg_launch_us"] = avg_s * 1e6
+        roof["alg_flops_per_launch"] = fl / nl
+        roof["alg_bytes_per_launch"] = by / nl
+        roof["hbm_frac_of_alg_bytes"] = by / nl / avg_s / 1e9 / hbm
+        out["roofline"] = roof
+        out["kernels"] = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items()}
+
+        # plain per-gate complex128 path on the same workload (the reference mode)
+        gb.grad(circ, w.theta, obs, gb.C128, gb.PLAIN)
+        torch.cuda.synchronize()
+        n_plain = 3
+        t0 = time.perf_counter()
+        for _ in range(n_plain):
+            gb.grad(circ, theta, obs, gb.C128, gb.PLAIN, stream=stream, out=(e_out, g_out))
+        torch.cuda.synchronize()
+        plain_rate = n_plain / (time.perf_counter() - t0)
+        out["plain_c128"] = {"value": plain_rate, "unit": UNIT,
+                             "speedup_fused_c64": value / world / plain_rate}
+
+        out["sweep"] = gate_sweep(gb, I, torch, dev, stream, pk)
+        if not args.no_cpu:
+            rate, sample, cores = oracle_grad_rate(25.0)
+            out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                   "sample": sample}
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "qubits": 20, "params": w.circuit.n_params,
+                       "mode": "fused tile passes, CUDA-graph replay, device pointers",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk}
+    line.update(out)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def gate_sweep(gb, I, torch, dev, stream, pk):
+    """28-qubit random circuit (4x7 grid, 20 cycles) applied in complex64: fused tile
+    passes vs one launch per gate; GB/s = algorithmic bytes (one read + one write of the
+    state per pass or per gate) / time."""
+    w = I.precision_28q()
+    circ = gb.circuit_create(w.circuit)
+    passes, _, tq = circ.plan_info()
+    state = torch.zeros(1 << 28, dtype=torch.complex64, device=dev)
+    state[0] = 1
+    sv = gb.sv_wrap(state, 28, stream=stream)
+    res = {"workload": "rqc_4x7_c20: 28 qubits, 20 cycles of sqrt(X/Y/W) + FSIM couplers, "
+                       "785 gates, complex64 (2 GiB state, inputs larger than L2)",
+           "tile_qubits": tq, "fused_passes": passes}
+    for mode, key in ((gb.FUSED, "fused"), (gb.PLAIN, "plain")):
+        gb.apply_circuit(sv, circ, (), mode)
+        torch.cuda.synchronize()
+        reps = 3 if mode == gb.FUSED else 1
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            gb.apply_circuit(sv, circ, (), mode)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        sweeps = passes if mode == gb.FUSED else len(w.circuit.ops)
+        byts = sweeps * 2 * (8 << 28)
+        res[f"{key}_ms"] = ms
+        res[f"{key}_sweeps"] = sweeps
+        res[f"{key}_gbs"] = byts / (ms / 1e3) / 1e9
+        res[f"{key}_frac_hbm"] = res[f"{key}_gbs"] / pk["hbm_gbs"]
+    res["speedup_fused_vs_plain"] = res["plain_ms"] / res["fused_ms"]
+    sv.free()
+    del state
+    torch.cuda.empty_cache()
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank)
+    else:
+        rc = run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

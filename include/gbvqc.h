@@ -1,0 +1,217 @@
+/*
+ * gbvqc.h -- C ABI of the GB300 variational-circuit simulator core (libgbvqc.so).
+ *
+ * The library applies gates and noise channels to a 2^n complex amplitude vector
+ * on one GPU, evaluates Pauli-sum expectation values, and computes exact gradients
+ * with the memory-efficient reverse sweep, following JuliVQC (arXiv 2406.19212).
+ *
+ * Conventions (paper Sec. II.A-B):
+ *   - qubits are 0-based; qubit q is bit q of the amplitude index (the paper's
+ *     column-major order with its qubit 1 varying fastest);
+ *   - a k-qubit matrix acting on the ordered qubits (q_0 .. q_{k-1}) is indexed by
+ *     sum_t bit(q_t) 2^t (first listed qubit = least significant bit), and is passed
+ *     ROW-MAJOR as interleaved (re, im) doubles: M[row][col] at data[2*(row*2^k+col)];
+ *   - a density matrix of n qubits is the 2n-qubit vector |rho>> with rho_ab stored at
+ *     index a + 2^n b (ket bits low, bra bits high; Sec. II.A and Sec. III.D);
+ *   - amplitudes are interleaved complex: complex64 = {float re, im},
+ *     complex128 = {double re, im}, the layout of torch.complex64 / complex128.
+ *
+ * Errors: every call returns a gbvqc_status; no call throws or aborts.  On failure
+ * gbvqc_last_error() returns a message for the calling thread.  A CUDA error inside a
+ * call is reported as GBVQC_ERR_CUDA; bounded device-side waits that run out return
+ * GBVQC_ERR_TIMEOUT and leave the CUDA context usable.
+ *
+ * Streams: `stream` arguments are cudaStream_t values passed as void* (NULL = the
+ * legacy default stream).  Calls enqueue work on that stream; calls that return a
+ * host value (expect, grad with host outputs, sv_get to host) synchronise it.
+ */
+#ifndef GBVQC_API_H_
+#define GBVQC_API_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GBVQC_OK = 0,
+    GBVQC_ERR_ARG = 1,          /* bad handle, size, qubit index or option          */
+    GBVQC_ERR_OOM = 2,          /* device allocation failed                         */
+    GBVQC_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed      */
+    GBVQC_ERR_TIMEOUT = 4,      /* a bounded device wait ran out                    */
+    GBVQC_ERR_NOT_DENSITY = 5,  /* channel applied to a pure state                  */
+    GBVQC_ERR_UNSUPPORTED = 6   /* valid request this build does not implement      */
+} gbvqc_status;
+
+enum { GBVQC_C64 = 0, GBVQC_C128 = 1 };            /* amplitude dtype                */
+enum { GBVQC_MODE_PLAIN = 0, GBVQC_MODE_FUSED = 1 }; /* one launch per gate / tiled  */
+enum { GBVQC_PTR_HOST = 0, GBVQC_PTR_DEVICE = 1 };   /* where theta/outputs live      */
+
+/* Operation kinds (paper Sec. II.B).  Rotations: Rx = [[c,-is],[-is,c]],
+ * Ry = [[c,-s],[s,c]], Rz = diag(e^{-it/2}, e^{it/2}), c = cos(t/2), s = sin(t/2).
+ * SX/SY/SW = ((1+i)I + (1-i)G)/2 for G = X, Y, W=(X+Y)/sqrt2.  CNOT and CONTROL list
+ * (control, target).  FSIM takes params (theta, phi, d_plus, d_minus, d_minus_off) as
+ * in Eq. (FSIM).  Channels act on one logical qubit of a density matrix:
+ * DEPOL(p): K0 = sqrt(1-3p/4) I, K1..3 = sqrt(p/4) X, Y, Z;  AMPDAMP(g), PHASEDAMP(g)
+ * as printed in Sec. II.B;  KRAUS: n_kraus (1..4) 2x2 operators in data[]. */
+enum {
+    GBVQC_X = 0, GBVQC_Y, GBVQC_Z, GBVQC_H, GBVQC_S, GBVQC_T, GBVQC_SX, GBVQC_SY,
+    GBVQC_SW, GBVQC_RX, GBVQC_RY, GBVQC_RZ, GBVQC_CNOT, GBVQC_CZ, GBVQC_SWAP,
+    GBVQC_ISWAP, GBVQC_FSIM, GBVQC_CONTROL, GBVQC_DENSE1, GBVQC_DENSE2,
+    GBVQC_DEPOL, GBVQC_AMPDAMP, GBVQC_PHASEDAMP, GBVQC_KRAUS, GBVQC_NUM_KINDS
+};
+
+/* One circuit element (QuantumGate / QuantumMap, Sec. II.B-C). */
+typedef struct gbvqc_op {
+    int32_t kind;          /* GBVQC_X .. GBVQC_KRAUS                                    */
+    int32_t qubits[2];     /* logical qubits; qubits[1] unused for one-qubit kinds      */
+    int32_t param_index;   /* RX/RY/RZ: index into theta (the paper's isparas=true);
+                              -1 = fixed angle params[0].  Must be -1 for other kinds.  */
+    int32_t n_kraus;       /* KRAUS only: number of 2x2 operators in data (1..4)        */
+    int32_t reserved;      /* must be 0                                                 */
+    double  params[5];     /* fixed angle / FSIM angles / channel strength              */
+    double  data[32];      /* DENSE1 (2x2), DENSE2 (4x4), CONTROL (2x2 target block),
+                              KRAUS (n_kraus 2x2 blocks): row-major (re, im) pairs      */
+} gbvqc_op;
+
+/* One Pauli term coeff * P (Sec. II.E, QubitsTerm): qubit q carries X if only bit q of
+ * x_mask is set, Z if only bit q of z_mask, Y if both (Y = i X Z), I if neither. */
+typedef struct gbvqc_pauli {
+    double   coeff;
+    uint64_t x_mask;
+    uint64_t z_mask;
+} gbvqc_pauli;
+
+typedef struct gbvqc_sv *sv_handle;
+typedef struct gbvqc_circuit *circuit_handle;
+typedef struct gbvqc_obs *obs_handle;
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *gbvqc_last_error(void);
+/* Library version: major*10000 + minor*100 + patch. */
+int gbvqc_version(void);
+
+/* ---------------------------------------------------------------- states (Sec. II.A) */
+
+/* Allocate a state of n_qubits logical qubits (a density matrix holds 2^(2n) amplitudes)
+ * in device memory owned by the library, initialised to |0...0> (or |0..0><0..0|,
+ * Listing 1).  dtype GBVQC_C64 or GBVQC_C128.  1 <= n (2n for density) <= 34.
+ * Errors: ERR_ARG, ERR_OOM, ERR_CUDA.  Free with sv_free. */
+gbvqc_status sv_alloc(int n_qubits, int dtype, int is_density, void *stream, sv_handle *out);
+
+/* Wrap caller-owned device memory (e.g. a torch tensor's data_ptr) of 2^n (or 2^(2n))
+ * amplitudes; the library never frees it.  The pointer must be 16-byte aligned. */
+gbvqc_status sv_wrap(void *device_ptr, int n_qubits, int dtype, int is_density, void *stream,
+                     sv_handle *out);
+
+/* Release a handle (and its memory if the library allocated it).  NULL is accepted. */
+gbvqc_status sv_free(sv_handle sv);
+
+/* Reset to |0...0> (density: |0><0|). */
+gbvqc_status sv_reset(sv_handle sv);
+
+/* Copy n_amps amplitudes (must equal the state size) from src, in the state's dtype,
+ * from host (src_is_host = 1) or device memory (StateVector(T, data), Listing 1). */
+gbvqc_status sv_set(sv_handle sv, const void *src, size_t n_amps, int src_is_host);
+
+/* Copy the amplitudes out to host (dst_is_host = 1) or device memory; synchronous. */
+gbvqc_status sv_get(sv_handle sv, void *dst, size_t n_amps, int dst_is_host);
+
+/* Query a state: logical qubits, dtype, density flag, device pointer (any may be NULL). */
+gbvqc_status sv_info(sv_handle sv, int *n_qubits, int *dtype, int *is_density, void **device_ptr);
+
+/* ------------------------------------------------------------- circuits (Sec. II.C) */
+
+/* Build a circuit over n_qubits logical qubits from n_ops operations (copied; the caller
+ * keeps ownership of ops).  n_params = length of the theta vectors passed later; every
+ * param_index must lie in [0, n_params).  is_density = 1 allows channels and makes
+ * every unitary act as U rho U^dag (Sec. III.D).  Builds and caches the execution plans
+ * (per-gate records and the fused tile schedule).  Errors: ERR_ARG (bad kind, qubit,
+ * param index, Kraus count), ERR_NOT_DENSITY (channel with is_density = 0). */
+gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qubits, int n_params,
+                            int is_density, circuit_handle *out);
+gbvqc_status circuit_free(circuit_handle c);
+
+/* Tile-engine options: tile_qubits in [6, 13] (0 = autotune/default) and the number of
+ * contiguous low qubits every tile keeps for coalescing, low_qubits in [1, 6] (0 = default).
+ * Replaces the cached fused schedule. */
+gbvqc_status circuit_set_tiling(circuit_handle c, int tile_qubits, int low_qubits);
+
+/* Report the fused schedule: number of tile passes and of gate records it holds. */
+gbvqc_status circuit_plan_info(circuit_handle c, int *n_passes, int *n_gates, int *tile_qubits);
+
+/* ------------------------------------------------------------ execution (Sec. II.D) */
+
+/* psi <- C(theta) psi in place (apply!, Eq. circuitevolve; Eq. channel for density
+ * states).  theta: n_theta doubles on host or device (theta_loc).  mode PLAIN runs one
+ * kernel per gate (Eq. 3 / Eq. twoqubitgate); FUSED runs the tile passes.  The state's
+ * qubit count and density flag must match the circuit's.  Enqueued on the state's
+ * stream; returns without synchronising. */
+gbvqc_status apply_circuit(sv_handle sv, circuit_handle c, const double *theta, int n_theta,
+                           int theta_loc, int mode);
+
+/* Apply one single-qubit channel (Sec. II.B, Eq. channel / channel2) to a density state:
+ * kind GBVQC_DEPOL / AMPDAMP / PHASEDAMP with strength, or GBVQC_KRAUS with n_kraus 2x2
+ * operators in kraus (row-major (re,im), host memory).  Pure state: ERR_NOT_DENSITY. */
+gbvqc_status apply_channel(sv_handle sv, int kind, int qubit, double strength,
+                           const double *kraus, int n_kraus);
+
+/* ---------------------------------------------------------- observables (Sec. II.E) */
+
+/* Pauli sum H = sum_t terms[t].coeff P_t over n_qubits logical qubits (QubitsOperator).
+ * Terms are copied to the device; masks must not touch qubits >= n_qubits. */
+gbvqc_status obs_create(const gbvqc_pauli *terms, int n_terms, int n_qubits, obs_handle *out);
+gbvqc_status obs_free(obs_handle h);
+
+/* <psi|H|psi> (pure) or tr(H rho) (density), reduced in FP64 (expectation, Sec. II.E;
+ * Eq. loss_mixed).  Synchronises the state's stream and writes *out_energy (host). */
+gbvqc_status expect(sv_handle sv, obs_handle h, double *out_energy);
+
+/* ------------------------------------------------------ gradients (Sec. III.C, III.E) */
+
+/* Energy L(theta) = <0|C^dag H C|0> (Eq. loss_pure) or <<I|H C|0>> (Eq. loss_mixed) and
+ * its exact gradient dL/dtheta (n_params values; gates sharing a parameter add up) by
+ * the reverse sweep of Algorithm 2: two live states, no checkpoints.  dtype selects
+ * complex64 sweeps (FP64 reductions) or complex128.  mode PLAIN = per-gate kernels;
+ * FUSED = tile passes.  ptr_loc says whether theta, energy and grad_out are host or
+ * device pointers; with host pointers the call synchronises `stream`.  Work buffers are
+ * cached in the circuit handle (one grad call per circuit handle at a time).
+ * Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
+gbvqc_status grad(circuit_handle c, const double *theta, int n_theta, obs_handle h,
+                  int dtype, int mode, int ptr_loc, void *stream, double *energy,
+                  double *grad_out);
+
+/* Per-kernel timing of one gradient evaluation.  Runs the same launch sequence as grad
+ * (host theta), without graph replay, with CUDA events around every launch on `stream`,
+ * and aggregates by kernel name: launches, total milliseconds, and the algorithmic
+ * floating-point operations and bytes those launches must perform (flops: complex
+ * arithmetic of the applied matrices and generator inner products over 2^n amplitudes;
+ * bytes: one read and one write of every state a launch sweeps).  Fills at most
+ * max_stats entries and sets *n_stats.  Synchronises `stream`. */
+typedef struct gbvqc_kernel_stat {
+    char   name[32];
+    int    launches;
+    double ms;
+    double alg_flops;
+    double alg_bytes;
+} gbvqc_kernel_stat;
+
+gbvqc_status grad_profile(circuit_handle c, const double *theta, int n_theta, obs_handle h,
+                          int dtype, int mode, void *stream, gbvqc_kernel_stat *stats,
+                          int max_stats, int *n_stats);
+
+/* Batched energy + gradient of independent circuits (each with its own qubit count,
+ * parameters and observable), complex64 sweeps with FP64 reductions, executed as one
+ * persistent launch replayed through a CUDA graph.  theta_all concatenates every
+ * circuit's parameters (host); energies (n_circuits) and grads (sum of n_params) are
+ * host outputs.  All circuits must be pure-state circuits of at most 24 qubits. */
+gbvqc_status grad_batch(const circuit_handle *circuits, const obs_handle *observables,
+                        int n_circuits, const double *theta_all, void *stream,
+                        double *energies, double *grads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBVQC_API_H_ */

@@ -1,0 +1,315 @@
+"""GB300-native variational quantum circuit simulator core (JuliVQC, arXiv 2406.19212).
+
+Python face of libgbvqc.so.  The functions keep the names of the C entry points
+(sv_alloc, circuit_create, apply_circuit, apply_channel, obs_create, expect, grad,
+grad_batch) and only marshal arguments; every step runs in the library's CUDA kernels.
+There is no CPU fallback: calls fail if the library is missing.
+
+    import paper_2406_19212_gb300 as gb
+    from paper_2406_19212_gb300 import inputs
+    w = inputs.diff_20q()
+    circ = gb.circuit_create(w.circuit)
+    obs = gb.obs_create(w.observable, w.circuit.n_qubits)
+    energy, g = gb.grad(circ, w.theta, obs, dtype=gb.C64, mode=gb.FUSED)
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _abi
+from ._abi import C64, C128, FUSED, PLAIN, GbvqcError
+
+__all__ = ["C64", "C128", "PLAIN", "FUSED", "GbvqcError", "StateVector", "CircuitHandle",
+           "Observable", "sv_alloc", "sv_wrap", "sv_set", "sv_get", "sv_reset",
+           "circuit_create", "apply_circuit", "apply_channel", "obs_create", "expect", "grad",
+           "grad_profile", "grad_batch", "VQEEnergy", "load"]
+
+
+def load():
+    """Load the CUDA library (raises if it is not built)."""
+    return _abi.lib()
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _is_cuda_tensor(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+class StateVector:
+    """A state owned (sv_alloc) or wrapped (sv_wrap) by the library."""
+
+    def __init__(self, handle: int, n_qubits: int, dtype: int, density: bool, keep=None):
+        self.handle = handle
+        self.n_qubits = n_qubits
+        self.dtype = dtype
+        self.density = density
+        self._keep = keep
+
+    @property
+    def n_amps(self) -> int:
+        return 1 << (2 * self.n_qubits if self.density else self.n_qubits)
+
+    def free(self):
+        if self.handle:
+            _abi.lib().sv_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sv_alloc(n_qubits: int, dtype: int = C64, is_density: bool = False, stream=None) -> StateVector:
+    h = ctypes.c_void_p()
+    _abi.check(_abi.lib().sv_alloc(n_qubits, dtype, int(is_density), _stream_ptr(stream),
+                                   ctypes.byref(h)))
+    return StateVector(h.value, n_qubits, dtype, bool(is_density))
+
+
+def sv_wrap(tensor, n_qubits: int, is_density: bool = False, stream=None) -> StateVector:
+    """Wrap a CUDA torch.complex64/complex128 tensor (the library never frees it)."""
+    import torch
+    dtype = {torch.complex64: C64, torch.complex128: C128}[tensor.dtype]
+    h = ctypes.c_void_p()
+    _abi.check(_abi.lib().sv_wrap(tensor.data_ptr(), n_qubits, dtype, int(is_density),
+                                  _stream_ptr(stream), ctypes.byref(h)))
+    return StateVector(h.value, n_qubits, dtype, bool(is_density), keep=tensor)
+
+
+def _np_dtype(dtype: int):
+    return np.complex64 if dtype == C64 else np.complex128
+
+
+def sv_set(sv: StateVector, amps) -> None:
+    if _is_cuda_tensor(amps):
+        _abi.check(_abi.lib().sv_set(sv.handle, amps.data_ptr(), amps.numel(), 0))
+        return
+    a = np.ascontiguousarray(np.asarray(amps), dtype=_np_dtype(sv.dtype))
+    _abi.check(_abi.lib().sv_set(sv.handle, a.ctypes.data, a.size, 1))
+
+
+def sv_get(sv: StateVector) -> np.ndarray:
+    out = np.empty(sv.n_amps, dtype=_np_dtype(sv.dtype))
+    _abi.check(_abi.lib().sv_get(sv.handle, out.ctypes.data, out.size, 1))
+    return out
+
+
+def sv_reset(sv: StateVector) -> None:
+    _abi.check(_abi.lib().sv_reset(sv.handle))
+
+
+class CircuitHandle:
+    def __init__(self, handle: int, circuit):
+        self.handle = handle
+        self.n_qubits = circuit.n_qubits
+        self.n_params = circuit.n_params
+        self.density = circuit.density
+
+    def set_tiling(self, tile_qubits: int = 0, low_qubits: int = 0) -> None:
+        _abi.check(_abi.lib().circuit_set_tiling(self.handle, tile_qubits, low_qubits))
+
+    def plan_info(self) -> Tuple[int, int, int]:
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _abi.check(_abi.lib().circuit_plan_info(self.handle, ctypes.byref(a), ctypes.byref(b),
+                                                ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def free(self):
+        if self.handle:
+            _abi.lib().circuit_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def circuit_create(circuit) -> CircuitHandle:
+    """Build a circuit from an `inputs.Circuit` description."""
+    arr = _abi.ops_array(circuit.ops)
+    h = ctypes.c_void_p()
+    _abi.check(_abi.lib().circuit_create(arr, len(circuit.ops), circuit.n_qubits, circuit.n_params,
+                                         int(circuit.density), ctypes.byref(h)))
+    return CircuitHandle(h.value, circuit)
+
+
+def _theta_args(theta, n: int):
+    if _is_cuda_tensor(theta):
+        import torch
+        t = theta.detach().to(torch.float64).contiguous()
+        return t, t.data_ptr(), _abi.PTR_DEVICE
+    t = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1))
+    if t.size != n:
+        raise ValueError(f"expected {n} parameters, got {t.size}")
+    return t, (t.ctypes.data if t.size else None), _abi.PTR_HOST
+
+
+def apply_circuit(sv: StateVector, circ: CircuitHandle, theta=(), mode: int = FUSED) -> None:
+    """In-place psi <- C(theta) psi on the state's stream (apply!)."""
+    keep, ptr, loc = _theta_args(theta if circ.n_params else np.zeros(0), circ.n_params)
+    _abi.check(_abi.lib().apply_circuit(sv.handle, circ.handle, ptr, circ.n_params, loc, mode))
+    del keep
+
+
+CHANNELS = {"DEPOL": 20, "AMPDAMP": 21, "PHASEDAMP": 22, "KRAUS": 23}
+
+
+def apply_channel(sv: StateVector, name: str, qubit: int, strength: float = 0.0, kraus=None) -> None:
+    buf = None
+    n = 0
+    if kraus is not None:
+        mats = [np.asarray(k, dtype=np.complex128).reshape(4) for k in kraus]
+        n = len(mats)
+        buf = np.ascontiguousarray(np.concatenate(mats).view(np.float64))
+    _abi.check(_abi.lib().apply_channel(
+        sv.handle, CHANNELS[name], qubit, float(strength),
+        buf.ctypes.data_as(_abi.dp) if buf is not None else None, n))
+
+
+class Observable:
+    def __init__(self, handle: int, n_qubits: int, terms):
+        self.handle = handle
+        self.n_qubits = n_qubits
+        self.terms = list(terms)
+
+    def free(self):
+        if self.handle:
+            _abi.lib().obs_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def obs_create(terms, n_qubits: int) -> Observable:
+    arr = _abi.pauli_array(terms)
+    h = ctypes.c_void_p()
+    _abi.check(_abi.lib().obs_create(arr, len(terms), n_qubits, ctypes.byref(h)))
+    return Observable(h.value, n_qubits, terms)
+
+
+def expect(sv: StateVector, obs: Observable) -> float:
+    out = ctypes.c_double()
+    _abi.check(_abi.lib().expect(sv.handle, obs.handle, ctypes.byref(out)))
+    return out.value
+
+
+def grad(circ: CircuitHandle, theta, obs: Observable, dtype: int = C64, mode: int = FUSED,
+         stream=None, out=None):
+    """Energy and exact gradient by the reverse sweep (Algorithm 2).
+
+    Host theta (numpy / sequence): returns (float, numpy array) and synchronises.
+    CUDA theta (torch float64): results stay on the device, written into `out`
+    = (energy tensor of shape (1,), grad tensor of shape (n_params,)) if given, or into
+    new tensors; the call is asynchronous on `stream` (default: torch's current stream).
+    """
+    if _is_cuda_tensor(theta):
+        import torch
+        keep, ptr, loc = _theta_args(theta, circ.n_params)
+        if out is None:
+            e = torch.empty(1, dtype=torch.float64, device=theta.device)
+            g = torch.empty(circ.n_params, dtype=torch.float64, device=theta.device)
+        else:
+            e, g = out
+        s = _stream_ptr(stream if stream is not None else torch.cuda.current_stream(theta.device))
+        _abi.check(_abi.lib().grad(circ.handle, ptr, circ.n_params, obs.handle, dtype, mode, loc,
+                                   s, e.data_ptr(), g.data_ptr() if circ.n_params else None))
+        del keep
+        return e, g
+    keep, ptr, loc = _theta_args(theta, circ.n_params)
+    e = ctypes.c_double()
+    g = np.zeros(max(1, circ.n_params))
+    _abi.check(_abi.lib().grad(circ.handle, ptr, circ.n_params, obs.handle, dtype, mode, loc,
+                               _stream_ptr(stream), ctypes.byref(e), g.ctypes.data))
+    del keep
+    return e.value, g[:circ.n_params]
+
+
+def grad_profile(circ: CircuitHandle, theta, obs: Observable, dtype: int = C64,
+                 mode: int = FUSED, stream=None):
+    """Per-kernel CUDA-event timing of one gradient evaluation:
+    {name: (launches, ms, alg_flops, alg_bytes)}."""
+    keep, ptr, loc = _theta_args(theta, circ.n_params)
+    stats = (_abi.KernelStat * 64)()
+    n = ctypes.c_int()
+    _abi.check(_abi.lib().grad_profile(circ.handle, ptr, circ.n_params, obs.handle, dtype, mode,
+                                       _stream_ptr(stream), stats, 64, ctypes.byref(n)))
+    del keep
+    return {stats[i].name.decode(): (stats[i].launches, stats[i].ms, stats[i].alg_flops,
+                                     stats[i].alg_bytes) for i in range(n.value)}
+
+
+def grad_batch(circs: Sequence[CircuitHandle], obss: Sequence[Observable], thetas,
+               stream=None):
+    """Energies and gradients of independent circuits in one persistent launch."""
+    n = len(circs)
+    ch = (ctypes.c_void_p * n)(*[c.handle for c in circs])
+    oh = (ctypes.c_void_p * n)(*[o.handle for o in obss])
+    th = np.ascontiguousarray(np.concatenate([np.asarray(t, dtype=np.float64).reshape(-1)
+                                              for t in thetas]) if n else np.zeros(1))
+    total = sum(c.n_params for c in circs)
+    e = np.zeros(max(1, n))
+    g = np.zeros(max(1, total))
+    _abi.check(_abi.lib().grad_batch(ch, oh, n, th.ctypes.data_as(_abi.dp), _stream_ptr(stream),
+                                     e.ctypes.data_as(_abi.dp), g.ctypes.data_as(_abi.dp)))
+    out, off = [], 0
+    for c in circs:
+        out.append(g[off:off + c.n_params].copy())
+        off += c.n_params
+    return e[:n], out
+
+
+def _autograd_class():
+    import torch
+
+    class VQEEnergy(torch.autograd.Function):
+        """L(theta) = <H> after the circuit; backward scales the adjoint gradient.
+
+        forward(theta, circ, obs, dtype, mode) runs `grad` once (energy and gradient),
+        saves the gradient and returns the energy as a 0-d tensor on theta's device."""
+
+        @staticmethod
+        def forward(ctx, theta, circ, obs, dtype=C64, mode=FUSED):
+            if theta.is_cuda:
+                e, g = grad(circ, theta.detach().to(torch.float64), obs, dtype, mode)
+                ctx.save_for_backward(g)
+                return e.reshape(()).to(theta.dtype)
+            e, g = grad(circ, theta.detach().cpu().numpy(), obs, dtype, mode)
+            ctx.save_for_backward(torch.from_numpy(g))
+            return torch.tensor(e, dtype=theta.dtype)
+
+        @staticmethod
+        def backward(ctx, dE):
+            (g,) = ctx.saved_tensors
+            return (dE.to(g.dtype) * g).to(dE.dtype), None, None, None, None
+
+    return VQEEnergy
+
+
+class _LazyAutograd:
+    _cls = None
+
+    def __getattr__(self, name):
+        if _LazyAutograd._cls is None:
+            _LazyAutograd._cls = _autograd_class()
+        return getattr(_LazyAutograd._cls, name)
+
+
+VQEEnergy = _LazyAutograd()

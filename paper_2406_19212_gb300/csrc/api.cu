@@ -1,0 +1,1298 @@
+// C ABI of libgbvqc (declared in include/gbvqc.h): states, circuits, observables,
+// apply / expect / grad.  Host-side gate matrices, structural classification, the
+// per-gate (plain) schedule, the fused tile schedule and CUDA-graph replay of grad.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gbvqc.h"
+#include "kernels.h"
+#include "planner.h"
+
+using namespace gbvqc;
+typedef std::complex<double> cd;
+
+// ------------------------------------------------------------------------ errors
+
+static thread_local std::string g_last_error;
+
+static gbvqc_status fail(gbvqc_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? GBVQC_ERR_OOM : GBVQC_ERR_CUDA,   \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define ST_TRY(expr)                      \
+    do {                                  \
+        gbvqc_status s_ = (expr);         \
+        if (s_ != GBVQC_OK) return s_;    \
+    } while (0)
+
+// ----------------------------------------------------------------- profiling hooks
+
+// When grad_profile is active, every launch of the gradient sequence is bracketed by
+// CUDA events and tagged with its algorithmic flops and bytes.
+struct ProfRec {
+    std::string name;
+    cudaEvent_t a, b;
+    double flops, bytes;
+};
+static thread_local std::vector<ProfRec> *g_prof = nullptr;
+
+template <typename F>
+static gbvqc_status run_k(const char *name, double flops, double bytes, cudaStream_t s, F &&launch)
+{
+    if (!g_prof) {
+        CUDA_TRY(launch());
+        return GBVQC_OK;
+    }
+    ProfRec r{name, nullptr, nullptr, flops, bytes};
+    CUDA_TRY(cudaEventCreate(&r.a));
+    CUDA_TRY(cudaEventCreate(&r.b));
+    CUDA_TRY(cudaEventRecord(r.a, s));
+    CUDA_TRY(launch());
+    CUDA_TRY(cudaEventRecord(r.b, s));
+    g_prof->push_back(r);
+    return GBVQC_OK;
+}
+
+// Real floating-point operations per amplitude of one matrix application.
+static double shape_flops(int sh)
+{
+    switch (sh) {
+    case SH_DENSE1: return 14;  // two complex products and a sum per output
+    case SH_DENSE2: return 30;  // four complex products and three sums per output
+    case SH_CTRL2: return 7;    // a dense 2x2 on half of the amplitudes
+    case SH_REAL1: return 6;
+    default: return 6;          // one complex product
+    }
+}
+
+static double ftype_flops(int ft)
+{
+    switch (ft) {
+    case FT_DENSE1: return 14;
+    case FT_DENSE2: return 30;
+    case FT_CTRL2: return 7;
+    default: return 6;
+    }
+}
+
+// ------------------------------------------------------------------ host matrices
+
+typedef std::vector<cd> Mat;  // row-major d x d
+
+static Mat mat_from(const double *m, int d)
+{
+    Mat M(d * d);
+    for (int i = 0; i < d * d; i++) M[i] = cd(m[2 * i], m[2 * i + 1]);
+    return M;
+}
+
+static void mat_to(const Mat &M, double *m)
+{
+    for (int i = 0; i < 32; i++) m[i] = 0.0;
+    for (size_t i = 0; i < M.size(); i++) {
+        m[2 * i] = M[i].real();
+        m[2 * i + 1] = M[i].imag();
+    }
+}
+
+static Mat mat_dagger(const Mat &M, int d)
+{
+    Mat D(d * d);
+    for (int r = 0; r < d; r++)
+        for (int c = 0; c < d; c++) D[r * d + c] = std::conj(M[c * d + r]);
+    return D;
+}
+
+static Mat mat_conj(const Mat &M)
+{
+    Mat D(M.size());
+    for (size_t i = 0; i < M.size(); i++) D[i] = std::conj(M[i]);
+    return D;
+}
+
+// Inverse by Gauss-Jordan elimination with partial pivoting (channels are not unitary).
+static bool mat_inverse(const Mat &A, int d, Mat &out)
+{
+    std::vector<cd> m(d * 2 * d);
+    for (int r = 0; r < d; r++)
+        for (int c = 0; c < 2 * d; c++) m[r * 2 * d + c] = c < d ? A[r * d + c] : cd(c - d == r ? 1 : 0);
+    for (int k = 0; k < d; k++) {
+        int piv = k;
+        for (int r = k + 1; r < d; r++)
+            if (std::abs(m[r * 2 * d + k]) > std::abs(m[piv * 2 * d + k])) piv = r;
+        if (std::abs(m[piv * 2 * d + k]) < 1e-14) return false;
+        for (int c = 0; c < 2 * d; c++) std::swap(m[k * 2 * d + c], m[piv * 2 * d + c]);
+        cd p = m[k * 2 * d + k];
+        for (int c = 0; c < 2 * d; c++) m[k * 2 * d + c] /= p;
+        for (int r = 0; r < d; r++)
+            if (r != k) {
+                cd f = m[r * 2 * d + k];
+                for (int c = 0; c < 2 * d; c++) m[r * 2 * d + c] -= f * m[k * 2 * d + c];
+            }
+    }
+    out.assign(d * d, 0);
+    for (int r = 0; r < d; r++)
+        for (int c = 0; c < d; c++) out[r * d + c] = m[r * 2 * d + d + c];
+    return true;
+}
+
+static bool is_channel(int kind) { return kind >= GBVQC_DEPOL && kind <= GBVQC_KRAUS; }
+static bool is_rotation(int kind) { return kind == GBVQC_RX || kind == GBVQC_RY || kind == GBVQC_RZ; }
+static int kind_qubits(int kind)
+{
+    return (kind >= GBVQC_CNOT && kind <= GBVQC_CONTROL) || kind == GBVQC_DENSE2 ? 2 : 1;
+}
+
+// Matrix of a unitary op with its fixed parameters (Sec. II.B); rotations use params[0].
+static Mat gate_matrix(const gbvqc_op &op)
+{
+    const double r2 = 1.0 / std::sqrt(2.0);
+    const cd I(0, 1);
+    if (is_rotation(op.kind)) {
+        double m[8];
+        rot2(op.kind - GBVQC_RX, VAR_FWD, op.params[0], m);
+        return mat_from(m, 2);
+    }
+    switch (op.kind) {
+    case GBVQC_X: return {0, 1, 1, 0};
+    case GBVQC_Y: return {0, -I, I, 0};
+    case GBVQC_Z: return {1, 0, 0, -1};
+    case GBVQC_H: return {r2, r2, r2, -r2};
+    case GBVQC_S: return {1, 0, 0, I};
+    case GBVQC_T: return {1, 0, 0, std::exp(I * (M_PI / 4))};
+    case GBVQC_SX: return {cd(0.5, 0.5), cd(0.5, -0.5), cd(0.5, -0.5), cd(0.5, 0.5)};
+    case GBVQC_SY: return {cd(0.5, 0.5), cd(-0.5, -0.5), cd(0.5, 0.5), cd(0.5, 0.5)};
+    case GBVQC_SW: return {cd(0.5, 0.5), cd(0, -r2), cd(r2, 0), cd(0.5, 0.5)};
+    case GBVQC_DENSE1: return mat_from(op.data, 2);
+    default: break;
+    }
+    Mat M(16, 0);
+    auto at = [&](int r, int c) -> cd & { return M[r * 4 + c]; };
+    switch (op.kind) {
+    case GBVQC_CNOT:  // control = qubits[0] (matrix bit 0), target = qubits[1]
+        at(0, 0) = 1; at(2, 2) = 1; at(1, 3) = 1; at(3, 1) = 1;
+        break;
+    case GBVQC_CZ: at(0, 0) = 1; at(1, 1) = 1; at(2, 2) = 1; at(3, 3) = -1; break;
+    case GBVQC_SWAP: at(0, 0) = 1; at(1, 2) = 1; at(2, 1) = 1; at(3, 3) = 1; break;
+    case GBVQC_ISWAP: at(0, 0) = 1; at(1, 2) = I; at(2, 1) = I; at(3, 3) = 1; break;
+    case GBVQC_FSIM: {  // Eq. (FSIM)
+        double th = op.params[0], ph = op.params[1], dp = op.params[2], dm = op.params[3],
+               dmo = op.params[4];
+        at(0, 0) = 1;
+        at(1, 1) = std::exp(I * (dp + dm)) * std::cos(th);
+        at(1, 2) = -I * std::exp(I * (dp - dmo)) * std::sin(th);
+        at(2, 1) = -I * std::exp(I * (dp + dmo)) * std::sin(th);
+        at(2, 2) = std::exp(I * (dp - dm)) * std::cos(th);
+        at(3, 3) = std::exp(I * (2 * dp - ph));
+        break;
+    }
+    case GBVQC_CONTROL:
+        at(0, 0) = 1; at(2, 2) = 1;
+        at(1, 1) = cd(op.data[0], op.data[1]);
+        at(1, 3) = cd(op.data[2], op.data[3]);
+        at(3, 1) = cd(op.data[4], op.data[5]);
+        at(3, 3) = cd(op.data[6], op.data[7]);
+        break;
+    case GBVQC_DENSE2: return mat_from(op.data, 4);
+    default: break;
+    }
+    return M;
+}
+
+// Kraus operators of a single-qubit channel (Sec. II.B; depolarising with p/4 weights).
+static std::vector<Mat> channel_kraus(int kind, double g, const double *kraus, int n_kraus)
+{
+    const cd I(0, 1);
+    switch (kind) {
+    case GBVQC_AMPDAMP: return {{1, 0, 0, std::sqrt(1 - g)}, {0, std::sqrt(g), 0, 0}};
+    case GBVQC_PHASEDAMP: return {{1, 0, 0, std::sqrt(1 - g)}, {0, 0, 0, std::sqrt(g)}};
+    case GBVQC_DEPOL: {
+        double a = std::sqrt(1 - 0.75 * g), b = std::sqrt(0.25 * g);
+        return {{a, 0, 0, a}, {0, b, b, 0}, {0, -I * b, I * b, 0}, {b, 0, 0, -b}};
+    }
+    default: {
+        std::vector<Mat> ks;
+        for (int s = 0; s < n_kraus; s++) ks.push_back(mat_from(kraus + 8 * s, 2));
+        return ks;
+    }
+    }
+}
+
+// Superoperator on (ket q, bra q): S[(r1 + 2 r2), (c1 + 2 c2)] = sum_s K[r1][c1] conj(K[r2][c2])
+// (Eq. channel2 with the conjugate on the bra index: vec(K rho K^dag)).
+static Mat superop(const std::vector<Mat> &ks)
+{
+    Mat S(16, 0);
+    for (const Mat &K : ks)
+        for (int r1 = 0; r1 < 2; r1++)
+            for (int r2 = 0; r2 < 2; r2++)
+                for (int c1 = 0; c1 < 2; c1++)
+                    for (int c2 = 0; c2 < 2; c2++)
+                        S[(r1 + 2 * r2) * 4 + (c1 + 2 * c2)] += K[r1 * 2 + c1] * std::conj(K[r2 * 2 + c2]);
+    return S;
+}
+
+static bool nz(cd v) { return v.real() != 0.0 || v.imag() != 0.0; }
+
+static int classify(const Mat &M)
+{
+    if (M.size() == 4) {
+        if (!nz(M[1]) && !nz(M[2])) return SH_DIAG1;
+        if (!nz(M[0]) && !nz(M[3])) return SH_ANTI1;
+        bool real = true;
+        for (cd v : M) real = real && v.imag() == 0.0;
+        return real ? SH_REAL1 : SH_DENSE1;
+    }
+    bool diag = true;
+    for (int r = 0; r < 4; r++)
+        for (int c = 0; c < 4; c++)
+            if (r != c && nz(M[r * 4 + c])) diag = false;
+    if (diag) return SH_DIAG2;
+    // controlled: identity on the q0 = 0 block (indices 0, 2), no coupling to 1, 3
+    bool ctrl = M[0] == cd(1) && M[10] == cd(1) && !nz(M[2]) && !nz(M[8]);
+    for (int r : {0, 2})
+        for (int c : {1, 3}) ctrl = ctrl && !nz(M[r * 4 + c]) && !nz(M[c * 4 + r]);
+    if (ctrl) return SH_CTRL2;
+    bool perm = true;
+    for (int r = 0; r < 4 && perm; r++) {
+        int cnt = 0, cntc = 0;
+        for (int c = 0; c < 4; c++) {
+            cnt += nz(M[r * 4 + c]);
+            cntc += nz(M[c * 4 + r]);
+        }
+        perm = cnt == 1 && cntc == 1;
+    }
+    return perm ? SH_PERM2 : SH_DENSE2;
+}
+
+static int perm_bits(const Mat &M)
+{
+    int bits = 0;
+    for (int r = 0; r < 4; r++)
+        for (int c = 0; c < 4; c++)
+            if (nz(M[r * 4 + c])) bits |= c << (2 * r);
+    return bits;
+}
+
+// Shape that covers two matrices (reverse sweeps apply different matrices to Phi, Psi).
+static int join_shape(int a, int b)
+{
+    if (a == b) return a;
+    return shape_qubits(a) == 1 ? SH_DENSE1 : SH_DENSE2;
+}
+
+static int ftype_of(int sh)
+{
+    switch (sh) {
+    case SH_DENSE1: return FT_DENSE1;
+    case SH_REAL1: return FT_REAL1;
+    case SH_ANTI1: return FT_ANTI1;
+    case SH_DIAG1: return FT_DIAG1;
+    case SH_DENSE2: return FT_DENSE2;
+    case SH_DIAG2: return FT_DIAG2;
+    case SH_PERM2: return FT_PERM2;
+    default: return FT_CTRL2;
+    }
+}
+
+// ------------------------------------------------------------------- handle types
+
+struct gbvqc_sv {
+    int n_log = 0, n_phys = 0, dtype = 0, density = 0;
+    void *data = nullptr;
+    bool owned = false;
+    cudaStream_t stream = nullptr;
+    double *d_scratch = nullptr;   // kMaxRedBlocks partials + result
+    unsigned *d_counter = nullptr;
+    MatRec *d_rec = nullptr;       // matrix of apply_channel
+    size_t amps() const { return size_t(1) << n_phys; }
+    size_t bytes() const { return amps() * (dtype == GBVQC_C64 ? 8 : 16); }
+};
+
+struct gbvqc_obs {
+    int n_qubits = 0;
+    std::vector<ObsGroup> groups;
+    std::vector<ObsTerm> terms;
+    ObsGroup *d_groups = nullptr;
+    ObsTerm *d_terms = nullptr;
+    ObsDev dev() const { return ObsDev{d_groups, d_terms, (int)groups.size()}; }
+};
+
+// One gate of the per-gate schedule.
+struct PlainGate {
+    int shape, q0, q1;
+    int rec_f, rec_i, rec_a;
+    int der_k, dq0, dq1, rec_d;  // derivative operator (rec_d = -1 if none)
+    int param;
+    double gscale;
+    int slot;
+};
+
+struct Workspace {
+    int dtype = -1;
+    void *phi = nullptr, *psi = nullptr;
+    double *d_theta = nullptr, *d_energy = nullptr, *d_grad = nullptr, *d_slot_grad = nullptr;
+    double *d_slot_partials = nullptr;
+    double *d_red = nullptr;
+    unsigned *d_counter = nullptr;
+};
+
+struct DevPlan {  // device copies of a FusedPlan
+    FusedPlan p;
+    std::vector<double> fwd_flops_per_amp, rev_flops_per_amp;  // algorithmic flops / amplitude
+    PassDesc *d_fwd = nullptr, *d_rev = nullptr;
+    SubRun *d_fsubs = nullptr, *d_rsubs = nullptr;
+    FGate *d_fgates = nullptr, *d_rgates = nullptr;
+    int *d_csr_ptr = nullptr, *d_csr_slots = nullptr;
+};
+
+struct gbvqc_circuit {
+    int n_log = 0, n_phys = 0, n_params = 0, density = 0;
+    std::vector<gbvqc_op> ops;
+    std::vector<MatRec> recs;
+    std::vector<DynRec> dyn;
+    MatRec *d_recs = nullptr;
+    DynRec *d_dyn = nullptr;
+    // per-gate schedule (standard layout)
+    std::vector<PlainGate> plain;
+    int plain_slots = 0;
+    int *d_plain_ptr = nullptr, *d_plain_slots = nullptr;
+    // fused: physical gate lists for the standard and the grad layout
+    std::vector<PGate> pg_std, pg_grad;
+    DensMap map_std{}, map_grad{};
+    int tile_qubits = 0, low_qubits = 0;
+    std::map<int, std::unique_ptr<DevPlan>> plans;  // key: dtype*2 + (grad layout)
+    Workspace ws;
+    cudaStream_t cap_stream = nullptr;
+    std::map<int, cudaGraphExec_t> graphs;           // key: dtype*2 + mode
+    const void *graph_obs = nullptr;                 // observable the graphs were captured with
+    int n_param_ops = 0;                             // ops driven by a parameter
+    size_t partials_cap = 0;                         // doubles in ws.d_slot_partials
+    std::mutex mu;
+};
+
+// ------------------------------------------------------------------------- basics
+
+extern "C" const char *gbvqc_last_error(void) { return g_last_error.c_str(); }
+extern "C" int gbvqc_version(void) { return 100; }
+
+static size_t amp_size(int dtype) { return dtype == GBVQC_C64 ? 8 : 16; }
+
+template <typename T>
+static gbvqc_status dev_alloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? GBVQC_ERR_OOM : GBVQC_ERR_CUDA,
+                    "cudaMalloc of %zu bytes: %s", sizeof(T) * count, cudaGetErrorString(e));
+    }
+    return GBVQC_OK;
+}
+
+template <typename T>
+static gbvqc_status upload(T **p, const std::vector<T> &v)
+{
+    ST_TRY(dev_alloc(p, v.size()));
+    if (!v.empty()) CUDA_TRY(cudaMemcpy(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return GBVQC_OK;
+}
+
+static gbvqc_status sv_init_common(gbvqc_sv *s)
+{
+    ST_TRY(dev_alloc(&s->d_scratch, kMaxRedBlocks + 8));
+    ST_TRY(dev_alloc(&s->d_counter, 1));
+    ST_TRY(dev_alloc(&s->d_rec, 1));
+    CUDA_TRY(cudaMemset(s->d_counter, 0, sizeof(unsigned)));
+    return GBVQC_OK;
+}
+
+static void sv_release(gbvqc_sv *s)
+{
+    if (!s) return;
+    if (s->owned && s->data) cudaFree(s->data);
+    if (s->d_scratch) cudaFree(s->d_scratch);
+    if (s->d_counter) cudaFree(s->d_counter);
+    if (s->d_rec) cudaFree(s->d_rec);
+    delete s;
+}
+
+static gbvqc_status check_state_args(int n_qubits, int dtype, int is_density)
+{
+    if (dtype != GBVQC_C64 && dtype != GBVQC_C128) return fail(GBVQC_ERR_ARG, "dtype %d", dtype);
+    int np = is_density ? 2 * n_qubits : n_qubits;
+    if (n_qubits < 1 || np > 34) return fail(GBVQC_ERR_ARG, "qubit count %d out of range", n_qubits);
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status sv_alloc(int n_qubits, int dtype, int is_density, void *stream, sv_handle *out)
+{
+    if (!out) return fail(GBVQC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    ST_TRY(check_state_args(n_qubits, dtype, is_density));
+    gbvqc_sv *s = new gbvqc_sv();
+    s->n_log = n_qubits;
+    s->n_phys = is_density ? 2 * n_qubits : n_qubits;
+    s->dtype = dtype;
+    s->density = is_density ? 1 : 0;
+    s->stream = (cudaStream_t)stream;
+    s->owned = true;
+    gbvqc_status st = dev_alloc((unsigned char **)&s->data, s->bytes());
+    if (st == GBVQC_OK) st = sv_init_common(s);
+    if (st == GBVQC_OK) {
+        cudaError_t e = launch_zero_state(dtype, s->data, s->n_phys, s->stream);
+        if (e != cudaSuccess) st = fail(GBVQC_ERR_CUDA, "zero state: %s", cudaGetErrorString(e));
+    }
+    if (st != GBVQC_OK) {
+        sv_release(s);
+        return st;
+    }
+    *out = s;
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status sv_wrap(void *device_ptr, int n_qubits, int dtype, int is_density, void *stream,
+                                sv_handle *out)
+{
+    if (!out || !device_ptr) return fail(GBVQC_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (((uintptr_t)device_ptr) & 15) return fail(GBVQC_ERR_ARG, "device pointer not 16-byte aligned");
+    ST_TRY(check_state_args(n_qubits, dtype, is_density));
+    gbvqc_sv *s = new gbvqc_sv();
+    s->n_log = n_qubits;
+    s->n_phys = is_density ? 2 * n_qubits : n_qubits;
+    s->dtype = dtype;
+    s->density = is_density ? 1 : 0;
+    s->stream = (cudaStream_t)stream;
+    s->data = device_ptr;
+    s->owned = false;
+    gbvqc_status st = sv_init_common(s);
+    if (st != GBVQC_OK) {
+        sv_release(s);
+        return st;
+    }
+    *out = s;
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status sv_free(sv_handle sv)
+{
+    sv_release(sv);
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status sv_reset(sv_handle sv)
+{
+    if (!sv) return fail(GBVQC_ERR_ARG, "NULL state");
+    CUDA_TRY(launch_zero_state(sv->dtype, sv->data, sv->n_phys, sv->stream));
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status sv_set(sv_handle sv, const void *src, size_t n_amps, int src_is_host)
+{
+    if (!sv || !src) return fail(GBVQC_ERR_ARG, "NULL argument");
+    if (n_amps != sv->amps()) return fail(GBVQC_ERR_ARG, "expected %zu amplitudes, got %zu", sv->amps(), n_amps);
+    CUDA_TRY(cudaMemcpyAsync(sv->data, src, sv->bytes(),
+                             src_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, sv->stream));
+    if (src_is_host) CUDA_TRY(cudaStreamSynchronize(sv->stream));
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status sv_get(sv_handle sv, void *dst, size_t n_amps, int dst_is_host)
+{
+    if (!sv || !dst) return fail(GBVQC_ERR_ARG, "NULL argument");
+    if (n_amps != sv->amps()) return fail(GBVQC_ERR_ARG, "expected %zu amplitudes, got %zu", sv->amps(), n_amps);
+    CUDA_TRY(cudaMemcpyAsync(dst, sv->data, sv->bytes(),
+                             dst_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, sv->stream));
+    CUDA_TRY(cudaStreamSynchronize(sv->stream));
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status sv_info(sv_handle sv, int *n_qubits, int *dtype, int *is_density, void **device_ptr)
+{
+    if (!sv) return fail(GBVQC_ERR_ARG, "NULL state");
+    if (n_qubits) *n_qubits = sv->n_log;
+    if (dtype) *dtype = sv->dtype;
+    if (is_density) *is_density = sv->density;
+    if (device_ptr) *device_ptr = sv->data;
+    return GBVQC_OK;
+}
+
+// --------------------------------------------------------------------- observables
+
+extern "C" gbvqc_status obs_create(const gbvqc_pauli *terms, int n_terms, int n_qubits, obs_handle *out)
+{
+    if (!out || (!terms && n_terms > 0) || n_terms < 0) return fail(GBVQC_ERR_ARG, "bad arguments");
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > 34) return fail(GBVQC_ERR_ARG, "qubit count %d", n_qubits);
+    const uint64_t valid = n_qubits >= 64 ? ~0ull : ((uint64_t(1) << n_qubits) - 1);
+    std::map<uint64_t, std::vector<ObsTerm>> by_x;
+    for (int i = 0; i < n_terms; i++) {
+        if ((terms[i].x_mask | terms[i].z_mask) & ~valid)
+            return fail(GBVQC_ERR_ARG, "term %d touches a qubit >= %d", i, n_qubits);
+        ObsTerm t{};
+        t.coeff = terms[i].coeff;
+        t.z = terms[i].z_mask;
+        t.ph = __builtin_popcountll(terms[i].x_mask & terms[i].z_mask) & 3;  // Y = i X Z
+        by_x[terms[i].x_mask].push_back(t);
+    }
+    gbvqc_obs *h = new gbvqc_obs();
+    h->n_qubits = n_qubits;
+    for (auto &kv : by_x) {
+        ObsGroup g{};
+        g.x = kv.first;
+        g.t_begin = (int)h->terms.size();
+        for (auto &t : kv.second) h->terms.push_back(t);
+        g.t_end = (int)h->terms.size();
+        h->groups.push_back(g);
+    }
+    gbvqc_status st = upload(&h->d_groups, h->groups);
+    if (st == GBVQC_OK) st = upload(&h->d_terms, h->terms);
+    if (st != GBVQC_OK) {
+        obs_free(h);
+        return st;
+    }
+    *out = h;
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status obs_free(obs_handle h)
+{
+    if (!h) return GBVQC_OK;
+    if (h->d_groups) cudaFree(h->d_groups);
+    if (h->d_terms) cudaFree(h->d_terms);
+    delete h;
+    return GBVQC_OK;
+}
+
+static DensMap standard_map(int n)
+{
+    DensMap m{};
+    for (int q = 0; q < n; q++) {
+        m.ket[q] = (int8_t)q;
+        m.bra[q] = (int8_t)(q + n);
+    }
+    return m;
+}
+
+static DensMap interleaved_map(int n)
+{
+    DensMap m{};
+    for (int q = 0; q < n; q++) {
+        m.ket[q] = (int8_t)(2 * q);
+        m.bra[q] = (int8_t)(2 * q + 1);
+    }
+    return m;
+}
+
+extern "C" gbvqc_status expect(sv_handle sv, obs_handle h, double *out_energy)
+{
+    if (!sv || !h || !out_energy) return fail(GBVQC_ERR_ARG, "NULL argument");
+    if (h->n_qubits != sv->n_log) return fail(GBVQC_ERR_ARG, "observable has %d qubits, state %d", h->n_qubits, sv->n_log);
+    RedScratch red{sv->d_scratch, sv->d_counter};
+    double *d_out = sv->d_scratch + kMaxRedBlocks;
+    if (sv->density)
+        CUDA_TRY(launch_density_expect(sv->dtype, sv->data, sv->n_log, standard_map(sv->n_log), h->dev(), red,
+                                       d_out, sv->stream));
+    else
+        CUDA_TRY(launch_pauli_expect(sv->dtype, sv->data, nullptr, sv->n_phys, h->dev(), red, d_out, sv->stream));
+    CUDA_TRY(cudaMemcpyAsync(out_energy, d_out, sizeof(double), cudaMemcpyDeviceToHost, sv->stream));
+    CUDA_TRY(cudaStreamSynchronize(sv->stream));
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status apply_channel(sv_handle sv, int kind, int qubit, double strength, const double *kraus,
+                                      int n_kraus)
+{
+    if (!sv) return fail(GBVQC_ERR_ARG, "NULL state");
+    if (!sv->density) return fail(GBVQC_ERR_NOT_DENSITY, "apply_channel needs a density state");
+    if (!is_channel(kind)) return fail(GBVQC_ERR_ARG, "kind %d is not a channel", kind);
+    if (qubit < 0 || qubit >= sv->n_log) return fail(GBVQC_ERR_ARG, "qubit %d out of range", qubit);
+    if (kind == GBVQC_KRAUS && (!kraus || n_kraus < 1 || n_kraus > 4))
+        return fail(GBVQC_ERR_ARG, "KRAUS needs 1..4 operators");
+    if (kind != GBVQC_KRAUS && !(strength >= 0.0 && strength <= 1.0))
+        return fail(GBVQC_ERR_ARG, "channel strength %g outside [0, 1]", strength);
+    Mat S = superop(channel_kraus(kind, strength, kraus, n_kraus));
+    MatRec r;
+    double m[32];
+    mat_to(S, m);
+    for (int i = 0; i < 32; i++) {
+        r.d[i] = m[i];
+        r.f[i] = (float)m[i];
+    }
+    CUDA_TRY(cudaMemcpyAsync(sv->d_rec, &r, sizeof r, cudaMemcpyHostToDevice, sv->stream));
+    CUDA_TRY(launch_gate(sv->dtype, sv->data, sv->n_phys, classify(S), qubit, qubit + sv->n_log, sv->d_rec,
+                         sv->stream));
+    CUDA_TRY(cudaStreamSynchronize(sv->stream));  // the host record must outlive the copy
+    return GBVQC_OK;
+}
+
+// ------------------------------------------------------------------------ circuits
+
+static int add_rec(gbvqc_circuit *c, const Mat &M)
+{
+    MatRec r;
+    double m[32];
+    mat_to(M, m);
+    for (int i = 0; i < 32; i++) {
+        r.d[i] = m[i];
+        r.f[i] = (float)m[i];
+    }
+    c->recs.push_back(r);
+    return (int)c->recs.size() - 1;
+}
+
+static int add_dyn(gbvqc_circuit *c, int param, int rot, int variant, int domain)
+{
+    DynRec d{};
+    d.rec = (int)c->recs.size();
+    d.param = param;
+    d.rot = rot;
+    d.variant = variant;
+    d.domain = domain;
+    MatRec r;
+    materialize(d, 0.0, &r);  // placeholder, refreshed from theta before every use
+    c->recs.push_back(r);
+    c->dyn.push_back(d);
+    return d.rec;
+}
+
+// Records of one unitary op in a domain: forward, inverse, derivative (or -1), and shape.
+struct OpRecs {
+    int f, i, d, shape, dshape;
+    Mat Mf, Mi;
+};
+
+static OpRecs op_records(gbvqc_circuit *c, const gbvqc_op &op, int domain)
+{
+    OpRecs o{};
+    o.d = -1;
+    if (is_rotation(op.kind) && op.param_index >= 0) {
+        int rot = op.kind - GBVQC_RX;
+        o.f = add_dyn(c, op.param_index, rot, VAR_FWD, domain);
+        o.i = add_dyn(c, op.param_index, rot, VAR_INV, domain);
+        o.d = add_dyn(c, op.param_index, rot, VAR_DER, domain);
+        if (domain == DOM_SUPER) o.shape = rot == ROT_Z ? SH_DIAG2 : SH_DENSE2;
+        else o.shape = rot == ROT_Z ? SH_DIAG1 : rot == ROT_Y ? SH_REAL1 : SH_DENSE1;
+        o.dshape = o.shape;
+        return o;
+    }
+    Mat U = gate_matrix(op);
+    int d = (int)std::lround(std::sqrt((double)U.size()));
+    if (domain == DOM_BRA) U = mat_conj(U);
+    if (domain == DOM_SUPER) {
+        Mat S(16, 0);
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++)
+                for (int cc = 0; cc < 2; cc++)
+                    for (int dd = 0; dd < 2; dd++)
+                        S[(a + 2 * b) * 4 + (cc + 2 * dd)] = U[a * 2 + cc] * std::conj(U[b * 2 + dd]);
+        U = S;
+        d = 4;
+    }
+    o.Mf = U;
+    o.Mi = mat_dagger(U, d);
+    o.f = add_rec(c, o.Mf);
+    o.i = add_rec(c, o.Mi);
+    o.shape = join_shape(classify(o.Mf), classify(o.Mi));
+    return o;
+}
+
+static void free_plan(DevPlan *p)
+{
+    if (!p) return;
+    cudaFree(p->d_fwd); cudaFree(p->d_rev); cudaFree(p->d_fsubs); cudaFree(p->d_rsubs);
+    cudaFree(p->d_fgates); cudaFree(p->d_rgates); cudaFree(p->d_csr_ptr); cudaFree(p->d_csr_slots);
+}
+
+static void free_graphs(gbvqc_circuit *c)
+{
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
+static void free_workspace(Workspace &w)
+{
+    cudaFree(w.phi); cudaFree(w.psi); cudaFree(w.d_theta); cudaFree(w.d_energy); cudaFree(w.d_grad);
+    cudaFree(w.d_slot_grad); cudaFree(w.d_slot_partials); cudaFree(w.d_red); cudaFree(w.d_counter);
+    w = Workspace();
+}
+
+extern "C" gbvqc_status circuit_free(circuit_handle c)
+{
+    if (!c) return GBVQC_OK;
+    free_graphs(c);
+    for (auto &kv : c->plans) free_plan(kv.second.get());
+    free_workspace(c->ws);
+    cudaFree(c->d_recs); cudaFree(c->d_dyn); cudaFree(c->d_plain_ptr); cudaFree(c->d_plain_slots);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+    return GBVQC_OK;
+}
+
+static gbvqc_status csr_upload(const std::vector<int> &slot_param, int n_params, int **d_ptr, int **d_slots)
+{
+    std::vector<int> ptr(n_params + 1, 0), slots;
+    for (int p : slot_param)
+        if (p >= 0) ptr[p + 1]++;
+    for (int p = 0; p < n_params; p++) ptr[p + 1] += ptr[p];
+    slots.assign(ptr[n_params], 0);
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (size_t s = 0; s < slot_param.size(); s++)
+        if (slot_param[s] >= 0) slots[fill[slot_param[s]]++] = (int)s;
+    ST_TRY(upload(d_ptr, ptr));
+    ST_TRY(upload(d_slots, slots));
+    return GBVQC_OK;
+}
+
+// Physical gate list of the fused engine for a density layout `map` (or pure, map unused).
+static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGate> &out)
+{
+    out.clear();
+    for (const gbvqc_op &op : c->ops) {
+        if (!c->density) {
+            OpRecs r = op_records(c, op, DOM_KET);
+            PGate g{};
+            g.k = kind_qubits(op.kind);
+            g.q[0] = op.qubits[0];
+            g.q[1] = g.k == 2 ? op.qubits[1] : 0;
+            g.diag = shape_is_diag(r.shape);
+            g.ftype = ftype_of(r.shape);
+            g.rec_f = r.f;
+            g.rec_i = r.i;
+            g.rec_a = r.i;
+            g.perm_f = r.Mf.size() == 16 ? perm_bits(r.Mf) : 0;
+            g.perm_r = r.Mi.size() == 16 ? perm_bits(r.Mi) : 0;
+            g.gen = GEN_NONE;
+            g.param = -1;
+            if (is_rotation(op.kind) && op.param_index >= 0) {
+                g.gen = op.kind == GBVQC_RX ? GEN_X : op.kind == GBVQC_RY ? GEN_Y : GEN_Z;
+                g.gq = op.qubits[0];
+                g.coef = 1.0f;
+                g.param = op.param_index;
+            }
+            out.push_back(g);
+            continue;
+        }
+        if (is_channel(op.kind)) {
+            Mat S = superop(channel_kraus(op.kind, op.params[0], op.data, op.n_kraus)), Si;
+            mat_inverse(S, 4, Si);
+            Mat Sa = mat_dagger(S, 4);
+            PGate g{};
+            g.k = 2;
+            g.q[0] = map.ket[op.qubits[0]];
+            g.q[1] = map.bra[op.qubits[0]];
+            int sh = join_shape(join_shape(classify(S), classify(Si)), classify(Sa));
+            if (sh == SH_PERM2 || sh == SH_CTRL2) sh = SH_DENSE2;
+            g.diag = sh == SH_DIAG2;
+            g.ftype = ftype_of(sh);
+            g.rec_f = add_rec(c, S);
+            g.rec_i = add_rec(c, Si);
+            g.rec_a = add_rec(c, Sa);
+            g.gen = GEN_NONE;
+            g.param = -1;
+            out.push_back(g);
+            continue;
+        }
+        // unitary on a density matrix: U on the ket qubits, conj(U) on the bra qubits
+        for (int side = 0; side < 2; side++) {
+            OpRecs r = op_records(c, op, side == 0 ? DOM_KET : DOM_BRA);
+            PGate g{};
+            g.k = kind_qubits(op.kind);
+            const int8_t *pos = side == 0 ? map.ket : map.bra;
+            g.q[0] = pos[op.qubits[0]];
+            g.q[1] = g.k == 2 ? pos[op.qubits[1]] : 0;
+            g.diag = shape_is_diag(r.shape);
+            g.ftype = ftype_of(r.shape);
+            g.rec_f = r.f;
+            g.rec_i = r.i;
+            g.rec_a = r.i;
+            g.perm_f = r.Mf.size() == 16 ? perm_bits(r.Mf) : 0;
+            g.perm_r = r.Mi.size() == 16 ? perm_bits(r.Mi) : 0;
+            g.gen = GEN_NONE;
+            g.param = -1;
+            if (is_rotation(op.kind) && op.param_index >= 0) {
+                g.gen = op.kind == GBVQC_RX ? GEN_X : op.kind == GBVQC_RY ? GEN_Y : GEN_Z;
+                g.gq = g.q[0];
+                // ket: Re<<Psi|(-i/2)P|Phi>> = Im/2; bra: Re<<Psi|(i/2)P*|Phi>>, P* = -Y for Y
+                g.coef = side == 0 ? 0.5f : (op.kind == GBVQC_RY ? 0.5f : -0.5f);
+                g.param = op.param_index;
+            }
+            out.push_back(g);
+        }
+    }
+}
+
+extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qubits, int n_params,
+                                       int is_density, circuit_handle *out)
+{
+    if (!out || (!ops && n_ops > 0) || n_ops < 0 || n_params < 0) return fail(GBVQC_ERR_ARG, "bad arguments");
+    *out = nullptr;
+    int n_phys = is_density ? 2 * n_qubits : n_qubits;
+    if (n_qubits < 1 || n_phys > 34) return fail(GBVQC_ERR_ARG, "qubit count %d out of range", n_qubits);
+    for (int j = 0; j < n_ops; j++) {
+        const gbvqc_op &op = ops[j];
+        if (op.kind < 0 || op.kind >= GBVQC_NUM_KINDS) return fail(GBVQC_ERR_ARG, "op %d: kind %d", j, op.kind);
+        int k = kind_qubits(op.kind);
+        for (int u = 0; u < k; u++)
+            if (op.qubits[u] < 0 || op.qubits[u] >= n_qubits)
+                return fail(GBVQC_ERR_ARG, "op %d: qubit %d out of range", j, op.qubits[u]);
+        if (k == 2 && op.qubits[0] == op.qubits[1]) return fail(GBVQC_ERR_ARG, "op %d: repeated qubit", j);
+        if (op.param_index >= 0 && (!is_rotation(op.kind) || op.param_index >= n_params))
+            return fail(GBVQC_ERR_ARG, "op %d: bad param_index %d", j, op.param_index);
+        if (op.param_index < -1) return fail(GBVQC_ERR_ARG, "op %d: bad param_index %d", j, op.param_index);
+        if (is_channel(op.kind)) {
+            if (!is_density) return fail(GBVQC_ERR_NOT_DENSITY, "op %d: channel in a pure-state circuit", j);
+            if (op.kind == GBVQC_KRAUS && (op.n_kraus < 1 || op.n_kraus > 4))
+                return fail(GBVQC_ERR_ARG, "op %d: n_kraus %d", j, op.n_kraus);
+            if (op.kind != GBVQC_KRAUS && !(op.params[0] >= 0.0 && op.params[0] <= 1.0))
+                return fail(GBVQC_ERR_ARG, "op %d: channel strength %g", j, op.params[0]);
+            if (op.kind == GBVQC_KRAUS || op.params[0] > 0.0) {
+                Mat S = superop(channel_kraus(op.kind, op.params[0], op.data, op.n_kraus)), Si;
+                if (!mat_inverse(S, 4, Si))
+                    return fail(GBVQC_ERR_ARG, "op %d: channel superoperator is singular", j);
+            }
+        }
+    }
+    gbvqc_circuit *c = new gbvqc_circuit();
+    c->n_log = n_qubits;
+    c->n_phys = n_phys;
+    c->n_params = n_params;
+    c->density = is_density ? 1 : 0;
+    c->ops.assign(ops, ops + n_ops);
+    for (const gbvqc_op &op : c->ops) c->n_param_ops += op.param_index >= 0 ? 1 : 0;
+    // per-gate schedule in the standard layout
+    for (const gbvqc_op &op : c->ops) {
+        int k = kind_qubits(op.kind);
+        if (!c->density) {
+            OpRecs r = op_records(c, op, DOM_KET);
+            PlainGate g{r.shape, op.qubits[0], k == 2 ? op.qubits[1] : 0, r.f, r.i, r.i, 1, op.qubits[0], 0,
+                        r.d, op.param_index, 2.0, -1};
+            c->plain.push_back(g);
+        } else if (is_channel(op.kind)) {
+            Mat S = superop(channel_kraus(op.kind, op.params[0], op.data, op.n_kraus)), Si;
+            mat_inverse(S, 4, Si);
+            Mat Sa = mat_dagger(S, 4);
+            int sh = join_shape(join_shape(classify(S), classify(Si)), classify(Sa));
+            PlainGate g{sh, op.qubits[0], op.qubits[0] + n_qubits, add_rec(c, S), add_rec(c, Si), add_rec(c, Sa),
+                        2, op.qubits[0], op.qubits[0] + n_qubits, -1, -1, 1.0, -1};
+            c->plain.push_back(g);
+        } else if (k == 1) {
+            OpRecs r = op_records(c, op, DOM_SUPER);
+            PlainGate g{r.shape, op.qubits[0], op.qubits[0] + n_qubits, r.f, r.i, r.i, 2, op.qubits[0],
+                        op.qubits[0] + n_qubits, r.d, op.param_index, 1.0, -1};
+            c->plain.push_back(g);
+        } else {
+            for (int side = 0; side < 2; side++) {
+                OpRecs r = op_records(c, op, side == 0 ? DOM_KET : DOM_BRA);
+                int off = side == 0 ? 0 : n_qubits;
+                PlainGate g{r.shape, op.qubits[0] + off, op.qubits[1] + off, r.f, r.i, r.i, 1, 0, 0, -1, -1, 1.0, -1};
+                c->plain.push_back(g);
+            }
+        }
+    }
+    std::vector<int> slot_param;
+    for (PlainGate &g : c->plain)
+        if (g.param >= 0 && g.rec_d >= 0) {
+            g.slot = (int)slot_param.size();
+            slot_param.push_back(g.param);
+        }
+    c->plain_slots = (int)slot_param.size();
+    c->map_std = standard_map(n_qubits);
+    c->map_grad = interleaved_map(n_qubits);
+    fused_gates_of(c, c->map_std, c->pg_std);
+    if (c->density) fused_gates_of(c, c->map_grad, c->pg_grad);
+    gbvqc_status st = csr_upload(slot_param, n_params, &c->d_plain_ptr, &c->d_plain_slots);
+    if (st == GBVQC_OK) st = upload(&c->d_recs, c->recs);
+    if (st == GBVQC_OK) st = upload(&c->d_dyn, c->dyn);
+    if (st == GBVQC_OK) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) st = fail(GBVQC_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+    }
+    if (st != GBVQC_OK) {
+        circuit_free(c);
+        return st;
+    }
+    *out = c;
+    return GBVQC_OK;
+}
+
+static int default_tile(int dtype) { return 12; }
+static int default_low(int dtype) { return dtype == GBVQC_C64 ? 4 : 3; }
+
+// Fused plan for (dtype, layout); built on first use.
+static gbvqc_status get_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out)
+{
+    int key = dtype * 2 + (grad_layout && c->density ? 1 : 0);
+    auto it = c->plans.find(key);
+    if (it != c->plans.end()) {
+        *out = it->second.get();
+        return GBVQC_OK;
+    }
+    const std::vector<PGate> &pg = (grad_layout && c->density) ? c->pg_grad : c->pg_std;
+    int t = c->tile_qubits ? c->tile_qubits : default_tile(dtype);
+    int low = c->low_qubits ? c->low_qubits : default_low(dtype);
+    // at most 256 threads per CTA: 2^(t - NR) <= 256 for both the forward and reverse kernels
+    const int t_max = std::min(fused_nr(dtype, false), fused_nr(dtype, true)) + 8;
+    if (t > t_max) t = t_max;
+    std::unique_ptr<DevPlan> dp(new DevPlan());
+    std::string err;
+    CUDA_TRY(fused_prepare());
+    if (!build_fused_plan(pg, c->n_phys, t, low, fused_nr(dtype, false), fused_nr(dtype, true), 256, dp->p, err))
+        return fail(GBVQC_ERR_UNSUPPORTED, "fused plan: %s", err.c_str());
+    for (const PassDesc &d : dp->p.fwd) {
+        double f = 0;
+        for (int i = 0; i < d.n_sub; i++) {
+            const SubRun &r = dp->p.fsubs[d.sub_begin + i];
+            for (int g = r.g_begin; g < r.g_end; g++) f += ftype_flops(dp->p.fgates[g].type);
+        }
+        dp->fwd_flops_per_amp.push_back(f);
+    }
+    for (const PassDesc &d : dp->p.rev) {
+        double f = 0;
+        for (int i = 0; i < d.n_sub; i++) {
+            const SubRun &r = dp->p.rsubs[d.sub_begin + i];
+            for (int g = r.g_begin; g < r.g_end; g++) {
+                const FGate &fg = dp->p.rgates[g];
+                f += 2 * ftype_flops(fg.type);
+                if (fg.gen == GEN_Z) f += 3;
+                else if (fg.gen != GEN_NONE) f += 4;
+            }
+        }
+        dp->rev_flops_per_amp.push_back(f);
+    }
+    ST_TRY(upload(&dp->d_fwd, dp->p.fwd));
+    ST_TRY(upload(&dp->d_rev, dp->p.rev));
+    ST_TRY(upload(&dp->d_fsubs, dp->p.fsubs));
+    ST_TRY(upload(&dp->d_rsubs, dp->p.rsubs));
+    ST_TRY(upload(&dp->d_fgates, dp->p.fgates));
+    ST_TRY(upload(&dp->d_rgates, dp->p.rgates));
+    ST_TRY(csr_upload(dp->p.slot_param, c->n_params, &dp->d_csr_ptr, &dp->d_csr_slots));
+    *out = dp.get();
+    c->plans[key] = std::move(dp);
+    return GBVQC_OK;
+}
+
+static bool fused_supported(const gbvqc_circuit *c, int dtype)
+{
+    return c->n_phys >= std::max(fused_nr(dtype, false), fused_nr(dtype, true)) + 1;
+}
+
+extern "C" gbvqc_status circuit_set_tiling(circuit_handle c, int tile_qubits, int low_qubits)
+{
+    if (!c) return fail(GBVQC_ERR_ARG, "NULL circuit");
+    if (tile_qubits != 0 && (tile_qubits < 6 || tile_qubits > 13)) return fail(GBVQC_ERR_ARG, "tile_qubits %d", tile_qubits);
+    if (low_qubits != 0 && (low_qubits < 1 || low_qubits > 6)) return fail(GBVQC_ERR_ARG, "low_qubits %d", low_qubits);
+    std::lock_guard<std::mutex> lk(c->mu);
+    free_graphs(c);
+    for (auto &kv : c->plans) free_plan(kv.second.get());
+    c->plans.clear();
+    cudaFree(c->ws.d_slot_partials);
+    c->ws.d_slot_partials = nullptr;
+    c->partials_cap = 0;
+    c->tile_qubits = tile_qubits;
+    c->low_qubits = low_qubits;
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status circuit_plan_info(circuit_handle c, int *n_passes, int *n_gates, int *tile_qubits)
+{
+    if (!c) return fail(GBVQC_ERR_ARG, "NULL circuit");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DevPlan *p = nullptr;
+    if (!fused_supported(c, GBVQC_C64)) return fail(GBVQC_ERR_UNSUPPORTED, "too few qubits for tiles");
+    ST_TRY(get_plan(c, GBVQC_C64, c->density != 0, &p));
+    if (n_passes) *n_passes = (int)p->p.fwd.size();
+    if (n_gates) *n_gates = (int)p->p.fgates.size();
+    if (tile_qubits) *tile_qubits = p->p.t;
+    return GBVQC_OK;
+}
+
+// ------------------------------------------------------------------- execution
+
+static gbvqc_status ensure_theta(gbvqc_circuit *c)
+{
+    if (!c->ws.d_theta) ST_TRY(dev_alloc(&c->ws.d_theta, c->n_params + 1));
+    return GBVQC_OK;
+}
+
+static gbvqc_status stage_theta(gbvqc_circuit *c, const double *theta, int n_theta, int loc, cudaStream_t s)
+{
+    if (n_theta != c->n_params) return fail(GBVQC_ERR_ARG, "expected %d parameters, got %d", c->n_params, n_theta);
+    if (n_theta > 0 && !theta) return fail(GBVQC_ERR_ARG, "theta is NULL");
+    ST_TRY(ensure_theta(c));
+    if (n_theta > 0)
+        CUDA_TRY(cudaMemcpyAsync(c->ws.d_theta, theta, sizeof(double) * n_theta,
+                                 loc == GBVQC_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    return GBVQC_OK;
+}
+
+static double state_bytes(const gbvqc_circuit *c, int dtype) { return double(size_t(1) << c->n_phys) * amp_size(dtype); }
+
+static gbvqc_status plain_gate(gbvqc_circuit *c, int dtype, void *psi, const PlainGate &g, int rec, cudaStream_t s)
+{
+    const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
+    const bool one = shape_qubits(g.shape) == 1;
+    return run_k(one ? "gate1q" : "gate2q", shape_flops(g.shape) * amps, (g.shape == SH_CTRL2 ? 1.0 : 2.0) * sb, s,
+                 [&] { return launch_gate(dtype, psi, c->n_phys, g.shape, g.q0, g.q1, c->d_recs + rec, s); });
+}
+
+static gbvqc_status run_plain_forward(gbvqc_circuit *c, int dtype, void *psi, cudaStream_t s)
+{
+    for (const PlainGate &g : c->plain) ST_TRY(plain_gate(c, dtype, psi, g, g.rec_f, s));
+    return GBVQC_OK;
+}
+
+static gbvqc_status run_fused_forward(gbvqc_circuit *c, DevPlan *p, int dtype, void *psi, cudaStream_t s)
+{
+    const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
+    for (size_t i = 0; i < p->p.fwd.size(); i++)
+        ST_TRY(run_k("fused_forward", p->fwd_flops_per_amp[i] * amps, 2 * sb, s, [&] {
+            return launch_fused_forward(dtype, psi, p->d_fwd + i, p->p.fwd[i], p->d_fsubs, p->d_fgates, c->d_recs, s);
+        }));
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status apply_circuit(sv_handle sv, circuit_handle c, const double *theta, int n_theta, int theta_loc,
+                                      int mode)
+{
+    if (!sv || !c) return fail(GBVQC_ERR_ARG, "NULL argument");
+    if (sv->n_log != c->n_log || sv->density != c->density)
+        return fail(GBVQC_ERR_ARG, "state (%d qubits, density %d) does not match circuit (%d, %d)", sv->n_log,
+                    sv->density, c->n_log, c->density);
+    if (mode != GBVQC_MODE_PLAIN && mode != GBVQC_MODE_FUSED) return fail(GBVQC_ERR_ARG, "mode %d", mode);
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t s = sv->stream;
+    ST_TRY(stage_theta(c, theta, n_theta, theta_loc, s));
+    CUDA_TRY(launch_materialize(c->d_dyn, (int)c->dyn.size(), c->ws.d_theta, c->d_recs, s));
+    if (mode == GBVQC_MODE_FUSED && fused_supported(c, sv->dtype)) {
+        DevPlan *p = nullptr;
+        ST_TRY(get_plan(c, sv->dtype, false, &p));
+        return run_fused_forward(c, p, sv->dtype, sv->data, s);
+    }
+    return run_plain_forward(c, sv->dtype, sv->data, s);
+}
+
+// ------------------------------------------------------------------------ gradient
+
+static gbvqc_status ensure_workspace(gbvqc_circuit *c, int dtype, size_t slot_partials)
+{
+    Workspace &w = c->ws;
+    if (w.dtype != dtype) {
+        free_graphs(c);
+        cudaFree(w.phi);
+        cudaFree(w.psi);
+        w.phi = w.psi = nullptr;
+        size_t bytes = (size_t(1) << c->n_phys) * amp_size(dtype);
+        ST_TRY(dev_alloc((unsigned char **)&w.phi, bytes));
+        ST_TRY(dev_alloc((unsigned char **)&w.psi, bytes));
+        w.dtype = dtype;
+    }
+    ST_TRY(ensure_theta(c));
+    if (!w.d_energy) ST_TRY(dev_alloc(&w.d_energy, 1));
+    if (!w.d_grad) ST_TRY(dev_alloc(&w.d_grad, c->n_params + 1));
+    if (!w.d_red) ST_TRY(dev_alloc(&w.d_red, kMaxRedBlocks));
+    if (!w.d_counter) {
+        ST_TRY(dev_alloc(&w.d_counter, 1));
+        CUDA_TRY(cudaMemset(w.d_counter, 0, sizeof(unsigned)));
+    }
+    return GBVQC_OK;
+}
+
+// The whole gradient evaluation as a stream-ordered launch sequence (capturable).
+static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int mode, DevPlan *p, cudaStream_t s)
+{
+    Workspace &w = c->ws;
+    RedScratch red{w.d_red, w.d_counter};
+    const bool fused = mode == GBVQC_MODE_FUSED && p;
+    const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
+    ST_TRY(run_k("materialize", 0, 0, s, [&] {
+        return launch_materialize(c->d_dyn, (int)c->dyn.size(), w.d_theta, c->d_recs, s);
+    }));
+    ST_TRY(run_k("zero_state", 0, sb, s, [&] { return launch_zero_state(dtype, w.phi, c->n_phys, s); }));
+    if (fused) ST_TRY(run_fused_forward(c, p, dtype, w.phi, s));
+    else ST_TRY(run_plain_forward(c, dtype, w.phi, s));
+    // energy and adjoint seed
+    if (c->density) {
+        const DensMap &m = fused ? c->map_grad : c->map_std;
+        ST_TRY(run_k("density_expect", 0, 0, s, [&] {
+            return launch_density_expect(dtype, w.phi, c->n_log, m, h->dev(), red, w.d_energy, s);
+        }));
+        ST_TRY(run_k("density_seed", 0, sb, s, [&] {
+            return launch_density_seed(dtype, w.psi, c->n_log, m, h->dev(), s);
+        }));
+    } else {
+        ST_TRY(run_k("pauli_expect_seed", (8.0 * h->groups.size() + 4) * amps, 2 * sb, s, [&] {
+            return launch_pauli_expect(dtype, w.phi, w.psi, c->n_phys, h->dev(), red, w.d_energy, s);
+        }));
+    }
+    if (fused) {
+        const int tiles = 1 << (c->n_phys - p->p.t);
+        for (int i = (int)p->p.rev.size() - 1; i >= 0; i--)
+            ST_TRY(run_k("fused_reverse", p->rev_flops_per_amp[i] * amps, 4 * sb, s, [&] {
+                return launch_fused_reverse(dtype, w.phi, w.psi, p->d_rev + i, p->p.rev[i], p->d_rsubs, p->d_rgates,
+                                            c->d_recs, w.d_slot_partials, tiles, s);
+            }));
+        ST_TRY(run_k("reduce_slots", 0, 0, s, [&] {
+            return launch_reduce_slots(w.d_slot_partials, p->p.n_slots, tiles, tiles, w.d_slot_grad, s);
+        }));
+        ST_TRY(run_k("accumulate", 0, 0, s, [&] {
+            return launch_accumulate(w.d_slot_grad, p->d_csr_ptr, p->d_csr_slots, c->n_params, w.d_grad, s);
+        }));
+    } else {
+        // Algorithm 2: Phi <- Q^-1 Phi; g = scale Re <Psi|dQ|Phi>; Psi <- Q^-1 Psi (Q^dag for channels)
+        for (int j = (int)c->plain.size() - 1; j >= 0; j--) {
+            const PlainGate &g = c->plain[j];
+            ST_TRY(plain_gate(c, dtype, w.phi, g, g.rec_i, s));
+            if (g.slot >= 0)
+                ST_TRY(run_k("dot_derivative", (shape_flops(g.der_k == 1 ? SH_DENSE1 : SH_DENSE2) + 4) * amps, 2 * sb, s,
+                             [&] {
+                                 return launch_dot_matrix(dtype, w.psi, w.phi, c->n_phys, g.der_k, g.dq0, g.dq1,
+                                                          c->d_recs + g.rec_d, g.gscale, red, w.d_slot_grad + g.slot, s);
+                             }));
+            ST_TRY(plain_gate(c, dtype, w.psi, g, g.rec_a, s));
+        }
+        ST_TRY(run_k("accumulate", 0, 0, s, [&] {
+            return launch_accumulate(w.d_slot_grad, c->d_plain_ptr, c->d_plain_slots, c->n_params, w.d_grad, s);
+        }));
+    }
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status grad(circuit_handle c, const double *theta, int n_theta, obs_handle h, int dtype, int mode,
+                             int ptr_loc, void *stream, double *energy, double *grad_out)
+{
+    if (!c || !h || !energy || (!grad_out && c->n_params > 0)) return fail(GBVQC_ERR_ARG, "NULL argument");
+    if (dtype != GBVQC_C64 && dtype != GBVQC_C128) return fail(GBVQC_ERR_ARG, "dtype %d", dtype);
+    if (mode != GBVQC_MODE_PLAIN && mode != GBVQC_MODE_FUSED) return fail(GBVQC_ERR_ARG, "mode %d", mode);
+    if (ptr_loc != GBVQC_PTR_HOST && ptr_loc != GBVQC_PTR_DEVICE) return fail(GBVQC_ERR_ARG, "ptr_loc %d", ptr_loc);
+    if (h->n_qubits != c->n_log) return fail(GBVQC_ERR_ARG, "observable has %d qubits, circuit %d", h->n_qubits, c->n_log);
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    DevPlan *p = nullptr;
+    if (mode == GBVQC_MODE_FUSED && fused_supported(c, dtype)) ST_TRY(get_plan(c, dtype, true, &p));
+    else mode = GBVQC_MODE_PLAIN;
+    ST_TRY(ensure_workspace(c, dtype, 0));
+    Workspace &w = c->ws;
+    // a gradient slot per variational physical gate: at most two per op (ket and bra)
+    if (!w.d_slot_grad) ST_TRY(dev_alloc(&w.d_slot_grad, (size_t)2 * c->n_param_ops + 1));
+    if (p) {
+        size_t need = (size_t)p->p.n_slots * (size_t(1) << (c->n_phys - p->p.t));
+        if (need > c->partials_cap) {
+            free_graphs(c);
+            cudaFree(w.d_slot_partials);
+            w.d_slot_partials = nullptr;
+            ST_TRY(dev_alloc(&w.d_slot_partials, std::max<size_t>(need, 1)));
+            c->partials_cap = std::max<size_t>(need, 1);
+        }
+    }
+    ST_TRY(stage_theta(c, theta, n_theta, ptr_loc, s));
+    if (g_prof) {  // grad_profile: plain stream launches with events
+        ST_TRY(enqueue_grad(c, h, dtype, mode, p, s));
+        cudaMemcpyKind k = ptr_loc == GBVQC_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        CUDA_TRY(cudaMemcpyAsync(energy, w.d_energy, sizeof(double), k, s));
+        if (c->n_params > 0) CUDA_TRY(cudaMemcpyAsync(grad_out, w.d_grad, sizeof(double) * c->n_params, k, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return GBVQC_OK;
+    }
+    // replay the captured launch sequence
+    if ((const void *)h != c->graph_obs) {
+        free_graphs(c);
+        c->graph_obs = h;
+    }
+    const int gkey = dtype * 2 + mode;
+    auto it = c->graphs.find(gkey);
+    if (it == c->graphs.end()) {
+        cudaGraph_t graph = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        gbvqc_status st = enqueue_grad(c, h, dtype, mode, p, c->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (st != GBVQC_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        CUDA_TRY(e);
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CUDA_TRY(e);
+        it = c->graphs.emplace(gkey, exec).first;
+    }
+    CUDA_TRY(cudaGraphLaunch(it->second, s));
+    cudaMemcpyKind kind = ptr_loc == GBVQC_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CUDA_TRY(cudaMemcpyAsync(energy, w.d_energy, sizeof(double), kind, s));
+    if (c->n_params > 0) CUDA_TRY(cudaMemcpyAsync(grad_out, w.d_grad, sizeof(double) * c->n_params, kind, s));
+    if (ptr_loc == GBVQC_PTR_HOST) CUDA_TRY(cudaStreamSynchronize(s));
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status grad_profile(circuit_handle c, const double *theta, int n_theta, obs_handle h, int dtype,
+                                     int mode, void *stream, gbvqc_kernel_stat *stats, int max_stats, int *n_stats)
+{
+    if (!stats || !n_stats || max_stats < 0) return fail(GBVQC_ERR_ARG, "NULL argument");
+    std::vector<ProfRec> recs;
+    std::vector<double> g(c ? std::max(c->n_params, 1) : 1);
+    double e = 0;
+    g_prof = &recs;
+    gbvqc_status st = grad(c, theta, n_theta, h, dtype, mode, GBVQC_PTR_HOST, stream, &e, g.data());
+    g_prof = nullptr;
+    std::vector<gbvqc_kernel_stat> agg;
+    for (ProfRec &r : recs) {
+        float ms = 0;
+        if (st == GBVQC_OK && cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+            st = fail(GBVQC_ERR_CUDA, "event timing failed");
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+        size_t i = 0;
+        while (i < agg.size() && r.name != agg[i].name) i++;
+        if (i == agg.size()) {
+            gbvqc_kernel_stat k{};
+            snprintf(k.name, sizeof k.name, "%s", r.name.c_str());
+            agg.push_back(k);
+        }
+        agg[i].launches++;
+        agg[i].ms += ms;
+        agg[i].alg_flops += r.flops;
+        agg[i].alg_bytes += r.bytes;
+    }
+    if (st != GBVQC_OK) return st;
+    *n_stats = (int)std::min<size_t>(agg.size(), (size_t)max_stats);
+    for (int i = 0; i < *n_stats; i++) stats[i] = agg[i];
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status grad_batch(const circuit_handle *circuits, const obs_handle *observables, int n_circuits,
+                                   const double *theta_all, void *stream, double *energies, double *grads)
+{
+    (void)circuits; (void)observables; (void)n_circuits; (void)theta_all; (void)stream; (void)energies; (void)grads;
+    return fail(GBVQC_ERR_UNSUPPORTED, "grad_batch is not built yet");
+}

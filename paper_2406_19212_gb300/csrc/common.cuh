@@ -1,0 +1,163 @@
+// Shared definitions of the GB300 library: matrix records, structural shapes of gate
+// kernels, and materialisation of the theta-dependent rotation matrices (host + device).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace gbvqc {
+
+// One gate matrix (up to 4x4 complex, row-major, interleaved re/im) kept in both
+// precisions so that complex64 and complex128 sweeps read the same record.
+struct alignas(16) MatRec {
+    double d[32];
+    float f[32];
+};
+
+// Structural specialisation of a gate kernel (paper Sec. II.B: predefined gates run
+// faster than the general QuantumGate by exploiting their structure).
+enum Shape : int32_t {
+    SH_DENSE1 = 0,  // general 2x2
+    SH_DIAG1 = 1,   // diagonal 2x2 (Z, S, T, Rz)
+    SH_ANTI1 = 2,   // anti-diagonal 2x2 (X, Y)
+    SH_REAL1 = 3,   // real 2x2 (Ry, H)
+    SH_DENSE2 = 4,  // general 4x4
+    SH_DIAG2 = 5,   // diagonal 4x4 (CZ, superoperators of Rz)
+    SH_PERM2 = 6,   // one non-zero per row (SWAP, iSWAP)
+    SH_CTRL2 = 7    // identity unless the first qubit is 1, then a 2x2 on the second
+};
+
+inline __host__ __device__ bool shape_is_diag(int sh) { return sh == SH_DIAG1 || sh == SH_DIAG2; }
+inline __host__ __device__ int shape_qubits(int sh) { return sh >= SH_DENSE2 ? 2 : 1; }
+
+enum Rot : int32_t { ROT_X = 0, ROT_Y = 1, ROT_Z = 2 };
+enum Variant : int32_t { VAR_FWD = 0, VAR_INV = 1, VAR_DER = 2 };
+// KET: U on the ket (or pure) qubit; BRA: conj(U) on the bra qubit q+n;
+// SUPER: the 4x4 U (x) conj(U) on (q, q+n) of the vectorised density matrix (Eq. channel2).
+enum Domain : int32_t { DOM_KET = 0, DOM_BRA = 1, DOM_SUPER = 2 };
+
+// A matrix record whose entries depend on theta[param].
+struct DynRec {
+    int32_t rec, param, rot, variant, domain, pad;
+};
+
+// 2x2 rotation exp(-i t P / 2) for P = X, Y, Z (Sec. II.B: Rx, Ry with the unitary sign,
+// Rz), its inverse R(-t) and its derivative dR/dt; row-major (re, im).
+inline __host__ __device__ void rot2(int rot, int variant, double t, double *m)
+{
+    double s, c;
+#ifdef __CUDA_ARCH__
+    sincos(0.5 * t, &s, &c);
+#else
+    s = sin(0.5 * t);
+    c = cos(0.5 * t);
+#endif
+    for (int i = 0; i < 8; i++) m[i] = 0.0;
+    if (variant == VAR_INV) s = -s;  // R(-t) = R(t)^dag
+    if (variant == VAR_DER) {
+        if (rot == ROT_X) {        // [[-s/2, -i c/2], [-i c/2, -s/2]]
+            m[0] = -0.5 * s; m[3] = -0.5 * c; m[5] = -0.5 * c; m[6] = -0.5 * s;
+        } else if (rot == ROT_Y) { // [[-s/2, -c/2], [c/2, -s/2]]
+            m[0] = -0.5 * s; m[2] = -0.5 * c; m[4] = 0.5 * c; m[6] = -0.5 * s;
+        } else {                   // diag(-s/2 - i c/2, -s/2 + i c/2)
+            m[0] = -0.5 * s; m[1] = -0.5 * c; m[6] = -0.5 * s; m[7] = 0.5 * c;
+        }
+        return;
+    }
+    if (rot == ROT_X) {            // [[c, -i s], [-i s, c]]
+        m[0] = c; m[3] = -s; m[5] = -s; m[6] = c;
+    } else if (rot == ROT_Y) {     // [[c, -s], [s, c]]
+        m[0] = c; m[2] = -s; m[4] = s; m[6] = c;
+    } else {                       // diag(c - i s, c + i s)
+        m[0] = c; m[1] = -s; m[6] = c; m[7] = s;
+    }
+}
+
+// S[(a + 2b), (c + 2d)] = A[a][c] * conj(B[b][d]) (4x4 from two 2x2, row-major re/im).
+inline __host__ __device__ void kron_conj(const double *A, const double *B, double *S, bool add)
+{
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+            for (int c = 0; c < 2; c++)
+                for (int d = 0; d < 2; d++) {
+                    double ar = A[2 * (2 * a + c)], ai = A[2 * (2 * a + c) + 1];
+                    double br = B[2 * (2 * b + d)], bi = -B[2 * (2 * b + d) + 1];
+                    int o = 2 * ((a + 2 * b) * 4 + (c + 2 * d));
+                    double re = ar * br - ai * bi, im = ar * bi + ai * br;
+                    if (add) { S[o] += re; S[o + 1] += im; }
+                    else { S[o] = re; S[o + 1] = im; }
+                }
+}
+
+// Fill a record for a theta-dependent matrix.
+inline __host__ __device__ void materialize(const DynRec &r, double t, MatRec *out)
+{
+    double m[32];
+    for (int i = 0; i < 32; i++) m[i] = 0.0;
+    if (r.domain == DOM_SUPER) {
+        double U[8], dU[8];
+        if (r.variant == VAR_DER) {
+            rot2(r.rot, VAR_FWD, t, U);
+            rot2(r.rot, VAR_DER, t, dU);
+            kron_conj(dU, U, m, false);
+            kron_conj(U, dU, m, true);
+        } else {
+            rot2(r.rot, r.variant, t, U);
+            kron_conj(U, U, m, false);
+        }
+    } else {
+        rot2(r.rot, r.variant, t, m);
+        if (r.domain == DOM_BRA)
+            for (int i = 1; i < 8; i += 2) m[i] = -m[i];
+    }
+    for (int i = 0; i < 32; i++) {
+        out->d[i] = m[i];
+        out->f[i] = (float)m[i];
+    }
+}
+
+// ------------------------------------------------------------------ fused tile plan
+
+// Gate of a fused pass.  Non-diagonal gates name register slots (0..NR-1) of their
+// sub-run.  Diagonal gates and Z generators name a position code c: c < NR is a
+// register slot, NR <= c is local tile position c - NR (not held in registers), and
+// c < 0 is the tile-index bit of physical qubit -1 - c (constant over the tile).
+enum FType : int32_t {
+    FT_DENSE1 = 0, FT_REAL1 = 1, FT_ANTI1 = 2, FT_DIAG1 = 3,
+    FT_DENSE2 = 4, FT_DIAG2 = 5, FT_PERM2 = 6, FT_CTRL2 = 7
+};
+// Generator of a variational gate for the fused reverse sweep: the gradient term is
+// coef * Im <Psi| P |Phi> with both states taken right after the gate.
+enum GenType : int32_t { GEN_NONE = 0, GEN_X = 1, GEN_Y = 2, GEN_Z = 3 };
+
+struct FGate {
+    int32_t type;      // FType
+    int32_t a, b;      // register slots (non-diagonal) or position codes (diagonal)
+    int32_t rec;       // matrix record: forward U; reverse: the matrix applied to Phi
+    int32_t rec2;      // reverse only: the matrix applied to Psi (S^dag for channels)
+    int32_t gen;       // GenType
+    int32_t gpos;      // generator qubit: register slot (X, Y) or position code (Z)
+    int32_t slot;      // gradient slot, -1 if none
+    float coef;        // gradient weight
+    int32_t perm;      // FT_PERM2: source column of output row r in bits 2r, 2r+1
+    int32_t pad[2];
+};
+
+struct SubRun {
+    int8_t R[8];       // local positions held in registers (NR of them)
+    int32_t g_begin, g_end;
+};
+
+struct PassDesc {
+    int32_t t;               // tile qubits
+    int32_t n;               // physical qubits of the state
+    int32_t sub_begin, n_sub;
+    int32_t slot_begin, n_slots;  // gradient slots touched by this pass (reverse sweep)
+    int8_t S[16];            // local position -> physical qubit (ascending)
+    int8_t NS[64];           // tile-index bit -> physical qubit (ascending)
+    int32_t low;             // S[0..low-1] = 0..low-1 (contiguous in memory)
+    int32_t pad;
+};
+
+}  // namespace gbvqc

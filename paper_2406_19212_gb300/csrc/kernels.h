@@ -1,0 +1,84 @@
+// Host-side launchers of the CUDA kernels (implemented in kernels_*.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace gbvqc {
+
+// Pauli sum on the device, terms grouped by X mask: for group g with mask x_g,
+// c_g(b) = sum_{k in g} coeff_k i^{ph_k} (-1)^{popcount(b & z_k)}, and
+// (H psi)_a = sum_g c_g(a ^ x_g) psi_{a ^ x_g}.
+struct ObsTerm {
+    double coeff;
+    uint64_t z;
+    int32_t ph;   // number of Y factors mod 4
+    int32_t pad;
+};
+struct ObsGroup {
+    uint64_t x;
+    int32_t t_begin, t_end;
+};
+struct ObsDev {
+    const ObsGroup *groups;
+    const ObsTerm *terms;
+    int n_groups;
+};
+
+// Scratch of a grid reduction: one double per block plus an arrival counter that the
+// last block resets to zero.
+struct RedScratch {
+    double *partials;   // kMaxRedBlocks doubles
+    unsigned *counter;  // one counter, zero between launches
+};
+constexpr int kMaxRedBlocks = 1024;
+
+// ---- per-gate kernels (kernels_plain.cu)
+cudaError_t launch_gate(int dtype, void *psi, int n, int shape, int q0, int q1,
+                        const MatRec *rec, cudaStream_t s);
+cudaError_t launch_zero_state(int dtype, void *psi, int n, cudaStream_t s);
+cudaError_t launch_materialize(const DynRec *dyn, int n_dyn, const double *theta,
+                               MatRec *recs, cudaStream_t s);
+cudaError_t launch_accumulate(const double *slot_grad, const int *csr_ptr, const int *csr_slots,
+                              int n_params, double *grad, cudaStream_t s);
+
+// ---- reductions (kernels_reduce.cu)
+// out[0] = scale * Re sum conj(psi) (D phi), D a 2x2 (k=1) or 4x4 (k=2) on (q0, q1).
+cudaError_t launch_dot_matrix(int dtype, const void *psi, const void *phi, int n, int k,
+                              int q0, int q1, const MatRec *rec, double scale,
+                              RedScratch red, double *out, cudaStream_t s);
+// Pure state: out[0] = Re <psi|H|psi>; if lam != nullptr also writes lam = H psi.
+cudaError_t launch_pauli_expect(int dtype, const void *psi, void *lam, int n, ObsDev obs,
+                                RedScratch red, double *out, cudaStream_t s);
+// Physical layout of a density matrix of n logical qubits: ket bit q of rho_ab sits at
+// physical bit ket[q], bra bit q at bra[q] (standard layout: ket[q] = q, bra[q] = q + n).
+struct DensMap {
+    int8_t ket[32];
+    int8_t bra[32];
+};
+// out[0] = Re tr(H rho).
+cudaError_t launch_density_expect(int dtype, const void *rho, int n, DensMap map, ObsDev obs,
+                                  RedScratch red, double *out, cudaStream_t s);
+// Density adjoint seed psi = vec(H) (psi_ab = H_ab) in the layout `map`; the whole
+// vector is written (zeros off the Pauli support).
+cudaError_t launch_density_seed(int dtype, void *psi, int n, DensMap map, ObsDev obs,
+                                cudaStream_t s);
+
+// ---- fused tile passes (kernels_fused.cu)
+int fused_nr(int dtype, bool reverse);           // register qubits per sub-run
+cudaError_t fused_prepare();                     // shared-memory opt-in, outside capture
+size_t fused_smem_bytes(int dtype, int t, bool reverse, int max_slots);
+cudaError_t launch_fused_forward(int dtype, void *psi, const PassDesc *pass_dev,
+                                 const PassDesc &pass_host, const SubRun *subs,
+                                 const FGate *gates, const MatRec *recs, cudaStream_t s);
+cudaError_t launch_fused_reverse(int dtype, void *phi, void *psi, const PassDesc *pass_dev,
+                                 const PassDesc &pass_host, const SubRun *subs,
+                                 const FGate *gates, const MatRec *recs,
+                                 double *slot_partials, int n_tiles_stride, cudaStream_t s);
+// slot_grad[s] = sum_tile slot_partials[s * stride + tile], tiles in index order.
+cudaError_t launch_reduce_slots(const double *slot_partials, int n_slots, int n_tiles,
+                                int stride, double *slot_grad, cudaStream_t s);
+
+}  // namespace gbvqc

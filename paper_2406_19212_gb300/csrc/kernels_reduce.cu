@@ -1,0 +1,318 @@
+// Reductions over 2^n amplitudes: Pauli-sum expectation (Sec. II.E) fused with the
+// adjoint seed lambda = H psi (Algorithm 2 initialisation), the per-gate gradient term
+// 2 Re <Psi|dQ|Phi> of Algorithm 2, and the density-matrix trace tr(H rho) / vec(H)
+// seed of Sec. III.E.  Complex64 states accumulate in FP32 over runs of 16 terms and
+// in FP64 above that; warp shuffles and a last-block-done pass make every sum a
+// deterministic FP64 tree.
+#include "kernels.h"
+
+namespace gbvqc {
+
+template <typename R> struct CTr;
+template <> struct CTr<float> { typedef float2 T; };
+template <> struct CTr<double> { typedef double2 T; };
+
+template <typename R> __device__ __forceinline__ const R *mat_r(const MatRec *r);
+template <> __device__ __forceinline__ const float *mat_r<float>(const MatRec *r) { return r->f; }
+template <> __device__ __forceinline__ const double *mat_r<double>(const MatRec *r) { return r->d; }
+
+// Per-thread accumulator: FP64 directly, or FP32 runs of 16 folded into FP64.
+template <typename R> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct Acc<float> {
+    double s = 0.0;
+    float run = 0.f;
+    int k = 0;
+    __device__ __forceinline__ void add(float v)
+    {
+        run += v;
+        if (++k == 16) { s += (double)run; run = 0.f; k = 0; }
+    }
+    __device__ __forceinline__ double get() const { return s + (double)run; }
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block (result valid in thread 0); blockDim.x a multiple of 32, <= 1024.
+__device__ double block_sum(double v)
+{
+    __shared__ double sh[32];
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = l < nw ? sh[l] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+// Each block writes its partial; the last block to arrive sums them in index order.
+__device__ void grid_finish(double v, RedScratch red, double *out, double scale)
+{
+    __shared__ bool last;
+    double b = block_sum(v);
+    if (threadIdx.x == 0) {
+        red.partials[blockIdx.x] = b;
+        __threadfence();
+        unsigned prev = atomicAdd(red.counter, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(&red.partials[i]);
+    s = block_sum(s);
+    if (threadIdx.x == 0) {
+        *out = s * scale;
+        *red.counter = 0u;
+    }
+}
+
+static inline int red_grid(int64_t items, int threads)
+{
+    int64_t b = (items + threads - 1) / threads;
+    if (b > 152 * 4) b = 152 * 4;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+__device__ __forceinline__ int64_t insert0(int64_t g, int q)
+{
+    return ((g >> q) << (q + 1)) | (g & ((int64_t(1) << q) - 1));
+}
+
+// ---------------------------------------------------------------- 2 Re <Psi|D|Phi>
+
+template <typename R, int K>
+__global__ void __launch_bounds__(256) k_dot_matrix(const typename CTr<R>::T *__restrict__ psi,
+                                                    const typename CTr<R>::T *__restrict__ phi,
+                                                    int64_t ngroups, int q0, int q1,
+                                                    const MatRec *__restrict__ rec, double scale,
+                                                    RedScratch red, double *out)
+{
+    typedef typename CTr<R>::T T;
+    constexpr int D = 1 << K;
+    R m[2 * D * D];
+    const R *src = mat_r<R>(rec);
+#pragma unroll
+    for (int i = 0; i < 2 * D * D; i++) m[i] = src[i];
+    const int lo = q0 < q1 ? q0 : q1, hi = q0 < q1 ? q1 : q0;
+    Acc<R> acc;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+        int64_t idx[D];
+        if (K == 1) {
+            idx[0] = insert0(g, q0);
+            idx[1] = idx[0] | (int64_t(1) << q0);
+        } else {
+            int64_t base = insert0(insert0(g, lo), hi);
+            idx[0] = base;
+            idx[1] = base | (int64_t(1) << q0);
+            idx[2] = base | (int64_t(1) << q1);
+            idx[3] = idx[1] | (int64_t(1) << q1);
+        }
+        T f[D];
+#pragma unroll
+        for (int l = 0; l < D; l++) f[l] = phi[idx[l]];
+        R part = 0;
+#pragma unroll
+        for (int r = 0; r < D; r++) {
+            R wr = 0, wi = 0;
+#pragma unroll
+            for (int c = 0; c < D; c++) {
+                R mr = m[2 * (r * D + c)], mi = m[2 * (r * D + c) + 1];
+                wr += mr * f[c].x - mi * f[c].y;
+                wi += mr * f[c].y + mi * f[c].x;
+            }
+            T p = psi[idx[r]];
+            part += p.x * wr + p.y * wi;   // Re(conj(p) * w)
+        }
+        acc.add(part);
+    }
+    grid_finish(acc.get(), red, out, scale);
+}
+
+cudaError_t launch_dot_matrix(int dtype, const void *psi, const void *phi, int n, int k, int q0,
+                              int q1, const MatRec *rec, double scale, RedScratch red, double *out,
+                              cudaStream_t s)
+{
+    int64_t ng = int64_t(1) << (n - k);
+    int gr = red_grid(ng, 256);
+    if (dtype == 0) {
+        if (k == 1)
+            k_dot_matrix<float, 1><<<gr, 256, 0, s>>>((const float2 *)psi, (const float2 *)phi, ng,
+                                                      q0, q1, rec, scale, red, out);
+        else
+            k_dot_matrix<float, 2><<<gr, 256, 0, s>>>((const float2 *)psi, (const float2 *)phi, ng,
+                                                      q0, q1, rec, scale, red, out);
+    } else {
+        if (k == 1)
+            k_dot_matrix<double, 1><<<gr, 256, 0, s>>>((const double2 *)psi, (const double2 *)phi,
+                                                       ng, q0, q1, rec, scale, red, out);
+        else
+            k_dot_matrix<double, 2><<<gr, 256, 0, s>>>((const double2 *)psi, (const double2 *)phi,
+                                                       ng, q0, q1, rec, scale, red, out);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- Pauli sums
+
+// c_g(b) = sum_{k in g} coeff_k i^{ph_k} (-1)^{popcount(b & z_k)}
+template <typename R>
+__device__ __forceinline__ void group_coeff(const ObsTerm *__restrict__ terms, int t0, int t1,
+                                            uint64_t b, R &cr, R &ci)
+{
+    cr = 0;
+    ci = 0;
+    for (int k = t0; k < t1; k++) {
+        ObsTerm t = terms[k];
+        R c = (R)t.coeff;
+        if (__popcll(b & t.z) & 1) c = -c;
+        switch (t.ph & 3) {
+        case 0: cr += c; break;
+        case 1: ci += c; break;
+        case 2: cr -= c; break;
+        default: ci -= c; break;
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_pauli_expect(const typename CTr<R>::T *__restrict__ psi,
+                                                      typename CTr<R>::T *__restrict__ lam,
+                                                      int64_t len, ObsDev obs, RedScratch red,
+                                                      double *out)
+{
+    typedef typename CTr<R>::T T;
+    Acc<R> acc;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < len; a += stride) {
+        T pa = psi[a];
+        R lr = 0, li = 0;
+        for (int g = 0; g < obs.n_groups; g++) {
+            ObsGroup gr = obs.groups[g];
+            uint64_t b = (uint64_t)a ^ gr.x;
+            T pb = gr.x ? psi[b] : pa;
+            R cr, ci;
+            group_coeff<R>(obs.terms, gr.t_begin, gr.t_end, b, cr, ci);
+            lr += cr * pb.x - ci * pb.y;
+            li += cr * pb.y + ci * pb.x;
+        }
+        if (lam) {
+            T l;
+            l.x = lr;
+            l.y = li;
+            lam[a] = l;
+        }
+        acc.add(pa.x * lr + pa.y * li);
+    }
+    grid_finish(acc.get(), red, out, 1.0);
+}
+
+cudaError_t launch_pauli_expect(int dtype, const void *psi, void *lam, int n, ObsDev obs,
+                                RedScratch red, double *out, cudaStream_t s)
+{
+    int64_t len = int64_t(1) << n;
+    int gr = red_grid(len, 256);
+    if (dtype == 0)
+        k_pauli_expect<float><<<gr, 256, 0, s>>>((const float2 *)psi, (float2 *)lam, len, obs, red, out);
+    else
+        k_pauli_expect<double><<<gr, 256, 0, s>>>((const double2 *)psi, (double2 *)lam, len, obs, red,
+                                                  out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ density path
+
+__device__ __forceinline__ uint64_t deposit(uint64_t v, const int8_t *pos, int n)
+{
+    uint64_t r = 0;
+    for (int q = 0; q < n; q++)
+        if ((v >> q) & 1) r |= uint64_t(1) << pos[q];
+    return r;
+}
+
+// tr(P rho) = sum_a ph(a) rho_{a, a ^ x}: E = Re sum_a sum_g c_g(a) rho[a, a ^ x_g].
+template <typename R>
+__global__ void __launch_bounds__(256) k_density_expect(const typename CTr<R>::T *__restrict__ rho,
+                                                        int n, DensMap map, ObsDev obs,
+                                                        RedScratch red, double *out)
+{
+    typedef typename CTr<R>::T T;
+    const int64_t dim = int64_t(1) << n;
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < dim; a += stride) {
+        uint64_t ka = deposit((uint64_t)a, map.ket, n);
+        for (int g = 0; g < obs.n_groups; g++) {
+            ObsGroup gr = obs.groups[g];
+            uint64_t b = (uint64_t)a ^ gr.x;
+            T v = rho[ka | deposit(b, map.bra, n)];
+            R cr, ci;
+            group_coeff<R>(obs.terms, gr.t_begin, gr.t_end, (uint64_t)a, cr, ci);
+            acc += (double)(cr * v.x - ci * v.y);
+        }
+    }
+    grid_finish(acc, red, out, 1.0);
+}
+
+cudaError_t launch_density_expect(int dtype, const void *rho, int n, DensMap map, ObsDev obs,
+                                  RedScratch red, double *out, cudaStream_t s)
+{
+    int gr = red_grid(int64_t(1) << n, 256);
+    if (dtype == 0)
+        k_density_expect<float><<<gr, 256, 0, s>>>((const float2 *)rho, n, map, obs, red, out);
+    else
+        k_density_expect<double><<<gr, 256, 0, s>>>((const double2 *)rho, n, map, obs, red, out);
+    return cudaGetLastError();
+}
+
+// psi_ab = H_ab = sum_k coeff_k ph_k(b) [a == b ^ x_k]
+template <typename R>
+__global__ void k_density_seed(typename CTr<R>::T *__restrict__ psi, int n, DensMap map, ObsDev obs)
+{
+    typedef typename CTr<R>::T T;
+    const int64_t dim = int64_t(1) << n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < dim; b += stride) {
+        uint64_t kb = deposit((uint64_t)b, map.bra, n);
+        for (int g = 0; g < obs.n_groups; g++) {
+            ObsGroup gr = obs.groups[g];
+            uint64_t a = (uint64_t)b ^ gr.x;
+            R cr, ci;
+            group_coeff<R>(obs.terms, gr.t_begin, gr.t_end, (uint64_t)b, cr, ci);
+            T v;
+            v.x = cr;
+            v.y = ci;
+            psi[deposit(a, map.ket, n) | kb] = v;
+        }
+    }
+}
+
+cudaError_t launch_density_seed(int dtype, void *psi, int n, DensMap map, ObsDev obs, cudaStream_t s)
+{
+    size_t bytes = (size_t(1) << (2 * n)) * (dtype == 0 ? 8 : 16);
+    cudaError_t e = cudaMemsetAsync(psi, 0, bytes, s);
+    if (e != cudaSuccess) return e;
+    int gr = red_grid(int64_t(1) << n, 256);
+    if (dtype == 0) k_density_seed<float><<<gr, 256, 0, s>>>((float2 *)psi, n, map, obs);
+    else k_density_seed<double><<<gr, 256, 0, s>>>((double2 *)psi, n, map, obs);
+    return cudaGetLastError();
+}
+
+}  // namespace gbvqc

@@ -1,0 +1,100 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and loads, it
+exports every entry point include/gbvqc.h declares, and argument validation returns
+the documented status codes before any CUDA call is made."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2406_19212_gb300 as gb
+from paper_2406_19212_gb300 import _abi
+from paper_2406_19212_gb300 import build as gbuild
+from paper_2406_19212_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gbuild.build()
+    return gb.load()
+
+
+def declared_functions():
+    names = set()
+    for fname in os.listdir(os.path.join(ROOT, "include")):
+        if not fname.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fname)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, re.M):
+            if m.group(1) not in ("if", "for", "while", "sizeof"):
+                names.add(m.group(1))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = declared_functions()
+    assert {"sv_alloc", "apply_circuit", "apply_channel", "expect", "grad"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert set(_abi.exported_symbols()) <= declared
+
+
+def test_version(lib):
+    assert lib.gbvqc_version() >= 100
+
+
+def expect_status(status, fn, *args):
+    with pytest.raises(gb.GbvqcError) as ei:
+        fn(*args)
+    assert ei.value.status == status, str(ei.value)
+
+
+def test_circuit_validation(lib):
+    ARG, NOT_DENSITY = 1, 5
+    expect_status(ARG, gb.circuit_create, I.Circuit(2, [I.Op("RX", (2,), param=0)], 1))
+    expect_status(ARG, gb.circuit_create, I.Circuit(2, [I.Op("RX", (0,), param=3)], 1))
+    expect_status(ARG, gb.circuit_create, I.Circuit(2, [I.Op("CNOT", (1, 1))], 0))
+    expect_status(ARG, gb.circuit_create, I.Circuit(2, [I.Op("CZ", (0, 1), param=0)], 1))
+    expect_status(ARG, gb.circuit_create, I.Circuit(0, [], 0))
+    expect_status(ARG, gb.circuit_create, I.Circuit(18, [], 0, True))
+    expect_status(NOT_DENSITY, gb.circuit_create, I.Circuit(2, [I.Op("DEPOL", (0,), fixed=(0.1,))], 0))
+    expect_status(ARG, gb.circuit_create, I.Circuit(2, [I.Op("DEPOL", (0,), fixed=(1.5,))], 0, True))
+    expect_status(ARG, gb.circuit_create, I.Circuit(2, [I.Op("KRAUS", (0,), data=[])], 0, True))
+    # a channel whose superoperator has no inverse cannot be uncomputed (Algorithm 2)
+    expect_status(ARG, gb.circuit_create, I.Circuit(2, [I.Op("AMPDAMP", (0,), fixed=(1.0,))], 0, True))
+
+
+def test_observable_and_state_validation(lib):
+    ARG = 1
+    expect_status(ARG, gb.obs_create, [(1.0, ((3, "X"),))], 3)
+    expect_status(ARG, gb.obs_create, [(1.0, ())], 0)
+    expect_status(ARG, gb.sv_alloc, 4, 5)
+    expect_status(ARG, gb.sv_alloc, 0, gb.C64)
+    expect_status(ARG, gb.sv_alloc, 18, gb.C64, True)
+
+
+def test_null_handles(lib):
+    L = lib
+    out = ctypes.c_double()
+    assert L.expect(None, None, ctypes.byref(out)) == 1
+    assert L.apply_circuit(None, None, None, 0, 0, 0) == 1
+    assert L.grad(None, None, 0, None, 0, 0, 0, None, None, None) == 1
+    assert b"NULL" in L.gbvqc_last_error()
+    assert L.sv_free(None) == 0 and L.circuit_free(None) == 0 and L.obs_free(None) == 0
+
+
+def test_pauli_marshalling():
+    arr = _abi.pauli_array([(0.5, ((0, "X"), (2, "Y"), (3, "Z")))])
+    assert arr[0].x_mask == 0b0101 and arr[0].z_mask == 0b1100 and arr[0].coeff == 0.5
+
+
+def test_op_marshalling():
+    u = I.random_unitary(2, np.random.default_rng(0))
+    arr = _abi.ops_array([I.Op("DENSE2", (3, 1), data=u), I.Op("FSIM", (0, 2), fixed=(0.1, 0.2))])
+    assert arr[0].kind == _abi.KIND["DENSE2"] and list(arr[0].qubits) == [3, 1]
+    assert arr[0].data[2 * 6] == u.reshape(-1)[6].real and arr[0].data[2 * 6 + 1] == u.reshape(-1)[6].imag
+    assert arr[1].params[0] == 0.1 and arr[1].params[1] == 0.2 and arr[1].param_index == -1

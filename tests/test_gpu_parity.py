@@ -1,0 +1,276 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 CPU oracle.
+
+Tolerances: complex128 amplitudes 1e-12; complex64 fidelity >= 1 - 1e-6 and
+amplitudes 2e-5; energies 1e-5 relative (complex64) / 1e-10 (complex128); gradients
+1e-4 * max|g| (complex64) / 1e-10 * max(1, max|g|) (complex128).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_2406_19212_gb300 as gb
+from oracle import oracle as O
+from paper_2406_19212_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+AMP_TOL = {gb.C64: 2e-5, gb.C128: 1e-12}
+MODES = [gb.PLAIN, gb.FUSED]
+DTYPES = [gb.C64, gb.C128]
+
+
+def fidelity(a, b):
+    return abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
+
+
+def run_apply(circuit, theta, dtype, mode, start=None, tiling=None):
+    c = gb.circuit_create(circuit)
+    if tiling:
+        c.set_tiling(*tiling)
+    sv = gb.sv_alloc(circuit.n_qubits, dtype, circuit.density)
+    if start is not None:
+        gb.sv_set(sv, start)
+    gb.apply_circuit(sv, c, theta, mode)
+    return gb.sv_get(sv).astype(np.complex128)
+
+
+def check_amps(got, ref, dtype):
+    np.testing.assert_allclose(got, ref, atol=AMP_TOL[dtype], rtol=0)
+    if dtype == gb.C64:
+        assert fidelity(got, ref) >= 1 - 1e-6
+
+
+def check_grad(g, ref, dtype):
+    scale = max(1.0, float(np.abs(ref).max())) if ref.size else 1.0
+    tol = 1e-4 * max(float(np.abs(ref).max()), 1e-12) if dtype == gb.C64 else 1e-10 * scale
+    np.testing.assert_allclose(g, ref, atol=tol, rtol=0)
+
+
+def check_energy(e, ref, dtype):
+    if dtype == gb.C64:
+        assert abs(e - ref) <= 1e-5 * max(1.0, abs(ref))
+    else:
+        assert abs(e - ref) <= 1e-10 * max(1.0, abs(ref))
+
+
+# ----------------------------------------------------------------- state evolution
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,ops,seed", [(1, 20, 0), (2, 30, 1), (5, 60, 2), (6, 80, 3),
+                                        (9, 120, 4), (13, 200, 5), (15, 150, 6)])
+def test_apply_matches_oracle(n, ops, seed, dtype, mode):
+    w = I.random_circuit(n, ops, seed)
+    ref = O.apply_circuit(w.circuit, w.theta)
+    check_amps(run_apply(w.circuit, w.theta, dtype, mode), ref, dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_apply_from_custom_state(dtype):
+    w = I.random_circuit(11, 150, 7)
+    start = I.random_state(11, 8)
+    ref = O.apply_circuit(w.circuit, w.theta, start)
+    for mode in MODES:
+        check_amps(run_apply(w.circuit, w.theta, dtype, mode, start=start), ref, dtype)
+
+
+@pytest.mark.parametrize("tiling", [(6, 1), (7, 2), (8, 3), (10, 4), (12, 6), (13, 4), (13, 1)])
+def test_fused_tilings(tiling):
+    w = I.random_circuit(14, 250, 9)
+    ref = O.apply_circuit(w.circuit, w.theta)
+    for dtype in DTYPES:
+        t = tiling if not (dtype == gb.C128 and tiling[0] > 12) else (12, tiling[1])
+        check_amps(run_apply(w.circuit, w.theta, dtype, gb.FUSED, tiling=t), ref, dtype)
+
+
+def test_ghz_and_qft_closed_forms():
+    n = 16
+    ops = [I.Op("H", (0,))] + [I.Op("CNOT", (i, i + 1)) for i in range(n - 1)]
+    ref = np.zeros(1 << n, dtype=complex)
+    ref[0] = ref[-1] = 1 / math.sqrt(2)
+    for dtype in DTYPES:
+        for mode in MODES:
+            check_amps(run_apply(I.Circuit(n, ops, 0), [], dtype, mode), ref, dtype)
+    from tests.test_oracle import qft_ops
+    n, x = 12, 1234
+    psi0 = np.zeros(1 << n, dtype=complex)
+    psi0[x] = 1
+    y = np.arange(1 << n)
+    ref = np.exp(2j * np.pi * x * y / 2 ** n) / 2 ** (n / 2)
+    for dtype in DTYPES:
+        for mode in MODES:
+            check_amps(run_apply(I.Circuit(n, qft_ops(n), 0), [], dtype, mode, start=psi0), ref, dtype)
+
+
+def test_empty_circuit_and_reset():
+    for dtype in DTYPES:
+        for mode in MODES:
+            got = run_apply(I.Circuit(7, [], 0), [], dtype, mode)
+            assert got[0] == 1 and np.count_nonzero(got) == 1
+
+
+# ------------------------------------------------------------------- expectation
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,seed", [(1, 0), (4, 1), (10, 2), (16, 3)])
+def test_expect_matches_oracle(n, seed, dtype):
+    psi = I.random_state(n, seed)
+    terms = I.random_circuit(n, 1, seed).observable
+    if n > 1:
+        terms = terms + I.heisenberg_1d(n, 0.7, -1.3) + [(0.25, tuple((q, "Y") for q in range(n)))]
+    sv = gb.sv_alloc(n, dtype)
+    gb.sv_set(sv, psi)
+    e = gb.expect(sv, gb.obs_create(terms, n))
+    check_energy(e, O.expect(terms, psi, n), dtype)
+
+
+# --------------------------------------------------------------------- gradients
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,ops,seed,share", [(2, 30, 11, False), (6, 80, 12, True),
+                                              (9, 150, 13, False), (13, 160, 14, True)])
+def test_grad_matches_oracle(n, ops, seed, share, dtype, mode):
+    w = I.random_circuit(n, ops, seed, param_share=share)
+    e_ref, g_ref = O.adjoint_grad(w.circuit, w.theta, w.observable)
+    c = gb.circuit_create(w.circuit)
+    e, g = gb.grad(c, w.theta, gb.obs_create(w.observable, n), dtype, mode)
+    check_energy(e, e_ref, dtype)
+    check_grad(g, g_ref, dtype)
+    # second call replays the captured graph with new angles
+    th2 = w.theta + 0.37
+    e_ref2, g_ref2 = O.adjoint_grad(w.circuit, th2, w.observable)
+    e2, g2 = gb.grad(c, th2, gb.obs_create(w.observable, n), dtype, mode)
+    check_energy(e2, e_ref2, dtype)
+    check_grad(g2, g_ref2, dtype)
+
+
+def test_plain10_config_and_finite_differences():
+    w = I.plain_10q()
+    e_ref, g_ref = O.adjoint_grad(w.circuit, w.theta, w.observable)
+    c = gb.circuit_create(w.circuit)
+    obs = gb.obs_create(w.observable, 10)
+    for dtype in DTYPES:
+        for mode in MODES:
+            e, g = gb.grad(c, w.theta, obs, dtype, mode)
+            check_energy(e, e_ref, dtype)
+            check_grad(g, g_ref, dtype)
+    # central differences of the GPU complex128 energy, h = 1e-5
+    e, g = gb.grad(c, w.theta, obs, gb.C128, gb.PLAIN)
+    for j in (0, 41, 119):
+        tp, tm = w.theta.copy(), w.theta.copy()
+        tp[j] += 1e-5
+        tm[j] -= 1e-5
+        fd = (gb.grad(c, tp, obs, gb.C128, gb.PLAIN)[0] - gb.grad(c, tm, obs, gb.C128, gb.PLAIN)[0]) / 2e-5
+        assert abs(fd - g[j]) < 1e-8
+
+
+def test_grad_device_pointers_and_autograd():
+    import torch
+    w = I.plain_10q(seed=5)
+    e_ref, g_ref = O.adjoint_grad(w.circuit, w.theta, w.observable)
+    c = gb.circuit_create(w.circuit)
+    obs = gb.obs_create(w.observable, 10)
+    th = torch.tensor(w.theta, device="cuda", dtype=torch.float64)
+    e, g = gb.grad(c, th, obs, gb.C64, gb.FUSED)
+    torch.cuda.synchronize()
+    check_energy(float(e.item()), e_ref, gb.C64)
+    check_grad(g.cpu().numpy(), g_ref, gb.C64)
+    th.requires_grad_(True)
+    loss = gb.VQEEnergy.apply(th, c, obs, gb.C128, gb.FUSED)
+    loss.backward()
+    check_energy(float(loss.item()), e_ref, gb.C128)
+    check_grad(th.grad.cpu().numpy(), g_ref, gb.C128)
+
+
+def test_zero_parameter_grad():
+    w = I.random_circuit(8, 40, 21)
+    ops = [o for o in w.circuit.ops if o.param < 0]
+    circ = I.Circuit(8, ops, 0)
+    c = gb.circuit_create(circ)
+    for dtype in DTYPES:
+        e, g = gb.grad(c, np.zeros(0), gb.obs_create(w.observable, 8), dtype, gb.FUSED)
+        check_energy(e, O.energy(circ, [], w.observable), dtype)
+        assert g.size == 0
+
+
+# ------------------------------------------------------------------------ density
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,ops,seed", [(1, 10, 0), (3, 40, 1), (4, 60, 2), (6, 80, 3)])
+def test_density_apply_matches_oracle(n, ops, seed, dtype, mode):
+    w = I.random_circuit(n, ops, seed, density=True, with_channels=True)
+    start = I.random_density(n, seed + 50)
+    ref = O.rho_apply_circuit(w.circuit, w.theta, start)
+    check_amps(run_apply(w.circuit, w.theta, dtype, mode, start=start), ref, dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_apply_channel_matches_oracle(dtype):
+    n = 5
+    rho = I.random_density(n, 3)
+    rng = np.random.default_rng(4)
+    sv = gb.sv_alloc(n, dtype, True)
+    gb.sv_set(sv, rho)
+    ops = []
+    for name, q, p in (("DEPOL", 0, 0.2), ("AMPDAMP", 4, 0.3), ("PHASEDAMP", 2, 0.5)):
+        gb.apply_channel(sv, name, q, p)
+        ops.append(I.Op(name, (q,), fixed=(p,)))
+    ks = I.random_kraus(rng, 3)
+    gb.apply_channel(sv, "KRAUS", 3, kraus=ks)
+    ops.append(I.Op("KRAUS", (3,), data=ks))
+    ref = O.rho_apply_circuit(I.Circuit(n, ops, 0, True), [], rho)
+    check_amps(gb.sv_get(sv).astype(np.complex128), ref, dtype)
+    with pytest.raises(gb.GbvqcError):
+        gb.apply_channel(gb.sv_alloc(3, dtype), "DEPOL", 0, 0.1)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,ops,seed", [(2, 30, 31), (3, 50, 32), (5, 70, 33)])
+def test_noisy_grad_matches_oracle(n, ops, seed, dtype, mode):
+    w = I.random_circuit(n, ops, seed, density=True, with_channels=True, param_share=True)
+    e_ref, g_ref = O.noisy_adjoint_grad(w.circuit, w.theta, w.observable)
+    c = gb.circuit_create(w.circuit)
+    e, g = gb.grad(c, w.theta, gb.obs_create(w.observable, n), dtype, mode)
+    check_energy(e, e_ref, dtype)
+    check_grad(g, g_ref, dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_noisy_hea_small_matches_oracle(dtype):
+    w = I.noisy_hea(6, 3, 9)
+    e_ref, g_ref = O.noisy_adjoint_grad(w.circuit, w.theta, w.observable)
+    c = gb.circuit_create(w.circuit)
+    obs = gb.obs_create(w.observable, 6)
+    for mode in MODES:
+        e, g = gb.grad(c, w.theta, obs, dtype, mode)
+        check_energy(e, e_ref, dtype)
+        check_grad(g, g_ref, dtype)
+
+
+def test_density_trace_and_expect():
+    w = I.noisy_hea(5, 2, 3)
+    ref = O.rho_apply_circuit(w.circuit, w.theta)
+    for dtype in DTYPES:
+        sv = gb.sv_alloc(5, dtype, True)
+        gb.apply_circuit(sv, gb.circuit_create(w.circuit), w.theta, gb.FUSED)
+        tr = gb.expect(sv, gb.obs_create([(1.0, ())], 5))
+        assert abs(tr - 1.0) < (1e-6 if dtype == gb.C64 else 1e-13)
+        check_energy(gb.expect(sv, gb.obs_create(w.observable, 5)),
+                     O.rho_expect(w.observable, ref, 5), dtype)
+
+
+# ------------------------------------------------------------------------- errors
+
+def test_argument_errors():
+    w = I.random_circuit(4, 10, 1)
+    c = gb.circuit_create(w.circuit)
+    with pytest.raises(gb.GbvqcError):
+        gb.apply_circuit(gb.sv_alloc(5, gb.C64), c, w.theta)
+    with pytest.raises(gb.GbvqcError):
+        gb.grad(c, np.zeros(w.circuit.n_params + 1), gb.obs_create(w.observable, 4))
+    with pytest.raises(gb.GbvqcError):
+        gb.grad(c, w.theta, gb.obs_create(w.observable + [(1.0, ((5, "Z"),))], 6))
