@@ -153,15 +153,17 @@ def _theta_args(theta, n: int):
         t = theta.detach().to(torch.float64).contiguous()
         return t, t.data_ptr(), _abi.PTR_DEVICE
     t = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1))
-    if t.size != n:
-        raise ValueError(f"expected {n} parameters, got {t.size}")
     return t, (t.ctypes.data if t.size else None), _abi.PTR_HOST
+
+
+def _len(t) -> int:
+    return int(t.numel()) if hasattr(t, "numel") else int(t.size)
 
 
 def apply_circuit(sv: StateVector, circ: CircuitHandle, theta=(), mode: int = FUSED) -> None:
     """In-place psi <- C(theta) psi on the state's stream (apply!)."""
-    keep, ptr, loc = _theta_args(theta if circ.n_params else np.zeros(0), circ.n_params)
-    _abi.check(_abi.lib().apply_circuit(sv.handle, circ.handle, ptr, circ.n_params, loc, mode))
+    keep, ptr, loc = _theta_args(theta, circ.n_params)
+    _abi.check(_abi.lib().apply_circuit(sv.handle, circ.handle, ptr, _len(keep), loc, mode))
     del keep
 
 
@@ -229,14 +231,14 @@ def grad(circ: CircuitHandle, theta, obs: Observable, dtype: int = C64, mode: in
         else:
             e, g = out
         s = _stream_ptr(stream if stream is not None else torch.cuda.current_stream(theta.device))
-        _abi.check(_abi.lib().grad(circ.handle, ptr, circ.n_params, obs.handle, dtype, mode, loc,
+        _abi.check(_abi.lib().grad(circ.handle, ptr, _len(keep), obs.handle, dtype, mode, loc,
                                    s, e.data_ptr(), g.data_ptr() if circ.n_params else None))
         del keep
         return e, g
     keep, ptr, loc = _theta_args(theta, circ.n_params)
     e = ctypes.c_double()
     g = np.zeros(max(1, circ.n_params))
-    _abi.check(_abi.lib().grad(circ.handle, ptr, circ.n_params, obs.handle, dtype, mode, loc,
+    _abi.check(_abi.lib().grad(circ.handle, ptr, _len(keep), obs.handle, dtype, mode, loc,
                                _stream_ptr(stream), ctypes.byref(e), g.ctypes.data))
     del keep
     return e.value, g[:circ.n_params]
@@ -249,7 +251,7 @@ def grad_profile(circ: CircuitHandle, theta, obs: Observable, dtype: int = C64,
     keep, ptr, loc = _theta_args(theta, circ.n_params)
     stats = (_abi.KernelStat * 64)()
     n = ctypes.c_int()
-    _abi.check(_abi.lib().grad_profile(circ.handle, ptr, circ.n_params, obs.handle, dtype, mode,
+    _abi.check(_abi.lib().grad_profile(circ.handle, ptr, _len(keep), obs.handle, dtype, mode,
                                        _stream_ptr(stream), stats, 64, ctypes.byref(n)))
     del keep
     return {stats[i].name.decode(): (stats[i].launches, stats[i].ms, stats[i].alg_flops,
