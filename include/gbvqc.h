@@ -142,6 +142,13 @@ gbvqc_status circuit_set_tiling(circuit_handle c, int tile_qubits, int low_qubit
 /* Report the fused schedule: number of tile passes and of gate records it holds. */
 gbvqc_status circuit_plan_info(circuit_handle c, int *n_passes, int *n_gates, int *tile_qubits);
 
+/* Host-only statistics of the fused schedule for dtype (the reverse layout of grad if
+ * for_grad = 1); needs no GPU.  stats[0..9] = tile qubits, passes, forward sub-runs,
+ * forward gate records, forward phase blocks, reverse sub-runs, gradient slots,
+ * largest per-pass shared memory in bytes (forward, reverse), gates in the circuit's
+ * physical gate list.  Fills min(n_stats, 10) entries. */
+gbvqc_status circuit_plan_stats(circuit_handle c, int dtype, int for_grad, int64_t *stats, int n_stats);
+
 /* ------------------------------------------------------------ execution (Sec. II.D) */
 
 /* psi <- C(theta) psi in place (apply!, Eq. circuitevolve; Eq. channel for density

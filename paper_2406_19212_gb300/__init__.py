@@ -126,6 +126,15 @@ class CircuitHandle:
                                                 ctypes.byref(c)))
         return a.value, b.value, c.value
 
+    STAT_NAMES = ("tile_qubits", "passes", "fwd_subruns", "fwd_gates", "fwd_phase_blocks",
+                  "rev_subruns", "grad_slots", "fwd_smem_max", "rev_smem_max", "phys_gates")
+
+    def plan_stats(self, dtype: int = C64, for_grad: bool = False) -> dict:
+        """Host-only statistics of the fused schedule (no GPU needed)."""
+        arr = (ctypes.c_int64 * 10)()
+        _abi.check(_abi.lib().circuit_plan_stats(self.handle, dtype, int(for_grad), arr, 10))
+        return dict(zip(self.STAT_NAMES, list(arr)))
+
     def free(self):
         if self.handle:
             _abi.lib().circuit_free(self.handle)

@@ -363,12 +363,16 @@ struct Workspace {
     unsigned *d_counter = nullptr;
 };
 
-struct DevPlan {  // device copies of a FusedPlan
+struct DevPlan {  // a FusedPlan and its device copies (uploaded on first launch)
     FusedPlan p;
-    std::vector<double> fwd_flops_per_amp, rev_flops_per_amp;  // algorithmic flops / amplitude
+    bool uploaded = false;
+    int elem = 4;
+    std::vector<size_t> fwd_smem, rev_smem;
     PassDesc *d_fwd = nullptr, *d_rev = nullptr;
     SubRun *d_fsubs = nullptr, *d_rsubs = nullptr;
     FGate *d_fgates = nullptr, *d_rgates = nullptr;
+    DEnt *d_fents = nullptr, *d_rents = nullptr;
+    MatUnit *d_funits = nullptr, *d_runits = nullptr;
     int *d_csr_ptr = nullptr, *d_csr_slots = nullptr;
 };
 
@@ -394,6 +398,8 @@ struct gbvqc_circuit {
     const void *graph_obs = nullptr;                 // observable the graphs were captured with
     int n_param_ops = 0;                             // ops driven by a parameter
     size_t partials_cap = 0;                         // doubles in ws.d_slot_partials
+    bool dev_ready = false;                          // records, CSR and stream on the device
+    std::vector<int> plain_slot_param;
     std::mutex mu;
 };
 
@@ -731,7 +737,8 @@ static void free_plan(DevPlan *p)
 {
     if (!p) return;
     cudaFree(p->d_fwd); cudaFree(p->d_rev); cudaFree(p->d_fsubs); cudaFree(p->d_rsubs);
-    cudaFree(p->d_fgates); cudaFree(p->d_rgates); cudaFree(p->d_csr_ptr); cudaFree(p->d_csr_slots);
+    cudaFree(p->d_fgates); cudaFree(p->d_rgates); cudaFree(p->d_fents); cudaFree(p->d_rents);
+    cudaFree(p->d_funits); cudaFree(p->d_runits); cudaFree(p->d_csr_ptr); cudaFree(p->d_csr_slots);
 }
 
 static void free_graphs(gbvqc_circuit *c)
@@ -920,7 +927,7 @@ extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qub
             }
         }
     }
-    std::vector<int> slot_param;
+    std::vector<int> slot_param;  // parameter of each per-gate gradient slot
     for (PlainGate &g : c->plain)
         if (g.param >= 0 && g.rec_d >= 0) {
             g.slot = (int)slot_param.size();
@@ -931,26 +938,29 @@ extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qub
     c->map_grad = interleaved_map(n_qubits);
     fused_gates_of(c, c->map_std, c->pg_std);
     if (c->density) fused_gates_of(c, c->map_grad, c->pg_grad);
-    gbvqc_status st = csr_upload(slot_param, n_params, &c->d_plain_ptr, &c->d_plain_slots);
-    if (st == GBVQC_OK) st = upload(&c->d_recs, c->recs);
-    if (st == GBVQC_OK) st = upload(&c->d_dyn, c->dyn);
-    if (st == GBVQC_OK) {
-        cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
-        if (e != cudaSuccess) st = fail(GBVQC_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
-    }
-    if (st != GBVQC_OK) {
-        circuit_free(c);
-        return st;
-    }
+    c->plain_slot_param = slot_param;
     *out = c;
+    return GBVQC_OK;
+}
+
+// Device copies of the circuit's matrix records, dynamic-record list and per-gate CSR,
+// and the capture stream: made on the first call that launches work.
+static gbvqc_status ensure_device(gbvqc_circuit *c)
+{
+    if (c->dev_ready) return GBVQC_OK;
+    ST_TRY(csr_upload(c->plain_slot_param, c->n_params, &c->d_plain_ptr, &c->d_plain_slots));
+    ST_TRY(upload(&c->d_recs, c->recs));
+    ST_TRY(upload(&c->d_dyn, c->dyn));
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    c->dev_ready = true;
     return GBVQC_OK;
 }
 
 static int default_tile(int dtype) { return 12; }
 static int default_low(int dtype) { return dtype == GBVQC_C64 ? 4 : 3; }
 
-// Fused plan for (dtype, layout); built on first use.
-static gbvqc_status get_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out)
+// Fused plan for (dtype, layout); built on first use (host only).
+static gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out)
 {
     int key = dtype * 2 + (grad_layout && c->density ? 1 : 0);
     auto it = c->plans.find(key);
@@ -959,46 +969,53 @@ static gbvqc_status get_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevP
         return GBVQC_OK;
     }
     const std::vector<PGate> &pg = (grad_layout && c->density) ? c->pg_grad : c->pg_std;
-    int t = c->tile_qubits ? c->tile_qubits : default_tile(dtype);
-    int low = c->low_qubits ? c->low_qubits : default_low(dtype);
+    PlanOptions opt;
+    opt.t = c->tile_qubits ? c->tile_qubits : default_tile(dtype);
+    opt.low = c->low_qubits ? c->low_qubits : default_low(dtype);
+    opt.nr_f = fused_nr(dtype, false);
+    opt.nr_r = fused_nr(dtype, true);
     // at most 256 threads per CTA: 2^(t - NR) <= 256 for both the forward and reverse kernels
-    const int t_max = std::min(fused_nr(dtype, false), fused_nr(dtype, true)) + 8;
-    if (t > t_max) t = t_max;
+    opt.t = std::min(opt.t, std::min(opt.nr_f, opt.nr_r) + 8);
+    opt.elem_bytes = dtype == GBVQC_C64 ? 4 : 8;
+    opt.max_slots = 128;
+    opt.gate_smem = 24 * 1024;
     std::unique_ptr<DevPlan> dp(new DevPlan());
+    dp->elem = opt.elem_bytes;
     std::string err;
-    CUDA_TRY(fused_prepare());
-    if (!build_fused_plan(pg, c->n_phys, t, low, fused_nr(dtype, false), fused_nr(dtype, true), 256, dp->p, err))
+    if (!build_fused_plan(pg, c->n_phys, opt, dp->p, err))
         return fail(GBVQC_ERR_UNSUPPORTED, "fused plan: %s", err.c_str());
-    for (const PassDesc &d : dp->p.fwd) {
-        double f = 0;
-        for (int i = 0; i < d.n_sub; i++) {
-            const SubRun &r = dp->p.fsubs[d.sub_begin + i];
-            for (int g = r.g_begin; g < r.g_end; g++) f += ftype_flops(dp->p.fgates[g].type);
-        }
-        dp->fwd_flops_per_amp.push_back(f);
-    }
-    for (const PassDesc &d : dp->p.rev) {
-        double f = 0;
-        for (int i = 0; i < d.n_sub; i++) {
-            const SubRun &r = dp->p.rsubs[d.sub_begin + i];
-            for (int g = r.g_begin; g < r.g_end; g++) {
-                const FGate &fg = dp->p.rgates[g];
-                f += 2 * ftype_flops(fg.type);
-                if (fg.gen == GEN_Z) f += 3;
-                else if (fg.gen != GEN_NONE) f += 4;
-            }
-        }
-        dp->rev_flops_per_amp.push_back(f);
-    }
-    ST_TRY(upload(&dp->d_fwd, dp->p.fwd));
-    ST_TRY(upload(&dp->d_rev, dp->p.rev));
-    ST_TRY(upload(&dp->d_fsubs, dp->p.fsubs));
-    ST_TRY(upload(&dp->d_rsubs, dp->p.rsubs));
-    ST_TRY(upload(&dp->d_fgates, dp->p.fgates));
-    ST_TRY(upload(&dp->d_rgates, dp->p.rgates));
-    ST_TRY(csr_upload(dp->p.slot_param, c->n_params, &dp->d_csr_ptr, &dp->d_csr_slots));
+    for (const PassDesc &d : dp->p.fwd) dp->fwd_smem.push_back(pass_smem_bytes(dp->p, d, false, opt.elem_bytes));
+    for (const PassDesc &d : dp->p.rev) dp->rev_smem.push_back(pass_smem_bytes(dp->p, d, true, opt.elem_bytes));
+    for (size_t b : dp->fwd_smem)
+        if (b > 200 * 1024) return fail(GBVQC_ERR_UNSUPPORTED, "fused pass needs %zu bytes of shared memory", b);
+    for (size_t b : dp->rev_smem)
+        if (b > 200 * 1024) return fail(GBVQC_ERR_UNSUPPORTED, "fused pass needs %zu bytes of shared memory", b);
     *out = dp.get();
     c->plans[key] = std::move(dp);
+    return GBVQC_OK;
+}
+
+// Fused plan with its device copies.
+static gbvqc_status get_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out)
+{
+    DevPlan *dp = nullptr;
+    ST_TRY(get_host_plan(c, dtype, grad_layout, &dp));
+    if (!dp->uploaded) {
+        CUDA_TRY(fused_prepare());
+        ST_TRY(upload(&dp->d_fwd, dp->p.fwd));
+        ST_TRY(upload(&dp->d_rev, dp->p.rev));
+        ST_TRY(upload(&dp->d_fsubs, dp->p.fsubs));
+        ST_TRY(upload(&dp->d_rsubs, dp->p.rsubs));
+        ST_TRY(upload(&dp->d_fgates, dp->p.fgates));
+        ST_TRY(upload(&dp->d_rgates, dp->p.rgates));
+        ST_TRY(upload(&dp->d_fents, dp->p.fents));
+        ST_TRY(upload(&dp->d_rents, dp->p.rents));
+        ST_TRY(upload(&dp->d_funits, dp->p.funits));
+        ST_TRY(upload(&dp->d_runits, dp->p.runits));
+        ST_TRY(csr_upload(dp->p.slot_param, c->n_params, &dp->d_csr_ptr, &dp->d_csr_slots));
+        dp->uploaded = true;
+    }
+    *out = dp;
     return GBVQC_OK;
 }
 
@@ -1030,10 +1047,29 @@ extern "C" gbvqc_status circuit_plan_info(circuit_handle c, int *n_passes, int *
     std::lock_guard<std::mutex> lk(c->mu);
     DevPlan *p = nullptr;
     if (!fused_supported(c, GBVQC_C64)) return fail(GBVQC_ERR_UNSUPPORTED, "too few qubits for tiles");
-    ST_TRY(get_plan(c, GBVQC_C64, c->density != 0, &p));
+    ST_TRY(get_host_plan(c, GBVQC_C64, c->density != 0, &p));
     if (n_passes) *n_passes = (int)p->p.fwd.size();
-    if (n_gates) *n_gates = (int)p->p.fgates.size();
+    if (n_gates) *n_gates = (int)p->p.fgates.size();  // forward gate records (phase blocks count once)
     if (tile_qubits) *tile_qubits = p->p.t;
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status circuit_plan_stats(circuit_handle c, int dtype, int for_grad, int64_t *stats, int n_stats)
+{
+    if (!c || !stats || n_stats < 0) return fail(GBVQC_ERR_ARG, "NULL argument");
+    if (dtype != GBVQC_C64 && dtype != GBVQC_C128) return fail(GBVQC_ERR_ARG, "dtype %d", dtype);
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!fused_supported(c, dtype)) return fail(GBVQC_ERR_UNSUPPORTED, "too few qubits for tiles");
+    DevPlan *p = nullptr;
+    ST_TRY(get_host_plan(c, dtype, for_grad != 0, &p));
+    int64_t blocks = 0;
+    for (const FGate &g : p->p.fgates) blocks += g.type == FT_DIAGB;
+    int64_t v[10] = {p->p.t, (int64_t)p->p.fwd.size(), (int64_t)p->p.fsubs.size(), (int64_t)p->p.fgates.size(),
+                     blocks, (int64_t)p->p.rsubs.size(), p->p.n_slots,
+                     (int64_t)*std::max_element(p->fwd_smem.begin(), p->fwd_smem.end()),
+                     (int64_t)*std::max_element(p->rev_smem.begin(), p->rev_smem.end()),
+                     (int64_t)((for_grad && c->density) ? c->pg_grad.size() : c->pg_std.size())};
+    for (int i = 0; i < n_stats && i < 10; i++) stats[i] = v[i];
     return GBVQC_OK;
 }
 
@@ -1075,9 +1111,10 @@ static gbvqc_status run_plain_forward(gbvqc_circuit *c, int dtype, void *psi, cu
 static gbvqc_status run_fused_forward(gbvqc_circuit *c, DevPlan *p, int dtype, void *psi, cudaStream_t s)
 {
     const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
+    const FusedDev fd{p->d_fwd, p->d_fsubs, p->d_fgates, p->d_fents, p->d_funits, c->d_recs};
     for (size_t i = 0; i < p->p.fwd.size(); i++)
-        ST_TRY(run_k("fused_forward", p->fwd_flops_per_amp[i] * amps, 2 * sb, s, [&] {
-            return launch_fused_forward(dtype, psi, p->d_fwd + i, p->p.fwd[i], p->d_fsubs, p->d_fgates, c->d_recs, s);
+        ST_TRY(run_k("fused_forward", p->p.fwd_flops[i] * amps, 2 * sb, s, [&] {
+            return launch_fused_forward(dtype, psi, fd, (int)i, p->p.fwd[i], p->fwd_smem[i], s);
         }));
     return GBVQC_OK;
 }
@@ -1092,6 +1129,7 @@ extern "C" gbvqc_status apply_circuit(sv_handle sv, circuit_handle c, const doub
     if (mode != GBVQC_MODE_PLAIN && mode != GBVQC_MODE_FUSED) return fail(GBVQC_ERR_ARG, "mode %d", mode);
     std::lock_guard<std::mutex> lk(c->mu);
     cudaStream_t s = sv->stream;
+    ST_TRY(ensure_device(c));
     ST_TRY(stage_theta(c, theta, n_theta, theta_loc, s));
     CUDA_TRY(launch_materialize(c->d_dyn, (int)c->dyn.size(), c->ws.d_theta, c->d_recs, s));
     if (mode == GBVQC_MODE_FUSED && fused_supported(c, sv->dtype)) {
@@ -1157,10 +1195,11 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
     }
     if (fused) {
         const int tiles = 1 << (c->n_phys - p->p.t);
+        const FusedDev fd{p->d_rev, p->d_rsubs, p->d_rgates, p->d_rents, p->d_runits, c->d_recs};
         for (int i = (int)p->p.rev.size() - 1; i >= 0; i--)
-            ST_TRY(run_k("fused_reverse", p->rev_flops_per_amp[i] * amps, 4 * sb, s, [&] {
-                return launch_fused_reverse(dtype, w.phi, w.psi, p->d_rev + i, p->p.rev[i], p->d_rsubs, p->d_rgates,
-                                            c->d_recs, w.d_slot_partials, tiles, s);
+            ST_TRY(run_k("fused_reverse", p->p.rev_flops[i] * amps, 4 * sb, s, [&] {
+                return launch_fused_reverse(dtype, w.phi, w.psi, fd, i, p->p.rev[i], p->rev_smem[i],
+                                            w.d_slot_partials, tiles, s);
             }));
         ST_TRY(run_k("reduce_slots", 0, 0, s, [&] {
             return launch_reduce_slots(w.d_slot_partials, p->p.n_slots, tiles, tiles, w.d_slot_grad, s);
@@ -1198,6 +1237,7 @@ extern "C" gbvqc_status grad(circuit_handle c, const double *theta, int n_theta,
     if (h->n_qubits != c->n_log) return fail(GBVQC_ERR_ARG, "observable has %d qubits, circuit %d", h->n_qubits, c->n_log);
     std::lock_guard<std::mutex> lk(c->mu);
     cudaStream_t s = (cudaStream_t)stream;
+    ST_TRY(ensure_device(c));
     DevPlan *p = nullptr;
     if (mode == GBVQC_MODE_FUSED && fused_supported(c, dtype)) ST_TRY(get_plan(c, dtype, true, &p));
     else mode = GBVQC_MODE_PLAIN;

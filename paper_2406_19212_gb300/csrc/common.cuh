@@ -125,35 +125,57 @@ inline __host__ __device__ void materialize(const DynRec &r, double t, MatRec *o
 // c < 0 is the tile-index bit of physical qubit -1 - c (constant over the tile).
 enum FType : int32_t {
     FT_DENSE1 = 0, FT_REAL1 = 1, FT_ANTI1 = 2, FT_DIAG1 = 3,
-    FT_DENSE2 = 4, FT_DIAG2 = 5, FT_PERM2 = 6, FT_CTRL2 = 7
+    FT_DENSE2 = 4, FT_DIAG2 = 5, FT_PERM2 = 6, FT_CTRL2 = 7,
+    FT_DIAGB = 8   // a run of commuting diagonal gates (DEnt list) fused into one phase table
 };
 // Generator of a variational gate for the fused reverse sweep: the gradient term is
 // coef * Im <Psi| P |Phi> with both states taken right after the gate.
 enum GenType : int32_t { GEN_NONE = 0, GEN_X = 1, GEN_Y = 2, GEN_Z = 3 };
 
-struct FGate {
-    int32_t type;      // FType
-    int32_t a, b;      // register slots (non-diagonal) or position codes (diagonal)
-    int32_t rec;       // matrix record: forward U; reverse: the matrix applied to Phi
-    int32_t rec2;      // reverse only: the matrix applied to Psi (S^dag for channels)
-    int32_t gen;       // GenType
-    int32_t gpos;      // generator qubit: register slot (X, Y) or position code (Z)
-    int32_t slot;      // gradient slot, -1 if none
-    float coef;        // gradient weight
-    int32_t perm;      // FT_PERM2: source column of output row r in bits 2r, 2r+1
-    int32_t pad[2];
+// Matrices of a pass are staged in shared memory in units of 8 elements (a 2x2 matrix is
+// one unit, a 4x4 matrix four); unit u copies elements 8*part .. 8*part+7 of record rec.
+struct MatUnit {
+    int32_t rec, part;
+};
+
+struct FGate {               // 32 bytes, staged in shared memory
+    int8_t type;             // FType
+    int8_t a, b;             // register slots (non-diagonal) or position codes (FT_DIAG1/2)
+    int8_t gen;              // GEN_X / GEN_Y generator of a variational non-diagonal gate
+    int8_t gpos;             // its register slot
+    int8_t flags;            // FT_DIAGB: bit 0 = Psi uses separate phases (non-unitary block)
+    int8_t nz;               // FT_DIAGB: number of Z-generator entries (listed first)
+    int8_t pad0;
+    int16_t mat, mat2;       // pass-local matrix units: Phi (forward: U) / Psi (reverse)
+    int16_t ent, n_ent;      // FT_DIAGB: first pass-local DEnt and count (incl. Z entries)
+    int32_t slot;            // gradient slot of the X/Y generator, -1 if none
+    float coef;              // gradient weight
+    int32_t perm;            // FT_PERM2: source column of output row r in bits 2r, 2r+1
+    int32_t pad1;
+};
+
+struct DEnt {                // 16 bytes: one diagonal gate or Z generator of an FT_DIAGB
+    int8_t k;                // 1 or 2 positions with phases; 3 = Z generator only
+    int8_t ca, cb;           // position codes
+    int8_t pad;
+    int16_t mat, mat2;       // pass-local matrix units of the Phi / Psi phases
+    int32_t slot;            // Z generator: gradient slot
+    float coef;              // Z generator: gradient weight
 };
 
 struct SubRun {
-    int8_t R[8];       // local positions held in registers (NR of them)
-    int32_t g_begin, g_end;
+    int8_t R[8];             // local positions held in registers (NR of them)
+    int32_t g_begin, g_end;  // pass-local gate range
 };
 
 struct PassDesc {
     int32_t t;               // tile qubits
     int32_t n;               // physical qubits of the state
     int32_t sub_begin, n_sub;
-    int32_t slot_begin, n_slots;  // gradient slots touched by this pass (reverse sweep)
+    int32_t slot_begin, n_slots;    // gradient slots touched by this pass (reverse sweep)
+    int32_t gate_begin, n_gates;    // FGate range (global array)
+    int32_t ent_begin, n_ent;       // DEnt range
+    int32_t unit_begin, n_units;    // MatUnit range
     int8_t S[16];            // local position -> physical qubit (ascending)
     int8_t NS[64];           // tile-index bit -> physical qubit (ascending)
     int32_t low;             // S[0..low-1] = 0..low-1 (contiguous in memory)

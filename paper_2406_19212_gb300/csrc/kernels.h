@@ -67,16 +67,22 @@ cudaError_t launch_density_seed(int dtype, void *psi, int n, DensMap map, ObsDev
                                 cudaStream_t s);
 
 // ---- fused tile passes (kernels_fused.cu)
+// Device arrays of one direction (forward or reverse) of a fused plan.
+struct FusedDev {
+    const PassDesc *passes;
+    const SubRun *subs;
+    const FGate *gates;
+    const DEnt *ents;
+    const MatUnit *units;
+    const MatRec *recs;
+};
 int fused_nr(int dtype, bool reverse);           // register qubits per sub-run
 cudaError_t fused_prepare();                     // shared-memory opt-in, outside capture
-size_t fused_smem_bytes(int dtype, int t, bool reverse, int max_slots);
-cudaError_t launch_fused_forward(int dtype, void *psi, const PassDesc *pass_dev,
-                                 const PassDesc &pass_host, const SubRun *subs,
-                                 const FGate *gates, const MatRec *recs, cudaStream_t s);
-cudaError_t launch_fused_reverse(int dtype, void *phi, void *psi, const PassDesc *pass_dev,
-                                 const PassDesc &pass_host, const SubRun *subs,
-                                 const FGate *gates, const MatRec *recs,
-                                 double *slot_partials, int n_tiles_stride, cudaStream_t s);
+cudaError_t launch_fused_forward(int dtype, void *psi, const FusedDev &fd, int pass,
+                                 const PassDesc &pass_host, size_t smem, cudaStream_t s);
+cudaError_t launch_fused_reverse(int dtype, void *phi, void *psi, const FusedDev &fd, int pass,
+                                 const PassDesc &pass_host, size_t smem, double *slot_partials,
+                                 int n_tiles_stride, cudaStream_t s);
 // slot_grad[s] = sum_tile slot_partials[s * stride + tile], tiles in index order.
 cudaError_t launch_reduce_slots(const double *slot_partials, int n_slots, int n_tiles,
                                 int stride, double *slot_grad, cudaStream_t s);

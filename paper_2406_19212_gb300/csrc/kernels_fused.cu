@@ -2,12 +2,15 @@
 //
 // A pass names a set S of t "tile" qubits (the lowest `low` qubits are always in S, so
 // every tile is made of contiguous 2^low-amplitude segments).  CTA i owns the 2^t
-// amplitudes whose non-tile bits spell i, stages them in shared memory, applies the
-// pass's gates and writes them back.  Inside the tile, gates run in "sub-runs": each
-// sub-run names NR tile positions that every thread gathers into registers (2^NR
-// amplitudes per thread), applies all of the sub-run's gates on them with no further
-// memory traffic, and scatters back.  Diagonal gates need no register position and
-// ride along in any sub-run, including diagonal gates on non-tile qubits.
+// amplitudes whose non-tile bits spell i, stages them in shared memory together with
+// the pass's gate records and matrices, applies the gates and writes the tile back.
+// Inside the tile, gates run in "sub-runs": each sub-run names NR tile positions that
+// every thread gathers into registers (2^NR amplitudes per thread), applies all of the
+// sub-run's gates on them with no further memory traffic, and scatters back.
+//
+// Diagonal gates need no register position: a run of them is applied as one phase per
+// amplitude, the product of a per-thread constant (bits outside the registers) and a
+// table over the register bits built by doubling (2^(NR+1) complex products).
 //
 // This is the GPU counterpart of the paper's gate fusion for compute density (Sec. III.B,
 // citing gate fusion) and of its aggregation of independent amplitude groups (Fig. 3):
@@ -18,9 +21,10 @@
 // in reverse order it accumulates the gradient term coef * Im <Psi|P|Phi> of the gate's
 // Pauli generator P (dQ/dtheta = -i/2 P Q for Q = exp(-i theta P/2), so
 // 2 Re <Psi|dQ|Phi_{j-1}> = Im <Psi|P|Phi_j>), then uncomputes Phi with Q^{-1} and Psi
-// with Q^dag.  Per-thread FP32 partials over 2^NR terms are reduced across the warp in
-// FP64 with shuffles and across warps in fixed order, giving one FP64 partial per
-// (gradient slot, tile).
+// with Q^dag.  In a diagonal run every Z generator is read from the states after the
+// whole run (diagonal matrices commute with Z).  Per-thread FP32 partials over 2^NR
+// terms are summed across the warp with FP32 shuffles and across warps in FP64 in fixed
+// order, giving one FP64 partial per (gradient slot, tile).
 #include "devmath.cuh"
 #include "kernels.h"
 
@@ -90,8 +94,7 @@ __device__ __forceinline__ void rg2(typename CT<R>::T *a, const R *m, int perm)
             for (int r = 0; r < 4; r++) {
                 const int c = (perm >> (2 * r)) & 3;
                 T x = c == 0 ? v[0] : c == 1 ? v[1] : c == 2 ? v[2] : v[3];
-                R mr = c == 0 ? m[8 * r] : c == 1 ? m[8 * r + 2] : c == 2 ? m[8 * r + 4] : m[8 * r + 6];
-                R mi = c == 0 ? m[8 * r + 1] : c == 1 ? m[8 * r + 3] : c == 2 ? m[8 * r + 5] : m[8 * r + 7];
+                R mr = m[8 * r + 2 * c], mi = m[8 * r + 2 * c + 1];
                 w[r] = cmul<T, R>(mr, mi, x);
             }
         }
@@ -119,13 +122,20 @@ __device__ __forceinline__ void rg2_dispatch(int k0, int k1, typename CT<R>::T *
 #undef GBVQC_RG2
 }
 
+// Bit of a non-register position code (constant over the thread's amplitudes).
+template <int NR>
+__device__ __forceinline__ int const_bit(int code, int base, int64_t tilebase)
+{
+    if (code < 0) return (int)((tilebase >> (-1 - code)) & 1);
+    return (base >> (code - NR)) & 1;
+}
+
 // Bit of a position code for register amplitude j (j compile-time after unrolling).
 template <int NR>
 __device__ __forceinline__ int code_bit(int code, int j, int base, int64_t tilebase)
 {
-    if (code < 0) return (int)((tilebase >> (-1 - code)) & 1);
-    if (code >= NR) return (base >> (code - NR)) & 1;
-    return (j >> code) & 1;
+    if (code >= 0 && code < NR) return (j >> code) & 1;
+    return const_bit<NR>(code, base, tilebase);
 }
 
 // Diagonal one-qubit gate on a position code.
@@ -138,7 +148,7 @@ __device__ __forceinline__ void dg1(typename CT<R>::T *a, const R *m, int code, 
         rg1_dispatch<R, NR, SH_DIAG1>(code, a, m);
         return;
     }
-    const int bit = code_bit<NR>(code, 0, base, tilebase);
+    const int bit = const_bit<NR>(code, base, tilebase);
     const R pr = bit ? m[6] : m[0], pi = bit ? m[7] : m[1];
 #pragma unroll
     for (int j = 0; j < (1 << NR); j++) a[j] = cmul<T, R>(pr, pi, a[j]);
@@ -162,18 +172,129 @@ __device__ __forceinline__ void dg2(typename CT<R>::T *a, const R *m, int ca, in
 }
 
 template <typename R, int NR>
-__device__ __forceinline__ void apply_fgate(const FGate &g, const R *m, typename CT<R>::T *a,
-                                            int base, int64_t tilebase)
+__device__ __forceinline__ void apply_fgate(int type, int ga, int gb, int perm, const R *m,
+                                            typename CT<R>::T *a, int base, int64_t tilebase)
 {
-    switch (g.type) {
-    case FT_DENSE1: rg1_dispatch<R, NR, SH_DENSE1>(g.a, a, m); break;
-    case FT_REAL1: rg1_dispatch<R, NR, SH_REAL1>(g.a, a, m); break;
-    case FT_ANTI1: rg1_dispatch<R, NR, SH_ANTI1>(g.a, a, m); break;
-    case FT_DIAG1: dg1<R, NR>(a, m, g.a, base, tilebase); break;
-    case FT_DENSE2: rg2_dispatch<R, NR, SH_DENSE2>(g.a, g.b, a, m, 0); break;
-    case FT_DIAG2: dg2<R, NR>(a, m, g.a, g.b, base, tilebase); break;
-    case FT_PERM2: rg2_dispatch<R, NR, SH_PERM2>(g.a, g.b, a, m, g.perm); break;
-    default: rg2_dispatch<R, NR, SH_CTRL2>(g.a, g.b, a, m, 0); break;
+    switch (type) {
+    case FT_DENSE1: rg1_dispatch<R, NR, SH_DENSE1>(ga, a, m); break;
+    case FT_REAL1: rg1_dispatch<R, NR, SH_REAL1>(ga, a, m); break;
+    case FT_ANTI1: rg1_dispatch<R, NR, SH_ANTI1>(ga, a, m); break;
+    case FT_DIAG1: dg1<R, NR>(a, m, ga, base, tilebase); break;
+    case FT_DENSE2: rg2_dispatch<R, NR, SH_DENSE2>(ga, gb, a, m, 0); break;
+    case FT_DIAG2: dg2<R, NR>(a, m, ga, gb, base, tilebase); break;
+    case FT_PERM2: rg2_dispatch<R, NR, SH_PERM2>(ga, gb, a, m, perm); break;
+    default: rg2_dispatch<R, NR, SH_CTRL2>(ga, gb, a, m, 0); break;
+    }
+}
+
+// ------------------------------------------------------------- diagonal phase blocks
+
+// Element r of the diagonal of a k-qubit matrix staged as 2x2 (one unit) or 4x4 (four).
+template <typename R>
+__device__ __forceinline__ void diag_elem(const R *m, int k, int r, R &re, R &im)
+{
+    const int o = k == 1 ? 6 * r : 10 * r;
+    re = m[o];
+    im = m[o + 1];
+}
+
+template <typename R>
+__device__ __forceinline__ void cmul_inplace(R &xr, R &xi, R yr, R yi)
+{
+    R t = xr * yr - xi * yi;
+    xi = xr * yi + xi * yr;
+    xr = t;
+}
+
+// Multiply one-qubit phases (e0, e1) on register bit k into the two half tables.
+template <typename R, int NR>
+__device__ __forceinline__ void table_mul(R *lr, R *li, R *hr, R *hi, int k, R e0r, R e0i, R e1r, R e1i)
+{
+    constexpr int H = NR / 2;
+    if (k < H) {
+#pragma unroll
+        for (int j = 0; j < (1 << H); j++) {
+            const bool one = (j >> k) & 1;
+            cmul_inplace<R>(lr[j], li[j], one ? e1r : e0r, one ? e1i : e0i);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < (1 << (NR - H)); j++) {
+            const bool one = (j >> (k - H)) & 1;
+            cmul_inplace<R>(hr[j], hi[j], one ? e1r : e0r, one ? e1i : e0i);
+        }
+    }
+}
+
+// Multiply the register amplitudes of a (and b, if given) by the product of the
+// entries' diagonals.  `second` selects the Psi phases (mat2) of the reverse sweep.
+// The phase of register amplitude j is c * TL[j & lo] * TH[j >> H]: c collects the
+// entries on bits that are constant for the thread, TL and TH the low / high halves of
+// the register bits.
+template <typename R, int NR>
+__device__ __forceinline__ void phase_table(const DEnt *ents, int n, const R *smat, bool second,
+                                            typename CT<R>::T *a, typename CT<R>::T *b, int base,
+                                            int64_t tilebase)
+{
+    typedef typename CT<R>::T T;
+    constexpr int H = NR / 2;
+    R cr = 1, ci = 0;
+    R lr[1 << H], li[1 << H], hr[1 << (NR - H)], hi[1 << (NR - H)];
+#pragma unroll
+    for (int j = 0; j < (1 << H); j++) { lr[j] = 1; li[j] = 0; }
+#pragma unroll
+    for (int j = 0; j < (1 << (NR - H)); j++) { hr[j] = 1; hi[j] = 0; }
+    for (int e = 0; e < n; e++) {
+        const DEnt d = ents[e];
+        if (d.k == 3) continue;
+        const R *m = smat + 8 * (second ? d.mat2 : d.mat);
+        const bool ra = d.ca >= 0 && d.ca < NR;
+        if (d.k == 1) {
+            R d0r, d0i, d1r, d1i;
+            diag_elem<R>(m, 1, 0, d0r, d0i);
+            diag_elem<R>(m, 1, 1, d1r, d1i);
+            if (ra) {
+                table_mul<R, NR>(lr, li, hr, hi, d.ca, d0r, d0i, d1r, d1i);
+            } else {
+                const int bit = const_bit<NR>(d.ca, base, tilebase);
+                cmul_inplace<R>(cr, ci, bit ? d1r : d0r, bit ? d1i : d0i);
+            }
+            continue;
+        }
+        const bool rb = d.cb >= 0 && d.cb < NR;
+        if (ra && rb) continue;  // applied to the amplitudes below
+        if (!ra && !rb) {
+            const int idx = const_bit<NR>(d.ca, base, tilebase) | (const_bit<NR>(d.cb, base, tilebase) << 1);
+            R er, ei;
+            diag_elem<R>(m, 2, idx, er, ei);
+            cmul_inplace<R>(cr, ci, er, ei);
+        } else {
+            // one register position: a one-qubit diagonal on it, chosen by the constant bit
+            const int kreg = ra ? d.ca : d.cb;
+            const int cbit = ra ? const_bit<NR>(d.cb, base, tilebase) : const_bit<NR>(d.ca, base, tilebase);
+            const int i0 = ra ? 2 * cbit : cbit, i1 = ra ? 1 + 2 * cbit : cbit + 2;
+            R e0r, e0i, e1r, e1i;
+            diag_elem<R>(m, 2, i0, e0r, e0i);
+            diag_elem<R>(m, 2, i1, e1r, e1i);
+            table_mul<R, NR>(lr, li, hr, hi, kreg, e0r, e0i, e1r, e1i);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < (1 << (NR - H)); j++) cmul_inplace<R>(hr[j], hi[j], cr, ci);
+#pragma unroll
+    for (int j = 0; j < (1 << NR); j++) {
+        const int jl = j & ((1 << H) - 1), jh = j >> H;
+        const R pr = lr[jl] * hr[jh] - li[jl] * hi[jh], pi = lr[jl] * hi[jh] + li[jl] * hr[jh];
+        a[j] = cmul<T, R>(pr, pi, a[j]);
+        if (b) b[j] = cmul<T, R>(pr, pi, b[j]);
+    }
+    // two-qubit entries with both positions in registers
+    for (int e = 0; e < n; e++) {
+        const DEnt d = ents[e];
+        if (d.k != 2 || !(d.ca >= 0 && d.ca < NR && d.cb >= 0 && d.cb < NR)) continue;
+        const R *m = smat + 8 * (second ? d.mat2 : d.mat);
+        dg2<R, NR>(a, m, d.ca, d.cb, base, tilebase);
+        if (b) dg2<R, NR>(b, m, d.ca, d.cb, base, tilebase);
     }
 }
 
@@ -211,18 +332,19 @@ __device__ __forceinline__ R gen_xy_dispatch(int k, const typename CT<R>::T *f, 
     return 0;
 }
 
-// Im <Psi| Z |Phi> with the Z bit given by a position code.
-template <typename R, int NR>
-__device__ __forceinline__ R gen_z(int code, const typename CT<R>::T *f, const typename CT<R>::T *p,
-                                   int base, int64_t tilebase)
+struct RedCtx {
+    double *sgrad;
+    int slot_begin, nwarps, warp, lane, lanes;
+    unsigned lanemask;
+};
+
+// Sum a per-thread partial over the warp (FP32 shuffles) and store it for its slot.
+__device__ __forceinline__ void emit_partial(const RedCtx &c, int slot, float v)
 {
-    R s = 0;
 #pragma unroll
-    for (int j = 0; j < (1 << NR); j++) {
-        const R v = p[j].x * f[j].y - p[j].y * f[j].x;
-        s += code_bit<NR>(code, j, base, tilebase) ? -v : v;
-    }
-    return s;
+    for (int o = 16; o > 0; o >>= 1)
+        if (o < c.lanes) v += __shfl_xor_sync(c.lanemask, v, o);
+    if (c.lane == 0) c.sgrad[(slot - c.slot_begin) * c.nwarps + c.warp] = (double)v;
 }
 
 // ----------------------------------------------------------------------- the kernel
@@ -231,6 +353,8 @@ struct FusedArgs {
     const PassDesc *pd;
     const SubRun *subs;
     const FGate *gates;
+    const DEnt *ents;
+    const MatUnit *units;
     const MatRec *recs;
     double *slot_partials;
     int tiles_stride;
@@ -242,7 +366,7 @@ __device__ __forceinline__ void tile_io(typename CT<R>::T *gmem, typename CT<R>:
 {
     typedef typename CT<R>::T T;
     const int L = 1 << t, lowmask = (1 << low) - 1;
-    if (sizeof(T) == 8) {  // complex64: two amplitudes per 16-byte access
+    if constexpr (sizeof(T) == 8) {  // complex64: two amplitudes per 16-byte access
         for (int v = threadIdx.x; v < (L >> 1); v += blockDim.x) {
             const int l = v << 1;
             const int64_t g = tilebase | hitab[l >> low] | (l & lowmask);
@@ -266,23 +390,37 @@ __device__ __forceinline__ void tile_io(typename CT<R>::T *gmem, typename CT<R>:
     }
 }
 
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Forward kernels run 2^(t-NR) <= 128 threads (three CTAs per SM), reverse kernels
+// <= 256 threads (two CTAs per SM).
 template <typename R, int NR, bool REV>
-__global__ void __launch_bounds__(256) k_fused(typename CT<R>::T *__restrict__ phi,
-                                               typename CT<R>::T *__restrict__ psi, FusedArgs args)
+__global__ void __launch_bounds__(REV ? 256 : 128, REV ? 2 : 3) k_fused(typename CT<R>::T *__restrict__ phi,
+                                                  typename CT<R>::T *__restrict__ psi, FusedArgs args)
 {
     typedef typename CT<R>::T T;
     extern __shared__ __align__(16) unsigned char smem[];
     const PassDesc &pd = *args.pd;
     const int t = pd.t, n = pd.n, low = pd.low;
     const int L = 1 << t;
-    T *sphi = reinterpret_cast<T *>(smem);
-    T *spsi = sphi + (REV ? L : 0);
-    int64_t *hitab = reinterpret_cast<int64_t *>(smem + (REV ? 2 : 1) * (size_t)L * sizeof(T));
     const int nhi = 1 << (t - low);
-    double *sgrad = reinterpret_cast<double *>(hitab + nhi);
     const int lanes = blockDim.x < 32 ? blockDim.x : 32;
     const int nwarps = (blockDim.x + 31) >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lanemask = lanes == 32 ? 0xffffffffu : ((1u << lanes) - 1u);
+
+    unsigned char *p = smem;
+    T *sphi = reinterpret_cast<T *>(p);
+    p += align16((size_t)(REV ? 2 : 1) * L * sizeof(T));
+    T *spsi = sphi + (REV ? L : 0);
+    int64_t *hitab = reinterpret_cast<int64_t *>(p);
+    p += align16(sizeof(int64_t) * nhi);
+    double *sgrad = reinterpret_cast<double *>(p);
+    if (REV) p += align16(sizeof(double) * (size_t)pd.n_slots * nwarps);
+    FGate *sgates = reinterpret_cast<FGate *>(p);
+    p += align16(sizeof(FGate) * (size_t)pd.n_gates);
+    DEnt *sents = reinterpret_cast<DEnt *>(p);
+    p += align16(sizeof(DEnt) * (size_t)pd.n_ent);
+    R *smat = reinterpret_cast<R *>(p);
 
     const int64_t tile = blockIdx.x;
     int64_t tilebase = 0;
@@ -294,6 +432,19 @@ __global__ void __launch_bounds__(256) k_fused(typename CT<R>::T *__restrict__ p
             if ((h >> i) & 1) o |= int64_t(1) << pd.S[low + i];
         hitab[h] = o;
     }
+    // stage the pass's gates, diagonal entries and matrices
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(args.gates + pd.gate_begin);
+        int4 *dst = reinterpret_cast<int4 *>(sgates);
+        for (int i = threadIdx.x; i < pd.n_gates * 2; i += blockDim.x) dst[i] = src[i];
+        const int4 *esrc = reinterpret_cast<const int4 *>(args.ents + pd.ent_begin);
+        int4 *edst = reinterpret_cast<int4 *>(sents);
+        for (int i = threadIdx.x; i < pd.n_ent; i += blockDim.x) edst[i] = esrc[i];
+        for (int i = threadIdx.x; i < pd.n_units * 8; i += blockDim.x) {
+            const MatUnit u = args.units[pd.unit_begin + (i >> 3)];
+            smat[i] = mat_of<R>(&args.recs[u.rec])[8 * u.part + (i & 7)];
+        }
+    }
     if (REV)
         for (int i = threadIdx.x; i < pd.n_slots * nwarps; i += blockDim.x) sgrad[i] = 0.0;
     __syncthreads();
@@ -301,6 +452,7 @@ __global__ void __launch_bounds__(256) k_fused(typename CT<R>::T *__restrict__ p
     if (REV) tile_io<R>(psi, spsi, t, low, tilebase, hitab, true);
     __syncthreads();
 
+    RedCtx rc{sgrad, pd.slot_begin, nwarps, warp, lane, lanes, lanemask};
     T a[1 << NR], b[REV ? (1 << NR) : 1];
     for (int s = 0; s < pd.n_sub; s++) {
         const SubRun sr = args.subs[pd.sub_begin + s];
@@ -309,9 +461,9 @@ __global__ void __launch_bounds__(256) k_fused(typename CT<R>::T *__restrict__ p
 #pragma unroll
         for (int k = 0; k < NR; k++) rmask |= 1 << sr.R[k];
         int base = 0;
-        for (int p = 0, i = 0; p < t; p++) {
-            if ((rmask >> p) & 1) continue;
-            if ((threadIdx.x >> i) & 1) base |= 1 << p;
+        for (int q = 0, i = 0; q < t; q++) {
+            if ((rmask >> q) & 1) continue;
+            if ((threadIdx.x >> i) & 1) base |= 1 << q;
             i++;
         }
         int off[NR];
@@ -327,22 +479,54 @@ __global__ void __launch_bounds__(256) k_fused(typename CT<R>::T *__restrict__ p
             if constexpr (REV) b[j] = spsi[swz<R>(l)];
         }
         for (int gi = sr.g_begin; gi < sr.g_end; gi++) {
-            const FGate g = args.gates[gi];
-            if constexpr (REV) {
-                if (g.gen != GEN_NONE) {
-                R part;
-                if (g.gen == GEN_Z) part = gen_z<R, NR>(g.gpos, a, b, base, tilebase);
-                else if (g.gen == GEN_X) part = gen_xy_dispatch<R, NR, GEN_X>(g.gpos, a, b);
-                else part = gen_xy_dispatch<R, NR, GEN_Y>(g.gpos, a, b);
-                double v = (double)part * (double)g.coef;
+            const FGate g = sgates[gi];
+            if (g.type == FT_DIAGB) {
+                const DEnt *ents = sents + g.ent;
+                if constexpr (REV) {
+                    if (g.nz > 0) {  // Z generators on the states after the block
+                        R tot = 0, dk[NR];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
-                    if (o < lanes) v += __shfl_xor_sync(lanemask, v, o);
-                if (lane == 0) sgrad[(g.slot - pd.slot_begin) * nwarps + warp] = v;
+                        for (int k = 0; k < NR; k++) dk[k] = 0;
+#pragma unroll
+                        for (int j = 0; j < (1 << NR); j++) {
+                            const R v = b[j].x * a[j].y - b[j].y * a[j].x;  // Im(conj(Psi) Phi)
+                            tot += v;
+#pragma unroll
+                            for (int k = 0; k < NR; k++) dk[k] += ((j >> k) & 1) ? -v : v;
+                        }
+                        for (int e = 0; e < g.nz; e++) {
+                            const DEnt d = ents[e];
+                            R part;
+                            if (d.ca >= 0 && d.ca < NR) {
+                                part = dk[0];
+#pragma unroll
+                                for (int k = 1; k < NR; k++)
+                                    if (k == d.ca) part = dk[k];
+                            } else {
+                                part = const_bit<NR>(d.ca, base, tilebase) ? -tot : tot;
+                            }
+                            emit_partial(rc, d.slot, (float)part * d.coef);
+                        }
+                    }
+                    if (g.flags & 1) {
+                        phase_table<R, NR>(ents + g.nz, g.n_ent - g.nz, smat, false, a, nullptr, base, tilebase);
+                        phase_table<R, NR>(ents + g.nz, g.n_ent - g.nz, smat, true, b, nullptr, base, tilebase);
+                    } else {
+                        phase_table<R, NR>(ents + g.nz, g.n_ent - g.nz, smat, false, a, b, base, tilebase);
+                    }
+                } else {
+                    phase_table<R, NR>(ents, g.n_ent, smat, false, a, nullptr, base, tilebase);
                 }
+                continue;
             }
-            apply_fgate<R, NR>(g, mat_of<R>(&args.recs[g.rec]), a, base, tilebase);
-            if constexpr (REV) apply_fgate<R, NR>(g, mat_of<R>(&args.recs[g.rec2]), b, base, tilebase);
+            if constexpr (REV) {
+                if (g.gen == GEN_X)
+                    emit_partial(rc, g.slot, (float)gen_xy_dispatch<R, NR, GEN_X>(g.gpos, a, b) * g.coef);
+                else if (g.gen == GEN_Y)
+                    emit_partial(rc, g.slot, (float)gen_xy_dispatch<R, NR, GEN_Y>(g.gpos, a, b) * g.coef);
+            }
+            apply_fgate<R, NR>(g.type, g.a, g.b, g.perm, smat + 8 * g.mat, a, base, tilebase);
+            if constexpr (REV) apply_fgate<R, NR>(g.type, g.a, g.b, g.perm, smat + 8 * g.mat2, b, base, tilebase);
         }
 #pragma unroll
         for (int j = 0; j < (1 << NR); j++) {
@@ -374,32 +558,6 @@ int fused_nr(int dtype, bool reverse)
     return reverse ? 3 : 4;
 }
 
-size_t fused_smem_bytes(int dtype, int t, bool reverse, int max_slots)
-{
-    const int nr = fused_nr(dtype, reverse);
-    const size_t amp = dtype == 0 ? 8 : 16;
-    const int threads = 1 << (t - nr);
-    const int nwarps = (threads + 31) / 32;
-    size_t b = (reverse ? 2 : 1) * (size_t(1) << t) * amp;
-    b += sizeof(int64_t) * (size_t(1) << t);  // upper bound of the hi table
-    if (reverse) b += sizeof(double) * (size_t)max_slots * nwarps;
-    return b;
-}
-
-template <typename R, int NR, bool REV>
-static cudaError_t fused_launch(void *phi, void *psi, const PassDesc &ph, FusedArgs args, cudaStream_t s)
-{
-    typedef typename CT<R>::T T;
-    const int threads = 1 << (ph.t - NR);
-    const int64_t tiles = int64_t(1) << (ph.n - ph.t);
-    const int nwarps = (threads + 31) / 32;
-    size_t smem = (REV ? 2 : 1) * (size_t(1) << ph.t) * sizeof(T) +
-                  sizeof(int64_t) * (size_t(1) << (ph.t - ph.low)) +
-                  (REV ? sizeof(double) * (size_t)ph.n_slots * nwarps : 0);
-    k_fused<R, NR, REV><<<(unsigned)tiles, threads, smem, s>>>((T *)phi, (T *)psi, args);
-    return cudaGetLastError();
-}
-
 // Opt the fused kernels in to large dynamic shared memory (call outside stream capture).
 cudaError_t fused_prepare()
 {
@@ -414,23 +572,32 @@ cudaError_t fused_prepare()
     return e;
 }
 
-cudaError_t launch_fused_forward(int dtype, void *psi, const PassDesc *pass_dev, const PassDesc &ph,
-                                 const SubRun *subs, const FGate *gates, const MatRec *recs,
-                                 cudaStream_t s)
+template <typename R, int NR, bool REV>
+static cudaError_t fused_launch(void *phi, void *psi, const PassDesc &ph, size_t smem, FusedArgs args,
+                                cudaStream_t s)
 {
-    FusedArgs args{pass_dev, subs, gates, recs, nullptr, 0};
-    if (dtype == 0) return fused_launch<float, 5, false>(psi, nullptr, ph, args, s);
-    return fused_launch<double, 4, false>(psi, nullptr, ph, args, s);
+    typedef typename CT<R>::T T;
+    const int threads = 1 << (ph.t - NR);
+    const int64_t tiles = int64_t(1) << (ph.n - ph.t);
+    k_fused<R, NR, REV><<<(unsigned)tiles, threads, smem, s>>>((T *)phi, (T *)psi, args);
+    return cudaGetLastError();
 }
 
-cudaError_t launch_fused_reverse(int dtype, void *phi, void *psi, const PassDesc *pass_dev,
-                                 const PassDesc &ph, const SubRun *subs, const FGate *gates,
-                                 const MatRec *recs, double *slot_partials, int n_tiles_stride,
+cudaError_t launch_fused_forward(int dtype, void *psi, const FusedDev &fd, int pass, const PassDesc &ph,
+                                 size_t smem, cudaStream_t s)
+{
+    FusedArgs args{fd.passes + pass, fd.subs, fd.gates, fd.ents, fd.units, fd.recs, nullptr, 0};
+    if (dtype == 0) return fused_launch<float, 5, false>(psi, nullptr, ph, smem, args, s);
+    return fused_launch<double, 4, false>(psi, nullptr, ph, smem, args, s);
+}
+
+cudaError_t launch_fused_reverse(int dtype, void *phi, void *psi, const FusedDev &fd, int pass,
+                                 const PassDesc &ph, size_t smem, double *slot_partials, int n_tiles_stride,
                                  cudaStream_t s)
 {
-    FusedArgs args{pass_dev, subs, gates, recs, slot_partials, n_tiles_stride};
-    if (dtype == 0) return fused_launch<float, 4, true>(phi, psi, ph, args, s);
-    return fused_launch<double, 3, true>(phi, psi, ph, args, s);
+    FusedArgs args{fd.passes + pass, fd.subs, fd.gates, fd.ents, fd.units, fd.recs, slot_partials, n_tiles_stride};
+    if (dtype == 0) return fused_launch<float, 4, true>(phi, psi, ph, smem, args, s);
+    return fused_launch<double, 3, true>(phi, psi, ph, smem, args, s);
 }
 
 // slot_grad[s] = sum over tiles, in tile order within each thread, then a fixed tree.

@@ -5,16 +5,21 @@
 // qubits (the lowest `low` qubits are always in S).  Diagonal gates never need to be in
 // S: their phase depends on bits every thread knows.  A rejected gate blocks its qubits
 // for the rest of the pass, which keeps every gate after all gates it does not commute
-// with (the light-cone rule of gate fusion).
+// with (the light-cone rule of gate fusion).  A pass also closes when its gate data
+// would overflow the kernel's shared-memory budget or its gradient slots the cap.
 //
 // Sub-runs: inside a pass, repeatedly pick up to NR tile positions and take, in circuit
 // order, every ready gate whose non-diagonal qubits fit in those positions; a gate is
 // ready when every earlier gate of the pass sharing a qubit with it is done (two
-// diagonal gates commute and do not order each other).
+// diagonal gates commute and do not order each other).  The sub-run's gates are then
+// re-ordered so that diagonal gates form maximal runs (non-diagonal gates first while
+// they are ready), and every run of diagonal gates becomes one phase block.  The NR
+// register positions are padded to avoid shared-memory bank conflicts.
 #include "planner.h"
 
 #include <algorithm>
 #include <cstdint>
+#include <map>
 
 namespace gbvqc {
 
@@ -27,17 +32,78 @@ inline uint64_t qmask(const PGate &g)
     return m;
 }
 
-struct PassBuild {
-    uint64_t S = 0;
-    std::vector<int> gates;   // gate indices in circuit order
+inline bool conflicts(const PGate &x, const PGate &y)
+{
+    return (qmask(x) & qmask(y)) && !(x.diag && y.diag);
+}
+
+double ftype_flops(int ft)
+{
+    switch (ft) {
+    case FT_DENSE1: return 14;
+    case FT_DENSE2: return 30;
+    case FT_CTRL2: return 7;
+    default: return 6;
+    }
+}
+
+// Shared-memory wavefronts of one warp's register gather for register positions R
+// (bitmask) in a tile of t positions; elements of elem_bytes * 2 bytes, XOR swizzle of
+// the kernel (bits [SB, 2SB) folded onto [0, SB)).
+int gather_wavefronts(uint32_t Rmask, int t, int NR, int elem_bytes)
+{
+    const int SB = elem_bytes == 4 ? 4 : 3;        // 16 x 8 B or 8 x 16 B slots
+    const int group = elem_bytes == 4 ? 16 : 8;     // lanes served per wavefront
+    int pos[32], np = 0;
+    for (int p = 0; p < t && np < 32; p++)
+        if (!((Rmask >> p) & 1)) pos[np++] = p;
+    const int lanes = std::min(32, 1 << std::max(0, t - NR));
+    int total = 0;
+    for (int g0 = 0; g0 < lanes; g0 += group) {
+        int count[16] = {0}, worst = 0;
+        for (int L = g0; L < std::min(lanes, g0 + group); L++) {
+            int l = 0;
+            for (int i = 0; i < 5 && i < np; i++)
+                if ((L >> i) & 1) l |= 1 << pos[i];
+            int swz = l ^ ((l >> SB) & ((1 << SB) - 1));
+            int slot = swz & ((1 << SB) - 1);
+            worst = std::max(worst, ++count[slot]);
+        }
+        total += worst;
+    }
+    return total;
+}
+
+struct Emitter {
+    const std::vector<PGate> &G;
+    const int *local_of;
+    int t, NR, elem_bytes;
+    bool reverse;
+    int &slot_counter;
+    std::vector<int> &slot_param;
+    std::vector<SubRun> &subs;
+    std::vector<FGate> &gates;
+    std::vector<DEnt> &ents;
+    std::vector<MatUnit> &units;
+    int gate_base, ent_base, unit_base;   // pass-local indices start here
+    std::map<int, int> unit_of_rec;
+    double flops = 0;
+
+    int unit(int rec, int k)
+    {
+        auto it = unit_of_rec.find(rec);
+        if (it != unit_of_rec.end()) return it->second;
+        int u = (int)units.size() - unit_base;
+        for (int part = 0; part < (k == 2 ? 4 : 1); part++) units.push_back(MatUnit{rec, part});
+        unit_of_rec[rec] = u;
+        return u;
+    }
 };
 
-// Emit the sub-runs of one pass (gate order `order`, already reversed for the reverse
-// sweep) into subs / fgates.  Reverse passes also number their gradient slots.
-void build_subruns(const std::vector<int> &order, const std::vector<PGate> &G, const int *local_of,
-                   int t, int NR, bool reverse, int &slot_counter, std::vector<int> &slot_param,
-                   std::vector<SubRun> &subs, std::vector<FGate> &fgates)
+void build_subruns(const std::vector<int> &order, Emitter &E)
 {
+    const std::vector<PGate> &G = E.G;
+    const int NR = E.NR, t = E.t;
     const int m = (int)order.size();
     std::vector<std::vector<int>> lists(64);
     for (int pos = 0; pos < m; pos++) {
@@ -59,16 +125,17 @@ void build_subruns(const std::vector<int> &order, const std::vector<PGate> &G, c
         return true;
     };
     while (ndone < m) {
+        // 1. select the sub-run's gates
         int R[8], nR = 0;
         uint32_t Rmask = 0;
-        std::vector<int> sub;
+        std::vector<int> sel;
         for (int pos = 0; pos < m; pos++) {
             if (done[pos] || !ready(pos)) continue;
             const PGate &g = G[order[pos]];
             if (!g.diag) {
                 int need[2], nn = 0;
                 for (int u = 0; u < g.k; u++) {
-                    int l = local_of[g.q[u]];
+                    int l = E.local_of[g.q[u]];
                     if (!((Rmask >> l) & 1)) need[nn++] = l;
                 }
                 if (nR + nn > NR) continue;
@@ -77,7 +144,7 @@ void build_subruns(const std::vector<int> &order, const std::vector<PGate> &G, c
                     Rmask |= 1u << need[u];
                 }
             }
-            sub.push_back(pos);
+            sel.push_back(pos);
             done[pos] = 1;
             ndone++;
             for (int u = 0; u < g.k; u++) {
@@ -85,84 +152,245 @@ void build_subruns(const std::vector<int> &order, const std::vector<PGate> &G, c
                 while (head[q] < (int)lists[q].size() && done[lists[q][head[q]]]) head[q]++;
             }
         }
-        for (int p = 0; p < t && nR < NR; p++)
-            if (!((Rmask >> p) & 1)) {
-                R[nR++] = p;
-                Rmask |= 1u << p;
+        // 2. pad the register positions, fewest bank conflicts first
+        {
+            std::vector<int> cand;
+            for (int p = 0; p < t; p++)
+                if (!((Rmask >> p) & 1)) cand.push_back(p);
+            int need = NR - nR;
+            uint32_t best = 0;
+            int best_score = 1 << 30;
+            // exhaustive over combinations when small, else greedy
+            std::vector<int> idx(need);
+            long combos = 1;
+            for (int i = 0; i < need; i++) combos = combos * (long)(cand.size() - i) / (i + 1);
+            if (need > 0 && combos <= 400) {
+                for (int i = 0; i < need; i++) idx[i] = i;
+                while (true) {
+                    uint32_t msk = Rmask;
+                    for (int i = 0; i < need; i++) msk |= 1u << cand[idx[i]];
+                    int sc = gather_wavefronts(msk, t, NR, E.elem_bytes);
+                    if (sc < best_score) { best_score = sc; best = msk; }
+                    int i = need - 1;
+                    while (i >= 0 && idx[i] == (int)cand.size() - need + i) i--;
+                    if (i < 0) break;
+                    idx[i]++;
+                    for (int k2 = i + 1; k2 < need; k2++) idx[k2] = idx[k2 - 1] + 1;
+                }
+            } else if (need > 0) {
+                best = Rmask;
+                for (int i = 0; i < need; i++) {
+                    int bp = -1, bs = 1 << 30;
+                    for (int p : cand)
+                        if (!((best >> p) & 1)) {
+                            int sc = gather_wavefronts(best | (1u << p), t, NR, E.elem_bytes);
+                            if (sc < bs) { bs = sc; bp = p; }
+                        }
+                    best |= 1u << bp;
+                }
+            } else {
+                best = Rmask;
             }
+            for (int p = 0; p < t && nR < NR; p++)
+                if (((best >> p) & 1) && !((Rmask >> p) & 1)) {
+                    R[nR++] = p;
+                    Rmask |= 1u << p;
+                }
+        }
         auto slot_of = [&](int l) {
             for (int k = 0; k < NR; k++)
                 if (R[k] == l) return k;
             return -1;
         };
-        auto code_of = [&](int q) {  // position code of physical qubit q
-            int l = local_of[q];
+        auto code_of = [&](int q) {
+            int l = E.local_of[q];
             if (l < 0) return -1 - q;
             int k = slot_of(l);
             return k >= 0 ? k : NR + l;
         };
+        // 3. order: ready non-diagonal gates first, then the ready diagonal run
+        std::vector<std::vector<int>> runs;   // each run: gate positions; diagonal runs flagged
+        std::vector<char> run_diag;
+        {
+            std::vector<char> emitted(sel.size(), 0);
+            size_t left = sel.size();
+            auto is_ready = [&](size_t i) {
+                for (size_t j = 0; j < i; j++)
+                    if (!emitted[j] && conflicts(G[order[sel[j]]], G[order[sel[i]]])) return false;
+                return true;
+            };
+            while (left > 0) {
+                bool progress = true;
+                std::vector<int> nd;
+                while (progress) {
+                    progress = false;
+                    for (size_t i = 0; i < sel.size(); i++)
+                        if (!emitted[i] && !G[order[sel[i]]].diag && is_ready(i)) {
+                            emitted[i] = 1;
+                            left--;
+                            nd.push_back(sel[i]);
+                            progress = true;
+                        }
+                }
+                if (!nd.empty()) {
+                    runs.push_back(nd);
+                    run_diag.push_back(0);
+                }
+                std::vector<int> dg;
+                for (size_t i = 0; i < sel.size(); i++)
+                    if (!emitted[i] && G[order[sel[i]]].diag && is_ready(i)) dg.push_back((int)i);
+                for (int i : dg) emitted[i] = 1;
+                left -= dg.size();
+                if (!dg.empty()) {
+                    std::vector<int> run;
+                    for (int i : dg) run.push_back(sel[i]);
+                    runs.push_back(run);
+                    run_diag.push_back(1);
+                }
+            }
+        }
+        // 4. emit
         SubRun sr{};
         for (int k = 0; k < 8; k++) sr.R[k] = (int8_t)(k < NR ? R[k] : 0);
-        sr.g_begin = (int)fgates.size();
-        for (int pos : sub) {
-            const PGate &g = G[order[pos]];
+        sr.g_begin = (int)E.gates.size() - E.gate_base;
+        const double st = E.reverse ? 2.0 : 1.0;
+        for (size_t r = 0; r < runs.size(); r++) {
+            if (!run_diag[r]) {
+                for (int pos : runs[r]) {
+                    const PGate &g = G[order[pos]];
+                    FGate f{};
+                    f.type = (int8_t)g.ftype;
+                    f.a = (int8_t)slot_of(E.local_of[g.q[0]]);
+                    f.b = (int8_t)(g.k == 2 ? slot_of(E.local_of[g.q[1]]) : 0);
+                    f.mat = (int16_t)E.unit(E.reverse ? g.rec_i : g.rec_f, g.k);
+                    f.mat2 = (int16_t)(E.reverse ? E.unit(g.rec_a, g.k) : f.mat);
+                    f.perm = E.reverse ? g.perm_r : g.perm_f;
+                    f.slot = -1;
+                    E.flops += st * ftype_flops(g.ftype);
+                    if (E.reverse && g.gen != GEN_NONE) {
+                        f.gen = (int8_t)g.gen;
+                        f.gpos = (int8_t)slot_of(E.local_of[g.gq]);
+                        f.coef = g.coef;
+                        f.slot = E.slot_counter++;
+                        E.slot_param.push_back(g.param);
+                        E.flops += 4;
+                    }
+                    E.gates.push_back(f);
+                }
+                continue;
+            }
+            const std::vector<int> &run = runs[r];
+            int nz = 0;
+            for (int pos : run) nz += (E.reverse && G[order[pos]].gen == GEN_Z) ? 1 : 0;
+            if (run.size() == 1 && nz == 0) {  // a lone diagonal gate
+                const PGate &g = G[order[run[0]]];
+                FGate f{};
+                f.type = (int8_t)g.ftype;
+                f.a = (int8_t)code_of(g.q[0]);
+                f.b = (int8_t)(g.k == 2 ? code_of(g.q[1]) : 0);
+                f.mat = (int16_t)E.unit(E.reverse ? g.rec_i : g.rec_f, g.k);
+                f.mat2 = (int16_t)(E.reverse ? E.unit(g.rec_a, g.k) : f.mat);
+                f.slot = -1;
+                E.flops += st * 6;
+                E.gates.push_back(f);
+                continue;
+            }
             FGate f{};
-            f.type = g.ftype;
-            if (g.diag) {
-                f.a = code_of(g.q[0]);
-                f.b = g.k == 2 ? code_of(g.q[1]) : 0;
-            } else {
-                f.a = slot_of(local_of[g.q[0]]);
-                f.b = g.k == 2 ? slot_of(local_of[g.q[1]]) : 0;
-            }
-            f.rec = reverse ? g.rec_i : g.rec_f;
-            f.rec2 = reverse ? g.rec_a : -1;
-            f.perm = reverse ? g.perm_r : g.perm_f;
-            f.gen = GEN_NONE;
+            f.type = FT_DIAGB;
             f.slot = -1;
-            if (reverse && g.gen != GEN_NONE) {
-                f.gen = g.gen;
-                f.gpos = g.gen == GEN_Z ? code_of(g.gq) : slot_of(local_of[g.gq]);
-                f.coef = g.coef;
-                f.slot = slot_counter++;
-                slot_param.push_back(g.param);
+            f.nz = (int8_t)nz;
+            f.ent = (int16_t)((int)E.ents.size() - E.ent_base);
+            if (nz) E.flops += 2 + NR;
+            for (int pos : run) {   // Z generators first: all read the states after the block
+                const PGate &g = G[order[pos]];
+                if (!(E.reverse && g.gen == GEN_Z)) continue;
+                DEnt d{};
+                d.k = 3;
+                d.ca = (int8_t)code_of(g.gq);
+                d.slot = E.slot_counter++;
+                d.coef = g.coef;
+                E.slot_param.push_back(g.param);
+                E.ents.push_back(d);
             }
-            fgates.push_back(f);
+            int pairs = 0;
+            bool separate = false;
+            for (int pos : run) {
+                const PGate &g = G[order[pos]];
+                DEnt d{};
+                d.k = (int8_t)g.k;
+                d.ca = (int8_t)code_of(g.q[0]);
+                d.cb = (int8_t)(g.k == 2 ? code_of(g.q[1]) : 0);
+                d.mat = (int16_t)E.unit(E.reverse ? g.rec_i : g.rec_f, g.k);
+                d.mat2 = (int16_t)(E.reverse ? E.unit(g.rec_a, g.k) : d.mat);
+                d.slot = -1;
+                if (d.mat2 != d.mat) separate = true;
+                if (g.k == 2 && d.ca >= 0 && d.ca < NR && d.cb >= 0 && d.cb < NR) pairs++;
+                E.ents.push_back(d);
+            }
+            f.flags = separate ? 1 : 0;
+            f.n_ent = (int16_t)((int)E.ents.size() - E.ent_base - f.ent);
+            // phase table: 2^(NR+1) products per 2^NR amplitudes, pairs, one product per state
+            E.flops += (separate ? 2.0 : 1.0) * (12 + 6.0 * pairs) + st * 6;
+            E.gates.push_back(f);
         }
-        sr.g_end = (int)fgates.size();
-        subs.push_back(sr);
+        sr.g_end = (int)E.gates.size() - E.gate_base;
+        E.subs.push_back(sr);
     }
+}
+
+int gate_weight(const PGate &g, int elem_bytes)
+{
+    int units = g.k == 2 ? 4 : 1;
+    return (int)sizeof(FGate) + (g.diag ? (int)sizeof(DEnt) : 0) + 2 * units * 8 * elem_bytes;
 }
 
 }  // namespace
 
-bool build_fused_plan(const std::vector<PGate> &G, int n, int t, int low, int nr_f, int nr_r,
-                      int max_slots, FusedPlan &out, std::string &err)
+size_t pass_smem_bytes(const FusedPlan &plan, const PassDesc &d, bool reverse, int elem_bytes)
 {
-    if (t > n) t = n;
-    int nr = std::max(nr_f, nr_r);
+    const int nr = reverse ? plan.nr_r : plan.nr_f;
+    const int threads = 1 << (d.t - nr);
+    const int nwarps = (threads + 31) / 32;
+    auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
+    size_t b = al((reverse ? 2 : 1) * (size_t(1) << d.t) * 2 * elem_bytes);
+    b += al(sizeof(int64_t) * (size_t(1) << (d.t - d.low)));
+    if (reverse) b += al(sizeof(double) * (size_t)d.n_slots * nwarps);
+    b += al(sizeof(FGate) * (size_t)d.n_gates);
+    b += al(sizeof(DEnt) * (size_t)d.n_ent);
+    b += al((size_t)8 * elem_bytes * d.n_units);
+    return b;
+}
+
+bool build_fused_plan(const std::vector<PGate> &G, int n, const PlanOptions &opt, FusedPlan &out,
+                      std::string &err)
+{
+    int t = std::min(opt.t, n);
+    const int nr = std::max(opt.nr_f, opt.nr_r);
     if (t < nr || t > 16) {
         err = "tile of " + std::to_string(t) + " qubits cannot hold " + std::to_string(nr) +
               " register qubits";
         return false;
     }
-    if (low < 1) low = 1;
-    if (low > t) low = t;
+    int low = std::max(1, std::min(opt.low, t));
     out = FusedPlan();
     out.t = t;
     out.low = low;
     out.n = n;
-    out.nr_f = nr_f;
-    out.nr_r = nr_r;
+    out.nr_f = opt.nr_f;
+    out.nr_r = opt.nr_r;
     const int m = (int)G.size();
     std::vector<char> applied(m, 0);
-    std::vector<PassBuild> passes;
+    struct PB {
+        uint64_t S;
+        std::vector<int> gates;
+    };
+    std::vector<PB> passes;
     int done = 0;
     const uint64_t lowmask = (uint64_t(1) << low) - 1;
     while (done < m) {
-        PassBuild pb;
+        PB pb;
         pb.S = lowmask;
-        int cnt = low, slots = 0;
+        int cnt = low, slots = 0, bytes = 0;
         uint64_t blocked = 0;
         for (int i = 0; i < m; i++) {
             if (applied[i]) continue;
@@ -172,7 +400,8 @@ bool build_fused_plan(const std::vector<PGate> &G, int n, int t, int low, int nr
                 blocked |= qm;
                 continue;
             }
-            if (g.gen != GEN_NONE && slots >= max_slots) {
+            const int w = gate_weight(g, opt.elem_bytes);
+            if ((g.gen != GEN_NONE && slots >= opt.max_slots) || (bytes + w > opt.gate_smem && !pb.gates.empty())) {
                 blocked |= qm;
                 continue;
             }
@@ -187,6 +416,7 @@ bool build_fused_plan(const std::vector<PGate> &G, int n, int t, int low, int nr
                 cnt += c;
             }
             pb.gates.push_back(i);
+            bytes += w;
             if (g.gen != GEN_NONE) slots++;
         }
         if (pb.gates.empty()) {
@@ -204,10 +434,15 @@ bool build_fused_plan(const std::vector<PGate> &G, int n, int t, int low, int nr
     }
 
     int slot_counter = 0;
-    out.fwd.resize(passes.size());
-    out.rev.resize(passes.size());
-    std::vector<std::vector<int>> local_of_pass(passes.size(), std::vector<int>(64, -1));
-    for (size_t p = 0; p < passes.size(); p++) {
+    std::vector<int> dummy_params;
+    int dummy_counter = 0;
+    const size_t P = passes.size();
+    out.fwd.resize(P);
+    out.rev.resize(P);
+    out.fwd_flops.assign(P, 0.0);
+    out.rev_flops.assign(P, 0.0);
+    std::vector<std::vector<int>> local_of(P, std::vector<int>(64, -1));
+    for (size_t p = 0; p < P; p++) {
         PassDesc d{};
         d.t = t;
         d.n = n;
@@ -216,7 +451,7 @@ bool build_fused_plan(const std::vector<PGate> &G, int n, int t, int low, int nr
         for (int q = 0; q < n; q++) {
             if ((passes[p].S >> q) & 1) {
                 d.S[li] = (int8_t)q;
-                local_of_pass[p][q] = li++;
+                local_of[p][q] = li++;
             } else {
                 d.NS[ni++] = (int8_t)q;
             }
@@ -224,27 +459,39 @@ bool build_fused_plan(const std::vector<PGate> &G, int n, int t, int low, int nr
         out.fwd[p] = d;
         out.rev[p] = d;
     }
-    // forward sub-runs, pass order
-    for (size_t p = 0; p < passes.size(); p++) {
-        int dummy = 0;
-        std::vector<int> dummy_params;
-        out.fwd[p].sub_begin = (int)out.fsubs.size();
-        build_subruns(passes[p].gates, G, local_of_pass[p].data(), t, nr_f, false, dummy, dummy_params,
-                      out.fsubs, out.fgates);
-        out.fwd[p].n_sub = (int)out.fsubs.size() - out.fwd[p].sub_begin;
-    }
-    // reverse sub-runs: passes and gates in reverse order; slots numbered in launch order
-    for (size_t pr = 0; pr < passes.size(); pr++) {
-        size_t p = passes.size() - 1 - pr;
-        std::vector<int> order(passes[p].gates.rbegin(), passes[p].gates.rend());
-        PassDesc &d = out.rev[p];
-        d.sub_begin = (int)out.rsubs.size();
-        d.slot_begin = slot_counter;
-        build_subruns(order, G, local_of_pass[p].data(), t, nr_r, true, slot_counter, out.slot_param,
-                      out.rsubs, out.rgates);
-        d.n_sub = (int)out.rsubs.size() - d.sub_begin;
-        d.n_slots = slot_counter - d.slot_begin;
-        out.max_pass_slots = std::max(out.max_pass_slots, d.n_slots);
+    for (int dir = 0; dir < 2; dir++) {
+        const bool rev = dir == 1;
+        for (size_t pi = 0; pi < P; pi++) {
+            const size_t p = rev ? P - 1 - pi : pi;   // reverse passes in launch order
+            PassDesc &d = rev ? out.rev[p] : out.fwd[p];
+            std::vector<int> order = passes[p].gates;
+            if (rev) std::reverse(order.begin(), order.end());
+            Emitter E{G, local_of[p].data(), t, rev ? opt.nr_r : opt.nr_f, opt.elem_bytes, rev,
+                      rev ? slot_counter : dummy_counter, rev ? out.slot_param : dummy_params,
+                      rev ? out.rsubs : out.fsubs, rev ? out.rgates : out.fgates,
+                      rev ? out.rents : out.fents, rev ? out.runits : out.funits,
+                      0, 0, 0, {}, 0.0};
+            E.gate_base = (int)E.gates.size();
+            E.ent_base = (int)E.ents.size();
+            E.unit_base = (int)E.units.size();
+            d.sub_begin = (int)E.subs.size();
+            d.gate_begin = E.gate_base;
+            d.ent_begin = E.ent_base;
+            d.unit_begin = E.unit_base;
+            d.slot_begin = rev ? slot_counter : 0;
+            build_subruns(order, E);
+            d.n_sub = (int)E.subs.size() - d.sub_begin;
+            d.n_gates = (int)E.gates.size() - d.gate_begin;
+            d.n_ent = (int)E.ents.size() - d.ent_begin;
+            d.n_units = (int)E.units.size() - d.unit_begin;
+            d.n_slots = rev ? slot_counter - d.slot_begin : 0;
+            if (d.n_gates > 32767 || d.n_ent > 32767 || d.n_units > 32767) {
+                err = "pass too large";
+                return false;
+            }
+            (rev ? out.rev_flops : out.fwd_flops)[p] = E.flops;
+            if (rev) out.max_pass_slots = std::max(out.max_pass_slots, d.n_slots);
+        }
     }
     out.n_slots = slot_counter;
     return true;

@@ -1,5 +1,6 @@
 // Host planner of the fused tile engine: partitions a physical gate list into tile
-// passes and register sub-runs, and numbers the gradient slots of the reverse sweep.
+// passes and register sub-runs, groups runs of diagonal gates into phase blocks, and
+// numbers the gradient slots of the reverse sweep.
 #pragma once
 
 #include <string>
@@ -26,20 +27,33 @@ struct PGate {
     int param;        // parameter index or -1
 };
 
+struct PlanOptions {
+    int t = 12;            // tile qubits (clamped to n)
+    int low = 4;           // contiguous low qubits kept in every tile
+    int nr_f = 5, nr_r = 4;  // register qubits of forward / reverse sub-runs
+    int max_slots = 128;   // gradient slots per pass
+    int elem_bytes = 4;    // real element size (4: complex64, 8: complex128)
+    int gate_smem = 24 * 1024;  // shared-memory budget of a pass's gate data
+};
+
 struct FusedPlan {
     int t = 0, low = 0, n = 0, nr_f = 0, nr_r = 0;
     std::vector<PassDesc> fwd, rev;
     std::vector<SubRun> fsubs, rsubs;
     std::vector<FGate> fgates, rgates;
+    std::vector<DEnt> fents, rents;
+    std::vector<MatUnit> funits, runits;
     int n_slots = 0;                // gradient slots over all passes
     std::vector<int> slot_param;    // parameter of each slot
     int max_pass_slots = 0;
+    // algorithmic flops per amplitude of every pass (forward / reverse)
+    std::vector<double> fwd_flops, rev_flops;
 };
 
-// Build the schedule.  t = tile qubits (clamped to n), low = contiguous low qubits kept
-// in every tile, nr_f / nr_r = register qubits of forward / reverse sub-runs,
-// max_slots = cap on gradient slots per pass.  Returns false with a message on failure.
-bool build_fused_plan(const std::vector<PGate> &gates, int n, int t, int low, int nr_f, int nr_r,
-                      int max_slots, FusedPlan &out, std::string &err);
+bool build_fused_plan(const std::vector<PGate> &gates, int n, const PlanOptions &opt, FusedPlan &out,
+                      std::string &err);
+
+// Shared-memory bytes the fused kernel needs for pass p of `plan`.
+size_t pass_smem_bytes(const FusedPlan &plan, const PassDesc &d, bool reverse, int elem_bytes);
 
 }  // namespace gbvqc

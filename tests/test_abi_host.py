@@ -98,3 +98,40 @@ def test_op_marshalling():
     assert arr[0].kind == _abi.KIND["DENSE2"] and list(arr[0].qubits) == [3, 1]
     assert arr[0].data[2 * 6] == u.reshape(-1)[6].real and arr[0].data[2 * 6 + 1] == u.reshape(-1)[6].imag
     assert arr[1].params[0] == 0.1 and arr[1].params[1] == 0.2 and arr[1].param_index == -1
+
+
+@pytest.mark.parametrize("dtype", [gb.C64, gb.C128])
+def test_planner_invariants_host(lib, dtype):
+    # host-only schedule statistics: every variational gate gets a gradient slot (two
+    # per rotation on a density matrix: ket and bra), tiles respect the thread cap, and
+    # every pass fits the shared-memory opt-in
+    cases = [(I.diff_20q(), 800), (I.plain_10q(), 120), (I.noisy_hea(6, 2, 1), 2 * 36),
+             (I.precision_24q(), 0), (I.random_circuit(14, 300, 3, param_share=True), None)]
+    for w, slots in cases:
+        c = gb.circuit_create(w.circuit)
+        st = c.plan_stats(dtype, for_grad=True)
+        n_phys = (2 if w.circuit.density else 1) * w.circuit.n_qubits
+        nr_min = 4 if dtype == gb.C64 else 3
+        assert st["tile_qubits"] <= min(n_phys, nr_min + 8)
+        assert st["passes"] >= 1 and st["fwd_subruns"] >= st["passes"]
+        assert st["fwd_smem_max"] <= 200 * 1024 and st["rev_smem_max"] <= 200 * 1024
+        n_var = sum(1 for o in w.circuit.ops if o.param >= 0)
+        assert st["grad_slots"] == (2 * n_var if w.circuit.density else n_var)
+        if slots is not None:
+            assert st["grad_slots"] == slots
+        assert st["fwd_gates"] <= st["phys_gates"]
+
+
+def test_tiling_options_host(lib):
+    w = I.random_circuit(14, 200, 5)
+    c = gb.circuit_create(w.circuit)
+    last = None
+    for t in (6, 8, 10, 12):
+        c.set_tiling(t, 2)
+        st = c.plan_stats(gb.C64)
+        assert st["tile_qubits"] == t
+        if last is not None:
+            assert st["passes"] <= last   # larger tiles never need more passes here
+        last = st["passes"]
+    with pytest.raises(gb.GbvqcError):
+        c.set_tiling(20, 2)
