@@ -22,9 +22,9 @@
 // Pauli generator P (dQ/dtheta = -i/2 P Q for Q = exp(-i theta P/2), so
 // 2 Re <Psi|dQ|Phi_{j-1}> = Im <Psi|P|Phi_j>), then uncomputes Phi with Q^{-1} and Psi
 // with Q^dag.  In a diagonal run every Z generator is read from the states after the
-// whole run (diagonal matrices commute with Z).  Per-thread FP32 partials over 2^NR
-// terms are summed across the warp with FP32 shuffles and across warps in FP64 in fixed
-// order, giving one FP64 partial per (gradient slot, tile).
+// whole run (diagonal matrices commute with Z).  Per-thread partials over 2^NR terms
+// are summed across the warp with shuffles (FP32 for complex64, FP64 for complex128) and
+// across warps in FP64 in fixed order, giving one FP64 partial per (gradient slot, tile).
 #include "devmath.cuh"
 #include "kernels.h"
 
@@ -338,8 +338,10 @@ struct RedCtx {
     unsigned lanemask;
 };
 
-// Sum a per-thread partial over the warp (FP32 shuffles) and store it for its slot.
-__device__ __forceinline__ void emit_partial(const RedCtx &c, int slot, float v)
+// Sum a per-thread partial over the warp (shuffles in the state's precision: FP32 for
+// complex64, FP64 for complex128) and store it for its slot.
+template <typename R>
+__device__ __forceinline__ void emit_partial(const RedCtx &c, int slot, R v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
@@ -505,7 +507,7 @@ __global__ void __launch_bounds__(REV ? 256 : 128, REV ? 2 : 3) k_fused(typename
                             } else {
                                 part = const_bit<NR>(d.ca, base, tilebase) ? -tot : tot;
                             }
-                            emit_partial(rc, d.slot, (float)part * d.coef);
+                            emit_partial<R>(rc, d.slot, part * (R)d.coef);
                         }
                     }
                     if (g.flags & 1) {
@@ -521,9 +523,9 @@ __global__ void __launch_bounds__(REV ? 256 : 128, REV ? 2 : 3) k_fused(typename
             }
             if constexpr (REV) {
                 if (g.gen == GEN_X)
-                    emit_partial(rc, g.slot, (float)gen_xy_dispatch<R, NR, GEN_X>(g.gpos, a, b) * g.coef);
+                    emit_partial<R>(rc, g.slot, gen_xy_dispatch<R, NR, GEN_X>(g.gpos, a, b) * (R)g.coef);
                 else if (g.gen == GEN_Y)
-                    emit_partial(rc, g.slot, (float)gen_xy_dispatch<R, NR, GEN_Y>(g.gpos, a, b) * g.coef);
+                    emit_partial<R>(rc, g.slot, gen_xy_dispatch<R, NR, GEN_Y>(g.gpos, a, b) * (R)g.coef);
             }
             apply_fgate<R, NR>(g.type, g.a, g.b, g.perm, smat + 8 * g.mat, a, base, tilebase);
             if constexpr (REV) apply_fgate<R, NR>(g.type, g.a, g.b, g.perm, smat + 8 * g.mat2, b, base, tilebase);
