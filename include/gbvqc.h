@@ -218,6 +218,35 @@ gbvqc_status grad_batch(const circuit_handle *circuits, const obs_handle *observ
                         int n_circuits, const double *theta_all, void *stream,
                         double *energies, double *grads);
 
+/* ------------------------------------------------------ allocation-free expectation */
+
+/* <psi|H|psi> of a pure state for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this exists for code that runs while a stream is being
+ * captured into a CUDA graph (where cudaMalloc is refused or unsafe), for applications
+ * whose framework owns the device memory budget through its own pool, and for loops
+ * that cannot take an allocation's implicit synchronisation.  Unlike `expect`, which
+ * reduces through scratch owned by a state handle (sv_alloc / sv_wrap allocate it),
+ * this call needs no handle and allocates nothing: it calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *
+ * psi_device: 2^n_qubits amplitudes of dtype GBVQC_C64 / GBVQC_C128 in device memory,
+ * 16-byte aligned, owned by the caller.  terms: at most 64 Pauli terms in host memory
+ * (they are passed to the kernel as parameters).  energy_device: one double in device
+ * memory, written by the kernel.  The call only enqueues work on `stream` and returns.
+ *
+ * Scratch: a fixed 5120-byte array (256-byte arrival counter + 608 FP64 block partials)
+ * in the library's device memory, present on every GPU that loads the library until the
+ * process exits.  All calls share it: calls whose kernels overlap on the GPU race, so
+ * order them on one stream (or with events).  The counter is cleared before every
+ * launch.  The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.
+ * Errors: ERR_ARG for NULL pointers, a bad dtype or qubit count, a term on a qubit
+ * >= n_qubits, or more than 64 terms (the no-allocation maximum); ERR_CUDA if the
+ * launch fails. */
+gbvqc_status expect_noalloc(const void *psi_device, int n_qubits, int dtype,
+                            const gbvqc_pauli *terms, int n_terms, void *stream,
+                            double *energy_device);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ from ._abi import C64, C128, FUSED, PLAIN, GbvqcError
 __all__ = ["C64", "C128", "PLAIN", "FUSED", "GbvqcError", "StateVector", "CircuitHandle",
            "Observable", "sv_alloc", "sv_wrap", "sv_set", "sv_get", "sv_reset",
            "circuit_create", "apply_circuit", "apply_channel", "obs_create", "expect", "grad",
-           "grad_profile", "grad_batch", "VQEEnergy", "load"]
+           "grad_profile", "grad_batch", "expect_noalloc", "VQEEnergy", "load"]
 
 
 def load():
@@ -220,6 +220,22 @@ def expect(sv: StateVector, obs: Observable) -> float:
     out = ctypes.c_double()
     _abi.check(_abi.lib().expect(sv.handle, obs.handle, ctypes.byref(out)))
     return out.value
+
+
+def expect_noalloc(psi, n_qubits: int, terms, out, stream=None) -> None:
+    """<psi|H|psi> of a CUDA complex64/complex128 tensor without any device allocation.
+
+    For callers that cannot allocate (inside stream capture, under a framework that owns
+    the memory budget): `out` is a caller-provided CUDA float64 tensor of one element,
+    written asynchronously on `stream` (default: torch's current stream).  At most 64
+    terms.  Calls share one fixed scratch array in the library, so calls that overlap on
+    the GPU race; keep them on one stream."""
+    import torch
+    dtype = {torch.complex64: C64, torch.complex128: C128}[psi.dtype]
+    arr = _abi.pauli_array(terms)
+    s = _stream_ptr(stream if stream is not None else torch.cuda.current_stream(psi.device))
+    _abi.check(_abi.lib().expect_noalloc(psi.data_ptr(), n_qubits, dtype, arr, len(terms), s,
+                                         out.data_ptr()))
 
 
 def grad(circ: CircuitHandle, theta, obs: Observable, dtype: int = C64, mode: int = FUSED,

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbvqc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "planner.cpp", "kernels_plain.cu", "kernels_reduce.cu", "kernels_fused.cu",
-           "kernels_batch.cu"]
+           "kernels_batch.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

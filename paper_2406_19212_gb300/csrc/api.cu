@@ -406,6 +406,7 @@ struct gbvqc_circuit {
 // ------------------------------------------------------------------------- basics
 
 extern "C" const char *gbvqc_last_error(void) { return g_last_error.c_str(); }
+void gbvqc_internal_set_error(const char *msg) { g_last_error = msg; }
 extern "C" int gbvqc_version(void) { return 100; }
 
 static size_t amp_size(int dtype) { return dtype == GBVQC_C64 ? 8 : 16; }
