@@ -802,6 +802,7 @@ static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGa
             g.perm_r = r.Mi.size() == 16 ? perm_bits(r.Mi) : 0;
             g.gen = GEN_NONE;
             g.param = -1;
+            g.cz = op.kind == GBVQC_CZ;
             if (is_rotation(op.kind) && op.param_index >= 0) {
                 g.gen = op.kind == GBVQC_RX ? GEN_X : op.kind == GBVQC_RY ? GEN_Y : GEN_Z;
                 g.gq = op.qubits[0];
@@ -848,6 +849,7 @@ static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGa
             g.perm_r = r.Mi.size() == 16 ? perm_bits(r.Mi) : 0;
             g.gen = GEN_NONE;
             g.param = -1;
+            g.cz = op.kind == GBVQC_CZ;  // real: conj(CZ) = CZ on the bra side
             if (is_rotation(op.kind) && op.param_index >= 0) {
                 g.gen = op.kind == GBVQC_RX ? GEN_X : op.kind == GBVQC_RY ? GEN_Y : GEN_Z;
                 g.gq = g.q[0];

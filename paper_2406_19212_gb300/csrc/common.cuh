@@ -148,16 +148,26 @@ struct FGate {               // 32 bytes, staged in shared memory
     int8_t pad0;
     int16_t mat, mat2;       // pass-local matrix units: Phi (forward: U) / Psi (reverse)
     int16_t ent, n_ent;      // FT_DIAGB: first pass-local DEnt and count (incl. Z entries)
-    int32_t slot;            // gradient slot of the X/Y generator, -1 if none
+    int32_t slot;            // X/Y generator: gradient slot (-1 if none); FT_DIAGB: pass-local
+                             // block index (its tile-constant phase product in shared memory)
     float coef;              // gradient weight
-    int32_t perm;            // FT_PERM2: source column of output row r in bits 2r, 2r+1
+    int32_t perm;            // FT_PERM2: source column of output row r in bits 2r, 2r+1;
+                             // FT_DIAGB: entry counts per class after the Z entries:
+                             // tile | local << 8 | register << 16 | pair << 24
     int32_t pad1;
 };
+
+// Classes of diagonal entries inside a phase block, listed in this order after the Z
+// generators: TILE (every position is a tile-index bit: one product per CTA), LOCAL (no
+// register position: one factor per thread), REG (one register position, the other
+// constant: a factor pair on that register bit), PAIR (two register positions: factor
+// pairs plus a controlled phase on |11>), PAIR_CZ (the |11> sign flip of CZ).
+enum DClass : int8_t { DC_Z = 0, DC_TILE = 1, DC_LOCAL = 2, DC_REG = 3, DC_PAIR = 4, DC_PAIR_CZ = 5 };
 
 struct DEnt {                // 16 bytes: one diagonal gate or Z generator of an FT_DIAGB
     int8_t k;                // 1 or 2 positions with phases; 3 = Z generator only
     int8_t ca, cb;           // position codes
-    int8_t pad;
+    int8_t cls;              // DClass
     int16_t mat, mat2;       // pass-local matrix units of the Phi / Psi phases
     int32_t slot;            // Z generator: gradient slot
     float coef;              // Z generator: gradient weight
@@ -179,7 +189,9 @@ struct PassDesc {
     int8_t S[16];            // local position -> physical qubit (ascending)
     int8_t NS[64];           // tile-index bit -> physical qubit (ascending)
     int32_t low;             // S[0..low-1] = 0..low-1 (contiguous in memory)
-    int32_t pad;
+    int32_t n_blocks;        // FT_DIAGB gates in the pass
+    int32_t has_2q;          // the pass holds non-diagonal two-qubit gates (kernel flavour)
+    int32_t pad2;
 };
 
 }  // namespace gbvqc

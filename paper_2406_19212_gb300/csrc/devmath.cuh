@@ -29,32 +29,49 @@ __device__ __forceinline__ void cfma(R mr, R mi, T a, T &acc)
     acc.y = fma(mr, a.y, fma(mi, a.x, acc.y));
 }
 
-// (a, b) <- M (a, b) for a 2x2 matrix of the given structure (row-major re/im).
+// a <- (mr + i mi) a, written so the results can reuse a's registers: both products of
+// the old value go to temporaries first, then the final FMAs overwrite a.
+template <typename T, typename R>
+__device__ __forceinline__ void cmul_ip(R mr, R mi, T &a)
+{
+    const R p = mi * a.y, q = mi * a.x;
+    a.x = fma(mr, a.x, -p);
+    a.y = fma(mr, a.y, q);
+}
+
+// (a, b) <- M (a, b) for a 2x2 matrix of the given structure (row-major re/im).  The
+// update is in place: every product of an old value that a later output needs is taken
+// before that value's register is overwritten, so the compiler can keep a and b in the
+// same registers across gates.
 template <typename R, int SH>
 __device__ __forceinline__ void apply2(const R *m, typename CT<R>::T &a, typename CT<R>::T &b)
 {
-    typedef typename CT<R>::T T;
     if (SH == SH_DENSE1) {
-        T x = cmul<T, R>(m[0], m[1], a), y = cmul<T, R>(m[4], m[5], a);
-        cfma<T, R>(m[2], m[3], b, x);
-        cfma<T, R>(m[6], m[7], b, y);
-        a = x;
-        b = y;
+        // contributions of the old a to a' and b'
+        const R a1x = fma(m[0], a.x, -m[1] * a.y), a1y = fma(m[0], a.y, m[1] * a.x);
+        const R b1x = fma(m[4], a.x, -m[5] * a.y), b1y = fma(m[4], a.y, m[5] * a.x);
+        // a' = a1 + m01 b
+        a.x = fma(m[2], b.x, fma(-m[3], b.y, a1x));
+        a.y = fma(m[2], b.y, fma(m[3], b.x, a1y));
+        // b' = b1 + m11 b
+        const R bx = fma(-m[7], b.y, b1x), by = fma(m[7], b.x, b1y);
+        b.x = fma(m[6], b.x, bx);
+        b.y = fma(m[6], b.y, by);
     } else if (SH == SH_DIAG1) {
-        a = cmul<T, R>(m[0], m[1], a);
-        b = cmul<T, R>(m[6], m[7], b);
+        cmul_ip(m[0], m[1], a);
+        cmul_ip(m[6], m[7], b);
     } else if (SH == SH_ANTI1) {
-        T x = cmul<T, R>(m[2], m[3], b), y = cmul<T, R>(m[4], m[5], a);
-        a = x;
-        b = y;
+        const R x = fma(m[2], b.x, -m[3] * b.y), y = fma(m[2], b.y, m[3] * b.x);
+        b.x = fma(m[4], a.x, -m[5] * a.y);
+        b.y = fma(m[4], a.y, m[5] * a.x);
+        a.x = x;
+        a.y = y;
     } else {  // SH_REAL1
-        T x, y;
-        x.x = m[0] * a.x + m[2] * b.x;
-        x.y = m[0] * a.y + m[2] * b.y;
-        y.x = m[4] * a.x + m[6] * b.x;
-        y.y = m[4] * a.y + m[6] * b.y;
-        a = x;
-        b = y;
+        const R t0 = m[0] * a.x, t1 = m[0] * a.y, u0 = m[4] * a.x, u1 = m[4] * a.y;
+        a.x = fma(m[2], b.x, t0);
+        a.y = fma(m[2], b.y, t1);
+        b.x = fma(m[6], b.x, u0);
+        b.y = fma(m[6], b.y, u1);
     }
 }
 

@@ -9,8 +9,8 @@
 // sub-run's gates on them with no further memory traffic, and scatters back.
 //
 // Diagonal gates need no register position: a run of them is applied as one phase per
-// amplitude, the product of a per-thread constant (bits outside the registers) and a
-// table over the register bits built by doubling (2^(NR+1) complex products).
+// amplitude, the product of a per-CTA constant (tile-index bits), a per-thread constant
+// (tile bits outside the registers) and tables over the register bits built by doubling.
 //
 // This is the GPU counterpart of the paper's gate fusion for compute density (Sec. III.B,
 // citing gate fusion) and of its aggregation of independent amplitude groups (Fig. 3):
@@ -151,7 +151,7 @@ __device__ __forceinline__ void dg1(typename CT<R>::T *a, const R *m, int code, 
     const int bit = const_bit<NR>(code, base, tilebase);
     const R pr = bit ? m[6] : m[0], pi = bit ? m[7] : m[1];
 #pragma unroll
-    for (int j = 0; j < (1 << NR); j++) a[j] = cmul<T, R>(pr, pi, a[j]);
+    for (int j = 0; j < (1 << NR); j++) cmul_ip<T, R>(pr, pi, a[j]);
 }
 
 // Diagonal two-qubit gate on two position codes (matrix bit 0 = code ca).
@@ -167,23 +167,30 @@ __device__ __forceinline__ void dg2(typename CT<R>::T *a, const R *m, int ca, in
         const int idx = code_bit<NR>(ca, j, base, tilebase) | (code_bit<NR>(cb, j, base, tilebase) << 1);
         const R pr = idx == 0 ? p0r : idx == 1 ? p1r : idx == 2 ? p2r : p3r;
         const R pi = idx == 0 ? p0i : idx == 1 ? p1i : idx == 2 ? p2i : p3i;
-        a[j] = cmul<T, R>(pr, pi, a[j]);
+        cmul_ip<T, R>(pr, pi, a[j]);
     }
 }
 
-template <typename R, int NR>
+// Non-diagonal gate on register slots.  Kernels compiled without TWOQ never see
+// two-qubit gates (the planner flags every pass that holds one), which keeps their
+// code paths out of the common one-qubit loop.
+template <typename R, int NR, bool TWOQ>
 __device__ __forceinline__ void apply_fgate(int type, int ga, int gb, int perm, const R *m,
-                                            typename CT<R>::T *a, int base, int64_t tilebase)
+                                            typename CT<R>::T *a)
 {
     switch (type) {
     case FT_DENSE1: rg1_dispatch<R, NR, SH_DENSE1>(ga, a, m); break;
     case FT_REAL1: rg1_dispatch<R, NR, SH_REAL1>(ga, a, m); break;
     case FT_ANTI1: rg1_dispatch<R, NR, SH_ANTI1>(ga, a, m); break;
-    case FT_DIAG1: dg1<R, NR>(a, m, ga, base, tilebase); break;
-    case FT_DENSE2: rg2_dispatch<R, NR, SH_DENSE2>(ga, gb, a, m, 0); break;
-    case FT_DIAG2: dg2<R, NR>(a, m, ga, gb, base, tilebase); break;
-    case FT_PERM2: rg2_dispatch<R, NR, SH_PERM2>(ga, gb, a, m, perm); break;
-    default: rg2_dispatch<R, NR, SH_CTRL2>(ga, gb, a, m, 0); break;
+    default:
+        if constexpr (TWOQ) {
+            switch (type) {
+            case FT_DENSE2: rg2_dispatch<R, NR, SH_DENSE2>(ga, gb, a, m, 0); break;
+            case FT_PERM2: rg2_dispatch<R, NR, SH_PERM2>(ga, gb, a, m, perm); break;
+            default: rg2_dispatch<R, NR, SH_CTRL2>(ga, gb, a, m, 0); break;
+            }
+        }
+        break;
     }
 }
 
@@ -206,95 +213,174 @@ __device__ __forceinline__ void cmul_inplace(R &xr, R &xi, R yr, R yi)
     xr = t;
 }
 
-// Multiply one-qubit phases (e0, e1) on register bit k into the two half tables.
+// Factor pairs (f0, f1) of the register bits: the phase of register amplitude j is the
+// product over bits k of f_{bit k of j}[k].
 template <typename R, int NR>
-__device__ __forceinline__ void table_mul(R *lr, R *li, R *hr, R *hi, int k, R e0r, R e0i, R e1r, R e1i)
-{
-    constexpr int H = NR / 2;
-    if (k < H) {
+struct RegPairs {
+    R p0r[NR], p0i[NR], p1r[NR], p1i[NR];
+    __device__ __forceinline__ void init()
+    {
 #pragma unroll
-        for (int j = 0; j < (1 << H); j++) {
-            const bool one = (j >> k) & 1;
-            cmul_inplace<R>(lr[j], li[j], one ? e1r : e0r, one ? e1i : e0i);
+        for (int k = 0; k < NR; k++) {
+            p0r[k] = 1; p0i[k] = 0; p1r[k] = 1; p1i[k] = 0;
         }
-    } else {
+    }
+    // multiply (e0, e1) into register bit k (k uniform; one case runs)
+    __device__ __forceinline__ void mul(int k, R e0r, R e0i, R e1r, R e1i)
+    {
+#define GBVQC_PM(K)                                              \
+    case K:                                                      \
+        if constexpr (K < NR) {                                  \
+            cmul_inplace<R>(p0r[K], p0i[K], e0r, e0i);           \
+            cmul_inplace<R>(p1r[K], p1i[K], e1r, e1i);           \
+        }                                                        \
+        break;
+        switch (k) { GBVQC_PM(0) GBVQC_PM(1) GBVQC_PM(2) GBVQC_PM(3) GBVQC_PM(4) GBVQC_PM(5) }
+#undef GBVQC_PM
+    }
+};
+
+// a[j] *= c (or -a[j] for NEG) on the register amplitudes whose bits K0 and K1 are both 1.
+template <typename R, int NR, int K0, int K1, bool NEG>
+__device__ __forceinline__ void cphase(typename CT<R>::T *a, R cr, R ci)
+{
+    typedef typename CT<R>::T T;
 #pragma unroll
-        for (int j = 0; j < (1 << (NR - H)); j++) {
-            const bool one = (j >> (k - H)) & 1;
-            cmul_inplace<R>(hr[j], hi[j], one ? e1r : e0r, one ? e1i : e0i);
+    for (int j = 0; j < (1 << NR); j++) {
+        if (!(((j >> K0) & 1) && ((j >> K1) & 1))) continue;
+        if (NEG) {
+            a[j].x = -a[j].x;
+            a[j].y = -a[j].y;
+        } else {
+            cmul_ip<T, R>(cr, ci, a[j]);
         }
     }
 }
 
-// Multiply the register amplitudes of a (and b, if given) by the product of the
-// entries' diagonals.  `second` selects the Psi phases (mat2) of the reverse sweep.
-// The phase of register amplitude j is c * TL[j & lo] * TH[j >> H]: c collects the
-// entries on bits that are constant for the thread, TL and TH the low / high halves of
-// the register bits.
+template <typename R, int NR, bool NEG>
+__device__ __forceinline__ void cphase_dispatch(int k0, int k1, typename CT<R>::T *a, R cr, R ci)
+{
+    const int lo = k0 < k1 ? k0 : k1, hi = k0 < k1 ? k1 : k0;
+#define GBVQC_CP(L, H) \
+    case L * 8 + H:    \
+        if constexpr (H < NR) cphase<R, NR, L, H, NEG>(a, cr, ci); \
+        break;
+    switch (lo * 8 + hi) {
+        GBVQC_CP(0, 1) GBVQC_CP(0, 2) GBVQC_CP(0, 3) GBVQC_CP(0, 4) GBVQC_CP(1, 2)
+        GBVQC_CP(1, 3) GBVQC_CP(1, 4) GBVQC_CP(2, 3) GBVQC_CP(2, 4) GBVQC_CP(3, 4)
+    }
+#undef GBVQC_CP
+}
+
+template <typename R>
+__device__ __forceinline__ void cdiv(R ar, R ai, R br, R bi, R &qr, R &qi)
+{
+    const R inv = R(1) / (br * br + bi * bi);
+    qr = (ar * br + ai * bi) * inv;
+    qi = (ai * br - ar * bi) * inv;
+}
+
+// Apply one phase block to a (and b, if given).  `ents` points after the Z entries; the
+// tile-constant entries (the first nt) are already folded into (c0r, c0i).  The phase
+// of register amplitude j is c * TL[j & lo] * TH[j >> H] with c the product of the
+// tile-constant and thread-local entries and TL, TH tables over the low and high halves
+// of the register bits built by doubling from the factor pairs; PAIR entries are split
+// into factor pairs d0 (1, d1/d0) (1, d2/d0) and the controlled phase d3 d0 / (d1 d2).
 template <typename R, int NR>
-__device__ __forceinline__ void phase_table(const DEnt *ents, int n, const R *smat, bool second,
-                                            typename CT<R>::T *a, typename CT<R>::T *b, int base,
-                                            int64_t tilebase)
+__device__ __forceinline__ void phase_block(const DEnt *ents, int counts, const R *smat, bool second,
+                                            R c0r, R c0i, typename CT<R>::T *a, typename CT<R>::T *b,
+                                            int base, int64_t tilebase)
 {
     typedef typename CT<R>::T T;
     constexpr int H = NR / 2;
-    R cr = 1, ci = 0;
-    R lr[1 << H], li[1 << H], hr[1 << (NR - H)], hi[1 << (NR - H)];
-#pragma unroll
-    for (int j = 0; j < (1 << H); j++) { lr[j] = 1; li[j] = 0; }
-#pragma unroll
-    for (int j = 0; j < (1 << (NR - H)); j++) { hr[j] = 1; hi[j] = 0; }
-    for (int e = 0; e < n; e++) {
-        const DEnt d = ents[e];
-        if (d.k == 3) continue;
-        const R *m = smat + 8 * (second ? d.mat2 : d.mat);
-        const bool ra = d.ca >= 0 && d.ca < NR;
-        if (d.k == 1) {
-            R d0r, d0i, d1r, d1i;
-            diag_elem<R>(m, 1, 0, d0r, d0i);
-            diag_elem<R>(m, 1, 1, d1r, d1i);
-            if (ra) {
-                table_mul<R, NR>(lr, li, hr, hi, d.ca, d0r, d0i, d1r, d1i);
-            } else {
-                const int bit = const_bit<NR>(d.ca, base, tilebase);
-                cmul_inplace<R>(cr, ci, bit ? d1r : d0r, bit ? d1i : d0i);
-            }
+    const int nt = counts & 255, nl = (counts >> 8) & 255, nr = (counts >> 16) & 255, np = (counts >> 24) & 255;
+    const DEnt *e = ents + nt;
+    R cr = c0r, ci = c0i;
+    for (int i = 0; i < nl; i++, e++) {  // thread-local constants
+        const R *m = smat + 8 * (second ? e->mat2 : e->mat);
+        const int idx = e->k == 1 ? const_bit<NR>(e->ca, base, tilebase)
+                                  : const_bit<NR>(e->ca, base, tilebase) | (const_bit<NR>(e->cb, base, tilebase) << 1);
+        R er, ei;
+        diag_elem<R>(m, e->k, idx, er, ei);
+        cmul_inplace<R>(cr, ci, er, ei);
+    }
+    RegPairs<R, NR> P;
+    P.init();
+    for (int i = 0; i < nr; i++, e++) {  // one register bit
+        const R *m = smat + 8 * (second ? e->mat2 : e->mat);
+        R e0r, e0i, e1r, e1i;
+        int k;
+        if (e->k == 1) {
+            k = e->ca;
+            diag_elem<R>(m, 1, 0, e0r, e0i);
+            diag_elem<R>(m, 1, 1, e1r, e1i);
+        } else {
+            const bool ra = e->ca >= 0 && e->ca < NR;
+            k = ra ? e->ca : e->cb;
+            const int cbit = ra ? const_bit<NR>(e->cb, base, tilebase) : const_bit<NR>(e->ca, base, tilebase);
+            diag_elem<R>(m, 2, ra ? 2 * cbit : cbit, e0r, e0i);
+            diag_elem<R>(m, 2, ra ? 1 + 2 * cbit : cbit + 2, e1r, e1i);
+        }
+        P.mul(k, e0r, e0i, e1r, e1i);
+    }
+    for (int i = 0; i < np; i++, e++) {  // two register bits
+        if (e->cls == DC_PAIR_CZ) {
+            cphase_dispatch<R, NR, true>(e->ca, e->cb, a, R(0), R(0));
+            if (b) cphase_dispatch<R, NR, true>(e->ca, e->cb, b, R(0), R(0));
             continue;
         }
-        const bool rb = d.cb >= 0 && d.cb < NR;
-        if (ra && rb) continue;  // applied to the amplitudes below
-        if (!ra && !rb) {
-            const int idx = const_bit<NR>(d.ca, base, tilebase) | (const_bit<NR>(d.cb, base, tilebase) << 1);
-            R er, ei;
-            diag_elem<R>(m, 2, idx, er, ei);
-            cmul_inplace<R>(cr, ci, er, ei);
-        } else {
-            // one register position: a one-qubit diagonal on it, chosen by the constant bit
-            const int kreg = ra ? d.ca : d.cb;
-            const int cbit = ra ? const_bit<NR>(d.cb, base, tilebase) : const_bit<NR>(d.ca, base, tilebase);
-            const int i0 = ra ? 2 * cbit : cbit, i1 = ra ? 1 + 2 * cbit : cbit + 2;
-            R e0r, e0i, e1r, e1i;
-            diag_elem<R>(m, 2, i0, e0r, e0i);
-            diag_elem<R>(m, 2, i1, e1r, e1i);
-            table_mul<R, NR>(lr, li, hr, hi, kreg, e0r, e0i, e1r, e1i);
+        const R *m = smat + 8 * (second ? e->mat2 : e->mat);
+        R d0r, d0i, d1r, d1i, d2r, d2i, d3r, d3i;
+        diag_elem<R>(m, 2, 0, d0r, d0i);
+        diag_elem<R>(m, 2, 1, d1r, d1i);
+        diag_elem<R>(m, 2, 2, d2r, d2i);
+        diag_elem<R>(m, 2, 3, d3r, d3i);
+        R qr, qi;
+        cmul_inplace<R>(cr, ci, d0r, d0i);
+        cdiv<R>(d1r, d1i, d0r, d0i, qr, qi);
+        P.mul(e->ca, R(1), R(0), qr, qi);
+        cdiv<R>(d2r, d2i, d0r, d0i, qr, qi);
+        P.mul(e->cb, R(1), R(0), qr, qi);
+        R nr_ = d3r, ni_ = d3i, dr_ = d1r, di_ = d1i;
+        cmul_inplace<R>(nr_, ni_, d0r, d0i);
+        cmul_inplace<R>(dr_, di_, d2r, d2i);
+        cdiv<R>(nr_, ni_, dr_, di_, qr, qi);
+        cphase_dispatch<R, NR, false>(e->ca, e->cb, a, qr, qi);
+        if (b) cphase_dispatch<R, NR, false>(e->ca, e->cb, b, qr, qi);
+    }
+    R lr[1 << H], li[1 << H], hr[1 << (NR - H)], hi[1 << (NR - H)];
+    lr[0] = 1;
+    li[0] = 0;
+#pragma unroll
+    for (int k = 0; k < H; k++) {
+#pragma unroll
+        for (int j = 0; j < (1 << k); j++) {
+            lr[j | (1 << k)] = lr[j] * P.p1r[k] - li[j] * P.p1i[k];
+            li[j | (1 << k)] = lr[j] * P.p1i[k] + li[j] * P.p1r[k];
+            R x = lr[j] * P.p0r[k] - li[j] * P.p0i[k];
+            li[j] = lr[j] * P.p0i[k] + li[j] * P.p0r[k];
+            lr[j] = x;
         }
     }
+    hr[0] = cr;
+    hi[0] = ci;
 #pragma unroll
-    for (int j = 0; j < (1 << (NR - H)); j++) cmul_inplace<R>(hr[j], hi[j], cr, ci);
+    for (int k = 0; k < NR - H; k++) {
+#pragma unroll
+        for (int j = 0; j < (1 << k); j++) {
+            hr[j | (1 << k)] = hr[j] * P.p1r[H + k] - hi[j] * P.p1i[H + k];
+            hi[j | (1 << k)] = hr[j] * P.p1i[H + k] + hi[j] * P.p1r[H + k];
+            R x = hr[j] * P.p0r[H + k] - hi[j] * P.p0i[H + k];
+            hi[j] = hr[j] * P.p0i[H + k] + hi[j] * P.p0r[H + k];
+            hr[j] = x;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < (1 << NR); j++) {
         const int jl = j & ((1 << H) - 1), jh = j >> H;
         const R pr = lr[jl] * hr[jh] - li[jl] * hi[jh], pi = lr[jl] * hi[jh] + li[jl] * hr[jh];
-        a[j] = cmul<T, R>(pr, pi, a[j]);
-        if (b) b[j] = cmul<T, R>(pr, pi, b[j]);
-    }
-    // two-qubit entries with both positions in registers
-    for (int e = 0; e < n; e++) {
-        const DEnt d = ents[e];
-        if (d.k != 2 || !(d.ca >= 0 && d.ca < NR && d.cb >= 0 && d.cb < NR)) continue;
-        const R *m = smat + 8 * (second ? d.mat2 : d.mat);
-        dg2<R, NR>(a, m, d.ca, d.cb, base, tilebase);
-        if (b) dg2<R, NR>(b, m, d.ca, d.cb, base, tilebase);
+        cmul_ip<T, R>(pr, pi, a[j]);
+        if (b) cmul_ip<T, R>(pr, pi, b[j]);
     }
 }
 
@@ -396,7 +482,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(
 
 // Forward kernels run 2^(t-NR) <= 128 threads (three CTAs per SM), reverse kernels
 // <= 256 threads (two CTAs per SM).
-template <typename R, int NR, bool REV>
+template <typename R, int NR, bool REV, bool TWOQ>
 __global__ void __launch_bounds__(REV ? 256 : 128, REV ? 2 : 3) k_fused(typename CT<R>::T *__restrict__ phi,
                                                   typename CT<R>::T *__restrict__ psi, FusedArgs args)
 {
@@ -422,6 +508,8 @@ __global__ void __launch_bounds__(REV ? 256 : 128, REV ? 2 : 3) k_fused(typename
     p += align16(sizeof(FGate) * (size_t)pd.n_gates);
     DEnt *sents = reinterpret_cast<DEnt *>(p);
     p += align16(sizeof(DEnt) * (size_t)pd.n_ent);
+    R *sconst = reinterpret_cast<R *>(p);  // per phase block: tile-constant products (Phi, Psi)
+    p += align16((size_t)4 * sizeof(R) * pd.n_blocks);
     R *smat = reinterpret_cast<R *>(p);
 
     const int64_t tile = blockIdx.x;
@@ -450,6 +538,26 @@ __global__ void __launch_bounds__(REV ? 256 : 128, REV ? 2 : 3) k_fused(typename
     if (REV)
         for (int i = threadIdx.x; i < pd.n_slots * nwarps; i += blockDim.x) sgrad[i] = 0.0;
     __syncthreads();
+    // tile-constant phase products of every phase block (bits fixed by the tile index)
+    for (int gi = threadIdx.x; gi < pd.n_gates; gi += blockDim.x) {
+        const FGate g = sgates[gi];
+        if (g.type != FT_DIAGB) continue;
+        const DEnt *e = sents + g.ent + g.nz;
+        R r0 = 1, i0 = 0, r1 = 1, i1 = 0;
+        for (int i = 0; i < (g.perm & 255); i++, e++) {
+            const int idx = e->k == 1 ? (int)((tilebase >> (-1 - e->ca)) & 1)
+                                      : (int)((tilebase >> (-1 - e->ca)) & 1) | ((int)((tilebase >> (-1 - e->cb)) & 1) << 1);
+            R er, ei;
+            diag_elem<R>(smat + 8 * e->mat, e->k, idx, er, ei);
+            cmul_inplace<R>(r0, i0, er, ei);
+            diag_elem<R>(smat + 8 * e->mat2, e->k, idx, er, ei);
+            cmul_inplace<R>(r1, i1, er, ei);
+        }
+        sconst[4 * g.slot] = r0;
+        sconst[4 * g.slot + 1] = i0;
+        sconst[4 * g.slot + 2] = r1;
+        sconst[4 * g.slot + 3] = i1;
+    }
     tile_io<R>(phi, sphi, t, low, tilebase, hitab, true);
     if (REV) tile_io<R>(psi, spsi, t, low, tilebase, hitab, true);
     __syncthreads();
@@ -480,10 +588,13 @@ __global__ void __launch_bounds__(REV ? 256 : 128, REV ? 2 : 3) k_fused(typename
             a[j] = sphi[swz<R>(l)];
             if constexpr (REV) b[j] = spsi[swz<R>(l)];
         }
+        FGate gn = sgates[sr.g_begin < sr.g_end ? sr.g_begin : 0];
         for (int gi = sr.g_begin; gi < sr.g_end; gi++) {
-            const FGate g = sgates[gi];
+            const FGate g = gn;
+            if (gi + 1 < sr.g_end) gn = sgates[gi + 1];  // prefetch the next record
             if (g.type == FT_DIAGB) {
                 const DEnt *ents = sents + g.ent;
+                const R *cst = sconst + 4 * g.slot;
                 if constexpr (REV) {
                     if (g.nz > 0) {  // Z generators on the states after the block
                         R tot = 0, dk[NR];
@@ -511,13 +622,13 @@ __global__ void __launch_bounds__(REV ? 256 : 128, REV ? 2 : 3) k_fused(typename
                         }
                     }
                     if (g.flags & 1) {
-                        phase_table<R, NR>(ents + g.nz, g.n_ent - g.nz, smat, false, a, nullptr, base, tilebase);
-                        phase_table<R, NR>(ents + g.nz, g.n_ent - g.nz, smat, true, b, nullptr, base, tilebase);
+                        phase_block<R, NR>(ents + g.nz, g.perm, smat, false, cst[0], cst[1], a, nullptr, base, tilebase);
+                        phase_block<R, NR>(ents + g.nz, g.perm, smat, true, cst[2], cst[3], b, nullptr, base, tilebase);
                     } else {
-                        phase_table<R, NR>(ents + g.nz, g.n_ent - g.nz, smat, false, a, b, base, tilebase);
+                        phase_block<R, NR>(ents + g.nz, g.perm, smat, false, cst[0], cst[1], a, b, base, tilebase);
                     }
                 } else {
-                    phase_table<R, NR>(ents, g.n_ent, smat, false, a, nullptr, base, tilebase);
+                    phase_block<R, NR>(ents, g.perm, smat, false, cst[0], cst[1], a, nullptr, base, tilebase);
                 }
                 continue;
             }
@@ -527,8 +638,8 @@ __global__ void __launch_bounds__(REV ? 256 : 128, REV ? 2 : 3) k_fused(typename
                 else if (g.gen == GEN_Y)
                     emit_partial<R>(rc, g.slot, gen_xy_dispatch<R, NR, GEN_Y>(g.gpos, a, b) * (R)g.coef);
             }
-            apply_fgate<R, NR>(g.type, g.a, g.b, g.perm, smat + 8 * g.mat, a, base, tilebase);
-            if constexpr (REV) apply_fgate<R, NR>(g.type, g.a, g.b, g.perm, smat + 8 * g.mat2, b, base, tilebase);
+            apply_fgate<R, NR, TWOQ>(g.type, g.a, g.b, g.perm, smat + 8 * g.mat, a);
+            if constexpr (REV) apply_fgate<R, NR, TWOQ>(g.type, g.a, g.b, g.perm, smat + 8 * g.mat2, b);
         }
 #pragma unroll
         for (int j = 0; j < (1 << NR); j++) {
@@ -561,16 +672,22 @@ int fused_nr(int dtype, bool reverse)
 }
 
 // Opt the fused kernels in to large dynamic shared memory (call outside stream capture).
-cudaError_t fused_prepare()
+template <typename R, int NR, bool REV>
+static cudaError_t prepare_pair()
 {
     const int bytes = 200 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_fused<float, 5, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_fused<R, NR, REV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fused<float, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fused<double, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fused<double, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        e = cudaFuncSetAttribute(k_fused<R, NR, REV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+cudaError_t fused_prepare()
+{
+    cudaError_t e = prepare_pair<float, 5, false>();
+    if (e == cudaSuccess) e = prepare_pair<float, 4, true>();
+    if (e == cudaSuccess) e = prepare_pair<double, 4, false>();
+    if (e == cudaSuccess) e = prepare_pair<double, 3, true>();
     return e;
 }
 
@@ -581,7 +698,10 @@ static cudaError_t fused_launch(void *phi, void *psi, const PassDesc &ph, size_t
     typedef typename CT<R>::T T;
     const int threads = 1 << (ph.t - NR);
     const int64_t tiles = int64_t(1) << (ph.n - ph.t);
-    k_fused<R, NR, REV><<<(unsigned)tiles, threads, smem, s>>>((T *)phi, (T *)psi, args);
+    if (ph.has_2q)
+        k_fused<R, NR, REV, true><<<(unsigned)tiles, threads, smem, s>>>((T *)phi, (T *)psi, args);
+    else
+        k_fused<R, NR, REV, false><<<(unsigned)tiles, threads, smem, s>>>((T *)phi, (T *)psi, args);
     return cudaGetLastError();
 }
 

@@ -13,7 +13,8 @@
 // ready when every earlier gate of the pass sharing a qubit with it is done (two
 // diagonal gates commute and do not order each other).  The sub-run's gates are then
 // re-ordered so that diagonal gates form maximal runs (non-diagonal gates first while
-// they are ready), and every run of diagonal gates becomes one phase block.  The NR
+// they are ready), and every run of diagonal gates (even a single one) becomes one
+// phase block.  The NR
 // register positions are padded to avoid shared-memory bank conflicts.
 #include "planner.h"
 
@@ -88,6 +89,9 @@ struct Emitter {
     int gate_base, ent_base, unit_base;   // pass-local indices start here
     std::map<int, int> unit_of_rec;
     double flops = 0;
+    int n_blocks = 0;        // FT_DIAGB gates emitted in this pass
+    bool has_2q = false;     // a non-diagonal two-qubit gate was emitted
+    bool overflow = false;   // a phase block class with more than 255 entries
 
     int unit(int rec, int k)
     {
@@ -258,6 +262,7 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
             if (!run_diag[r]) {
                 for (int pos : runs[r]) {
                     const PGate &g = G[order[pos]];
+                    if (g.k == 2) E.has_2q = true;
                     FGate f{};
                     f.type = (int8_t)g.ftype;
                     f.a = (int8_t)slot_of(E.local_of[g.q[0]]);
@@ -282,22 +287,9 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
             const std::vector<int> &run = runs[r];
             int nz = 0;
             for (int pos : run) nz += (E.reverse && G[order[pos]].gen == GEN_Z) ? 1 : 0;
-            if (run.size() == 1 && nz == 0) {  // a lone diagonal gate
-                const PGate &g = G[order[run[0]]];
-                FGate f{};
-                f.type = (int8_t)g.ftype;
-                f.a = (int8_t)code_of(g.q[0]);
-                f.b = (int8_t)(g.k == 2 ? code_of(g.q[1]) : 0);
-                f.mat = (int16_t)E.unit(E.reverse ? g.rec_i : g.rec_f, g.k);
-                f.mat2 = (int16_t)(E.reverse ? E.unit(g.rec_a, g.k) : f.mat);
-                f.slot = -1;
-                E.flops += st * 6;
-                E.gates.push_back(f);
-                continue;
-            }
             FGate f{};
             f.type = FT_DIAGB;
-            f.slot = -1;
+            f.slot = E.n_blocks++;
             f.nz = (int8_t)nz;
             f.ent = (int16_t)((int)E.ents.size() - E.ent_base);
             if (nz) E.flops += 2 + NR;
@@ -306,13 +298,15 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
                 if (!(E.reverse && g.gen == GEN_Z)) continue;
                 DEnt d{};
                 d.k = 3;
+                d.cls = DC_Z;
                 d.ca = (int8_t)code_of(g.gq);
                 d.slot = E.slot_counter++;
                 d.coef = g.coef;
                 E.slot_param.push_back(g.param);
                 E.ents.push_back(d);
             }
-            int pairs = 0;
+            // phase entries, grouped by class
+            std::vector<DEnt> cls_ents[6];
             bool separate = false;
             for (int pos : run) {
                 const PGate &g = G[order[pos]];
@@ -324,13 +318,34 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
                 d.mat2 = (int16_t)(E.reverse ? E.unit(g.rec_a, g.k) : d.mat);
                 d.slot = -1;
                 if (d.mat2 != d.mat) separate = true;
-                if (g.k == 2 && d.ca >= 0 && d.ca < NR && d.cb >= 0 && d.cb < NR) pairs++;
-                E.ents.push_back(d);
+                auto reg = [&](int c) { return c >= 0 && c < NR; };
+                auto tile = [&](int c) { return c < 0; };
+                if (g.k == 1) {
+                    d.cls = reg(d.ca) ? DC_REG : tile(d.ca) ? DC_TILE : DC_LOCAL;
+                } else if (reg(d.ca) && reg(d.cb)) {
+                    d.cls = g.cz ? DC_PAIR_CZ : DC_PAIR;
+                } else if (reg(d.ca) || reg(d.cb)) {
+                    d.cls = DC_REG;
+                } else {
+                    d.cls = (tile(d.ca) && tile(d.cb)) ? DC_TILE : DC_LOCAL;
+                }
+                cls_ents[(int)d.cls].push_back(d);
             }
+            int cnt[6];
+            for (int c = 1; c < 6; c++) {
+                cnt[c] = (int)cls_ents[c].size();
+                for (const DEnt &d : cls_ents[c]) E.ents.push_back(d);
+            }
+            const int np = cnt[DC_PAIR] + cnt[DC_PAIR_CZ];
+            if (cnt[DC_TILE] > 255 || cnt[DC_LOCAL] > 255 || cnt[DC_REG] > 255 || np > 255) {
+                E.overflow = true;
+            }
+            f.perm = cnt[DC_TILE] | (cnt[DC_LOCAL] << 8) | (cnt[DC_REG] << 16) | (np << 24);
             f.flags = separate ? 1 : 0;
             f.n_ent = (int16_t)((int)E.ents.size() - E.ent_base - f.ent);
-            // phase table: 2^(NR+1) products per 2^NR amplitudes, pairs, one product per state
-            E.flops += (separate ? 2.0 : 1.0) * (12 + 6.0 * pairs) + st * 6;
+            // per thread: the block's local factors, register pairs, two half tables and one
+            // product per amplitude and state; PAIR entries add a controlled phase on a quarter
+            E.flops += (separate ? 2.0 : 1.0) * (6 + 6.0 * cnt[DC_PAIR] * 0.25 + 1.5 * cnt[DC_PAIR_CZ] * 0.25) + st * 6;
             E.gates.push_back(f);
         }
         sr.g_end = (int)E.gates.size() - E.gate_base;
@@ -357,6 +372,7 @@ size_t pass_smem_bytes(const FusedPlan &plan, const PassDesc &d, bool reverse, i
     if (reverse) b += al(sizeof(double) * (size_t)d.n_slots * nwarps);
     b += al(sizeof(FGate) * (size_t)d.n_gates);
     b += al(sizeof(DEnt) * (size_t)d.n_ent);
+    b += al((size_t)4 * elem_bytes * d.n_blocks);   // tile-constant products (Phi, Psi)
     b += al((size_t)8 * elem_bytes * d.n_units);
     return b;
 }
@@ -470,7 +486,7 @@ bool build_fused_plan(const std::vector<PGate> &G, int n, const PlanOptions &opt
                       rev ? slot_counter : dummy_counter, rev ? out.slot_param : dummy_params,
                       rev ? out.rsubs : out.fsubs, rev ? out.rgates : out.fgates,
                       rev ? out.rents : out.fents, rev ? out.runits : out.funits,
-                      0, 0, 0, {}, 0.0};
+                      0, 0, 0, {}, 0.0, 0, false, false};
             E.gate_base = (int)E.gates.size();
             E.ent_base = (int)E.ents.size();
             E.unit_base = (int)E.units.size();
@@ -480,6 +496,12 @@ bool build_fused_plan(const std::vector<PGate> &G, int n, const PlanOptions &opt
             d.unit_begin = E.unit_base;
             d.slot_begin = rev ? slot_counter : 0;
             build_subruns(order, E);
+            if (E.overflow) {
+                err = "phase block too large";
+                return false;
+            }
+            d.n_blocks = E.n_blocks;
+            d.has_2q = E.has_2q ? 1 : 0;
             d.n_sub = (int)E.subs.size() - d.sub_begin;
             d.n_gates = (int)E.gates.size() - d.gate_begin;
             d.n_ent = (int)E.ents.size() - d.ent_begin;

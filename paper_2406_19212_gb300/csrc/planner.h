@@ -25,6 +25,7 @@ struct PGate {
     int gq;           // physical qubit of the generator
     float coef;       // gradient weight
     int param;        // parameter index or -1
+    bool cz = false;  // exactly diag(1, 1, 1, -1) in every direction (CZ)
 };
 
 struct PlanOptions {
