@@ -209,11 +209,34 @@ gbvqc_status grad_profile(circuit_handle c, const double *theta, int n_theta, ob
                           int dtype, int mode, void *stream, gbvqc_kernel_stat *stats,
                           int max_stats, int *n_stats);
 
-/* Batched energy + gradient of independent circuits (each with its own qubit count,
- * parameters and observable), complex64 sweeps with FP64 reductions, executed as one
- * persistent launch replayed through a CUDA graph.  theta_all concatenates every
- * circuit's parameters (host); energies (n_circuits) and grads (sum of n_params) are
- * host outputs.  All circuits must be pure-state circuits of at most 24 qubits. */
+/* ------------------------------------------------ batched gradients (many circuits) */
+
+typedef struct gbvqc_batch *batch_handle;
+
+/* A batch of independent pure-state circuits (each with its own qubit count >= 6, gates,
+ * parameters and observable) evaluated together: every step of the gradient sequence
+ * (materialisation, state init, fused pass p of every circuit, expectation, reverse
+ * pass p, gradient reduction) is one launch over all circuits, and the whole sequence
+ * is captured once into a CUDA graph that batch_grad replays.  dtype GBVQC_C64 (FP32
+ * sweeps, FP64 reductions) or GBVQC_C128.  The batch keeps pointers to the circuit and
+ * observable handles: free the batch before them, and do not run the member circuits
+ * elsewhere while batch_grad runs (they share matrix records).  Work buffers: two states
+ * per circuit plus per-slot partials, owned by the batch.
+ * Errors: ERR_ARG (NULL, empty batch, density circuit, observable/circuit qubit
+ * mismatch), ERR_UNSUPPORTED (fewer than 6 qubits), ERR_OOM, ERR_CUDA. */
+gbvqc_status batch_create(const circuit_handle *circuits, const obs_handle *observables, int n_circuits,
+                          int dtype, batch_handle *out);
+gbvqc_status batch_free(batch_handle b);
+
+/* Energies (one per circuit) and gradients (concatenated in circuit order, n_params of
+ * each) for theta_all (all circuits' parameters concatenated, n_theta_total values).
+ * ptr_loc: theta_all, energies and grads are host or device pointers; host pointers
+ * synchronise `stream`. */
+gbvqc_status batch_grad(batch_handle b, const double *theta_all, int n_theta_total, int ptr_loc,
+                        void *stream, double *energies, double *grads);
+
+/* One-shot convenience: batch_create (complex64), batch_grad with host pointers,
+ * batch_free. */
 gbvqc_status grad_batch(const circuit_handle *circuits, const obs_handle *observables,
                         int n_circuits, const double *theta_all, void *stream,
                         double *energies, double *grads);

@@ -25,7 +25,8 @@ from ._abi import C64, C128, FUSED, PLAIN, GbvqcError
 __all__ = ["C64", "C128", "PLAIN", "FUSED", "GbvqcError", "StateVector", "CircuitHandle",
            "Observable", "sv_alloc", "sv_wrap", "sv_set", "sv_get", "sv_reset",
            "circuit_create", "apply_circuit", "apply_channel", "obs_create", "expect", "grad",
-           "grad_profile", "grad_batch", "expect_noalloc", "VQEEnergy", "load"]
+           "grad_profile", "grad_batch", "batch_create", "BatchHandle", "expect_noalloc", "VQEEnergy",
+           "load"]
 
 
 def load():
@@ -283,9 +284,70 @@ def grad_profile(circ: CircuitHandle, theta, obs: Observable, dtype: int = C64,
                                      stats[i].alg_bytes) for i in range(n.value)}
 
 
-def grad_batch(circs: Sequence[CircuitHandle], obss: Sequence[Observable], thetas,
-               stream=None):
-    """Energies and gradients of independent circuits in one persistent launch."""
+class BatchHandle:
+    """Many independent circuits evaluated together (batch_create / batch_grad)."""
+
+    def __init__(self, circs: Sequence[CircuitHandle], obss: Sequence[Observable], dtype: int = C64):
+        n = len(circs)
+        ch = (ctypes.c_void_p * n)(*[c.handle for c in circs])
+        oh = (ctypes.c_void_p * n)(*[o.handle for o in obss])
+        h = ctypes.c_void_p()
+        _abi.check(_abi.lib().batch_create(ch, oh, n, dtype, ctypes.byref(h)))
+        self.handle = h.value
+        self._keep = (list(circs), list(obss))   # the batch points at these handles
+        self.n_params = [c.n_params for c in circs]
+        self.total = sum(self.n_params)
+
+    def grad(self, thetas, stream=None, out=None):
+        """Energies and gradients.  Host input (list of arrays or one concatenated array)
+        returns (numpy energies, list of numpy gradients); a CUDA float64 tensor of all
+        parameters returns device tensors (energies, concatenated gradients)."""
+        n = len(self.n_params)
+        if _is_cuda_tensor(thetas):
+            import torch
+            t = thetas.detach().to(torch.float64).contiguous()
+            if out is None:
+                e = torch.empty(n, dtype=torch.float64, device=t.device)
+                g = torch.empty(max(1, self.total), dtype=torch.float64, device=t.device)
+            else:
+                e, g = out
+            s = _stream_ptr(stream if stream is not None else torch.cuda.current_stream(t.device))
+            _abi.check(_abi.lib().batch_grad(self.handle, t.data_ptr(), t.numel(), _abi.PTR_DEVICE, s,
+                                             e.data_ptr(), g.data_ptr()))
+            return e, g
+        if isinstance(thetas, np.ndarray) and thetas.ndim == 1:
+            th = np.ascontiguousarray(thetas, dtype=np.float64)
+        else:
+            th = np.ascontiguousarray(np.concatenate([np.asarray(t, dtype=np.float64).reshape(-1)
+                                                      for t in thetas]) if n else np.zeros(0))
+        e = np.zeros(n)
+        g = np.zeros(max(1, self.total))
+        _abi.check(_abi.lib().batch_grad(self.handle, th.ctypes.data if th.size else None, th.size,
+                                         _abi.PTR_HOST, _stream_ptr(stream), e.ctypes.data, g.ctypes.data))
+        out_g, off = [], 0
+        for k in self.n_params:
+            out_g.append(g[off:off + k].copy())
+            off += k
+        return e, out_g
+
+    def free(self):
+        if self.handle:
+            _abi.lib().batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def batch_create(circs, obss, dtype: int = C64) -> BatchHandle:
+    return BatchHandle(circs, obss, dtype)
+
+
+def grad_batch(circs: Sequence[CircuitHandle], obss: Sequence[Observable], thetas, stream=None):
+    """One-shot batched energies and gradients (complex64); see BatchHandle for reuse."""
     n = len(circs)
     ch = (ctypes.c_void_p * n)(*[c.handle for c in circs])
     oh = (ctypes.c_void_p * n)(*[o.handle for o in obss])

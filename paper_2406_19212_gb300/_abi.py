@@ -94,6 +94,9 @@ def lib() -> ctypes.CDLL:
                          ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
         "expect_noalloc": [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Pauli), ctypes.c_int, vp, vp],
         "grad_batch": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, dp, vp, dp, dp],
+        "batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)],
+        "batch_free": [vp],
+        "batch_grad": [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -112,7 +115,8 @@ def exported_symbols() -> List[str]:
     return ["gbvqc_last_error", "gbvqc_version", "sv_alloc", "sv_wrap", "sv_free", "sv_reset",
             "sv_set", "sv_get", "sv_info", "circuit_create", "circuit_free", "circuit_set_tiling",
             "circuit_plan_info", "circuit_plan_stats", "apply_circuit", "apply_channel", "obs_create", "obs_free",
-            "expect", "grad", "grad_profile", "grad_batch", "expect_noalloc"]
+            "expect", "grad", "grad_profile", "grad_batch", "batch_create", "batch_free",
+            "batch_grad", "expect_noalloc"]
 
 
 # ------------------------------------------------------------------ marshalling

@@ -76,6 +76,17 @@ struct FusedDev {
     const MatUnit *units;
     const MatRec *recs;
 };
+// Arguments of one tile pass of one circuit.
+struct FusedArgs {
+    const PassDesc *pd;
+    const SubRun *subs;
+    const FGate *gates;
+    const DEnt *ents;
+    const MatUnit *units;
+    const MatRec *recs;
+    double *slot_partials;
+    int tiles_stride;
+};
 int fused_nr(int dtype, bool reverse);           // register qubits per sub-run
 cudaError_t fused_prepare();                     // shared-memory opt-in, outside capture
 cudaError_t launch_fused_forward(int dtype, void *psi, const FusedDev &fd, int pass,
@@ -86,5 +97,43 @@ cudaError_t launch_fused_reverse(int dtype, void *phi, void *psi, const FusedDev
 // slot_grad[s] = sum_tile slot_partials[s * stride + tile], tiles in index order.
 cudaError_t launch_reduce_slots(const double *slot_partials, int n_slots, int n_tiles,
                                 int stride, double *slot_grad, cudaStream_t s);
+
+// ---- batched kernels (kernels_batch.cu): one launch covers many circuits; CTA c
+// belongs to the last entry whose `begin` is <= c.
+struct FusedBatchEntry {
+    FusedArgs args;
+    void *phi, *psi;
+    int64_t begin;           // first CTA (tile) of this circuit in the launch
+};
+constexpr int kPauliChunkBits = 12;  // amplitudes per CTA of the batched expectation
+struct PauliBatchEntry {
+    const void *psi;
+    void *lam;
+    ObsDev obs;
+    double *partials;        // one per chunk
+    int n;                   // qubits
+    int pad;
+    int64_t begin;           // first CTA (chunk)
+};
+struct SlotBatchEntry {
+    const double *partials;  // [slot][tile]
+    int n_tiles;
+    int pad;
+    int64_t begin;           // first global slot of this circuit
+};
+struct BatchDyn {            // theta-dependent record of a batch member
+    MatRec *rec;
+    int theta_index;         // into the concatenated parameter vector
+    int rot, variant, domain;
+};
+cudaError_t fused_batch_prepare();
+cudaError_t launch_fused_batch(int dtype, bool reverse, bool two_q, int t, const FusedBatchEntry *entries,
+                               int n_entries, int64_t total_tiles, size_t smem, cudaStream_t s);
+cudaError_t launch_pauli_batch(int dtype, const PauliBatchEntry *entries, int n_entries, int64_t total_chunks,
+                               double *energies, cudaStream_t s);
+cudaError_t launch_slots_batch(const SlotBatchEntry *entries, int n_entries, int64_t total_slots,
+                               double *slot_grad, cudaStream_t s);
+cudaError_t launch_batch_init(const BatchDyn *dyn, int n_dyn, const double *theta, int dtype, void *phi_all,
+                              size_t phi_bytes, const int64_t *offsets, int n_inst, cudaStream_t s);
 
 }  // namespace gbvqc

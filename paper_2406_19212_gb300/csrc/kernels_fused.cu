@@ -1,666 +1,17 @@
-// Fused tile passes: one HBM read and one write of the state apply a whole run of gates.
-//
-// A pass names a set S of t "tile" qubits (the lowest `low` qubits are always in S, so
-// every tile is made of contiguous 2^low-amplitude segments).  CTA i owns the 2^t
-// amplitudes whose non-tile bits spell i, stages them in shared memory together with
-// the pass's gate records and matrices, applies the gates and writes the tile back.
-// Inside the tile, gates run in "sub-runs": each sub-run names NR tile positions that
-// every thread gathers into registers (2^NR amplitudes per thread), applies all of the
-// sub-run's gates on them with no further memory traffic, and scatters back.
-//
-// Diagonal gates need no register position: a run of them is applied as one phase per
-// amplitude, the product of a per-CTA constant (tile-index bits), a per-thread constant
-// (tile bits outside the registers) and tables over the register bits built by doubling.
-//
-// This is the GPU counterpart of the paper's gate fusion for compute density (Sec. III.B,
-// citing gate fusion) and of its aggregation of independent amplitude groups (Fig. 3):
-// the 2^low contiguous amplitudes of a segment play the role of the paper's
-// vectorisable inner dimension.
-//
-// The reverse variant (Algorithm 2) carries Phi and Psi tiles together: for every gate
-// in reverse order it accumulates the gradient term coef * Im <Psi|P|Phi> of the gate's
-// Pauli generator P (dQ/dtheta = -i/2 P Q for Q = exp(-i theta P/2), so
-// 2 Re <Psi|dQ|Phi_{j-1}> = Im <Psi|P|Phi_j>), then uncomputes Phi with Q^{-1} and Psi
-// with Q^dag.  In a diagonal run every Z generator is read from the states after the
-// whole run (diagonal matrices commute with Z).  Per-thread partials over 2^NR terms
-// are summed across the warp with shuffles (FP32 for complex64, FP64 for complex128) and
-// across warps in FP64 in fixed order, giving one FP64 partial per (gradient slot, tile).
-#include "devmath.cuh"
-#include "kernels.h"
+// Fused tile-pass kernels of one circuit (one CTA per tile) and their launchers.  The
+// tile-pass body lives in fused_tile.cuh.
+#include "fused_tile.cuh"
 
 namespace gbvqc {
-
-template <typename R> struct SwzBits;
-template <> struct SwzBits<float> { static constexpr int B = 4; };   // 16 x 8 B = 128 B
-template <> struct SwzBits<double> { static constexpr int B = 3; };  // 8 x 16 B = 128 B
-
-// XOR swizzle of the shared-memory slot of local amplitude l: folds bits [B, 2B) onto
-// bits [0, B) so strided register gathers spread over all banks.
-template <typename R>
-__device__ __forceinline__ int swz(int l)
-{
-    constexpr int B = SwzBits<R>::B;
-    return l ^ ((l >> B) & ((1 << B) - 1));
-}
-
-// --------------------------------------------------------------- register-slot gates
-
-template <typename R, int NR, int K, int SH>
-__device__ __forceinline__ void rg1(typename CT<R>::T *a, const R *m)
-{
-#pragma unroll
-    for (int j = 0; j < (1 << NR); j++)
-        if (!(j & (1 << K))) apply2<R, SH>(m, a[j], a[j | (1 << K)]);
-}
-
-template <typename R, int NR, int SH>
-__device__ __forceinline__ void rg1_dispatch(int k, typename CT<R>::T *a, const R *m)
-{
-#define GBVQC_RG1(K) \
-    case K:          \
-        if constexpr (K < NR) rg1<R, NR, K, SH>(a, m); \
-        break;
-    switch (k) {
-        GBVQC_RG1(0) GBVQC_RG1(1) GBVQC_RG1(2) GBVQC_RG1(3) GBVQC_RG1(4) GBVQC_RG1(5)
-    }
-#undef GBVQC_RG1
-}
-
-// Two-qubit gate on register slots (K0 = matrix bit 0, K1 = matrix bit 1).
-template <typename R, int NR, int K0, int K1, int SH>
-__device__ __forceinline__ void rg2(typename CT<R>::T *a, const R *m, int perm)
-{
-    typedef typename CT<R>::T T;
-#pragma unroll
-    for (int j = 0; j < (1 << NR); j++) {
-        if (j & ((1 << K0) | (1 << K1))) continue;
-        const int i1 = j | (1 << K0), i2 = j | (1 << K1), i3 = j | (1 << K0) | (1 << K1);
-        if (SH == SH_CTRL2) {
-            R u[8] = {m[10], m[11], m[14], m[15], m[26], m[27], m[30], m[31]};
-            apply2<R, SH_DENSE1>(u, a[i1], a[i3]);
-            continue;
-        }
-        T v[4] = {a[j], a[i1], a[i2], a[i3]}, w[4];
-        if (SH == SH_DENSE2) {
-#pragma unroll
-            for (int r = 0; r < 4; r++) {
-                T acc = cmul<T, R>(m[8 * r], m[8 * r + 1], v[0]);
-#pragma unroll
-                for (int c = 1; c < 4; c++) cfma<T, R>(m[8 * r + 2 * c], m[8 * r + 2 * c + 1], v[c], acc);
-                w[r] = acc;
-            }
-        } else {  // SH_PERM2
-#pragma unroll
-            for (int r = 0; r < 4; r++) {
-                const int c = (perm >> (2 * r)) & 3;
-                T x = c == 0 ? v[0] : c == 1 ? v[1] : c == 2 ? v[2] : v[3];
-                R mr = m[8 * r + 2 * c], mi = m[8 * r + 2 * c + 1];
-                w[r] = cmul<T, R>(mr, mi, x);
-            }
-        }
-        a[j] = w[0];
-        a[i1] = w[1];
-        a[i2] = w[2];
-        a[i3] = w[3];
-    }
-}
-
-template <typename R, int NR, int SH>
-__device__ __forceinline__ void rg2_dispatch(int k0, int k1, typename CT<R>::T *a, const R *m, int perm)
-{
-#define GBVQC_RG2(K0, K1) \
-    case K0 * 8 + K1:     \
-        if constexpr (K0 < NR && K1 < NR) rg2<R, NR, K0, K1, SH>(a, m, perm); \
-        break;
-    switch (k0 * 8 + k1) {
-        GBVQC_RG2(0, 1) GBVQC_RG2(0, 2) GBVQC_RG2(0, 3) GBVQC_RG2(0, 4)
-        GBVQC_RG2(1, 0) GBVQC_RG2(1, 2) GBVQC_RG2(1, 3) GBVQC_RG2(1, 4)
-        GBVQC_RG2(2, 0) GBVQC_RG2(2, 1) GBVQC_RG2(2, 3) GBVQC_RG2(2, 4)
-        GBVQC_RG2(3, 0) GBVQC_RG2(3, 1) GBVQC_RG2(3, 2) GBVQC_RG2(3, 4)
-        GBVQC_RG2(4, 0) GBVQC_RG2(4, 1) GBVQC_RG2(4, 2) GBVQC_RG2(4, 3)
-    }
-#undef GBVQC_RG2
-}
-
-// Bit of a non-register position code (constant over the thread's amplitudes).
-template <int NR>
-__device__ __forceinline__ int const_bit(int code, int base, int64_t tilebase)
-{
-    if (code < 0) return (int)((tilebase >> (-1 - code)) & 1);
-    return (base >> (code - NR)) & 1;
-}
-
-// Bit of a position code for register amplitude j (j compile-time after unrolling).
-template <int NR>
-__device__ __forceinline__ int code_bit(int code, int j, int base, int64_t tilebase)
-{
-    if (code >= 0 && code < NR) return (j >> code) & 1;
-    return const_bit<NR>(code, base, tilebase);
-}
-
-// Diagonal one-qubit gate on a position code.
-template <typename R, int NR>
-__device__ __forceinline__ void dg1(typename CT<R>::T *a, const R *m, int code, int base,
-                                    int64_t tilebase)
-{
-    typedef typename CT<R>::T T;
-    if (code >= 0 && code < NR) {
-        rg1_dispatch<R, NR, SH_DIAG1>(code, a, m);
-        return;
-    }
-    const int bit = const_bit<NR>(code, base, tilebase);
-    const R pr = bit ? m[6] : m[0], pi = bit ? m[7] : m[1];
-#pragma unroll
-    for (int j = 0; j < (1 << NR); j++) cmul_ip<T, R>(pr, pi, a[j]);
-}
-
-// Diagonal two-qubit gate on two position codes (matrix bit 0 = code ca).
-template <typename R, int NR>
-__device__ __forceinline__ void dg2(typename CT<R>::T *a, const R *m, int ca, int cb, int base,
-                                    int64_t tilebase)
-{
-    typedef typename CT<R>::T T;
-    const R p0r = m[0], p0i = m[1], p1r = m[10], p1i = m[11];
-    const R p2r = m[20], p2i = m[21], p3r = m[30], p3i = m[31];
-#pragma unroll
-    for (int j = 0; j < (1 << NR); j++) {
-        const int idx = code_bit<NR>(ca, j, base, tilebase) | (code_bit<NR>(cb, j, base, tilebase) << 1);
-        const R pr = idx == 0 ? p0r : idx == 1 ? p1r : idx == 2 ? p2r : p3r;
-        const R pi = idx == 0 ? p0i : idx == 1 ? p1i : idx == 2 ? p2i : p3i;
-        cmul_ip<T, R>(pr, pi, a[j]);
-    }
-}
-
-// Non-diagonal gate on register slots.  Kernels compiled without TWOQ never see
-// two-qubit gates (the planner flags every pass that holds one), which keeps their
-// code paths out of the common one-qubit loop.
-template <typename R, int NR, bool TWOQ>
-__device__ __forceinline__ void apply_fgate(int type, int ga, int gb, int perm, const R *m,
-                                            typename CT<R>::T *a)
-{
-    switch (type) {
-    case FT_DENSE1: rg1_dispatch<R, NR, SH_DENSE1>(ga, a, m); break;
-    case FT_REAL1: rg1_dispatch<R, NR, SH_REAL1>(ga, a, m); break;
-    case FT_ANTI1: rg1_dispatch<R, NR, SH_ANTI1>(ga, a, m); break;
-    default:
-        if constexpr (TWOQ) {
-            switch (type) {
-            case FT_DENSE2: rg2_dispatch<R, NR, SH_DENSE2>(ga, gb, a, m, 0); break;
-            case FT_PERM2: rg2_dispatch<R, NR, SH_PERM2>(ga, gb, a, m, perm); break;
-            default: rg2_dispatch<R, NR, SH_CTRL2>(ga, gb, a, m, 0); break;
-            }
-        }
-        break;
-    }
-}
-
-// ------------------------------------------------------------- diagonal phase blocks
-
-// Element r of the diagonal of a k-qubit matrix staged as 2x2 (one unit) or 4x4 (four).
-template <typename R>
-__device__ __forceinline__ void diag_elem(const R *m, int k, int r, R &re, R &im)
-{
-    const int o = k == 1 ? 6 * r : 10 * r;
-    re = m[o];
-    im = m[o + 1];
-}
-
-template <typename R>
-__device__ __forceinline__ void cmul_inplace(R &xr, R &xi, R yr, R yi)
-{
-    R t = xr * yr - xi * yi;
-    xi = xr * yi + xi * yr;
-    xr = t;
-}
-
-// Factor pairs (f0, f1) of the register bits: the phase of register amplitude j is the
-// product over bits k of f_{bit k of j}[k].
-template <typename R, int NR>
-struct RegPairs {
-    R p0r[NR], p0i[NR], p1r[NR], p1i[NR];
-    __device__ __forceinline__ void init()
-    {
-#pragma unroll
-        for (int k = 0; k < NR; k++) {
-            p0r[k] = 1; p0i[k] = 0; p1r[k] = 1; p1i[k] = 0;
-        }
-    }
-    // multiply (e0, e1) into register bit k (k uniform; one case runs)
-    __device__ __forceinline__ void mul(int k, R e0r, R e0i, R e1r, R e1i)
-    {
-#define GBVQC_PM(K)                                              \
-    case K:                                                      \
-        if constexpr (K < NR) {                                  \
-            cmul_inplace<R>(p0r[K], p0i[K], e0r, e0i);           \
-            cmul_inplace<R>(p1r[K], p1i[K], e1r, e1i);           \
-        }                                                        \
-        break;
-        switch (k) { GBVQC_PM(0) GBVQC_PM(1) GBVQC_PM(2) GBVQC_PM(3) GBVQC_PM(4) GBVQC_PM(5) }
-#undef GBVQC_PM
-    }
-};
-
-// a[j] *= c (or -a[j] for NEG) on the register amplitudes whose bits K0 and K1 are both 1.
-template <typename R, int NR, int K0, int K1, bool NEG>
-__device__ __forceinline__ void cphase(typename CT<R>::T *a, R cr, R ci)
-{
-    typedef typename CT<R>::T T;
-#pragma unroll
-    for (int j = 0; j < (1 << NR); j++) {
-        if (!(((j >> K0) & 1) && ((j >> K1) & 1))) continue;
-        if (NEG) {
-            a[j].x = -a[j].x;
-            a[j].y = -a[j].y;
-        } else {
-            cmul_ip<T, R>(cr, ci, a[j]);
-        }
-    }
-}
-
-template <typename R, int NR, bool NEG>
-__device__ __forceinline__ void cphase_dispatch(int k0, int k1, typename CT<R>::T *a, R cr, R ci)
-{
-    const int lo = k0 < k1 ? k0 : k1, hi = k0 < k1 ? k1 : k0;
-#define GBVQC_CP(L, H) \
-    case L * 8 + H:    \
-        if constexpr (H < NR) cphase<R, NR, L, H, NEG>(a, cr, ci); \
-        break;
-    switch (lo * 8 + hi) {
-        GBVQC_CP(0, 1) GBVQC_CP(0, 2) GBVQC_CP(0, 3) GBVQC_CP(0, 4) GBVQC_CP(1, 2)
-        GBVQC_CP(1, 3) GBVQC_CP(1, 4) GBVQC_CP(2, 3) GBVQC_CP(2, 4) GBVQC_CP(3, 4)
-    }
-#undef GBVQC_CP
-}
-
-template <typename R>
-__device__ __forceinline__ void cdiv(R ar, R ai, R br, R bi, R &qr, R &qi)
-{
-    const R inv = R(1) / (br * br + bi * bi);
-    qr = (ar * br + ai * bi) * inv;
-    qi = (ai * br - ar * bi) * inv;
-}
-
-// Apply one phase block to a (and b, if given).  `ents` points after the Z entries; the
-// tile-constant entries (the first nt) are already folded into (c0r, c0i).  The phase
-// of register amplitude j is c * TL[j & lo] * TH[j >> H] with c the product of the
-// tile-constant and thread-local entries and TL, TH tables over the low and high halves
-// of the register bits built by doubling from the factor pairs; PAIR entries are split
-// into factor pairs d0 (1, d1/d0) (1, d2/d0) and the controlled phase d3 d0 / (d1 d2).
-template <typename R, int NR>
-__device__ __forceinline__ void phase_block(const DEnt *ents, int counts, const R *smat, bool second,
-                                            R c0r, R c0i, typename CT<R>::T *a, typename CT<R>::T *b,
-                                            int base, int64_t tilebase)
-{
-    typedef typename CT<R>::T T;
-    constexpr int H = NR / 2;
-    const int nt = counts & 255, nl = (counts >> 8) & 255, nr = (counts >> 16) & 255, np = (counts >> 24) & 255;
-    const DEnt *e = ents + nt;
-    R cr = c0r, ci = c0i;
-    for (int i = 0; i < nl; i++, e++) {  // thread-local constants
-        const R *m = smat + 8 * (second ? e->mat2 : e->mat);
-        const int idx = e->k == 1 ? const_bit<NR>(e->ca, base, tilebase)
-                                  : const_bit<NR>(e->ca, base, tilebase) | (const_bit<NR>(e->cb, base, tilebase) << 1);
-        R er, ei;
-        diag_elem<R>(m, e->k, idx, er, ei);
-        cmul_inplace<R>(cr, ci, er, ei);
-    }
-    RegPairs<R, NR> P;
-    P.init();
-    for (int i = 0; i < nr; i++, e++) {  // one register bit
-        const R *m = smat + 8 * (second ? e->mat2 : e->mat);
-        R e0r, e0i, e1r, e1i;
-        int k;
-        if (e->k == 1) {
-            k = e->ca;
-            diag_elem<R>(m, 1, 0, e0r, e0i);
-            diag_elem<R>(m, 1, 1, e1r, e1i);
-        } else {
-            const bool ra = e->ca >= 0 && e->ca < NR;
-            k = ra ? e->ca : e->cb;
-            const int cbit = ra ? const_bit<NR>(e->cb, base, tilebase) : const_bit<NR>(e->ca, base, tilebase);
-            diag_elem<R>(m, 2, ra ? 2 * cbit : cbit, e0r, e0i);
-            diag_elem<R>(m, 2, ra ? 1 + 2 * cbit : cbit + 2, e1r, e1i);
-        }
-        P.mul(k, e0r, e0i, e1r, e1i);
-    }
-    for (int i = 0; i < np; i++, e++) {  // two register bits
-        if (e->cls == DC_PAIR_CZ) {
-            cphase_dispatch<R, NR, true>(e->ca, e->cb, a, R(0), R(0));
-            if (b) cphase_dispatch<R, NR, true>(e->ca, e->cb, b, R(0), R(0));
-            continue;
-        }
-        const R *m = smat + 8 * (second ? e->mat2 : e->mat);
-        R d0r, d0i, d1r, d1i, d2r, d2i, d3r, d3i;
-        diag_elem<R>(m, 2, 0, d0r, d0i);
-        diag_elem<R>(m, 2, 1, d1r, d1i);
-        diag_elem<R>(m, 2, 2, d2r, d2i);
-        diag_elem<R>(m, 2, 3, d3r, d3i);
-        R qr, qi;
-        cmul_inplace<R>(cr, ci, d0r, d0i);
-        cdiv<R>(d1r, d1i, d0r, d0i, qr, qi);
-        P.mul(e->ca, R(1), R(0), qr, qi);
-        cdiv<R>(d2r, d2i, d0r, d0i, qr, qi);
-        P.mul(e->cb, R(1), R(0), qr, qi);
-        R nr_ = d3r, ni_ = d3i, dr_ = d1r, di_ = d1i;
-        cmul_inplace<R>(nr_, ni_, d0r, d0i);
-        cmul_inplace<R>(dr_, di_, d2r, d2i);
-        cdiv<R>(nr_, ni_, dr_, di_, qr, qi);
-        cphase_dispatch<R, NR, false>(e->ca, e->cb, a, qr, qi);
-        if (b) cphase_dispatch<R, NR, false>(e->ca, e->cb, b, qr, qi);
-    }
-    R lr[1 << H], li[1 << H], hr[1 << (NR - H)], hi[1 << (NR - H)];
-    lr[0] = 1;
-    li[0] = 0;
-#pragma unroll
-    for (int k = 0; k < H; k++) {
-#pragma unroll
-        for (int j = 0; j < (1 << k); j++) {
-            lr[j | (1 << k)] = lr[j] * P.p1r[k] - li[j] * P.p1i[k];
-            li[j | (1 << k)] = lr[j] * P.p1i[k] + li[j] * P.p1r[k];
-            R x = lr[j] * P.p0r[k] - li[j] * P.p0i[k];
-            li[j] = lr[j] * P.p0i[k] + li[j] * P.p0r[k];
-            lr[j] = x;
-        }
-    }
-    hr[0] = cr;
-    hi[0] = ci;
-#pragma unroll
-    for (int k = 0; k < NR - H; k++) {
-#pragma unroll
-        for (int j = 0; j < (1 << k); j++) {
-            hr[j | (1 << k)] = hr[j] * P.p1r[H + k] - hi[j] * P.p1i[H + k];
-            hi[j | (1 << k)] = hr[j] * P.p1i[H + k] + hi[j] * P.p1r[H + k];
-            R x = hr[j] * P.p0r[H + k] - hi[j] * P.p0i[H + k];
-            hi[j] = hr[j] * P.p0i[H + k] + hi[j] * P.p0r[H + k];
-            hr[j] = x;
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < (1 << NR); j++) {
-        const int jl = j & ((1 << H) - 1), jh = j >> H;
-        const R pr = lr[jl] * hr[jh] - li[jl] * hi[jh], pi = lr[jl] * hi[jh] + li[jl] * hr[jh];
-        cmul_ip<T, R>(pr, pi, a[j]);
-        if (b) cmul_ip<T, R>(pr, pi, b[j]);
-    }
-}
-
-// ------------------------------------------------------------ generator inner products
-
-// Im <Psi| P_K |Phi> over the thread's register amplitudes, P = X or Y on slot K.
-template <typename R, int NR, int K, int G>
-__device__ __forceinline__ R gen_xy(const typename CT<R>::T *f, const typename CT<R>::T *p)
-{
-    R s = 0;
-#pragma unroll
-    for (int j = 0; j < (1 << NR); j++) {
-        if (j & (1 << K)) continue;
-        const int j1 = j | (1 << K);
-        if (G == GEN_X) {  // Im(conj(p0) f1 + conj(p1) f0)
-            s += (p[j].x * f[j1].y - p[j].y * f[j1].x) + (p[j1].x * f[j].y - p[j1].y * f[j].x);
-        } else {           // Re(conj(p1) f0) - Re(conj(p0) f1)
-            s += (p[j1].x * f[j].x + p[j1].y * f[j].y) - (p[j].x * f[j1].x + p[j].y * f[j1].y);
-        }
-    }
-    return s;
-}
-
-template <typename R, int NR, int G>
-__device__ __forceinline__ R gen_xy_dispatch(int k, const typename CT<R>::T *f, const typename CT<R>::T *p)
-{
-#define GBVQC_GXY(K) \
-    case K:          \
-        if constexpr (K < NR) return gen_xy<R, NR, K, G>(f, p); \
-        break;
-    switch (k) {
-        GBVQC_GXY(0) GBVQC_GXY(1) GBVQC_GXY(2) GBVQC_GXY(3) GBVQC_GXY(4) GBVQC_GXY(5)
-    }
-#undef GBVQC_GXY
-    return 0;
-}
-
-struct RedCtx {
-    double *sgrad;
-    int slot_begin, nwarps, warp, lane, lanes;
-    unsigned lanemask;
-};
-
-// Sum a per-thread partial over the warp (shuffles in the state's precision: FP32 for
-// complex64, FP64 for complex128) and store it for its slot.
-template <typename R>
-__device__ __forceinline__ void emit_partial(const RedCtx &c, int slot, R v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        if (o < c.lanes) v += __shfl_xor_sync(c.lanemask, v, o);
-    if (c.lane == 0) c.sgrad[(slot - c.slot_begin) * c.nwarps + c.warp] = (double)v;
-}
-
-// ----------------------------------------------------------------------- the kernel
-
-struct FusedArgs {
-    const PassDesc *pd;
-    const SubRun *subs;
-    const FGate *gates;
-    const DEnt *ents;
-    const MatUnit *units;
-    const MatRec *recs;
-    double *slot_partials;
-    int tiles_stride;
-};
-
-template <typename R>
-__device__ __forceinline__ void tile_io(typename CT<R>::T *gmem, typename CT<R>::T *sm, int t, int low,
-                                        int64_t tilebase, const int64_t *hitab, bool load)
-{
-    typedef typename CT<R>::T T;
-    const int L = 1 << t, lowmask = (1 << low) - 1;
-    if constexpr (sizeof(T) == 8) {  // complex64: two amplitudes per 16-byte access
-        for (int v = threadIdx.x; v < (L >> 1); v += blockDim.x) {
-            const int l = v << 1;
-            const int64_t g = tilebase | hitab[l >> low] | (l & lowmask);
-            float4 *p = reinterpret_cast<float4 *>(gmem + g);
-            float2 *s = reinterpret_cast<float2 *>(sm);
-            if (load) {
-                float4 x = *p;
-                s[swz<R>(l)] = make_float2(x.x, x.y);
-                s[swz<R>(l + 1)] = make_float2(x.z, x.w);
-            } else {
-                float2 a = s[swz<R>(l)], b = s[swz<R>(l + 1)];
-                *p = make_float4(a.x, a.y, b.x, b.y);
-            }
-        }
-    } else {
-        for (int l = threadIdx.x; l < L; l += blockDim.x) {
-            const int64_t g = tilebase | hitab[l >> low] | (l & lowmask);
-            if (load) sm[swz<R>(l)] = gmem[g];
-            else gmem[g] = sm[swz<R>(l)];
-        }
-    }
-}
-
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // Forward kernels run 2^(t-NR) <= 128 threads (three CTAs per SM), reverse kernels
 // <= 256 threads (two CTAs per SM).
 template <typename R, int NR, bool REV, bool TWOQ>
 __global__ void __launch_bounds__(REV ? 256 : 128, REV ? 2 : 3) k_fused(typename CT<R>::T *__restrict__ phi,
-                                                  typename CT<R>::T *__restrict__ psi, FusedArgs args)
+                                                                        typename CT<R>::T *__restrict__ psi,
+                                                                        FusedArgs args)
 {
-    typedef typename CT<R>::T T;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const PassDesc &pd = *args.pd;
-    const int t = pd.t, n = pd.n, low = pd.low;
-    const int L = 1 << t;
-    const int nhi = 1 << (t - low);
-    const int lanes = blockDim.x < 32 ? blockDim.x : 32;
-    const int nwarps = (blockDim.x + 31) >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned lanemask = lanes == 32 ? 0xffffffffu : ((1u << lanes) - 1u);
-
-    unsigned char *p = smem;
-    T *sphi = reinterpret_cast<T *>(p);
-    p += align16((size_t)(REV ? 2 : 1) * L * sizeof(T));
-    T *spsi = sphi + (REV ? L : 0);
-    int64_t *hitab = reinterpret_cast<int64_t *>(p);
-    p += align16(sizeof(int64_t) * nhi);
-    double *sgrad = reinterpret_cast<double *>(p);
-    if (REV) p += align16(sizeof(double) * (size_t)pd.n_slots * nwarps);
-    FGate *sgates = reinterpret_cast<FGate *>(p);
-    p += align16(sizeof(FGate) * (size_t)pd.n_gates);
-    DEnt *sents = reinterpret_cast<DEnt *>(p);
-    p += align16(sizeof(DEnt) * (size_t)pd.n_ent);
-    R *sconst = reinterpret_cast<R *>(p);  // per phase block: tile-constant products (Phi, Psi)
-    p += align16((size_t)4 * sizeof(R) * pd.n_blocks);
-    R *smat = reinterpret_cast<R *>(p);
-
-    const int64_t tile = blockIdx.x;
-    int64_t tilebase = 0;
-    for (int i = 0; i < n - t; i++)
-        if ((tile >> i) & 1) tilebase |= int64_t(1) << pd.NS[i];
-    for (int h = threadIdx.x; h < nhi; h += blockDim.x) {
-        int64_t o = 0;
-        for (int i = 0; i < t - low; i++)
-            if ((h >> i) & 1) o |= int64_t(1) << pd.S[low + i];
-        hitab[h] = o;
-    }
-    // stage the pass's gates, diagonal entries and matrices
-    {
-        const int4 *src = reinterpret_cast<const int4 *>(args.gates + pd.gate_begin);
-        int4 *dst = reinterpret_cast<int4 *>(sgates);
-        for (int i = threadIdx.x; i < pd.n_gates * 2; i += blockDim.x) dst[i] = src[i];
-        const int4 *esrc = reinterpret_cast<const int4 *>(args.ents + pd.ent_begin);
-        int4 *edst = reinterpret_cast<int4 *>(sents);
-        for (int i = threadIdx.x; i < pd.n_ent; i += blockDim.x) edst[i] = esrc[i];
-        for (int i = threadIdx.x; i < pd.n_units * 8; i += blockDim.x) {
-            const MatUnit u = args.units[pd.unit_begin + (i >> 3)];
-            smat[i] = mat_of<R>(&args.recs[u.rec])[8 * u.part + (i & 7)];
-        }
-    }
-    if (REV)
-        for (int i = threadIdx.x; i < pd.n_slots * nwarps; i += blockDim.x) sgrad[i] = 0.0;
-    __syncthreads();
-    // tile-constant phase products of every phase block (bits fixed by the tile index)
-    for (int gi = threadIdx.x; gi < pd.n_gates; gi += blockDim.x) {
-        const FGate g = sgates[gi];
-        if (g.type != FT_DIAGB) continue;
-        const DEnt *e = sents + g.ent + g.nz;
-        R r0 = 1, i0 = 0, r1 = 1, i1 = 0;
-        for (int i = 0; i < (g.perm & 255); i++, e++) {
-            const int idx = e->k == 1 ? (int)((tilebase >> (-1 - e->ca)) & 1)
-                                      : (int)((tilebase >> (-1 - e->ca)) & 1) | ((int)((tilebase >> (-1 - e->cb)) & 1) << 1);
-            R er, ei;
-            diag_elem<R>(smat + 8 * e->mat, e->k, idx, er, ei);
-            cmul_inplace<R>(r0, i0, er, ei);
-            diag_elem<R>(smat + 8 * e->mat2, e->k, idx, er, ei);
-            cmul_inplace<R>(r1, i1, er, ei);
-        }
-        sconst[4 * g.slot] = r0;
-        sconst[4 * g.slot + 1] = i0;
-        sconst[4 * g.slot + 2] = r1;
-        sconst[4 * g.slot + 3] = i1;
-    }
-    tile_io<R>(phi, sphi, t, low, tilebase, hitab, true);
-    if (REV) tile_io<R>(psi, spsi, t, low, tilebase, hitab, true);
-    __syncthreads();
-
-    RedCtx rc{sgrad, pd.slot_begin, nwarps, warp, lane, lanes, lanemask};
-    T a[1 << NR], b[REV ? (1 << NR) : 1];
-    for (int s = 0; s < pd.n_sub; s++) {
-        const SubRun sr = args.subs[pd.sub_begin + s];
-        // thread bits -> tile positions outside R, ascending
-        int rmask = 0;
-#pragma unroll
-        for (int k = 0; k < NR; k++) rmask |= 1 << sr.R[k];
-        int base = 0;
-        for (int q = 0, i = 0; q < t; q++) {
-            if ((rmask >> q) & 1) continue;
-            if ((threadIdx.x >> i) & 1) base |= 1 << q;
-            i++;
-        }
-        int off[NR];
-#pragma unroll
-        for (int k = 0; k < NR; k++) off[k] = 1 << sr.R[k];
-#pragma unroll
-        for (int j = 0; j < (1 << NR); j++) {
-            int l = base;
-#pragma unroll
-            for (int k = 0; k < NR; k++)
-                if ((j >> k) & 1) l |= off[k];
-            a[j] = sphi[swz<R>(l)];
-            if constexpr (REV) b[j] = spsi[swz<R>(l)];
-        }
-        FGate gn = sgates[sr.g_begin < sr.g_end ? sr.g_begin : 0];
-        for (int gi = sr.g_begin; gi < sr.g_end; gi++) {
-            const FGate g = gn;
-            if (gi + 1 < sr.g_end) gn = sgates[gi + 1];  // prefetch the next record
-            if (g.type == FT_DIAGB) {
-                const DEnt *ents = sents + g.ent;
-                const R *cst = sconst + 4 * g.slot;
-                if constexpr (REV) {
-                    if (g.nz > 0) {  // Z generators on the states after the block
-                        R tot = 0, dk[NR];
-#pragma unroll
-                        for (int k = 0; k < NR; k++) dk[k] = 0;
-#pragma unroll
-                        for (int j = 0; j < (1 << NR); j++) {
-                            const R v = b[j].x * a[j].y - b[j].y * a[j].x;  // Im(conj(Psi) Phi)
-                            tot += v;
-#pragma unroll
-                            for (int k = 0; k < NR; k++) dk[k] += ((j >> k) & 1) ? -v : v;
-                        }
-                        for (int e = 0; e < g.nz; e++) {
-                            const DEnt d = ents[e];
-                            R part;
-                            if (d.ca >= 0 && d.ca < NR) {
-                                part = dk[0];
-#pragma unroll
-                                for (int k = 1; k < NR; k++)
-                                    if (k == d.ca) part = dk[k];
-                            } else {
-                                part = const_bit<NR>(d.ca, base, tilebase) ? -tot : tot;
-                            }
-                            emit_partial<R>(rc, d.slot, part * (R)d.coef);
-                        }
-                    }
-                    if (g.flags & 1) {
-                        phase_block<R, NR>(ents + g.nz, g.perm, smat, false, cst[0], cst[1], a, nullptr, base, tilebase);
-                        phase_block<R, NR>(ents + g.nz, g.perm, smat, true, cst[2], cst[3], b, nullptr, base, tilebase);
-                    } else {
-                        phase_block<R, NR>(ents + g.nz, g.perm, smat, false, cst[0], cst[1], a, b, base, tilebase);
-                    }
-                } else {
-                    phase_block<R, NR>(ents, g.perm, smat, false, cst[0], cst[1], a, nullptr, base, tilebase);
-                }
-                continue;
-            }
-            if constexpr (REV) {
-                if (g.gen == GEN_X)
-                    emit_partial<R>(rc, g.slot, gen_xy_dispatch<R, NR, GEN_X>(g.gpos, a, b) * (R)g.coef);
-                else if (g.gen == GEN_Y)
-                    emit_partial<R>(rc, g.slot, gen_xy_dispatch<R, NR, GEN_Y>(g.gpos, a, b) * (R)g.coef);
-            }
-            apply_fgate<R, NR, TWOQ>(g.type, g.a, g.b, g.perm, smat + 8 * g.mat, a);
-            if constexpr (REV) apply_fgate<R, NR, TWOQ>(g.type, g.a, g.b, g.perm, smat + 8 * g.mat2, b);
-        }
-#pragma unroll
-        for (int j = 0; j < (1 << NR); j++) {
-            int l = base;
-#pragma unroll
-            for (int k = 0; k < NR; k++)
-                if ((j >> k) & 1) l |= off[k];
-            sphi[swz<R>(l)] = a[j];
-            if constexpr (REV) spsi[swz<R>(l)] = b[j];
-        }
-        __syncthreads();
-    }
-    tile_io<R>(phi, sphi, t, low, tilebase, hitab, false);
-    if (REV) {
-        tile_io<R>(psi, spsi, t, low, tilebase, hitab, false);
-        for (int sl = threadIdx.x; sl < pd.n_slots; sl += blockDim.x) {
-            double acc = 0.0;
-            for (int w = 0; w < nwarps; w++) acc += sgrad[sl * nwarps + w];
-            args.slot_partials[(int64_t)(pd.slot_begin + sl) * args.tiles_stride + tile] = acc;
-        }
-    }
+    fused_tile<R, NR, REV, TWOQ>(phi, psi, args, blockIdx.x);
 }
 
 // -------------------------------------------------------------------------- launchers

@@ -5,6 +5,7 @@
 // in FP64 above that; warp shuffles and a last-block-done pass make every sum a
 // deterministic FP64 tree.
 #include "kernels.h"
+#include "pauli.cuh"
 
 namespace gbvqc {
 
@@ -171,26 +172,6 @@ cudaError_t launch_dot_matrix(int dtype, const void *psi, const void *phi, int n
 }
 
 // ------------------------------------------------------------------- Pauli sums
-
-// c_g(b) = sum_{k in g} coeff_k i^{ph_k} (-1)^{popcount(b & z_k)}
-template <typename R>
-__device__ __forceinline__ void group_coeff(const ObsTerm *__restrict__ terms, int t0, int t1,
-                                            uint64_t b, R &cr, R &ci)
-{
-    cr = 0;
-    ci = 0;
-    for (int k = t0; k < t1; k++) {
-        ObsTerm t = terms[k];
-        R c = (R)t.coeff;
-        if (__popcll(b & t.z) & 1) c = -c;
-        switch (t.ph & 3) {
-        case 0: cr += c; break;
-        case 1: ci += c; break;
-        case 2: cr -= c; break;
-        default: ci -= c; break;
-        }
-    }
-}
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_pauli_expect(const typename CTr<R>::T *__restrict__ psi,

@@ -135,3 +135,15 @@ def test_tiling_options_host(lib):
         last = st["passes"]
     with pytest.raises(gb.GbvqcError):
         c.set_tiling(20, 2)
+
+
+def test_batch_validation_host(lib):
+    pure = gb.circuit_create(I.plain_10q().circuit)
+    dens = gb.circuit_create(I.noisy_hea(4, 1, 0).circuit)
+    tiny = gb.circuit_create(I.hea_ry_rz_cz(3, 1, 0).circuit)
+    o10, o4, o3 = gb.obs_create([(1.0, ((0, "Z"),))], 10), gb.obs_create([(1.0, ((0, "Z"),))], 4), \
+        gb.obs_create([(1.0, ((0, "Z"),))], 3)
+    expect_status(1, gb.batch_create, [dens], [o4])        # density circuits are not batched
+    expect_status(1, gb.batch_create, [pure], [o4])        # observable / circuit qubit mismatch
+    expect_status(6, gb.batch_create, [tiny], [o3])        # fewer than 6 qubits: no tiles
+    expect_status(1, gb.batch_create, [], [])
