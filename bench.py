@@ -220,6 +220,8 @@ def run_ours(args, world, rank, local):
     w = I.diff_20q()
     circ = gb.circuit_create(w.circuit)
     obs = gb.obs_create(w.observable, w.circuit.n_qubits)
+    os.environ.setdefault("GBVQC_TUNE_CACHE", "off")
+    tile, low, tune_ms = circ.autotune(w.theta, obs, gb.C64)   # set-up, outside the timed region
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     theta = torch.tensor(w.theta, dtype=torch.float64, device=dev)
@@ -246,11 +248,13 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
+    torch.cuda.nvtx.range_push("bench_timed")   # lets ncu restrict a capture to the timed steps
     for i in range(args.steps):
         flush.zero_()
         starts[i].record(stream)
         step()
         ends[i].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier(world)
@@ -316,6 +320,8 @@ def run_ours(args, world, rank, local):
                              "speedup_fused_c64": value / world / plain_rate}
 
         out["sweep"] = gate_sweep(gb, I, torch, dev, stream, pk)
+        out["batch"] = batch_rate(gb, I, torch)
+        out["noisy"] = noisy_rate(gb, I, torch)
         if not args.no_cpu:
             rate, sample, cores = oracle_grad_rate(25.0)
             out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -327,6 +333,7 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "qubits": 20, "params": w.circuit.n_params,
                        "mode": "fused tile passes, CUDA-graph replay, device pointers",
+                       "tiling": {"tile_qubits": tile, "low_qubits": low, "autotuned": True},
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk}
@@ -370,6 +377,53 @@ def gate_sweep(gb, I, torch, dev, stream, pk):
     sv.free()
     del state
     torch.cuda.empty_cache()
+    return res
+
+
+def batch_rate(gb, I, torch):
+    """512 independent VQE instances (12..20 qubits, depths 4..16) per batch_grad call."""
+    ws = I.batch_512()
+    circs = [gb.circuit_create(w.circuit) for w in ws]
+    obss = [gb.obs_create(w.observable, w.circuit.n_qubits) for w in ws]
+    b = gb.batch_create(circs, obss, gb.C64)
+    th = torch.tensor(np.concatenate([w.theta for w in ws]), dtype=torch.float64, device="cuda")
+    e = torch.empty(len(ws), dtype=torch.float64, device="cuda")
+    g = torch.empty(th.numel(), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        b.grad(th, out=(e, g))
+    torch.cuda.synchronize()
+    reps = 5
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(reps):
+        b.grad(th, out=(e, g))
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    b.free()
+    return {"workload": "batch_512: 512 VQE instances, n ~ U{12..20}, depth ~ U{4..16}, Ry.Rz + CNOT ladder, "
+                        "random-field Ising H; complex64, FP64 reductions; one CUDA-graph replay per batch",
+            "ms_per_batch": ms, "gradient_evals_per_s": len(ws) * 1e3 / ms,
+            "amplitudes": int(sum(1 << w.circuit.n_qubits for w in ws))}
+
+
+def noisy_rate(gb, I, torch):
+    """13-qubit noisy density matrix (26 vectorised qubits): energy + 312-parameter gradient."""
+    w = I.noisy_13q()
+    c = gb.circuit_create(w.circuit)
+    obs = gb.obs_create(w.observable, 13)
+    res = {"workload": "noisy_13q_hea8: density matrix, 8 layers Rx.Rz.Rx + CNOT, depolarising + amplitude "
+                       "damping, 312 parameters, 2^26 amplitudes"}
+    for dtype, mode, key in ((gb.C64, gb.FUSED, "fused_c64"), (gb.C128, gb.PLAIN, "plain_c128")):
+        gb.grad(c, w.theta, obs, dtype, mode)
+        torch.cuda.synchronize()
+        reps = 3 if mode == gb.FUSED else 1
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            gb.grad(c, w.theta, obs, dtype, mode)
+        res[f"{key}_ms"] = (time.perf_counter() - t0) * 1e3 / reps
+    res["speedup"] = res["plain_c128_ms"] / res["fused_c64_ms"]
     return res
 
 

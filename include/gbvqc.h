@@ -139,6 +139,16 @@ gbvqc_status circuit_free(circuit_handle c);
  * Replaces the cached fused schedule. */
 gbvqc_status circuit_set_tiling(circuit_handle c, int tile_qubits, int low_qubits);
 
+/* Autotuner: time `grad` (fused mode, dtype) on this circuit for tile sizes 8..12 (within
+ * the kernel's limits) and 2..4 contiguous low qubits, keep the fastest tiling in the
+ * circuit (as circuit_set_tiling would), and return it with its time per evaluation.
+ * Results are cached on disk, keyed by the circuit's structure, dtype and GPU name, in
+ * the file named by the environment variable GBVQC_TUNE_CACHE (default
+ * $HOME/.cache/gbvqc/autotune.txt; set it to "off" to disable); a cached circuit is not
+ * re-timed (*best_ms is then the cached time).  theta (host) only feeds the timing runs. */
+gbvqc_status circuit_autotune(circuit_handle c, const double *theta, int n_theta, obs_handle h, int dtype,
+                              void *stream, int *best_tile, int *best_low, double *best_ms);
+
 /* Report the fused schedule: number of tile passes and of gate records it holds. */
 gbvqc_status circuit_plan_info(circuit_handle c, int *n_passes, int *n_gates, int *tile_qubits);
 

@@ -127,6 +127,16 @@ class CircuitHandle:
                                                 ctypes.byref(c)))
         return a.value, b.value, c.value
 
+    def autotune(self, theta, obs, dtype: int = C64, stream=None):
+        """Pick the fastest tiling for `grad` on this circuit (cached on disk, see
+        GBVQC_TUNE_CACHE); returns (tile_qubits, low_qubits, ms per evaluation)."""
+        t = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1))
+        bt, bl, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _abi.check(_abi.lib().circuit_autotune(self.handle, t.ctypes.data if t.size else None, t.size,
+                                               obs.handle, dtype, _stream_ptr(stream), ctypes.byref(bt),
+                                               ctypes.byref(bl), ctypes.byref(ms)))
+        return bt.value, bl.value, ms.value
+
     STAT_NAMES = ("tile_qubits", "passes", "fwd_subruns", "fwd_gates", "fwd_phase_blocks",
                   "rev_subruns", "grad_slots", "fwd_smem_max", "rev_smem_max", "phys_gates")
 

@@ -83,6 +83,8 @@ def lib() -> ctypes.CDLL:
         "circuit_set_tiling": [vp, ctypes.c_int, ctypes.c_int],
         "circuit_plan_info": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int)],
+        "circuit_autotune": [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)],
         "circuit_plan_stats": [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
         "apply_circuit": [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
         "apply_channel": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, ctypes.c_int],
@@ -114,7 +116,7 @@ def check(status: int) -> None:
 def exported_symbols() -> List[str]:
     return ["gbvqc_last_error", "gbvqc_version", "sv_alloc", "sv_wrap", "sv_free", "sv_reset",
             "sv_set", "sv_get", "sv_info", "circuit_create", "circuit_free", "circuit_set_tiling",
-            "circuit_plan_info", "circuit_plan_stats", "apply_circuit", "apply_channel", "obs_create", "obs_free",
+            "circuit_plan_info", "circuit_plan_stats", "circuit_autotune", "apply_circuit", "apply_channel", "obs_create", "obs_free",
             "expect", "grad", "grad_profile", "grad_batch", "batch_create", "batch_free",
             "batch_grad", "expect_noalloc"]
 

@@ -68,3 +68,20 @@ def test_batch512_full_sample():
         assert np.abs(gs[i] - g1).max() <= 1e-4 * np.abs(g1).max()
     assert np.all(np.isfinite(e)) and np.all(np.abs(e) <= [sum(abs(c) for c, _ in w.observable) for w in ws])
     b.free()
+
+
+def test_autotune_picks_valid_tiling_and_caches(tmp_path, monkeypatch):
+    monkeypatch.setenv("GBVQC_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    w = I.random_circuit(14, 200, 17, param_share=True)
+    c = gb.circuit_create(w.circuit)
+    obs = gb.obs_create(w.observable, 14)
+    t, lo, ms = c.autotune(w.theta, obs)
+    assert 8 <= t <= 12 and 2 <= lo <= 4 and ms > 0
+    assert c.plan_stats(gb.C64, True)["tile_qubits"] == t
+    e_ref, g_ref = O.adjoint_grad(w.circuit, w.theta, w.observable)
+    e, g = gb.grad(c, w.theta, obs, gb.C64, gb.FUSED)
+    assert abs(e - e_ref) <= 1e-5 * max(1.0, abs(e_ref))
+    assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max()
+    c2 = gb.circuit_create(w.circuit)          # same structure: served from the cache
+    assert c2.autotune(w.theta, obs) == (t, lo, ms)
+    assert (tmp_path / "tune.txt").read_text().count("\n") == 1
