@@ -126,7 +126,9 @@ inline __host__ __device__ void materialize(const DynRec &r, double t, MatRec *o
 enum FType : int32_t {
     FT_DENSE1 = 0, FT_REAL1 = 1, FT_ANTI1 = 2, FT_DIAG1 = 3,
     FT_DENSE2 = 4, FT_DIAG2 = 5, FT_PERM2 = 6, FT_CTRL2 = 7,
-    FT_DIAGB = 8   // a run of commuting diagonal gates (DEnt list) fused into one phase table
+    FT_DIAGB = 8,  // a run of commuting diagonal gates (DEnt list) fused into one phase table
+    FT_LAYER1 = 9  // one-qubit non-diagonal gates on distinct register slots (DEnt list):
+                   // a = slot mask; entry k = Shape, ca = slot, cls = GenType
 };
 // Generator of a variational gate for the fused reverse sweep: the gradient term is
 // coef * Im <Psi| P |Phi> with both states taken right after the gate.

@@ -428,6 +428,12 @@ struct RedCtx {
     unsigned lanemask;
 };
 
+// FT_LAYER1: one-qubit gates on distinct register slots, slot loop unrolled at compile
+// time (no per-gate dispatch on the slot).  Reverse: generator, then Phi and Psi.
+template <typename R, int NR, bool REV>
+__device__ __forceinline__ void apply_layer(int mask, const DEnt *le, const R *smat, typename CT<R>::T *a,
+                                            typename CT<R>::T *b, const RedCtx &rc);
+
 // Sum a per-thread partial over the warp (shuffles in the state's precision: FP32 for
 // complex64, FP64 for complex128) and store it for its slot.
 template <typename R>
@@ -437,6 +443,42 @@ __device__ __forceinline__ void emit_partial(const RedCtx &c, int slot, R v)
     for (int o = 16; o > 0; o >>= 1)
         if (o < c.lanes) v += __shfl_xor_sync(c.lanemask, v, o);
     if (c.lane == 0) c.sgrad[(slot - c.slot_begin) * c.nwarps + c.warp] = (double)v;
+}
+
+template <typename R, int NR, bool REV, int K>
+__device__ __forceinline__ void layer_slot(int mask, const DEnt *le, int &idx, const R *smat, typename CT<R>::T *a,
+                                           typename CT<R>::T *b, const RedCtx &rc)
+{
+    if constexpr (K < NR) {
+        if ((mask >> K) & 1) {
+            const DEnt d = le[idx++];
+            if constexpr (REV) {
+                if (d.cls == GEN_X) emit_partial<R>(rc, d.slot, gen_xy<R, NR, K, GEN_X>(a, b) * (R)d.coef);
+                else if (d.cls == GEN_Y) emit_partial<R>(rc, d.slot, gen_xy<R, NR, K, GEN_Y>(a, b) * (R)d.coef);
+            }
+            const R *m = smat + 8 * d.mat;
+            const R *m2 = smat + 8 * d.mat2;
+            if (d.k == SH_REAL1) {
+                rg1<R, NR, K, SH_REAL1>(a, m);
+                if constexpr (REV) rg1<R, NR, K, SH_REAL1>(b, m2);
+            } else if (d.k == SH_DENSE1) {
+                rg1<R, NR, K, SH_DENSE1>(a, m);
+                if constexpr (REV) rg1<R, NR, K, SH_DENSE1>(b, m2);
+            } else {
+                rg1<R, NR, K, SH_ANTI1>(a, m);
+                if constexpr (REV) rg1<R, NR, K, SH_ANTI1>(b, m2);
+            }
+        }
+        layer_slot<R, NR, REV, K + 1>(mask, le, idx, smat, a, b, rc);
+    }
+}
+
+template <typename R, int NR, bool REV>
+__device__ __forceinline__ void apply_layer(int mask, const DEnt *le, const R *smat, typename CT<R>::T *a,
+                                            typename CT<R>::T *b, const RedCtx &rc)
+{
+    int idx = 0;
+    layer_slot<R, NR, REV, 0>(mask, le, idx, smat, a, b, rc);
 }
 
 // ----------------------------------------------------------------------- the kernel
@@ -483,7 +525,12 @@ __device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, 
 {
     typedef typename CT<R>::T T;
     extern __shared__ __align__(16) unsigned char smem[];
-    const PassDesc &pd = *args.pd;
+    const PassDesc &pdg = *args.pd;
+    struct {
+        int t, n, low, n_sub, sub_begin, slot_begin, n_slots, gate_begin, n_gates, ent_begin, n_ent,
+            unit_begin, n_units, n_blocks;
+    } pd = {pdg.t, pdg.n, pdg.low, pdg.n_sub, pdg.sub_begin, pdg.slot_begin, pdg.n_slots, pdg.gate_begin,
+            pdg.n_gates, pdg.ent_begin, pdg.n_ent, pdg.unit_begin, pdg.n_units, pdg.n_blocks};
     const int t = pd.t, n = pd.n, low = pd.low;
     const int L = 1 << t;
     const int nhi = 1 << (t - low);
@@ -509,11 +556,11 @@ __device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, 
 
     int64_t tilebase = 0;
     for (int i = 0; i < n - t; i++)
-        if ((tile >> i) & 1) tilebase |= int64_t(1) << pd.NS[i];
+        if ((tile >> i) & 1) tilebase |= int64_t(1) << pdg.NS[i];
     for (int h = threadIdx.x; h < nhi; h += blockDim.x) {
         int64_t o = 0;
         for (int i = 0; i < t - low; i++)
-            if ((h >> i) & 1) o |= int64_t(1) << pd.S[low + i];
+            if ((h >> i) & 1) o |= int64_t(1) << pdg.S[low + i];
         hitab[h] = o;
     }
     // stage the pass's gates, diagonal entries and matrices
@@ -586,6 +633,10 @@ __device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, 
         for (int gi = sr.g_begin; gi < sr.g_end; gi++) {
             const FGate g = gn;
             if (gi + 1 < sr.g_end) gn = sgates[gi + 1];  // prefetch the next record
+            if (g.type == FT_LAYER1) {
+                apply_layer<R, NR, REV>(g.a, sents + g.ent, smat, a, b, rc);
+                continue;
+            }
             if (g.type == FT_DIAGB) {
                 const DEnt *ents = sents + g.ent;
                 const R *cst = sconst + 4 * g.slot;

@@ -260,8 +260,57 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
         const double st = E.reverse ? 2.0 : 1.0;
         for (size_t r = 0; r < runs.size(); r++) {
             if (!run_diag[r]) {
+                // one-qubit gates on distinct register slots are grouped into layers (they
+                // commute; in the reverse sweep each generator may be read before or after
+                // the other gates of its layer)
+                std::vector<int> layer;
+                auto flush_layer = [&]() {
+                    if (layer.empty()) return;
+                    std::sort(layer.begin(), layer.end(), [&](int x, int y) {
+                        return slot_of(E.local_of[G[order[x]].q[0]]) < slot_of(E.local_of[G[order[y]].q[0]]);
+                    });
+                    FGate f{};
+                    f.type = FT_LAYER1;
+                    f.slot = -1;
+                    f.ent = (int16_t)((int)E.ents.size() - E.ent_base);
+                    int mask = 0;
+                    for (int pos : layer) {
+                        const PGate &g = G[order[pos]];
+                        DEnt d{};
+                        const int k = slot_of(E.local_of[g.q[0]]);
+                        mask |= 1 << k;
+                        d.k = (int8_t)(g.ftype == FT_REAL1 ? SH_REAL1 : g.ftype == FT_ANTI1 ? SH_ANTI1 : SH_DENSE1);
+                        d.ca = (int8_t)k;
+                        d.mat = (int16_t)E.unit(E.reverse ? g.rec_i : g.rec_f, 1);
+                        d.mat2 = (int16_t)(E.reverse ? E.unit(g.rec_a, 1) : d.mat);
+                        d.cls = GEN_NONE;
+                        d.slot = -1;
+                        E.flops += st * ftype_flops(g.ftype);
+                        if (E.reverse && g.gen != GEN_NONE) {
+                            d.cls = (int8_t)g.gen;
+                            d.coef = g.coef;
+                            d.slot = E.slot_counter++;
+                            E.slot_param.push_back(g.param);
+                            E.flops += 4;
+                        }
+                        E.ents.push_back(d);
+                    }
+                    f.a = (int8_t)mask;
+                    f.n_ent = (int16_t)layer.size();
+                    E.gates.push_back(f);
+                    layer.clear();
+                };
                 for (int pos : runs[r]) {
                     const PGate &g = G[order[pos]];
+                    if (g.k == 1) {
+                        const int k = slot_of(E.local_of[g.q[0]]);
+                        bool clash = false;
+                        for (int x : layer) clash = clash || slot_of(E.local_of[G[order[x]].q[0]]) == k;
+                        if (clash) flush_layer();
+                        layer.push_back(pos);
+                        continue;
+                    }
+                    flush_layer();
                     if (g.k == 2) E.has_2q = true;
                     FGate f{};
                     f.type = (int8_t)g.ftype;
@@ -282,6 +331,7 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
                     }
                     E.gates.push_back(f);
                 }
+                flush_layer();
                 continue;
             }
             const std::vector<int> &run = runs[r];
