@@ -349,7 +349,7 @@ struct gbvqc_obs {
     std::vector<ObsTerm> terms;
     ObsGroup *d_groups = nullptr;
     ObsTerm *d_terms = nullptr;
-    ObsDev dev() const { return ObsDev{d_groups, d_terms, (int)groups.size()}; }
+    ObsDev dev() const { return ObsDev{d_groups, d_terms, (int)groups.size(), (int)terms.size()}; }
 };
 
 // One gate of the per-gate schedule.
@@ -576,6 +576,7 @@ extern "C" gbvqc_status obs_create(const gbvqc_pauli *terms, int n_terms, int n_
             return fail(GBVQC_ERR_ARG, "term %d touches a qubit >= %d", i, n_qubits);
         ObsTerm t{};
         t.coeff = terms[i].coeff;
+        t.coeff_f = (float)terms[i].coeff;
         t.z = terms[i].z_mask;
         t.ph = __builtin_popcountll(terms[i].x_mask & terms[i].z_mask) & 3;  // Y = i X Z
         by_x[terms[i].x_mask].push_back(t);
@@ -597,6 +598,7 @@ extern "C" gbvqc_status obs_create(const gbvqc_pauli *terms, int n_terms, int n_
 static gbvqc_status ensure_obs(gbvqc_obs *h)
 {
     if (h->d_groups) return GBVQC_OK;
+    CUDA_TRY(pauli_prepare());
     ST_TRY(upload(&h->d_terms, h->terms));
     ST_TRY(upload(&h->d_groups, h->groups));
     return GBVQC_OK;
@@ -678,7 +680,7 @@ extern "C" gbvqc_status apply_channel(sv_handle sv, int kind, int qubit, double 
 
 static int add_rec(gbvqc_circuit *c, const Mat &M)
 {
-    MatRec r;
+    MatRec r{};
     double m[32];
     mat_to(M, m);
     for (int i = 0; i < 32; i++) {
@@ -697,7 +699,7 @@ static int add_dyn(gbvqc_circuit *c, int param, int rot, int variant, int domain
     d.rot = rot;
     d.variant = variant;
     d.domain = domain;
-    MatRec r;
+    MatRec r{};               // zero: materialisation writes only the entries a matrix uses
     materialize(d, 0.0, &r);  // placeholder, refreshed from theta before every use
     c->recs.push_back(r);
     c->dyn.push_back(d);
@@ -1507,6 +1509,7 @@ struct gbvqc_batch {
     std::vector<BatchLaunch> fwd, rev;
     PauliBatchEntry *d_pauli = nullptr;
     int64_t pauli_chunks = 0;
+    size_t pauli_smem = 0;  // staged observables' shared memory (0: global-memory path)
     SlotBatchEntry *d_slots = nullptr;
     int64_t total_slots = 0;
     int *d_csr_ptr = nullptr, *d_csr_slots = nullptr;
@@ -1625,6 +1628,13 @@ static gbvqc_status batch_build(gbvqc_batch *b)
         for (int s = 0; s < plans[i]->p.n_slots; s++)
             gslot_param[slot_off[i] + s] = b->param_off[i] + plans[i]->p.slot_param[s];
     }
+    bool staged = true;
+    for (int i = 0; i < n; i++) {
+        const ObsDev od = b->obs[i]->dev();
+        staged = staged && obs_stageable(od, b->dtype);
+        b->pauli_smem = std::max(b->pauli_smem, obs_smem_bytes(od, b->dtype));
+    }
+    if (!staged) b->pauli_smem = 0;
     ST_TRY(upload(&b->d_pauli, pe));
     ST_TRY(upload(&b->d_slots, se));
     ST_TRY(csr_upload(gslot_param, b->total_params, &b->d_csr_ptr, &b->d_csr_slots));
@@ -1638,7 +1648,7 @@ static gbvqc_status batch_enqueue(gbvqc_batch *b, cudaStream_t s)
                                b->n, s));
     for (const BatchLaunch &L : b->fwd)
         CUDA_TRY(launch_fused_batch(b->dtype, false, L.twoq, L.t, L.d_entries, L.n_entries, L.tiles, L.smem, s));
-    CUDA_TRY(launch_pauli_batch(b->dtype, b->d_pauli, b->n, b->pauli_chunks, b->d_energies, s));
+    CUDA_TRY(launch_pauli_batch(b->dtype, b->d_pauli, b->n, b->pauli_chunks, b->pauli_smem, b->d_energies, s));
     for (const BatchLaunch &L : b->rev)
         CUDA_TRY(launch_fused_batch(b->dtype, true, L.twoq, L.t, L.d_entries, L.n_entries, L.tiles, L.smem, s));
     CUDA_TRY(launch_slots_batch(b->d_slots, b->n, b->total_slots, b->d_slot_grad, s));

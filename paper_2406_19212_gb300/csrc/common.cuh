@@ -111,7 +111,9 @@ inline __host__ __device__ void materialize(const DynRec &r, double t, MatRec *o
         if (r.domain == DOM_BRA)
             for (int i = 1; i < 8; i += 2) m[i] = -m[i];
     }
-    for (int i = 0; i < 32; i++) {
+    // a 2x2 fills the first 8 entries; the rest of the record stays zero
+    const int used = r.domain == DOM_SUPER ? 32 : 8;
+    for (int i = 0; i < used; i++) {
         out->d[i] = m[i];
         out->f[i] = (float)m[i];
     }

@@ -15,7 +15,7 @@ struct ObsTerm {
     double coeff;
     uint64_t z;
     int32_t ph;   // number of Y factors mod 4
-    int32_t pad;
+    float coeff_f;  // coeff rounded once to FP32 (complex64 sweeps never convert per amplitude)
 };
 struct ObsGroup {
     uint64_t x;
@@ -25,7 +25,23 @@ struct ObsDev {
     const ObsGroup *groups;
     const ObsTerm *terms;
     int n_groups;
+    int n_terms;
 };
+
+// Shared memory of the staged observable in the expectation kernels; observables
+// larger than kObsStageMax (or with 65536 terms or more) are read from global memory.
+constexpr size_t kObsStageMax = 160 * 1024;
+inline size_t obs_smem_bytes(const ObsDev &obs, int dtype)
+{
+    const size_t g = 16 * (size_t)((obs.n_groups + 1) & ~1);
+    return g + (size_t)obs.n_terms * (dtype == 0 ? 16 : 24);
+}
+inline bool obs_stageable(const ObsDev &obs, int dtype)
+{
+    return obs.n_terms < 65536 && obs_smem_bytes(obs, dtype) <= kObsStageMax;
+}
+cudaError_t pauli_prepare();  // shared-memory opt-in of the staged kernels, outside capture
+cudaError_t pauli_batch_prepare();
 
 // Scratch of a grid reduction: one double per block plus an arrival counter that the
 // last block resets to zero.
@@ -129,8 +145,10 @@ struct BatchDyn {            // theta-dependent record of a batch member
 cudaError_t fused_batch_prepare();
 cudaError_t launch_fused_batch(int dtype, bool reverse, bool two_q, int t, const FusedBatchEntry *entries,
                                int n_entries, int64_t total_tiles, size_t smem, cudaStream_t s);
+// smem: the largest obs_smem_bytes of the batch, or 0 to read every observable from
+// global memory.
 cudaError_t launch_pauli_batch(int dtype, const PauliBatchEntry *entries, int n_entries, int64_t total_chunks,
-                               double *energies, cudaStream_t s);
+                               size_t smem, double *energies, cudaStream_t s);
 cudaError_t launch_slots_batch(const SlotBatchEntry *entries, int n_entries, int64_t total_slots,
                                double *slot_grad, cudaStream_t s);
 cudaError_t launch_batch_init(const BatchDyn *dyn, int n_dyn, const double *theta, int dtype, void *phi_all,

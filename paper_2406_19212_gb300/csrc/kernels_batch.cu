@@ -82,10 +82,12 @@ __device__ __forceinline__ double bwarp_sum(double v)
 }
 
 // lambda = H psi on one chunk of one instance and the chunk's partial of Re <psi|lambda>.
-template <typename R>
+// STAGED: every CTA stages its instance's observable in shared memory first.
+template <typename R, bool STAGED>
 __global__ void __launch_bounds__(256) k_pauli_batch(const PauliBatchEntry *__restrict__ entries, int n_entries)
 {
     typedef typename CTb<R>::T T;
+    extern __shared__ __align__(16) unsigned char psm[];
     __shared__ int s_e;
     __shared__ double s_w[8];
     if (threadIdx.x == 0) s_e = find_entry(entries, n_entries, blockIdx.x);
@@ -97,16 +99,47 @@ __global__ void __launch_bounds__(256) k_pauli_batch(const PauliBatchEntry *__re
     const int64_t a1 = a0 + (int64_t(1) << kPauliChunkBits) < len ? a0 + (int64_t(1) << kPauliChunkBits) : len;
     const T *psi = (const T *)e.psi;
     T *lam = (T *)e.lam;
+    const PGroup *sg = nullptr;
+    const PTerm<R> *st = nullptr;
+    if (STAGED) stage_obs<R>(e.obs, psm, sg, st);
+    const bool wide = e.n > 32;
     double acc = 0.0;
-    for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
-        const T pa = psi[a];
-        R lr, li;
-        pauli_apply_amp<R, T>(psi, (uint64_t)a, pa, e.obs, lr, li);
-        T l;
-        l.x = lr;
-        l.y = li;
-        lam[a] = l;
-        acc += (double)(pa.x * lr + pa.y * li);
+    if (!STAGED) {
+        for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+            const T pa = psi[a];
+            R lr, li;
+            pauli_apply_amp<R, T>(psi, (uint64_t)a, pa, e.obs, lr, li);
+            T l;
+            l.x = lr;
+            l.y = li;
+            lam[a] = l;
+            acc += (double)(pa.x * lr + pa.y * li);
+        }
+    } else {
+        constexpr int V = 4;
+        for (int64_t base = a0 + threadIdx.x; base < a1; base += (int64_t)blockDim.x * V) {
+            uint64_t a[V];
+            bool ok[V];
+            T pa[V];
+            R lr[V], li[V];
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                a[j] = (uint64_t)(base + (int64_t)j * blockDim.x);
+                ok[j] = (int64_t)a[j] < a1;
+                pa[j] = ok[j] ? psi[a[j]] : T{};
+            }
+            if (wide) pauli_apply_staged<R, true, V, T>(psi, a, ok, pa, sg, st, e.obs.n_groups, lr, li);
+            else pauli_apply_staged<R, false, V, T>(psi, a, ok, pa, sg, st, e.obs.n_groups, lr, li);
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                if (!ok[j]) continue;
+                T l;
+                l.x = lr[j];
+                l.y = li[j];
+                lam[a[j]] = l;
+                acc += (double)(pa[j].x * lr[j] + pa[j].y * li[j]);
+            }
+        }
     }
     acc = bwarp_sum(acc);
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
@@ -116,6 +149,15 @@ __global__ void __launch_bounds__(256) k_pauli_batch(const PauliBatchEntry *__re
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_w[w];
         e.partials[chunk] = t;
     }
+}
+
+cudaError_t pauli_batch_prepare()
+{
+    const int bytes = (int)kObsStageMax;
+    cudaError_t e = cudaFuncSetAttribute(k_pauli_batch<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pauli_batch<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
 }
 
 // energy[i] = sum of instance i's chunk partials, in chunk order.
@@ -131,10 +173,16 @@ __global__ void k_energy_batch(const PauliBatchEntry *__restrict__ entries, int 
 }
 
 cudaError_t launch_pauli_batch(int dtype, const PauliBatchEntry *entries, int n_entries, int64_t total_chunks,
-                               double *energies, cudaStream_t s)
+                               size_t smem, double *energies, cudaStream_t s)
 {
-    if (dtype == 0) k_pauli_batch<float><<<(unsigned)total_chunks, 256, 0, s>>>(entries, n_entries);
-    else k_pauli_batch<double><<<(unsigned)total_chunks, 256, 0, s>>>(entries, n_entries);
+    const unsigned g = (unsigned)total_chunks;
+    if (dtype == 0) {
+        if (smem) k_pauli_batch<float, true><<<g, 256, smem, s>>>(entries, n_entries);
+        else k_pauli_batch<float, false><<<g, 256, 0, s>>>(entries, n_entries);
+    } else {
+        if (smem) k_pauli_batch<double, true><<<g, 256, smem, s>>>(entries, n_entries);
+        else k_pauli_batch<double, false><<<g, 256, 0, s>>>(entries, n_entries);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_energy_batch<<<(n_entries + 127) / 128, 128, 0, s>>>(entries, n_entries, energies);

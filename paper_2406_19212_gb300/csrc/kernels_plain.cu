@@ -214,7 +214,7 @@ cudaError_t launch_materialize(const DynRec *dyn, int n_dyn, const double *theta
                                cudaStream_t s)
 {
     if (n_dyn == 0) return cudaSuccess;
-    k_materialize<<<(n_dyn + 127) / 128, 128, 0, s>>>(dyn, n_dyn, theta, recs);
+    k_materialize<<<(n_dyn + 31) / 32, 32, 0, s>>>(dyn, n_dyn, theta, recs);  // spread over SMs
     return cudaGetLastError();
 }
 

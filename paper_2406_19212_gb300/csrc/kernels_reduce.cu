@@ -173,48 +173,102 @@ cudaError_t launch_dot_matrix(int dtype, const void *psi, const void *phi, int n
 
 // ------------------------------------------------------------------- Pauli sums
 
-template <typename R>
+// lambda = H psi (when lam is set) and Re <psi|H psi>.  MODE 0 reads the observable
+// from global memory; 1 and 2 stage it in shared memory (2: more than 32 qubits).
+template <typename R, int MODE>
 __global__ void __launch_bounds__(256) k_pauli_expect(const typename CTr<R>::T *__restrict__ psi,
                                                       typename CTr<R>::T *__restrict__ lam,
                                                       int64_t len, ObsDev obs, RedScratch red,
                                                       double *out)
 {
     typedef typename CTr<R>::T T;
+    extern __shared__ __align__(16) unsigned char psm[];
+    const PGroup *sg = nullptr;
+    const PTerm<R> *st = nullptr;
+    if (MODE != 0) stage_obs<R>(obs, psm, sg, st);
     Acc<R> acc;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < len; a += stride) {
-        T pa = psi[a];
-        R lr = 0, li = 0;
-        for (int g = 0; g < obs.n_groups; g++) {
-            ObsGroup gr = obs.groups[g];
-            uint64_t b = (uint64_t)a ^ gr.x;
-            T pb = gr.x ? psi[b] : pa;
-            R cr, ci;
-            group_coeff<R>(obs.terms, gr.t_begin, gr.t_end, b, cr, ci);
-            lr += cr * pb.x - ci * pb.y;
-            li += cr * pb.y + ci * pb.x;
+    if (MODE == 0) {
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < len; a += stride) {
+            const T pa = psi[a];
+            R lr, li;
+            pauli_apply_amp<R, T>(psi, (uint64_t)a, pa, obs, lr, li);
+            if (lam) {
+                T l;
+                l.x = lr;
+                l.y = li;
+                lam[a] = l;
+            }
+            acc.add(pa.x * lr + pa.y * li);
         }
-        if (lam) {
-            T l;
-            l.x = lr;
-            l.y = li;
-            lam[a] = l;
+    } else {
+        // V amplitudes per thread, blockDim apart (coalesced), per outer iteration
+        constexpr int V = 4;
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x * V;
+        for (int64_t base = (int64_t)blockIdx.x * blockDim.x * V + threadIdx.x; base < len; base += stride) {
+            uint64_t a[V];
+            bool ok[V];
+            T pa[V];
+            R lr[V], li[V];
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                a[j] = (uint64_t)(base + (int64_t)j * blockDim.x);
+                ok[j] = (int64_t)a[j] < len;
+                pa[j] = ok[j] ? psi[a[j]] : T{};
+            }
+            pauli_apply_staged<R, MODE == 2, V, T>(psi, a, ok, pa, sg, st, obs.n_groups, lr, li);
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                if (!ok[j]) continue;
+                if (lam) {
+                    T l;
+                    l.x = lr[j];
+                    l.y = li[j];
+                    lam[a[j]] = l;
+                }
+                acc.add(pa[j].x * lr[j] + pa[j].y * li[j]);
+            }
         }
-        acc.add(pa.x * lr + pa.y * li);
     }
     grid_finish(acc.get(), red, out, 1.0);
+}
+
+cudaError_t pauli_prepare()
+{
+    const int bytes = (int)kObsStageMax;
+    cudaError_t e = cudaFuncSetAttribute(k_pauli_expect<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pauli_expect<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pauli_expect<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pauli_expect<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = pauli_batch_prepare();
+    return e;
 }
 
 cudaError_t launch_pauli_expect(int dtype, const void *psi, void *lam, int n, ObsDev obs,
                                 RedScratch red, double *out, cudaStream_t s)
 {
     int64_t len = int64_t(1) << n;
-    int gr = red_grid(len, 256);
-    if (dtype == 0)
-        k_pauli_expect<float><<<gr, 256, 0, s>>>((const float2 *)psi, (float2 *)lam, len, obs, red, out);
-    else
-        k_pauli_expect<double><<<gr, 256, 0, s>>>((const double2 *)psi, (double2 *)lam, len, obs, red,
-                                                  out);
+    // up to the reduction scratch's 1024 blocks: about 54 warps per SM at 2^20 amplitudes
+    const int mode = obs_stageable(obs, dtype) ? (n > 32 ? 2 : 1) : 0;
+    const int64_t per_block = mode ? 1024 : 256;  // staged kernels take 4 amplitudes per thread
+    int64_t gb = (len + per_block - 1) / per_block;
+    const int gr = (int)(gb > kMaxRedBlocks ? kMaxRedBlocks : (gb < 1 ? 1 : gb));
+    const size_t smem = mode ? obs_smem_bytes(obs, dtype) : 0;
+#define GBVQC_PE(R, T, M) \
+    k_pauli_expect<R, M><<<gr, 256, smem, s>>>((const T *)psi, (T *)lam, len, obs, red, out)
+    if (dtype == 0) {
+        if (mode == 0) GBVQC_PE(float, float2, 0);
+        else if (mode == 1) GBVQC_PE(float, float2, 1);
+        else GBVQC_PE(float, float2, 2);
+    } else {
+        if (mode == 0) GBVQC_PE(double, double2, 0);
+        else if (mode == 1) GBVQC_PE(double, double2, 1);
+        else GBVQC_PE(double, double2, 2);
+    }
+#undef GBVQC_PE
     return cudaGetLastError();
 }
 
