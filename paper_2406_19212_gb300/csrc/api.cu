@@ -381,6 +381,7 @@ struct DevPlan {  // a FusedPlan and its device copies (uploaded on first launch
     FGate *d_fgates = nullptr, *d_rgates = nullptr;
     DEnt *d_fents = nullptr, *d_rents = nullptr;
     MatUnit *d_funits = nullptr, *d_runits = nullptr;
+    void *d_fimg = nullptr, *d_rimg = nullptr;  // per-step matrix images of the unit lists
     int *d_csr_ptr = nullptr, *d_csr_slots = nullptr;
 };
 
@@ -753,6 +754,7 @@ static void free_plan(DevPlan *p)
     cudaFree(p->d_fwd); cudaFree(p->d_rev); cudaFree(p->d_fsubs); cudaFree(p->d_rsubs);
     cudaFree(p->d_fgates); cudaFree(p->d_rgates); cudaFree(p->d_fents); cudaFree(p->d_rents);
     cudaFree(p->d_funits); cudaFree(p->d_runits); cudaFree(p->d_csr_ptr); cudaFree(p->d_csr_slots);
+    cudaFree(p->d_fimg); cudaFree(p->d_rimg);
 }
 
 static void free_graphs(gbvqc_circuit *c)
@@ -1028,6 +1030,9 @@ static gbvqc_status get_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevP
         ST_TRY(upload(&dp->d_rents, dp->p.rents));
         ST_TRY(upload(&dp->d_funits, dp->p.funits));
         ST_TRY(upload(&dp->d_runits, dp->p.runits));
+        const size_t eb = dtype == GBVQC_C64 ? 4 : 8;
+        ST_TRY(dev_alloc((unsigned char **)&dp->d_fimg, std::max<size_t>(1, 8 * eb * dp->p.funits.size())));
+        ST_TRY(dev_alloc((unsigned char **)&dp->d_rimg, std::max<size_t>(1, 8 * eb * dp->p.runits.size())));
         ST_TRY(csr_upload(dp->p.slot_param, c->n_params, &dp->d_csr_ptr, &dp->d_csr_slots));
         dp->uploaded = true;
     }
@@ -1124,10 +1129,19 @@ static gbvqc_status run_plain_forward(gbvqc_circuit *c, int dtype, void *psi, cu
     return GBVQC_OK;
 }
 
+// Matrix images of the plan's forward (and reverse) unit lists from this step's records.
+static gbvqc_status gather_images(gbvqc_circuit *c, DevPlan *p, int dtype, bool with_rev, cudaStream_t s)
+{
+    return run_k("gather_units", 0, 0, s, [&] {
+        return launch_gather_units(dtype, p->d_funits, (int)p->p.funits.size(), p->d_fimg, p->d_runits,
+                                   with_rev ? (int)p->p.runits.size() : 0, p->d_rimg, c->d_recs, s);
+    });
+}
+
 static gbvqc_status run_fused_forward(gbvqc_circuit *c, DevPlan *p, int dtype, void *psi, cudaStream_t s)
 {
     const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
-    const FusedDev fd{p->d_fwd, p->d_fsubs, p->d_fgates, p->d_fents, p->d_funits, c->d_recs};
+    const FusedDev fd{p->d_fwd, p->d_fsubs, p->d_fgates, p->d_fents, p->d_funits, c->d_recs, p->d_fimg};
     for (size_t i = 0; i < p->p.fwd.size(); i++)
         ST_TRY(run_k("fused_forward", p->p.fwd_flops[i] * amps, 2 * sb, s, [&] {
             return launch_fused_forward(dtype, psi, fd, (int)i, p->p.fwd[i], p->fwd_smem[i], s);
@@ -1151,6 +1165,7 @@ extern "C" gbvqc_status apply_circuit(sv_handle sv, circuit_handle c, const doub
     if (mode == GBVQC_MODE_FUSED && fused_supported(c, sv->dtype)) {
         DevPlan *p = nullptr;
         ST_TRY(get_plan(c, sv->dtype, false, &p));
+        ST_TRY(gather_images(c, p, sv->dtype, false, s));
         return run_fused_forward(c, p, sv->dtype, sv->data, s);
     }
     return run_plain_forward(c, sv->dtype, sv->data, s);
@@ -1192,6 +1207,7 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
     ST_TRY(run_k("materialize", 0, 0, s, [&] {
         return launch_materialize(c->d_dyn, (int)c->dyn.size(), w.d_theta, c->d_recs, s);
     }));
+    if (fused) ST_TRY(gather_images(c, p, dtype, true, s));
     ST_TRY(run_k("zero_state", 0, sb, s, [&] { return launch_zero_state(dtype, w.phi, c->n_phys, s); }));
     if (fused) ST_TRY(run_fused_forward(c, p, dtype, w.phi, s));
     else ST_TRY(run_plain_forward(c, dtype, w.phi, s));
@@ -1211,7 +1227,7 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
     }
     if (fused) {
         const int tiles = 1 << (c->n_phys - p->p.t);
-        const FusedDev fd{p->d_rev, p->d_rsubs, p->d_rgates, p->d_rents, p->d_runits, c->d_recs};
+        const FusedDev fd{p->d_rev, p->d_rsubs, p->d_rgates, p->d_rents, p->d_runits, c->d_recs, p->d_rimg};
         for (int i = (int)p->p.rev.size() - 1; i >= 0; i--)
             ST_TRY(run_k("fused_reverse", p->p.rev_flops[i] * amps, 4 * sb, s, [&] {
                 return launch_fused_reverse(dtype, w.phi, w.psi, fd, i, p->p.rev[i], p->rev_smem[i],
@@ -1598,11 +1614,11 @@ static gbvqc_status batch_build(gbvqc_batch *b)
                     FusedBatchEntry e{};
                     if (rev)
                         e.args = FusedArgs{dp->d_rev + p, dp->d_rsubs, dp->d_rgates, dp->d_rents, dp->d_runits,
-                                           b->circs[i]->d_recs, b->d_slot_partials + part_off[i],
+                                           b->circs[i]->d_recs, nullptr, b->d_slot_partials + part_off[i],
                                            1 << (b->circs[i]->n_phys - dp->p.t)};
                     else
                         e.args = FusedArgs{dp->d_fwd + p, dp->d_fsubs, dp->d_fgates, dp->d_fents, dp->d_funits,
-                                           b->circs[i]->d_recs, nullptr, 0};
+                                           b->circs[i]->d_recs, nullptr, nullptr, 0};
                     e.phi = state_ptr(b->phi_all, i);
                     e.psi = rev ? state_ptr(b->psi_all, i) : nullptr;
                     e.begin = L.tiles;

@@ -67,11 +67,21 @@ __device__ __forceinline__ void apply2(const R *m, typename CT<R>::T &a, typenam
         a.x = x;
         a.y = y;
     } else {  // SH_REAL1
-        const R t0 = m[0] * a.x, t1 = m[0] * a.y, u0 = m[4] * a.x, u1 = m[4] * a.y;
-        a.x = fma(m[2], b.x, t0);
-        a.y = fma(m[2], b.y, t1);
-        b.x = fma(m[6], b.x, u0);
-        b.y = fma(m[6], b.y, u1);
+        if constexpr (sizeof(R) == 4) {
+            // both components of an amplitude take the same real coefficient: one packed
+            // FP32x2 multiply or fma per coefficient (same IEEE operations per lane)
+            const float2 m0 = make_float2(m[0], m[0]), m2 = make_float2(m[2], m[2]);
+            const float2 m4 = make_float2(m[4], m[4]), m6 = make_float2(m[6], m[6]);
+            const float2 t = __fmul2_rn(m0, a), u = __fmul2_rn(m4, a);
+            a = __ffma2_rn(m2, b, t);
+            b = __ffma2_rn(m6, b, u);
+        } else {
+            const R t0 = m[0] * a.x, t1 = m[0] * a.y, u0 = m[4] * a.x, u1 = m[4] * a.y;
+            a.x = fma(m[2], b.x, t0);
+            a.y = fma(m[2], b.y, t1);
+            b.x = fma(m[6], b.x, u0);
+            b.y = fma(m[6], b.y, u1);
+        }
     }
 }
 

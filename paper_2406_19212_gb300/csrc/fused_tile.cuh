@@ -394,6 +394,19 @@ __device__ __forceinline__ void phase_block(const DEnt *ents, int counts, const 
 template <typename R, int NR, int K, int G>
 __device__ __forceinline__ R gen_xy(const typename CT<R>::T *f, const typename CT<R>::T *p)
 {
+    if constexpr (sizeof(R) == 4 && G == GEN_Y) {
+        // Re(conj(p1) f0) - Re(conj(p0) f1) as two packed accumulators of
+        // (re*re, im*im) products
+        float2 sp = make_float2(0.f, 0.f), sm = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < (1 << NR); j++) {
+            if (j & (1 << K)) continue;
+            const int j1 = j | (1 << K);
+            sp = __ffma2_rn(p[j1], f[j], sp);
+            sm = __ffma2_rn(p[j], f[j1], sm);
+        }
+        return (sp.x + sp.y) - (sm.x + sm.y);
+    }
     R s = 0;
 #pragma unroll
     for (int j = 0; j < (1 << NR); j++) {
@@ -422,8 +435,9 @@ __device__ __forceinline__ R gen_xy_dispatch(int k, const typename CT<R>::T *f, 
     return 0;
 }
 
+template <typename R>
 struct RedCtx {
-    double *sgrad;
+    R *sgrad;  // per (slot, warp) partials in the state's precision (exact in FP64 later)
     int slot_begin, nwarps, warp, lane, lanes;
     unsigned lanemask;
 };
@@ -432,22 +446,22 @@ struct RedCtx {
 // time (no per-gate dispatch on the slot).  Reverse: generator, then Phi and Psi.
 template <typename R, int NR, bool REV>
 __device__ __forceinline__ void apply_layer(int mask, const DEnt *le, const R *smat, typename CT<R>::T *a,
-                                            typename CT<R>::T *b, const RedCtx &rc);
+                                            typename CT<R>::T *b, const RedCtx<R> &rc);
 
 // Sum a per-thread partial over the warp (shuffles in the state's precision: FP32 for
 // complex64, FP64 for complex128) and store it for its slot.
 template <typename R>
-__device__ __forceinline__ void emit_partial(const RedCtx &c, int slot, R v)
+__device__ __forceinline__ void emit_partial(const RedCtx<R> &c, int slot, R v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
         if (o < c.lanes) v += __shfl_xor_sync(c.lanemask, v, o);
-    if (c.lane == 0) c.sgrad[(slot - c.slot_begin) * c.nwarps + c.warp] = (double)v;
+    if (c.lane == 0) c.sgrad[(slot - c.slot_begin) * c.nwarps + c.warp] = v;
 }
 
 template <typename R, int NR, bool REV, int K>
 __device__ __forceinline__ void layer_slot(int mask, const DEnt *le, int &idx, const R *smat, typename CT<R>::T *a,
-                                           typename CT<R>::T *b, const RedCtx &rc)
+                                           typename CT<R>::T *b, const RedCtx<R> &rc)
 {
     if constexpr (K < NR) {
         if ((mask >> K) & 1) {
@@ -475,7 +489,7 @@ __device__ __forceinline__ void layer_slot(int mask, const DEnt *le, int &idx, c
 
 template <typename R, int NR, bool REV>
 __device__ __forceinline__ void apply_layer(int mask, const DEnt *le, const R *smat, typename CT<R>::T *a,
-                                            typename CT<R>::T *b, const RedCtx &rc)
+                                            typename CT<R>::T *b, const RedCtx<R> &rc)
 {
     int idx = 0;
     layer_slot<R, NR, REV, 0>(mask, le, idx, smat, a, b, rc);
@@ -485,33 +499,60 @@ __device__ __forceinline__ void apply_layer(int mask, const DEnt *le, const R *s
 
 
 
-template <typename R>
-__device__ __forceinline__ void tile_io(typename CT<R>::T *gmem, typename CT<R>::T *sm, int t, int low,
-                                        int64_t tilebase, const int64_t *hitab, bool load)
+// Tile <-> shared memory.  Every thread moves CNT 16-byte words (two complex64 or one
+// complex128 amplitude each): tile_fetch issues all of its global loads into registers
+// (so their latencies overlap with each other and with the gate staging), tile_put
+// writes them to shared memory.  The block has exactly 2^t * size(T) / 16 / CNT threads.
+template <typename R, int CNT>
+__device__ __forceinline__ void tile_fetch(const typename CT<R>::T *gmem, float4 (&w)[CNT], int low, int64_t tilebase,
+                                           const int64_t *hitab)
 {
-    typedef typename CT<R>::T T;
-    const int L = 1 << t, lowmask = (1 << low) - 1;
-    if constexpr (sizeof(T) == 8) {  // complex64: two amplitudes per 16-byte access
-        for (int v = threadIdx.x; v < (L >> 1); v += blockDim.x) {
-            const int l = v << 1;
-            const int64_t g = tilebase | hitab[l >> low] | (l & lowmask);
-            float4 *p = reinterpret_cast<float4 *>(gmem + g);
-            float2 *s = reinterpret_cast<float2 *>(sm);
-            if (load) {
-                float4 x = *p;
-                s[swz<R>(l)] = make_float2(x.x, x.y);
-                s[swz<R>(l + 1)] = make_float2(x.z, x.w);
-            } else {
-                float2 a = s[swz<R>(l)], b = s[swz<R>(l + 1)];
-                *p = make_float4(a.x, a.y, b.x, b.y);
-            }
+    constexpr int AW = sizeof(typename CT<R>::T) == 8 ? 2 : 1;  // amplitudes per word
+    const int lowmask = (1 << low) - 1;
+#pragma unroll
+    for (int c = 0; c < CNT; c++) {
+        const int l = (int)(threadIdx.x + c * blockDim.x) * AW;
+        const int64_t g = tilebase | hitab[l >> low] | (l & lowmask);
+        w[c] = *reinterpret_cast<const float4 *>(gmem + g);
+    }
+}
+
+template <typename R, int CNT>
+__device__ __forceinline__ void tile_put(typename CT<R>::T *sm, const float4 (&w)[CNT])
+{
+    constexpr int AW = sizeof(typename CT<R>::T) == 8 ? 2 : 1;
+#pragma unroll
+    for (int c = 0; c < CNT; c++) {
+        const int l = (int)(threadIdx.x + c * blockDim.x) * AW;
+        if constexpr (AW == 2) {
+            float2 *s2 = reinterpret_cast<float2 *>(sm);
+            s2[swz<R>(l)] = make_float2(w[c].x, w[c].y);
+            s2[swz<R>(l + 1)] = make_float2(w[c].z, w[c].w);
+        } else {
+            reinterpret_cast<float4 *>(sm)[swz<R>(l)] = w[c];
         }
-    } else {
-        for (int l = threadIdx.x; l < L; l += blockDim.x) {
-            const int64_t g = tilebase | hitab[l >> low] | (l & lowmask);
-            if (load) sm[swz<R>(l)] = gmem[g];
-            else gmem[g] = sm[swz<R>(l)];
+    }
+}
+
+template <typename R, int CNT>
+__device__ __forceinline__ void tile_store(typename CT<R>::T *gmem, const typename CT<R>::T *sm, int low,
+                                           int64_t tilebase, const int64_t *hitab)
+{
+    constexpr int AW = sizeof(typename CT<R>::T) == 8 ? 2 : 1;
+    const int lowmask = (1 << low) - 1;
+#pragma unroll
+    for (int c = 0; c < CNT; c++) {
+        const int l = (int)(threadIdx.x + c * blockDim.x) * AW;
+        const int64_t g = tilebase | hitab[l >> low] | (l & lowmask);
+        float4 w;
+        if constexpr (AW == 2) {
+            const float2 *s2 = reinterpret_cast<const float2 *>(sm);
+            const float2 a = s2[swz<R>(l)], b = s2[swz<R>(l + 1)];
+            w = make_float4(a.x, a.y, b.x, b.y);
+        } else {
+            w = reinterpret_cast<const float4 *>(sm)[swz<R>(l)];
         }
+        *reinterpret_cast<float4 *>(gmem + g) = w;
     }
 }
 
@@ -544,8 +585,8 @@ __device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, 
     T *spsi = sphi + (REV ? L : 0);
     int64_t *hitab = reinterpret_cast<int64_t *>(p);
     p += align16(sizeof(int64_t) * nhi);
-    double *sgrad = reinterpret_cast<double *>(p);
-    if (REV) p += align16(sizeof(double) * (size_t)pd.n_slots * nwarps);
+    R *sgrad = reinterpret_cast<R *>(p);
+    if (REV) p += align16(sizeof(R) * (size_t)pd.n_slots * nwarps);
     FGate *sgates = reinterpret_cast<FGate *>(p);
     p += align16(sizeof(FGate) * (size_t)pd.n_gates);
     DEnt *sents = reinterpret_cast<DEnt *>(p);
@@ -555,15 +596,50 @@ __device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, 
     R *smat = reinterpret_cast<R *>(p);
 
     int64_t tilebase = 0;
-    for (int i = 0; i < n - t; i++)
-        if ((tile >> i) & 1) tilebase |= int64_t(1) << pdg.NS[i];
-    for (int h = threadIdx.x; h < nhi; h += blockDim.x) {
-        int64_t o = 0;
-        for (int i = 0; i < t - low; i++)
-            if ((h >> i) & 1) o |= int64_t(1) << pdg.S[low + i];
-        hitab[h] = o;
+    {
+        // S as two 64-bit words: byte j = physical qubit of tile position j (j < t <= 16)
+        const int4 sw = *reinterpret_cast<const int4 *>(pdg.S);
+        const uint64_t s_lo = (uint64_t)(uint32_t)sw.x | ((uint64_t)(uint32_t)sw.y << 32);
+        const uint64_t s_hi = (uint64_t)(uint32_t)sw.z | ((uint64_t)(uint32_t)sw.w << 32);
+        uint64_t smask = 0;
+#pragma unroll
+        for (int j = 0; j < 16; j++)
+            if (j < t) smask |= uint64_t(1) << (((j < 8 ? s_lo : s_hi) >> (8 * (j & 7))) & 0xff);
+        // tile-index bit i -> i-th lowest physical qubit outside S (bit deposit, no loads)
+        uint64_t rest = ~smask & (n >= 64 ? ~uint64_t(0) : ((uint64_t(1) << n) - 1));
+        for (uint64_t x = (uint64_t)tile; rest; rest &= rest - 1, x >>= 1)
+            if (x & 1) tilebase |= (int64_t)(rest & (~rest + 1));
+        // hitab[h] = sum over bits i of h of 2^S[low + i]; h = threadIdx.x + c * blockDim:
+        // the thread bits give one constant part, the bits of c a small second one
+        const int sh = 8 * low;  // S shifted down by low bytes (low <= 6)
+        const uint64_t p_lo = sh ? (s_lo >> sh) | (s_hi << (64 - sh)) : s_lo, p_hi = s_hi >> sh;
+        const int tb = __ffs(blockDim.x) - 1;  // log2(threads)
+        const int hb = t - low;                // bits of h
+        int64_t o_t = 0;
+#pragma unroll
+        for (int i = 0; i < 15; i++)
+            if (i < tb && i < hb && ((threadIdx.x >> i) & 1))
+                o_t |= int64_t(1) << (((i < 8 ? p_lo : p_hi) >> (8 * (i & 7))) & 0xff);
+        for (int c = 0, h = threadIdx.x; h < nhi; c++, h += blockDim.x) {
+            int64_t o = o_t;
+#pragma unroll
+            for (int i = 0; i < 6; i++)  // bits of c (h >> tb), fewer than 2^6 entries per thread
+                if (tb + i < hb && ((c >> i) & 1)) {
+                    const int k = tb + i;
+                    o |= int64_t(1) << (((k < 8 ? p_lo : p_hi) >> (8 * (k & 7))) & 0xff);
+                }
+            hitab[h] = o;
+        }
     }
-    // stage the pass's gates, diagonal entries and matrices
+    if (REV)
+        for (int i = threadIdx.x; i < pd.n_slots * nwarps; i += blockDim.x) sgrad[i] = R(0);
+    __syncthreads();
+    // words of 16 bytes per thread: 2^t amplitudes over 2^(t - NR) threads
+    constexpr int CNT = sizeof(T) == 8 ? (1 << (NR - 1)) : (1 << NR);
+    float4 wphi[CNT], wpsi[REV ? CNT : 1];
+    tile_fetch<R, CNT>(phi, wphi, low, tilebase, hitab);
+    if constexpr (REV) tile_fetch<R, CNT>(psi, wpsi, low, tilebase, hitab);
+    // stage the pass's gates, diagonal entries and matrices while the tile loads are in flight
     {
         const int4 *src = reinterpret_cast<const int4 *>(args.gates + pd.gate_begin);
         int4 *dst = reinterpret_cast<int4 *>(sgates);
@@ -571,13 +647,21 @@ __device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, 
         const int4 *esrc = reinterpret_cast<const int4 *>(args.ents + pd.ent_begin);
         int4 *edst = reinterpret_cast<int4 *>(sents);
         for (int i = threadIdx.x; i < pd.n_ent; i += blockDim.x) edst[i] = esrc[i];
-        for (int i = threadIdx.x; i < pd.n_units * 8; i += blockDim.x) {
-            const MatUnit u = args.units[pd.unit_begin + (i >> 3)];
-            smat[i] = mat_of<R>(&args.recs[u.rec])[8 * u.part + (i & 7)];
+        if (args.img) {  // contiguous copy of the pass's run of the matrix image
+            const int4 *msrc = reinterpret_cast<const int4 *>(reinterpret_cast<const R *>(args.img) +
+                                                              (size_t)8 * pd.unit_begin);
+            int4 *mdst = reinterpret_cast<int4 *>(smat);
+            const int words = pd.n_units * (int)(8 * sizeof(R) / 16);
+            for (int i = threadIdx.x; i < words; i += blockDim.x) mdst[i] = msrc[i];
+        } else {
+            for (int i = threadIdx.x; i < pd.n_units * 8; i += blockDim.x) {
+                const MatUnit u = args.units[pd.unit_begin + (i >> 3)];
+                smat[i] = mat_of<R>(&args.recs[u.rec])[8 * u.part + (i & 7)];
+            }
         }
     }
-    if (REV)
-        for (int i = threadIdx.x; i < pd.n_slots * nwarps; i += blockDim.x) sgrad[i] = 0.0;
+    tile_put<R, CNT>(sphi, wphi);
+    if constexpr (REV) tile_put<R, CNT>(spsi, wpsi);
     __syncthreads();
     // tile-constant phase products of every phase block (bits fixed by the tile index)
     for (int gi = threadIdx.x; gi < pd.n_gates; gi += blockDim.x) {
@@ -599,11 +683,9 @@ __device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, 
         sconst[4 * g.slot + 2] = r1;
         sconst[4 * g.slot + 3] = i1;
     }
-    tile_io<R>(phi, sphi, t, low, tilebase, hitab, true);
-    if (REV) tile_io<R>(psi, spsi, t, low, tilebase, hitab, true);
     __syncthreads();
 
-    RedCtx rc{sgrad, pd.slot_begin, nwarps, warp, lane, lanes, lanemask};
+    RedCtx<R> rc{sgrad, pd.slot_begin, nwarps, warp, lane, lanes, lanemask};
     T a[1 << NR], b[REV ? (1 << NR) : 1];
     for (int s = 0; s < pd.n_sub; s++) {
         const SubRun sr = args.subs[pd.sub_begin + s];
@@ -697,12 +779,12 @@ __device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, 
         }
         __syncthreads();
     }
-    tile_io<R>(phi, sphi, t, low, tilebase, hitab, false);
+    tile_store<R, CNT>(phi, sphi, low, tilebase, hitab);
     if (REV) {
-        tile_io<R>(psi, spsi, t, low, tilebase, hitab, false);
+        tile_store<R, CNT>(psi, spsi, low, tilebase, hitab);
         for (int sl = threadIdx.x; sl < pd.n_slots; sl += blockDim.x) {
             double acc = 0.0;
-            for (int w = 0; w < nwarps; w++) acc += sgrad[sl * nwarps + w];
+            for (int w = 0; w < nwarps; w++) acc += (double)sgrad[sl * nwarps + w];
             args.slot_partials[(int64_t)(pd.slot_begin + sl) * args.tiles_stride + tile] = acc;
         }
     }

@@ -91,6 +91,7 @@ struct FusedDev {
     const DEnt *ents;
     const MatUnit *units;
     const MatRec *recs;
+    const void *img;  // matrix image (8 reals per unit, unit order) or null
 };
 // Arguments of one tile pass of one circuit.
 struct FusedArgs {
@@ -100,9 +101,15 @@ struct FusedArgs {
     const DEnt *ents;
     const MatUnit *units;
     const MatRec *recs;
+    const void *img;  // 8 reals of every unit in unit order (the staged matrices of pass p
+                      // are one contiguous run), or null to gather them through units/recs
     double *slot_partials;
     int tiles_stride;
 };
+// img_f / img_r [8 u + e] = element e of unit u of the forward / reverse unit list, in the
+// state's precision (after the step's matrices are materialised).
+cudaError_t launch_gather_units(int dtype, const MatUnit *fu, int nf, void *img_f, const MatUnit *ru, int nr,
+                                void *img_r, const MatRec *recs, cudaStream_t s);
 int fused_nr(int dtype, bool reverse);           // register qubits per sub-run
 cudaError_t fused_prepare();                     // shared-memory opt-in, outside capture
 cudaError_t launch_fused_forward(int dtype, void *psi, const FusedDev &fd, int pass,

@@ -59,7 +59,7 @@ static cudaError_t fused_launch(void *phi, void *psi, const PassDesc &ph, size_t
 cudaError_t launch_fused_forward(int dtype, void *psi, const FusedDev &fd, int pass, const PassDesc &ph,
                                  size_t smem, cudaStream_t s)
 {
-    FusedArgs args{fd.passes + pass, fd.subs, fd.gates, fd.ents, fd.units, fd.recs, nullptr, 0};
+    FusedArgs args{fd.passes + pass, fd.subs, fd.gates, fd.ents, fd.units, fd.recs, fd.img, nullptr, 0};
     if (dtype == 0) return fused_launch<float, 5, false>(psi, nullptr, ph, smem, args, s);
     return fused_launch<double, 4, false>(psi, nullptr, ph, smem, args, s);
 }
@@ -68,9 +68,36 @@ cudaError_t launch_fused_reverse(int dtype, void *phi, void *psi, const FusedDev
                                  const PassDesc &ph, size_t smem, double *slot_partials, int n_tiles_stride,
                                  cudaStream_t s)
 {
-    FusedArgs args{fd.passes + pass, fd.subs, fd.gates, fd.ents, fd.units, fd.recs, slot_partials, n_tiles_stride};
+    FusedArgs args{fd.passes + pass, fd.subs, fd.gates, fd.ents, fd.units, fd.recs, fd.img, slot_partials,
+                   n_tiles_stride};
     if (dtype == 0) return fused_launch<float, 4, true>(phi, psi, ph, smem, args, s);
     return fused_launch<double, 3, true>(phi, psi, ph, smem, args, s);
+}
+
+template <typename R>
+__global__ void k_gather_units(const MatUnit *__restrict__ fu, int nf, R *img_f, const MatUnit *__restrict__ ru,
+                               int nr, R *img_r, const MatRec *__restrict__ recs)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int u = i >> 3, e = i & 7;
+    if (u < nf) {
+        const MatUnit m = fu[u];
+        img_f[i] = mat_of<R>(&recs[m.rec])[8 * m.part + e];
+    } else if (u < nf + nr) {
+        const MatUnit m = ru[u - nf];
+        img_r[i - 8 * nf] = mat_of<R>(&recs[m.rec])[8 * m.part + e];
+    }
+}
+
+cudaError_t launch_gather_units(int dtype, const MatUnit *fu, int nf, void *img_f, const MatUnit *ru, int nr,
+                                void *img_r, const MatRec *recs, cudaStream_t s)
+{
+    const int total = 8 * (nf + nr);
+    if (total == 0) return cudaSuccess;
+    const int blocks = (total + 255) / 256;
+    if (dtype == 0) k_gather_units<float><<<blocks, 256, 0, s>>>(fu, nf, (float *)img_f, ru, nr, (float *)img_r, recs);
+    else k_gather_units<double><<<blocks, 256, 0, s>>>(fu, nf, (double *)img_f, ru, nr, (double *)img_r, recs);
+    return cudaGetLastError();
 }
 
 // slot_grad[s] = sum over tiles, in tile order within each thread, then a fixed tree.

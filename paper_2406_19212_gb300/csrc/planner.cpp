@@ -419,7 +419,7 @@ size_t pass_smem_bytes(const FusedPlan &plan, const PassDesc &d, bool reverse, i
     auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
     size_t b = al((reverse ? 2 : 1) * (size_t(1) << d.t) * 2 * elem_bytes);
     b += al(sizeof(int64_t) * (size_t(1) << (d.t - d.low)));
-    if (reverse) b += al(sizeof(double) * (size_t)d.n_slots * nwarps);
+    if (reverse) b += al((size_t)elem_bytes * d.n_slots * nwarps);  // per-warp partials
     b += al(sizeof(FGate) * (size_t)d.n_gates);
     b += al(sizeof(DEnt) * (size_t)d.n_ent);
     b += al((size_t)4 * elem_bytes * d.n_blocks);   // tile-constant products (Phi, Psi)
