@@ -253,7 +253,9 @@ def grad(circ: CircuitHandle, theta, obs: Observable, dtype: int = C64, mode: in
          stream=None, out=None):
     """Energy and exact gradient by the reverse sweep (Algorithm 2).
 
-    Host theta (numpy / sequence): returns (float, numpy array) and synchronises.
+    Host theta (numpy / sequence): returns (float, numpy array) and synchronises; `out`
+    = (float64 array of shape (1,), float64 array of shape (n_params,)) receives the
+    results in caller memory (e.g. numpy views of pinned host buffers) if given.
     CUDA theta (torch float64): results stay on the device, written into `out`
     = (energy tensor of shape (1,), grad tensor of shape (n_params,)) if given, or into
     new tensors; the call is asynchronous on `stream` (default: torch's current stream).
@@ -272,6 +274,16 @@ def grad(circ: CircuitHandle, theta, obs: Observable, dtype: int = C64, mode: in
         del keep
         return e, g
     keep, ptr, loc = _theta_args(theta, circ.n_params)
+    if out is not None:
+        e_arr, g = out
+        for a, size in ((e_arr, 1), (g, circ.n_params)):
+            if a.dtype != np.float64 or not a.flags.c_contiguous or a.size < size:
+                raise ValueError("out arrays must be contiguous float64 of sizes (1, n_params)")
+        _abi.check(_abi.lib().grad(circ.handle, ptr, _len(keep), obs.handle, dtype, mode, loc,
+                                   _stream_ptr(stream), e_arr.ctypes.data,
+                                   g.ctypes.data if circ.n_params else None))
+        del keep
+        return float(e_arr[0]), g[:circ.n_params]
     e = ctypes.c_double()
     g = np.zeros(max(1, circ.n_params))
     _abi.check(_abi.lib().grad(circ.handle, ptr, _len(keep), obs.handle, dtype, mode, loc,
