@@ -94,6 +94,7 @@ static double shape_flops(int sh)
     case SH_DENSE1: return 14;  // two complex products and a sum per output
     case SH_DENSE2: return 30;  // four complex products and three sums per output
     case SH_CTRL2: return 7;    // a dense 2x2 on half of the amplitudes
+    case SH_BLOCK2: return 10;  // a dense 2x2 on half, one phase on each remaining quarter
     case SH_REAL1: return 6;
     default: return 6;          // one complex product
     }
@@ -105,6 +106,7 @@ static double ftype_flops(int ft)
     case FT_DENSE1: return 14;
     case FT_DENSE2: return 30;
     case FT_CTRL2: return 7;
+    case FT_BLOCK2: return 10;
     default: return 6;
     }
 }
@@ -296,7 +298,15 @@ static int classify(const Mat &M)
         }
         perm = cnt == 1 && cntc == 1;
     }
-    return perm ? SH_PERM2 : SH_DENSE2;
+    if (perm) return SH_PERM2;
+    // block: only (0,0), (3,3) and the 2x2 on rows/columns {1, 2} are non-zero
+    bool block = true;
+    for (int r = 0; r < 4; r++)
+        for (int c = 0; c < 4; c++) {
+            const bool inside = (r == c && (r == 0 || r == 3)) || ((r == 1 || r == 2) && (c == 1 || c == 2));
+            if (!inside && nz(M[r * 4 + c])) block = false;
+        }
+    return block ? SH_BLOCK2 : SH_DENSE2;
 }
 
 static int perm_bits(const Mat &M)
@@ -325,6 +335,7 @@ static int ftype_of(int sh)
     case SH_DENSE2: return FT_DENSE2;
     case SH_DIAG2: return FT_DIAG2;
     case SH_PERM2: return FT_PERM2;
+    case SH_BLOCK2: return FT_BLOCK2;
     default: return FT_CTRL2;
     }
 }

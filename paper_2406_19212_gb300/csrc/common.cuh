@@ -25,11 +25,16 @@ enum Shape : int32_t {
     SH_DENSE2 = 4,  // general 4x4
     SH_DIAG2 = 5,   // diagonal 4x4 (CZ, superoperators of Rz)
     SH_PERM2 = 6,   // one non-zero per row (SWAP, iSWAP)
-    SH_CTRL2 = 7    // identity unless the first qubit is 1, then a 2x2 on the second
+    SH_CTRL2 = 7,   // identity unless the first qubit is 1, then a 2x2 on the second
+    SH_BLOCK2 = 8   // phase on |00>, a 2x2 on {|01>, |10>}, phase on |11> (FSIM, iSWAP-like)
 };
 
 inline __host__ __device__ bool shape_is_diag(int sh) { return sh == SH_DIAG1 || sh == SH_DIAG2; }
 inline __host__ __device__ int shape_qubits(int sh) { return sh >= SH_DENSE2 ? 2 : 1; }
+
+// Row-major re/im offsets of the 2x2 block of an SH_BLOCK2 matrix (rows/columns 1 and 2)
+// and of its two diagonal phases (rows 0 and 3).
+#define GBVQC_BLOCK2_U(m) {(m)[10], (m)[11], (m)[12], (m)[13], (m)[18], (m)[19], (m)[20], (m)[21]}
 
 enum Rot : int32_t { ROT_X = 0, ROT_Y = 1, ROT_Z = 2 };
 enum Variant : int32_t { VAR_FWD = 0, VAR_INV = 1, VAR_DER = 2 };
@@ -129,8 +134,9 @@ enum FType : int32_t {
     FT_DENSE1 = 0, FT_REAL1 = 1, FT_ANTI1 = 2, FT_DIAG1 = 3,
     FT_DENSE2 = 4, FT_DIAG2 = 5, FT_PERM2 = 6, FT_CTRL2 = 7,
     FT_DIAGB = 8,  // a run of commuting diagonal gates (DEnt list) fused into one phase table
-    FT_LAYER1 = 9  // one-qubit non-diagonal gates on distinct register slots (DEnt list):
-                   // a = slot mask; entry k = Shape, ca = slot, cls = GenType
+    FT_LAYER1 = 9,  // one-qubit non-diagonal gates on distinct register slots (DEnt list):
+                    // a = slot mask; entry k = Shape, ca = slot, cls = GenType
+    FT_BLOCK2 = 10  // SH_BLOCK2 on two register slots
 };
 // Generator of a variational gate for the fused reverse sweep: the gradient term is
 // coef * Im <Psi| P |Phi> with both states taken right after the gate.

@@ -84,6 +84,13 @@ __device__ __forceinline__ void rg2(typename CT<R>::T *a, const R *m, int perm)
             apply2<R, SH_DENSE1>(u, a[i1], a[i3]);
             continue;
         }
+        if (SH == SH_BLOCK2) {
+            R u[8] = GBVQC_BLOCK2_U(m);
+            apply2<R, SH_DENSE1>(u, a[i1], a[i2]);
+            cmul_ip<T, R>(m[0], m[1], a[j]);
+            cmul_ip<T, R>(m[30], m[31], a[i3]);
+            continue;
+        }
         T v[4] = {a[j], a[i1], a[i2], a[i3]}, w[4];
         if (SH == SH_DENSE2) {
 #pragma unroll
@@ -191,6 +198,7 @@ __device__ __forceinline__ void apply_fgate(int type, int ga, int gb, int perm, 
             switch (type) {
             case FT_DENSE2: rg2_dispatch<R, NR, SH_DENSE2>(ga, gb, a, m, 0); break;
             case FT_PERM2: rg2_dispatch<R, NR, SH_PERM2>(ga, gb, a, m, perm); break;
+            case FT_BLOCK2: rg2_dispatch<R, NR, SH_BLOCK2>(ga, gb, a, m, 0); break;
             default: rg2_dispatch<R, NR, SH_CTRL2>(ga, gb, a, m, 0); break;
             }
         }

@@ -99,6 +99,19 @@ __global__ void __launch_bounds__(256) k_gate2(typename CT<R>::T *__restrict__ p
             psi[i1] = b;
             continue;
         }
+        if (SH == SH_BLOCK2) {  // phases on |00>, |11>; 2x2 on |01>, |10>
+            const int64_t i1 = base | b0, i2 = base | b1, i3 = base | b0 | b1;
+            T a = psi[i1], b = psi[i2], c = psi[base], d = psi[i3];
+            R u[8] = GBVQC_BLOCK2_U(m);
+            apply2<R, SH_DENSE1>(u, a, b);
+            cmul_ip<T, R>(m[0], m[1], c);
+            cmul_ip<T, R>(m[30], m[31], d);
+            psi[i1] = a;
+            psi[i2] = b;
+            psi[base] = c;
+            psi[i3] = d;
+            continue;
+        }
         int64_t idx[4] = {base, base | b0, base | b1, base | b0 | b1};
         T v[4], w[4];
 #pragma unroll
@@ -152,6 +165,7 @@ static cudaError_t gate_dispatch(void *psi_, int n, int shape, int q0, int q1, c
         case SH_DENSE2: k_gate2<R, SH_DENSE2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
         case SH_DIAG2: k_gate2<R, SH_DIAG2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
         case SH_PERM2: k_gate2<R, SH_PERM2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
+        case SH_BLOCK2: k_gate2<R, SH_BLOCK2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
         default: k_gate2<R, SH_CTRL2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
         }
     }

@@ -44,6 +44,7 @@ double ftype_flops(int ft)
     case FT_DENSE1: return 14;
     case FT_DENSE2: return 30;
     case FT_CTRL2: return 7;
+    case FT_BLOCK2: return 10;
     default: return 6;
     }
 }
