@@ -95,6 +95,7 @@ static double shape_flops(int sh)
     case SH_DENSE2: return 30;  // four complex products and three sums per output
     case SH_CTRL2: return 7;    // a dense 2x2 on half of the amplitudes
     case SH_BLOCK2: return 10;  // a dense 2x2 on half, one phase on each remaining quarter
+    case SH_IMAG1: return 6;    // two real products and a sum per output
     case SH_REAL1: return 6;
     default: return 6;          // one complex product
     }
@@ -107,7 +108,7 @@ static double ftype_flops(int ft)
     case FT_DENSE2: return 30;
     case FT_CTRL2: return 7;
     case FT_BLOCK2: return 10;
-    default: return 6;
+    default: return 6;  // real / imaginary / anti-diagonal / diagonal
     }
 }
 
@@ -277,7 +278,9 @@ static int classify(const Mat &M)
         if (!nz(M[0]) && !nz(M[3])) return SH_ANTI1;
         bool real = true;
         for (cd v : M) real = real && v.imag() == 0.0;
-        return real ? SH_REAL1 : SH_DENSE1;
+        if (real) return SH_REAL1;
+        const bool imag = M[0].imag() == 0.0 && M[3].imag() == 0.0 && M[1].real() == 0.0 && M[2].real() == 0.0;
+        return imag ? SH_IMAG1 : SH_DENSE1;
     }
     bool diag = true;
     for (int r = 0; r < 4; r++)
@@ -336,6 +339,7 @@ static int ftype_of(int sh)
     case SH_DIAG2: return FT_DIAG2;
     case SH_PERM2: return FT_PERM2;
     case SH_BLOCK2: return FT_BLOCK2;
+    case SH_IMAG1: return FT_IMAG1;
     default: return FT_CTRL2;
     }
 }
@@ -734,7 +738,7 @@ static OpRecs op_records(gbvqc_circuit *c, const gbvqc_op &op, int domain)
         o.i = add_dyn(c, op.param_index, rot, VAR_INV, domain);
         o.d = add_dyn(c, op.param_index, rot, VAR_DER, domain);
         if (domain == DOM_SUPER) o.shape = rot == ROT_Z ? SH_DIAG2 : SH_DENSE2;
-        else o.shape = rot == ROT_Z ? SH_DIAG1 : rot == ROT_Y ? SH_REAL1 : SH_DENSE1;
+        else o.shape = rot == ROT_Z ? SH_DIAG1 : rot == ROT_Y ? SH_REAL1 : SH_IMAG1;
         o.dshape = o.shape;
         return o;
     }
@@ -808,13 +812,98 @@ static gbvqc_status csr_upload(const std::vector<int> &slot_param, int n_params,
     return GBVQC_OK;
 }
 
+// A general one-qubit unitary U = e^{i alpha} V with V real (SH_REAL1) or with a real
+// diagonal and an imaginary off-diagonal (SH_IMAG1): sqrt(Y) and sqrt(X) are of this
+// kind up to the phase e^{i pi/4}, and V costs 6 instead of 14 flops per amplitude.
+// Components that the pattern makes zero are set to exactly zero (they are below
+// 1e-13 of the largest entry).
+static bool phase_normalize(const Mat &U, Mat &V, double &alpha)
+{
+    double mx = 0.0;
+    int kmax = 0;
+    for (int k = 0; k < 4; k++)
+        if (std::abs(U[k]) > mx) mx = std::abs(U[k]), kmax = k;
+    if (mx == 0.0) return false;
+    const double tol = 1e-13 * mx;
+    for (int pattern = 0; pattern < 2; pattern++) {
+        double a;
+        if (pattern == 0) a = std::arg(U[kmax]);  // real: any largest entry sets the phase
+        else {                                    // imaginary off-diagonal: the diagonal does
+            const int kd = std::abs(U[0]) >= std::abs(U[3]) ? 0 : 3;
+            if (std::abs(U[kd]) <= tol) continue;
+            a = std::arg(U[kd]);
+        }
+        const cd ph = std::polar(1.0, -a);
+        Mat W(4);
+        bool ok = true;
+        for (int k = 0; k < 4; k++) {
+            W[k] = U[k] * ph;
+            const bool diag = k == 0 || k == 3;
+            if (pattern == 0 || diag) {
+                ok = ok && std::abs(W[k].imag()) <= tol;
+                W[k] = cd(W[k].real(), 0.0);
+            } else {
+                ok = ok && std::abs(W[k].real()) <= tol;
+                W[k] = cd(0.0, W[k].imag());
+            }
+        }
+        if (ok) {
+            V = W;
+            alpha = a;
+            return true;
+        }
+    }
+    return false;
+}
+
+// Fixed one-qubit gate of shape SH_DENSE1 -> phase-normalised records (alpha returned).
+static bool normalize_fixed(gbvqc_circuit *c, const gbvqc_op &op, OpRecs &r, double &alpha)
+{
+    alpha = 0.0;
+    if (r.shape != SH_DENSE1 || (is_rotation(op.kind) && op.param_index >= 0) || r.Mf.size() != 4) return false;
+    Mat V;
+    if (!phase_normalize(r.Mf, V, alpha)) return false;
+    r.Mf = V;
+    r.Mi = mat_dagger(V, 2);
+    r.f = add_rec(c, r.Mf);
+    r.i = add_rec(c, r.Mi);
+    r.shape = join_shape(classify(r.Mf), classify(r.Mi));
+    return true;
+}
+
+static Mat mat_scaled(const Mat &M, cd z)
+{
+    Mat D(M.size());
+    for (size_t i = 0; i < M.size(); i++) D[i] = M[i] * z;
+    return D;
+}
+
 // Physical gate list of the fused engine for a density layout `map` (or pure, map unused).
+// Fixed one-qubit gates are phase-normalised (normalize_fixed).  On a density matrix the
+// phases cancel between the ket (U) and bra (conj U) sides; on a pure state their sum is
+// multiplied into one fixed gate whose shape is kept by a complex scale, or, if there is
+// none, undone on the first normalised gate, so the fused sweeps give the exact state.
 static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGate> &out)
 {
     out.clear();
+    double phase = 0.0;              // pure: sum of the phases taken out
+    int fold = -1, first_norm = -1;  // pure: gate that takes the phase back
+    Mat fold_f, fold_i, norm_f;
     for (const gbvqc_op &op : c->ops) {
         if (!c->density) {
             OpRecs r = op_records(c, op, DOM_KET);
+            double alpha = 0.0;
+            if (normalize_fixed(c, op, r, alpha)) {
+                phase += alpha;
+                if (first_norm < 0) first_norm = (int)out.size(), norm_f = r.Mf;
+            }
+            // (CZ is applied as a sign flip that ignores its matrix: never a fold target)
+            const bool fixed = !(is_rotation(op.kind) && op.param_index >= 0) && !r.Mf.empty() &&
+                               op.kind != GBVQC_CZ;
+            const bool scalable = r.shape == SH_DENSE1 || r.shape == SH_DENSE2 || r.shape == SH_BLOCK2 ||
+                                  r.shape == SH_DIAG1 || r.shape == SH_DIAG2 || r.shape == SH_PERM2 ||
+                                  r.shape == SH_ANTI1;
+            if (fold < 0 && fixed && scalable) fold = (int)out.size(), fold_f = r.Mf, fold_i = r.Mi;
             PGate g{};
             g.k = kind_qubits(op.kind);
             g.q[0] = op.qubits[0];
@@ -861,6 +950,8 @@ static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGa
         // unitary on a density matrix: U on the ket qubits, conj(U) on the bra qubits
         for (int side = 0; side < 2; side++) {
             OpRecs r = op_records(c, op, side == 0 ? DOM_KET : DOM_BRA);
+            double alpha;
+            normalize_fixed(c, op, r, alpha);  // conj side: conj(V) with phase -alpha
             PGate g{};
             g.k = kind_qubits(op.kind);
             const int8_t *pos = side == 0 ? map.ket : map.bra;
@@ -885,6 +976,18 @@ static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGa
             }
             out.push_back(g);
         }
+    }
+    const double ph = std::remainder(phase, 2.0 * M_PI);
+    if (c->density || ph == 0.0) return;
+    const cd z = std::polar(1.0, ph);
+    if (fold >= 0) {  // shape kept: same ftype and permutation bits
+        out[fold].rec_f = add_rec(c, mat_scaled(fold_f, z));
+        out[fold].rec_i = out[fold].rec_a = add_rec(c, mat_scaled(fold_i, std::conj(z)));
+    } else if (first_norm >= 0) {  // back to a general 2x2 on the first normalised gate
+        const Mat W = mat_scaled(norm_f, z);
+        out[first_norm].rec_f = add_rec(c, W);
+        out[first_norm].rec_i = out[first_norm].rec_a = add_rec(c, mat_dagger(W, 2));
+        out[first_norm].ftype = FT_DENSE1;
     }
 }
 

@@ -60,6 +60,21 @@ __device__ __forceinline__ void apply2(const R *m, typename CT<R>::T &a, typenam
     } else if (SH == SH_DIAG1) {
         cmul_ip(m[0], m[1], a);
         cmul_ip(m[6], m[7], b);
+    } else if (SH == SH_IMAG1) {
+        // [[p, i q], [i r, s]] with p = m[0], q = m[3], r = m[5], s = m[6] real:
+        // a' = p a + i q b, b' = i r a + s b
+        if constexpr (sizeof(R) == 4) {
+            const float2 t = make_float2(-m[3] * b.y, m[3] * b.x);
+            const float2 u = make_float2(-m[5] * a.y, m[5] * a.x);
+            a = __ffma2_rn(make_float2(m[0], m[0]), a, t);
+            b = __ffma2_rn(make_float2(m[6], m[6]), b, u);
+        } else {
+            const R tx = -m[3] * b.y, ty = m[3] * b.x, ux = -m[5] * a.y, uy = m[5] * a.x;
+            a.x = fma(m[0], a.x, tx);
+            a.y = fma(m[0], a.y, ty);
+            b.x = fma(m[6], b.x, ux);
+            b.y = fma(m[6], b.y, uy);
+        }
     } else if (SH == SH_ANTI1) {
         const R x = fma(m[2], b.x, -m[3] * b.y), y = fma(m[2], b.y, m[3] * b.x);
         b.x = fma(m[4], a.x, -m[5] * a.y);

@@ -193,6 +193,7 @@ __device__ __forceinline__ void apply_fgate(int type, int ga, int gb, int perm, 
     case FT_DENSE1: rg1_dispatch<R, NR, SH_DENSE1>(ga, a, m); break;
     case FT_REAL1: rg1_dispatch<R, NR, SH_REAL1>(ga, a, m); break;
     case FT_ANTI1: rg1_dispatch<R, NR, SH_ANTI1>(ga, a, m); break;
+    case FT_IMAG1: rg1_dispatch<R, NR, SH_IMAG1>(ga, a, m); break;
     default:
         if constexpr (TWOQ) {
             switch (type) {
@@ -483,6 +484,9 @@ __device__ __forceinline__ void layer_slot(int mask, const DEnt *le, int &idx, c
             if (d.k == SH_REAL1) {
                 rg1<R, NR, K, SH_REAL1>(a, m);
                 if constexpr (REV) rg1<R, NR, K, SH_REAL1>(b, m2);
+            } else if (d.k == SH_IMAG1) {
+                rg1<R, NR, K, SH_IMAG1>(a, m);
+                if constexpr (REV) rg1<R, NR, K, SH_IMAG1>(b, m2);
             } else if (d.k == SH_DENSE1) {
                 rg1<R, NR, K, SH_DENSE1>(a, m);
                 if constexpr (REV) rg1<R, NR, K, SH_DENSE1>(b, m2);

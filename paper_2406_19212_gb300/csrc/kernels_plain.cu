@@ -156,6 +156,7 @@ static cudaError_t gate_dispatch(void *psi_, int n, int shape, int q0, int q1, c
         case SH_DENSE1: k_gate1<R, SH_DENSE1><<<gr, th, 0, s>>>(psi, np, q0, rec); break;
         case SH_DIAG1: k_gate1<R, SH_DIAG1><<<gr, th, 0, s>>>(psi, np, q0, rec); break;
         case SH_ANTI1: k_gate1<R, SH_ANTI1><<<gr, th, 0, s>>>(psi, np, q0, rec); break;
+        case SH_IMAG1: k_gate1<R, SH_IMAG1><<<gr, th, 0, s>>>(psi, np, q0, rec); break;
         default: k_gate1<R, SH_REAL1><<<gr, th, 0, s>>>(psi, np, q0, rec); break;
         }
     } else {
@@ -183,6 +184,7 @@ cudaError_t launch_gate(int dtype, void *psi, int n, int shape, int q0, int q1, 
         case SH_DENSE1: k_gate1_q0_c64<SH_DENSE1><<<gr, 256, 0, s>>>(p, np, rec); break;
         case SH_DIAG1: k_gate1_q0_c64<SH_DIAG1><<<gr, 256, 0, s>>>(p, np, rec); break;
         case SH_ANTI1: k_gate1_q0_c64<SH_ANTI1><<<gr, 256, 0, s>>>(p, np, rec); break;
+        case SH_IMAG1: k_gate1_q0_c64<SH_IMAG1><<<gr, 256, 0, s>>>(p, np, rec); break;
         default: k_gate1_q0_c64<SH_REAL1><<<gr, 256, 0, s>>>(p, np, rec); break;
         }
         return cudaGetLastError();

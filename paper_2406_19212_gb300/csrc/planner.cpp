@@ -44,7 +44,7 @@ double ftype_flops(int ft)
     case FT_DENSE1: return 14;
     case FT_DENSE2: return 30;
     case FT_CTRL2: return 7;
-    case FT_BLOCK2: return 10;
+    case FT_BLOCK2: return 10;   // FT_REAL1 / FT_IMAG1 / FT_ANTI1 / FT_DIAG*: 6
     default: return 6;
     }
 }
@@ -280,7 +280,10 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
                         DEnt d{};
                         const int k = slot_of(E.local_of[g.q[0]]);
                         mask |= 1 << k;
-                        d.k = (int8_t)(g.ftype == FT_REAL1 ? SH_REAL1 : g.ftype == FT_ANTI1 ? SH_ANTI1 : SH_DENSE1);
+                        d.k = (int8_t)(g.ftype == FT_REAL1   ? SH_REAL1
+                                       : g.ftype == FT_ANTI1 ? SH_ANTI1
+                                       : g.ftype == FT_IMAG1 ? SH_IMAG1
+                                                             : SH_DENSE1);
                         d.ca = (int8_t)k;
                         d.mat = (int16_t)E.unit(E.reverse ? g.rec_i : g.rec_f, 1);
                         d.mat2 = (int16_t)(E.reverse ? E.unit(g.rec_a, 1) : d.mat);

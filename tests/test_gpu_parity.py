@@ -276,3 +276,42 @@ def test_argument_errors():
         gb.grad(c, np.zeros(w.circuit.n_params + 1), gb.obs_create(w.observable, 4))
     with pytest.raises(gb.GbvqcError):
         gb.grad(c, w.theta, gb.obs_create(w.observable + [(1.0, ((5, "Z"),))], 6))
+
+
+# ------------------------------------------- phase-normalised one-qubit gates (fused)
+
+def _sqrt_layers(n, extra, seed):
+    """sqrt(X/Y/W) layers plus `extra` gates: exercises the fused engine's global-phase
+    bookkeeping (normalised gates, and the gate that takes the phase back)."""
+    rng = np.random.default_rng(seed)
+    ops, n_par = [], 0
+    for layer in range(4):
+        for q in range(n):
+            ops.append(I.Op(("SX", "SY", "SW")[int(rng.integers(0, 3))], (q,)))
+        for q in range(layer % 2, n - 1, 2):
+            if extra == "cz":
+                ops.append(I.Op("CZ", (q, q + 1)))
+            elif extra == "t":
+                ops.append(I.Op("T", (q,)))
+            elif extra == "ry":
+                ops.append(I.Op("RY", (q,), param=n_par))
+                n_par += 1
+    return I.Circuit(n, ops, n_par), rng.uniform(0, 2 * math.pi, n_par)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("extra", ["none", "cz", "t", "ry"])
+def test_fused_sqrt_gates_exact_state(dtype, extra):
+    circ, theta = _sqrt_layers(9, extra, 11)
+    ref = O.apply_circuit(circ, theta)
+    got = run_apply(circ, theta, dtype, gb.FUSED, tiling=(7, 2))
+    check_amps(got, ref, dtype)
+    # gradient and energy do not depend on global phases either way
+    if circ.n_params:
+        obs = I.ising_chain(9, [0.7] * 9)
+        e_ref, g_ref = O.adjoint_grad(circ, theta, obs)
+        c = gb.circuit_create(circ)
+        o = gb.obs_create(obs, 9)
+        e, g = gb.grad(c, theta, o, dtype, gb.FUSED)
+        check_energy(e, e_ref, dtype)
+        check_grad(g, g_ref, dtype)
