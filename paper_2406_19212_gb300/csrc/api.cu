@@ -365,6 +365,8 @@ struct gbvqc_obs {
     ObsGroup *d_groups = nullptr;
     ObsTerm *d_terms = nullptr;
     ObsDev dev() const { return ObsDev{d_groups, d_terms, (int)groups.size(), (int)terms.size()}; }
+    // device copies with the X/Z masks permuted to a gradient layout (key: the layout)
+    std::map<std::vector<int8_t>, std::pair<ObsGroup *, ObsTerm *>> perm_dev;
 };
 
 // One gate of the per-gate schedule.
@@ -388,6 +390,7 @@ struct Workspace {
 
 struct DevPlan {  // a FusedPlan and its device copies (uploaded on first launch)
     FusedPlan p;
+    std::vector<int8_t> perm;  // pure gradient plans: physical qubit of logical q (empty: identity)
     bool uploaded = false;
     int elem = 4;
     std::vector<size_t> fwd_smem, rev_smem;
@@ -620,11 +623,46 @@ static gbvqc_status ensure_obs(gbvqc_obs *h)
     return GBVQC_OK;
 }
 
+static uint64_t permute_mask(uint64_t m, const std::vector<int8_t> &perm)
+{
+    uint64_t r = 0;
+    for (size_t q = 0; q < perm.size(); q++)
+        if ((m >> q) & 1) r |= uint64_t(1) << perm[q];
+    return r;
+}
+
+// The observable in a permuted qubit layout (device copies made once per layout; call
+// outside stream capture).
+static gbvqc_status obs_dev_perm(gbvqc_obs *h, const std::vector<int8_t> &perm, ObsDev *out)
+{
+    if (perm.empty()) {
+        *out = h->dev();
+        return GBVQC_OK;
+    }
+    auto it = h->perm_dev.find(perm);
+    if (it == h->perm_dev.end()) {
+        std::vector<ObsGroup> g = h->groups;
+        std::vector<ObsTerm> t = h->terms;
+        for (ObsGroup &x : g) x.x = permute_mask(x.x, perm);
+        for (ObsTerm &x : t) x.z = permute_mask(x.z, perm);
+        std::pair<ObsGroup *, ObsTerm *> d{nullptr, nullptr};
+        ST_TRY(upload(&d.first, g));
+        ST_TRY(upload(&d.second, t));
+        it = h->perm_dev.emplace(perm, d).first;
+    }
+    *out = ObsDev{it->second.first, it->second.second, (int)h->groups.size(), (int)h->terms.size()};
+    return GBVQC_OK;
+}
+
 extern "C" gbvqc_status obs_free(obs_handle h)
 {
     if (!h) return GBVQC_OK;
     if (h->d_groups) cudaFree(h->d_groups);
     if (h->d_terms) cudaFree(h->d_terms);
+    for (auto &kv : h->perm_dev) {
+        cudaFree(kv.second.first);
+        cudaFree(kv.second.second);
+    }
     delete h;
     return GBVQC_OK;
 }
@@ -1092,15 +1130,85 @@ static int default_tile(int dtype) { return 12; }
 static int default_low(int dtype) { return dtype == GBVQC_C64 ? 4 : 3; }
 
 // Fused plan for (dtype, layout); built on first use (host only).
+// Gradient layout of a pure circuit: the `low` physical low qubits (always in every
+// tile) are the logical qubits that give the fewest passes; the evaluation starts from
+// |0...0>, which is the same in every layout, and the observable's masks are permuted
+// to match, so the layout never leaves the gradient call.  Candidates: every pair (one
+// qubit if low = 1), the best pair grown greedily, and every window of `low` consecutive
+// qubits; ties keep the identity layout.
+static std::vector<int8_t> choose_grad_layout(const std::vector<PGate> &pg, int n, const PlanOptions &opt)
+{
+    const int low = std::max(1, std::min(opt.low, std::min(opt.t, n)));
+    auto mapped = [&](const std::vector<int> &lows, std::vector<int8_t> &perm) {
+        perm.assign(n, -1);
+        int next = 0;
+        for (int q : lows) perm[q] = (int8_t)next++;
+        for (int q = 0; q < n; q++)
+            if (perm[q] < 0) perm[q] = (int8_t)next++;
+        std::vector<PGate> G = pg;
+        for (PGate &g : G) {
+            g.q[0] = perm[g.q[0]];
+            if (g.k == 2) g.q[1] = perm[g.q[1]];
+            if (g.gen != GEN_NONE) g.gq = perm[g.gq];
+        }
+        return count_passes(G, n, opt);
+    };
+    std::vector<int> ident;
+    for (int q = 0; q < low; q++) ident.push_back(q);
+    std::vector<int8_t> perm;
+    int best = mapped(ident, perm);
+    if (best < 0 || pg.size() > 20000) return {};
+    std::vector<int> best_set = ident;
+    std::vector<int> cur;
+    if (low >= 2) {
+        for (int a = 0; a < n; a++)
+            for (int b = a + 1; b < n; b++) {
+                std::vector<int> s2 = {a, b};
+                const int v = mapped(s2, perm);
+                if (v >= 0 && v < best) best = v, best_set = s2;
+            }
+        cur = best_set.size() == 2 ? best_set : std::vector<int>{0, 1};
+        while ((int)cur.size() < low) {  // extend greedily
+            int bq = -1, bv = 1 << 30;
+            for (int q = 0; q < n; q++) {
+                if (std::find(cur.begin(), cur.end(), q) != cur.end()) continue;
+                std::vector<int> s3 = cur;
+                s3.push_back(q);
+                const int v = mapped(s3, perm);
+                if (v >= 0 && v < bv) bv = v, bq = q;
+            }
+            if (bq < 0) break;
+            cur.push_back(bq);
+            if ((int)cur.size() == low && bv < best) best = bv, best_set = cur;
+        }
+    } else {
+        for (int a = 1; a < n; a++) {
+            std::vector<int> s1 = {a};
+            const int v = mapped(s1, perm);
+            if (v >= 0 && v < best) best = v, best_set = s1;
+        }
+    }
+    for (int a = 1; a + low <= n; a++) {  // contiguous windows (chains, ladders, bricks)
+        std::vector<int> win;
+        for (int q = a; q < a + low; q++) win.push_back(q);
+        const int v = mapped(win, perm);
+        if (v >= 0 && v < best) best = v, best_set = win;
+    }
+    if ((int)best_set.size() != low || best_set == ident) return {};
+    std::sort(best_set.begin(), best_set.end());
+    mapped(best_set, perm);
+    return perm;
+}
+
 static gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out)
 {
-    int key = dtype * 2 + (grad_layout && c->density ? 1 : 0);
+    int key = dtype * 2 + (grad_layout ? 1 : 0);
     auto it = c->plans.find(key);
     if (it != c->plans.end()) {
         *out = it->second.get();
         return GBVQC_OK;
     }
-    const std::vector<PGate> &pg = (grad_layout && c->density) ? c->pg_grad : c->pg_std;
+    const std::vector<PGate> &pg0 = (grad_layout && c->density) ? c->pg_grad : c->pg_std;
     PlanOptions opt;
     opt.t = c->tile_qubits ? c->tile_qubits : default_tile(dtype);
     opt.low = c->low_qubits ? c->low_qubits : default_low(dtype);
@@ -1110,9 +1218,22 @@ static gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout,
     opt.t = std::min(opt.t, std::min(opt.nr_f, opt.nr_r) + 8);
     opt.elem_bytes = dtype == GBVQC_C64 ? 4 : 8;
     opt.max_slots = 128;
-    opt.gate_smem = 24 * 1024;
+    opt.gate_smem = 40 * 1024;
+    std::vector<int8_t> perm;
+    std::vector<PGate> permuted;
+    if (grad_layout && !c->density) perm = choose_grad_layout(pg0, c->n_phys, opt);
+    if (!perm.empty()) {
+        permuted = pg0;
+        for (PGate &g : permuted) {
+            g.q[0] = perm[g.q[0]];
+            if (g.k == 2) g.q[1] = perm[g.q[1]];
+            if (g.gen != GEN_NONE) g.gq = perm[g.gq];
+        }
+    }
+    const std::vector<PGate> &pg = perm.empty() ? pg0 : permuted;
     std::unique_ptr<DevPlan> dp(new DevPlan());
     dp->elem = opt.elem_bytes;
+    dp->perm = perm;
     std::string err;
     if (!build_fused_plan(pg, c->n_phys, opt, dp->p, err))
         return fail(GBVQC_ERR_UNSUPPORTED, "fused plan: %s", err.c_str());
@@ -1335,8 +1456,10 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
             return launch_density_seed(dtype, w.psi, c->n_log, m, h->dev(), s);
         }));
     } else {
+        ObsDev od;  // in the plan's gradient layout (copies made before any capture)
+        ST_TRY(obs_dev_perm(h, fused ? p->perm : std::vector<int8_t>(), &od));
         ST_TRY(run_k("pauli_expect_seed", (8.0 * h->groups.size() + 4) * amps, 2 * sb, s, [&] {
-            return launch_pauli_expect(dtype, w.phi, w.psi, c->n_phys, h->dev(), red, w.d_energy, s);
+            return launch_pauli_expect(dtype, w.phi, w.psi, c->n_phys, od, red, w.d_energy, s);
         }));
     }
     if (fused) {
@@ -1388,6 +1511,10 @@ extern "C" gbvqc_status grad(circuit_handle c, const double *theta, int n_theta,
     DevPlan *p = nullptr;
     if (mode == GBVQC_MODE_FUSED && fused_supported(c, dtype)) ST_TRY(get_plan(c, dtype, true, &p));
     else mode = GBVQC_MODE_PLAIN;
+    if (p && !c->density) {
+        ObsDev od;
+        ST_TRY(obs_dev_perm(h, p->perm, &od));
+    }
     ST_TRY(ensure_workspace(c, dtype, 0));
     Workspace &w = c->ws;
     // a gradient slot per variational physical gate: at most two per op (ket and bra)
@@ -1751,7 +1878,9 @@ static gbvqc_status batch_build(gbvqc_batch *b)
     std::vector<SlotBatchEntry> se(n);
     std::vector<int> gslot_param(slots, -1);
     for (int i = 0; i < n; i++) {
-        pe[i] = PauliBatchEntry{state_ptr(b->phi_all, i), state_ptr(b->psi_all, i), b->obs[i]->dev(),
+        ObsDev od;
+        ST_TRY(obs_dev_perm(b->obs[i], plans[i]->perm, &od));
+        pe[i] = PauliBatchEntry{state_ptr(b->phi_all, i), state_ptr(b->psi_all, i), od,
                                 b->d_pauli_partials + chunk_off[i], b->circs[i]->n_phys, 0, chunk_off[i]};
         se[i] = SlotBatchEntry{b->d_slot_partials + part_off[i], 1 << (b->circs[i]->n_phys - plans[i]->p.t), 0,
                                slot_off[i]};
@@ -1760,7 +1889,8 @@ static gbvqc_status batch_build(gbvqc_batch *b)
     }
     bool staged = true;
     for (int i = 0; i < n; i++) {
-        const ObsDev od = b->obs[i]->dev();
+        ObsDev od;
+        ST_TRY(obs_dev_perm(b->obs[i], plans[i]->perm, &od));
         staged = staged && obs_stageable(od, b->dtype);
         b->pauli_smem = std::max(b->pauli_smem, obs_smem_bytes(od, b->dtype));
     }

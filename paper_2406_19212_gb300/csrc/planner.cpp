@@ -431,34 +431,20 @@ size_t pass_smem_bytes(const FusedPlan &plan, const PassDesc &d, bool reverse, i
     return b;
 }
 
-bool build_fused_plan(const std::vector<PGate> &G, int n, const PlanOptions &opt, FusedPlan &out,
-                      std::string &err)
+// Greedy pass selection: scan the remaining gates in circuit order; a gate joins the pass
+// if every earlier remaining gate on its qubits joined (no qubit of it is blocked), its
+// non-diagonal qubits fit in the t tile qubits (the `low` lowest physical qubits are
+// always in the tile), and the pass's slot and shared-memory budgets allow it.
+bool select_passes(const std::vector<PGate> &G, int n, int t, int low, const PlanOptions &opt,
+                   std::vector<PassSel> &passes, std::string &err)
 {
-    int t = std::min(opt.t, n);
-    const int nr = std::max(opt.nr_f, opt.nr_r);
-    if (t < nr || t > 16) {
-        err = "tile of " + std::to_string(t) + " qubits cannot hold " + std::to_string(nr) +
-              " register qubits";
-        return false;
-    }
-    int low = std::max(1, std::min(opt.low, t));
-    out = FusedPlan();
-    out.t = t;
-    out.low = low;
-    out.n = n;
-    out.nr_f = opt.nr_f;
-    out.nr_r = opt.nr_r;
     const int m = (int)G.size();
     std::vector<char> applied(m, 0);
-    struct PB {
-        uint64_t S;
-        std::vector<int> gates;
-    };
-    std::vector<PB> passes;
     int done = 0;
     const uint64_t lowmask = (uint64_t(1) << low) - 1;
+    passes.clear();
     while (done < m) {
-        PB pb;
+        PassSel pb;
         pb.S = lowmask;
         int cnt = low, slots = 0, bytes = 0;
         uint64_t blocked = 0;
@@ -500,8 +486,40 @@ bool build_fused_plan(const std::vector<PGate> &G, int n, const PlanOptions &opt
                 pb.S |= uint64_t(1) << q;
                 cnt++;
             }
-        passes.push_back(pb);
+        passes.push_back(std::move(pb));
     }
+    return true;
+}
+
+int count_passes(const std::vector<PGate> &G, int n, const PlanOptions &opt)
+{
+    const int t = std::min(opt.t, n);
+    const int low = std::max(1, std::min(opt.low, t));
+    std::vector<PassSel> passes;
+    std::string err;
+    if (!select_passes(G, n, t, low, opt, passes, err)) return -1;
+    return (int)passes.size();
+}
+
+bool build_fused_plan(const std::vector<PGate> &G, int n, const PlanOptions &opt, FusedPlan &out,
+                      std::string &err)
+{
+    int t = std::min(opt.t, n);
+    const int nr = std::max(opt.nr_f, opt.nr_r);
+    if (t < nr || t > 16) {
+        err = "tile of " + std::to_string(t) + " qubits cannot hold " + std::to_string(nr) +
+              " register qubits";
+        return false;
+    }
+    int low = std::max(1, std::min(opt.low, t));
+    out = FusedPlan();
+    out.t = t;
+    out.low = low;
+    out.n = n;
+    out.nr_f = opt.nr_f;
+    out.nr_r = opt.nr_r;
+    std::vector<PassSel> passes;
+    if (!select_passes(G, n, t, low, opt, passes, err)) return false;
 
     int slot_counter = 0;
     std::vector<int> dummy_params;

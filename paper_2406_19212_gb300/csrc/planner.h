@@ -3,6 +3,7 @@
 // numbers the gradient slots of the reverse sweep.
 #pragma once
 
+#include <cstdint>
 #include <string>
 #include <vector>
 
@@ -53,6 +54,16 @@ struct FusedPlan {
 
 bool build_fused_plan(const std::vector<PGate> &gates, int n, const PlanOptions &opt, FusedPlan &out,
                       std::string &err);
+
+// The tile qubit set and the gates of one pass, from the greedy pass selection.
+struct PassSel {
+    uint64_t S = 0;
+    std::vector<int> gates;
+};
+bool select_passes(const std::vector<PGate> &gates, int n, int t, int low, const PlanOptions &opt,
+                   std::vector<PassSel> &passes, std::string &err);
+// Number of passes build_fused_plan would make (-1 if it cannot plan).
+int count_passes(const std::vector<PGate> &gates, int n, const PlanOptions &opt);
 
 // Shared-memory bytes the fused kernel needs for pass p of `plan`.
 size_t pass_smem_bytes(const FusedPlan &plan, const PassDesc &d, bool reverse, int elem_bytes);
