@@ -147,3 +147,17 @@ def test_batch_validation_host(lib):
     expect_status(1, gb.batch_create, [pure], [o4])        # observable / circuit qubit mismatch
     expect_status(6, gb.batch_create, [tiny], [o3])        # fewer than 6 qubits: no tiles
     expect_status(1, gb.batch_create, [], [])
+
+
+def test_gradient_layout_cuts_passes_of_a_ladder(lib):
+    """A CNOT ladder across more qubits than a tile: the gradient plan moves the physical
+    low qubits into the overlap of neighbouring tiles and needs fewer passes than the
+    identity layout of apply_circuit (host planner only)."""
+    rng = np.random.default_rng(0)
+    w = I.ry_rz_cnot_instance(20, 16, rng)
+    c = gb.circuit_create(w.circuit)
+    c.set_tiling(12, 4)
+    grad_passes = c.plan_stats(gb.C64, for_grad=True)["passes"]
+    apply_passes = c.plan_stats(gb.C64, for_grad=False)["passes"]
+    assert grad_passes < apply_passes
+    assert grad_passes <= 20

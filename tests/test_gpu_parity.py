@@ -315,3 +315,20 @@ def test_fused_sqrt_gates_exact_state(dtype, extra):
         e, g = gb.grad(c, theta, o, dtype, gb.FUSED)
         check_energy(e, e_ref, dtype)
         check_grad(g, g_ref, dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_fused_grad_permuted_layout_heisenberg(dtype):
+    """Gradient plan in a permuted qubit layout (CNOT ladder wider than the tile) with an
+    observable holding X, Y and Z factors: the masks are permuted on the host."""
+    rng = np.random.default_rng(5)
+    w = I.ry_rz_cnot_instance(14, 6, rng)
+    obs = I.heisenberg_1d(14, hz=0.3, J=0.8)
+    c = gb.circuit_create(w.circuit)
+    c.set_tiling(9, 2)
+    assert c.plan_stats(dtype, for_grad=True)["passes"] <= c.plan_stats(dtype, for_grad=False)["passes"]
+    o = gb.obs_create(obs, 14)
+    e, g = gb.grad(c, w.theta, o, dtype, gb.FUSED)
+    e_ref, g_ref = O.adjoint_grad(w.circuit, w.theta, obs)
+    check_energy(e, e_ref, dtype)
+    check_grad(g, g_ref, dtype)
