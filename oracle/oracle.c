@@ -19,7 +19,10 @@
  *     matrix (Eq. channel), and tr(H rho);
  *   - the noisy adjoint gradient of Sec. III.E on the vectorised |rho>> with
  *     superoperators M = sum_s K_s (x) conj(K_s) (Eq. channel2, read with the
- *     conjugate on the bra index).
+ *     conjugate on the bra index);
+ *   - measure!(state, i) of Sec. II.D: the probability of each outcome of qubit i, the
+ *     outcome picked by a caller-supplied uniform u (0 if u < P(0)), and the collapsed,
+ *     renormalised state (pure or density).
  *
  * Readings of the paper taken here (each also listed in the design notes):
  *   - the printed Ry matrix [[c,-s],[-s,c]] is not unitary: Ry = [[c,-s],[s,c]];
@@ -590,6 +593,44 @@ int orc_vec_apply_circuit(double *vec_, int n, const orc_op *ops, int n_ops, con
         int k2 = superop(&ops[j], theta, n, S, pq);
         if (k2 < 0) return -1;
         apply_k((cplx *)vec_, 2 * n, k2, pq, S);
+    }
+    return 0;
+}
+
+/* measure!(state, q) (Sec. II.D) on a pure state (density = 0, 2^n amplitudes) or a
+ * density matrix (density = 1, rho_ab at a + 2^n b).  P(k) = (sum of |psi_a|^2, or of
+ * rho_aa, over a with bit q of a equal to k) / (the same sum over all a).  The outcome
+ * is 0 if u < P(0), else 1 (u is the caller's uniform draw in [0, 1)); the state is
+ * projected on it and renormalised (pure: psi / sqrt(sum kept); density: P rho P / its
+ * trace).  Writes the outcome and its probability. */
+int orc_measure(double *state_, int n, int density, int q, double u, int *outcome, double *prob)
+{
+    cplx *st = (cplx *)state_;
+    const int64_t dim = (int64_t)1 << n;
+    double s[2] = {0.0, 0.0};
+    int64_t a, b;
+    if (q < 0 || q >= n) return -1;
+    for (a = 0; a < dim; a++) {
+        const int bit = (int)((a >> q) & 1);
+        if (density) s[bit] += creal(st[a + dim * a]);
+        else s[bit] += creal(st[a]) * creal(st[a]) + cimag(st[a]) * cimag(st[a]);
+    }
+    {
+        const double total = s[0] + s[1];
+        const int k = u < s[0] / total ? 0 : 1;
+        *outcome = k;
+        *prob = s[k] / total;
+        if (!density) {
+            const double scale = 1.0 / sqrt(s[k]);
+            for (a = 0; a < dim; a++) st[a] = ((int)((a >> q) & 1) == k) ? st[a] * scale : 0.0;
+        } else {
+            const double scale = 1.0 / s[k];
+            for (b = 0; b < dim; b++)
+                for (a = 0; a < dim; a++) {
+                    const int keep = (int)((a >> q) & 1) == k && (int)((b >> q) & 1) == k;
+                    st[a + dim * b] = keep ? st[a + dim * b] * scale : 0.0;
+                }
+        }
     }
     return 0;
 }

@@ -64,6 +64,8 @@ def lib():
         L.orc_noisy_adjoint_grad.argtypes = [ctypes.c_int, op_p, ctypes.c_int, dp, ctypes.c_int,
                                              dp, ctypes.c_char_p, ctypes.c_int, dp, dp]
         L.orc_vec_apply_circuit.argtypes = [dp, ctypes.c_int, op_p, ctypes.c_int, dp]
+        L.orc_measure.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                  ctypes.POINTER(ctypes.c_int), dp]
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -269,3 +271,16 @@ def finite_difference_grad(circuit, theta, terms, indices, h: float = 1e-5) -> n
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def measure(state: np.ndarray, n: int, qubit: int, u: float, density: bool = False):
+    """measure!(state, qubit) of Sec. II.D with the uniform draw u: returns
+    (outcome, probability, collapsed state); the input is not modified."""
+    st = np.ascontiguousarray(np.array(state, dtype=np.complex128).reshape(-1))
+    outcome = ctypes.c_int()
+    prob = ctypes.c_double()
+    r = lib().orc_measure(_dp(st.view(np.float64)), n, int(bool(density)), qubit, float(u),
+                          ctypes.byref(outcome), ctypes.byref(prob))
+    if r != 0:
+        raise ValueError("orc_measure failed")
+    return outcome.value, prob.value, st

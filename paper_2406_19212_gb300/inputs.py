@@ -193,6 +193,32 @@ def diff_20q(seed: int = 2) -> Workload:
     return hea_ry_rz_cz(20, 20, seed, 1.0, name="vqe_20q_hea20")
 
 
+def random_rotation_heisenberg(n: int, layers: int, seed: int, hz: float = 1.0, J: float = 1.0,
+                               name: str = "heisenberg_rand") -> Workload:
+    """Random variational circuit with the Heisenberg observable of the paper's operator
+    example: per layer a rotation drawn from {Rx, Ry, Rz} on every qubit (each with its
+    own angle), then CNOTs on alternating pairs (even layers (0,1),(2,3)..., odd layers
+    (1,2),(3,4)...); H = hz sum Z_i + J sum (X_iX_i+1 + Y_iY_i+1 + Z_iZ_i+1).  The random
+    circuit of the paper's gradient benchmark is not given in its text; this stands in."""
+    rng = _rng(seed)
+    ops: List[Op] = []
+    p = 0
+    for layer in range(layers):
+        for q in range(n):
+            ops.append(Op(ROTATIONS[int(rng.integers(0, 3))], (q,), param=p))
+            p += 1
+        for i in range(layer % 2, n - 1, 2):
+            ops.append(Op("CNOT", (i, i + 1)))
+    theta = rng.uniform(0.0, 2.0 * math.pi, size=p)
+    return Workload(name, Circuit(n, ops, p), theta, heisenberg_1d(n, hz, J))
+
+
+def heisenberg_20q(seed: int = 6) -> Workload:
+    """20 qubits, 10 layers of random rotations + CNOT brick, 200 angles, Heisenberg H
+    (20 Z terms + 57 XX/YY/ZZ terms)."""
+    return random_rotation_heisenberg(20, 10, seed, name="heisenberg_20q_rand10")
+
+
 def ry_rz_cnot_instance(n: int, depth: int, rng: np.random.Generator) -> Workload:
     """One batched-VQE instance: per layer Ry.Rz on every qubit then CNOT(i,i+1);
     H = sum Z_iZ_{i+1} + sum h_i X_i with h_i ~ U[-1, 1]."""

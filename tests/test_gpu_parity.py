@@ -332,3 +332,16 @@ def test_fused_grad_permuted_layout_heisenberg(dtype):
     e_ref, g_ref = O.adjoint_grad(w.circuit, w.theta, obs)
     check_energy(e, e_ref, dtype)
     check_grad(g, g_ref, dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", MODES)
+def test_heisenberg_random_circuit_gradient(dtype, mode):
+    """Random rotations + CNOT brick with the Heisenberg observable (XX and YY groups)."""
+    w = I.random_rotation_heisenberg(11, 6, 21)
+    c = gb.circuit_create(w.circuit)
+    o = gb.obs_create(w.observable, 11)
+    e, g = gb.grad(c, w.theta, o, dtype, mode)
+    e_ref, g_ref = O.adjoint_grad(w.circuit, w.theta, w.observable)
+    check_energy(e, e_ref, dtype)
+    check_grad(g, g_ref, dtype)

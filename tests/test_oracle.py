@@ -286,3 +286,53 @@ def test_noisy_hea_adjoint_matches_shift():
     e, g = O.noisy_adjoint_grad(w.circuit, w.theta, w.observable)
     ps = O.parameter_shift_grad(w.circuit, w.theta, w.observable)
     np.testing.assert_allclose(g, ps, atol=1e-12)
+
+
+# ----------------------------------------------------------------- measurement
+
+def test_measure_listing4_golden():
+    """measure!(state, 2) of the paper's Listing 4: outcome probabilities derived by hand
+    (tests/golden/listing4.txt) and the collapsed states |00> or |11>."""
+    g = _golden("listing4.txt")
+    c = I.Circuit(2, [op("H", (0,)), op("RY", (0,), fixed=(math.pi / 4,)),
+                      op("CNOT", (0, 1))], 0)
+    psi = O.apply_circuit(c, [])
+    k, p, post = O.measure(psi, 2, 1, 0.1)
+    assert k == 0 and p == pytest.approx(g["prob_q1_0"], abs=1e-15)
+    np.testing.assert_allclose(post, [1, 0, 0, 0], atol=1e-15)
+    k, p, post = O.measure(psi, 2, 1, 0.9)
+    assert k == 1 and p == pytest.approx(g["prob_q1_1"], abs=1e-15)
+    np.testing.assert_allclose(post, [0, 0, 0, 1], atol=1e-15)
+
+
+def test_measure_ghz_closed_form():
+    n = 6
+    ops = [op("H", (0,))] + [op("CNOT", (i, i + 1)) for i in range(n - 1)]
+    psi = O.apply_circuit(I.Circuit(n, ops, 0), [])
+    for u, k_ref, idx in ((0.3, 0, 0), (0.7, 1, (1 << n) - 1)):
+        k, p, post = O.measure(psi, n, 3, u)
+        assert k == k_ref and p == pytest.approx(0.5, abs=1e-15)
+        ref = np.zeros(1 << n, complex)
+        ref[idx] = 1.0
+        np.testing.assert_allclose(post, ref, atol=1e-15)
+
+
+def test_measure_density_matches_pure():
+    """On rho = |psi><psi| the density branch gives the same outcome and probability and
+    the projector of the pure branch's collapsed state (two independent code paths)."""
+    n = 5
+    w = I.random_circuit(n, 60, 13)
+    psi = O.apply_circuit(w.circuit, w.theta)
+    rho = np.outer(psi, psi.conj())
+    vec = rho.T.reshape(-1)  # rho_ab at a + 2^n b
+    for q, u in ((0, 0.2), (3, 0.42), (4, 0.97)):
+        k1, p1, post = O.measure(psi, n, q, u)
+        k2, p2, post_rho = O.measure(vec, n, q, u, density=True)
+        assert k1 == k2 and p1 == pytest.approx(p2, abs=1e-13)
+        np.testing.assert_allclose(post_rho, np.outer(post, post.conj()).T.reshape(-1), atol=1e-13)
+        assert np.linalg.norm(post) == pytest.approx(1.0, abs=1e-13)
+        # the collapsed state lives on the outcome's half and keeps the kept amplitudes' ratios
+        idx = np.arange(1 << n)
+        assert np.all(post[((idx >> q) & 1) != k1] == 0)
+        kept = ((idx >> q) & 1) == k1
+        np.testing.assert_allclose(post[kept] * math.sqrt(p1), psi[kept], atol=1e-13)
