@@ -175,6 +175,17 @@ gbvqc_status apply_circuit(sv_handle sv, circuit_handle c, const double *theta, 
 gbvqc_status apply_channel(sv_handle sv, int kind, int qubit, double strength,
                            const double *kraus, int n_kraus);
 
+/* measure!(state, qubit) of Sec. II.D (Listing 4): measures one qubit and collapses the
+ * state in place.  P(k) = w_k / (w_0 + w_1) with w_k the FP64 sum of |psi_a|^2 (pure) or
+ * rho_aa (density) over the indices a whose bit `qubit` is k.  The random draw is the
+ * caller's: u must lie in [0, 1); the outcome is 0 if u < P(0), else 1.  The state is
+ * projected on the outcome and renormalised (pure: divided by sqrt(w_k); density:
+ * P rho P divided by w_k).  Writes *outcome and *prob (its probability, host memory).
+ * Synchronises the state's stream before returning the outcome; the collapse is then
+ * enqueued on that stream.  Errors: ERR_ARG for a NULL pointer, qubit outside
+ * [0, n_qubits), u outside [0, 1) or a state of zero norm; ERR_CUDA if a launch fails. */
+gbvqc_status measure(sv_handle sv, int qubit, double u, int *outcome, double *prob);
+
 /* ---------------------------------------------------------- observables (Sec. II.E) */
 
 /* Pauli sum H = sum_t terms[t].coeff P_t over n_qubits logical qubits (QubitsOperator).

@@ -25,7 +25,8 @@ from ._abi import C64, C128, FUSED, PLAIN, GbvqcError
 __all__ = ["C64", "C128", "PLAIN", "FUSED", "GbvqcError", "StateVector", "CircuitHandle",
            "Observable", "sv_alloc", "sv_wrap", "sv_set", "sv_get", "sv_reset",
            "circuit_create", "apply_circuit", "apply_channel", "obs_create", "expect", "grad",
-           "grad_profile", "grad_batch", "batch_create", "BatchHandle", "expect_noalloc", "VQEEnergy",
+           "grad_profile", "grad_batch", "batch_create", "BatchHandle", "expect_noalloc", "measure",
+           "VQEEnergy",
            "load"]
 
 
@@ -231,6 +232,16 @@ def expect(sv: StateVector, obs: Observable) -> float:
     out = ctypes.c_double()
     _abi.check(_abi.lib().expect(sv.handle, obs.handle, ctypes.byref(out)))
     return out.value
+
+
+def measure(sv: StateVector, qubit: int, u: float) -> Tuple[int, float]:
+    """measure!(state, qubit) of Sec. II.D: collapses the state in place and returns
+    (outcome, probability); u in [0, 1) is the caller's uniform draw (outcome 0 if
+    u < P(0))."""
+    k = ctypes.c_int()
+    p = ctypes.c_double()
+    _abi.check(_abi.lib().measure(sv.handle, int(qubit), float(u), ctypes.byref(k), ctypes.byref(p)))
+    return k.value, p.value
 
 
 def expect_noalloc(psi, n_qubits: int, terms, out, stream=None) -> None:

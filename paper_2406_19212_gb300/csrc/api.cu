@@ -687,6 +687,29 @@ static DensMap interleaved_map(int n)
     return m;
 }
 
+extern "C" gbvqc_status measure(sv_handle sv, int qubit, double u, int *outcome, double *prob)
+{
+    if (!sv || !outcome || !prob) return fail(GBVQC_ERR_ARG, "NULL argument");
+    if (qubit < 0 || qubit >= sv->n_log) return fail(GBVQC_ERR_ARG, "qubit %d of %d", qubit, sv->n_log);
+    if (!(u >= 0.0 && u < 1.0)) return fail(GBVQC_ERR_ARG, "u = %g outside [0, 1)", u);
+    // scratch: 2 partials per block (508 blocks) then the two weights
+    const int max_blocks = 508;
+    double *d_w = sv->d_scratch + 2 * max_blocks;
+    CUDA_TRY(launch_measure_sums(sv->dtype, sv->data, sv->n_log, sv->density, qubit, sv->d_scratch, max_blocks,
+                                 d_w, sv->stream));
+    double w[2];
+    CUDA_TRY(cudaMemcpyAsync(w, d_w, sizeof(w), cudaMemcpyDeviceToHost, sv->stream));
+    CUDA_TRY(cudaStreamSynchronize(sv->stream));
+    const double total = w[0] + w[1];
+    if (!(total > 0.0)) return fail(GBVQC_ERR_ARG, "state has zero norm");
+    const int k = u < w[0] / total ? 0 : 1;
+    *outcome = k;
+    *prob = w[k] / total;
+    const double scale = sv->density ? 1.0 / w[k] : 1.0 / std::sqrt(w[k]);
+    CUDA_TRY(launch_collapse(sv->dtype, sv->data, sv->n_log, sv->density, qubit, k, scale, sv->stream));
+    return GBVQC_OK;
+}
+
 extern "C" gbvqc_status expect(sv_handle sv, obs_handle h, double *out_energy)
 {
     if (!sv || !h || !out_energy) return fail(GBVQC_ERR_ARG, "NULL argument");

@@ -79,6 +79,12 @@ cudaError_t launch_density_expect(int dtype, const void *rho, int n, DensMap map
                                   RedScratch red, double *out, cudaStream_t s);
 // Density adjoint seed psi = vec(H) (psi_ab = H_ab) in the layout `map`; the whole
 // vector is written (zeros off the Pauli support).
+// measure!: out[k] = weight of outcome k of qubit q (FP64, fixed order; scratch holds
+// 2 * max_blocks doubles), and the projection + renormalisation on outcome k.
+cudaError_t launch_measure_sums(int dtype, const void *st, int n, int density, int q, double *scratch,
+                                int max_blocks, double *out, cudaStream_t s);
+cudaError_t launch_collapse(int dtype, void *st, int n, int density, int q, int k, double scale,
+                            cudaStream_t s);
 cudaError_t launch_density_seed(int dtype, void *psi, int n, DensMap map, ObsDev obs,
                                 cudaStream_t s);
 

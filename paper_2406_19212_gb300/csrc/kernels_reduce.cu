@@ -350,4 +350,98 @@ cudaError_t launch_density_seed(int dtype, void *psi, int n, DensMap map, ObsDev
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- measurement
+
+// Per-block partial sums of the outcome weights of qubit q (Sec. II.D measure!):
+// part[2 blk + k] = sum over this block's indices a with bit q of a equal to k of
+// |psi_a|^2 (pure) or Re rho_aa (density, rho_ab at a + 2^n b), in FP64.
+template <typename R>
+__global__ void __launch_bounds__(256) k_measure_sums(const typename CTr<R>::T *__restrict__ st, int n,
+                                                      int density, int q, double *part)
+{
+    __shared__ double sh[2][256];
+    const int64_t dim = int64_t(1) << n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double acc[2] = {0.0, 0.0};
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < dim; a += stride) {
+        double v;
+        if (density) {
+            v = (double)st[a + dim * a].x;
+        } else {
+            const double x = (double)st[a].x, y = (double)st[a].y;
+            v = x * x + y * y;
+        }
+        acc[(a >> q) & 1] += v;
+    }
+    sh[0][threadIdx.x] = acc[0];
+    sh[1][threadIdx.x] = acc[1];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sh[0][0];
+        part[2 * blockIdx.x + 1] = sh[1][0];
+    }
+}
+
+// out[k] = sum over blocks of part[2 blk + k], in block order.
+__global__ void k_measure_finish(const double *__restrict__ part, int nblk, double *out)
+{
+    if (threadIdx.x < 2) {
+        double t = 0.0;
+        for (int b = 0; b < nblk; b++) t += part[2 * b + threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+}
+
+cudaError_t launch_measure_sums(int dtype, const void *st, int n, int density, int q, double *scratch,
+                                int max_blocks, double *out, cudaStream_t s)
+{
+    int64_t gb = ((int64_t(1) << n) + 255) / 256;
+    const int gr = (int)(gb > max_blocks ? max_blocks : gb);
+    if (dtype == 0) k_measure_sums<float><<<gr, 256, 0, s>>>((const float2 *)st, n, density, q, scratch);
+    else k_measure_sums<double><<<gr, 256, 0, s>>>((const double2 *)st, n, density, q, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_measure_finish<<<1, 32, 0, s>>>(scratch, gr, out);
+    return cudaGetLastError();
+}
+
+// Projection on outcome k of qubit q and renormalisation: pure psi_a -> psi_a * scale if
+// bit q of a is k, else 0; density rho_ab -> rho_ab * scale if bit q of a and of b are
+// both k, else 0.
+template <typename R>
+__global__ void k_collapse(typename CTr<R>::T *__restrict__ st, int n, int density, int q, int k, R scale)
+{
+    typedef typename CTr<R>::T T;
+    const int64_t len = int64_t(1) << (density ? 2 * n : n);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
+        const bool keep = density ? (((i >> q) & 1) == k && ((i >> (q + n)) & 1) == k) : ((i >> q) & 1) == k;
+        T v = st[i];
+        if (keep) {
+            v.x *= scale;
+            v.y *= scale;
+        } else {
+            v.x = 0;
+            v.y = 0;
+        }
+        st[i] = v;
+    }
+}
+
+cudaError_t launch_collapse(int dtype, void *st, int n, int density, int q, int k, double scale, cudaStream_t s)
+{
+    const int64_t len = int64_t(1) << (density ? 2 * n : n);
+    const int gr = red_grid(len, 256);
+    if (dtype == 0) k_collapse<float><<<gr, 256, 0, s>>>((float2 *)st, n, density, q, k, (float)scale);
+    else k_collapse<double><<<gr, 256, 0, s>>>((double2 *)st, n, density, q, k, scale);
+    return cudaGetLastError();
+}
+
 }  // namespace gbvqc

@@ -345,3 +345,52 @@ def test_heisenberg_random_circuit_gradient(dtype, mode):
     e_ref, g_ref = O.adjoint_grad(w.circuit, w.theta, w.observable)
     check_energy(e, e_ref, dtype)
     check_grad(g, g_ref, dtype)
+
+
+# ----------------------------------------------------------------- measurement
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_measure_listing4_on_gpu(dtype):
+    """Listing 4 end to end: apply the circuit, measure qubit 2 (0-based 1); the outcome
+    probabilities are the hand-derived ones of tests/golden/listing4.txt."""
+    c = I.Circuit(2, [I.Op("H", (0,)), I.Op("RY", (0,), fixed=(math.pi / 4,)),
+                      I.Op("CNOT", (0, 1))], 0)
+    for u, k_ref, p_ref, idx in ((0.1, 0, (2 - math.sqrt(2)) / 4, 0), (0.9, 1, (2 + math.sqrt(2)) / 4, 3)):
+        sv = gb.sv_alloc(2, dtype)
+        gb.apply_circuit(sv, gb.circuit_create(c), [], gb.PLAIN)
+        k, p = gb.measure(sv, 1, u)
+        assert k == k_ref
+        assert p == pytest.approx(p_ref, abs=1e-7 if dtype == gb.C64 else 1e-14)
+        ref = np.zeros(4, complex)
+        ref[idx] = 1
+        check_amps(gb.sv_get(sv).astype(np.complex128), ref, dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("density", [False, True])
+def test_measure_sequence_matches_oracle(dtype, density):
+    """Three measurements in a row on a random (pure: 11 qubits; density: 5) state:
+    outcome, probability and collapsed state against the oracle after each one."""
+    n = 5 if density else 11
+    if density:
+        rho = I.random_density(n, 8)
+        state = rho.T.reshape(-1).astype(np.complex128)
+    else:
+        state = I.random_state(n, 8)
+    sv = gb.sv_alloc(n, dtype, density)
+    gb.sv_set(sv, state)
+    ref = state
+    for q, u in ((0, 0.37), (n - 1, 0.81), (2, 0.05)):
+        k, p = gb.measure(sv, q, u)
+        k_ref, p_ref, ref = O.measure(ref, n, q, u, density=density)
+        assert k == k_ref
+        assert p == pytest.approx(p_ref, abs=1e-6 if dtype == gb.C64 else 1e-12)
+        got = gb.sv_get(sv).astype(np.complex128)
+        np.testing.assert_allclose(got, ref, atol=AMP_TOL[dtype] * (4 if density else 1), rtol=0)
+
+
+def test_measure_rejects_bad_arguments():
+    sv = gb.sv_alloc(3, gb.C64)
+    for q, u in ((3, 0.5), (-1, 0.5), (0, 1.0), (0, -0.1), (0, float("nan"))):
+        with pytest.raises(gb.GbvqcError):
+            gb.measure(sv, q, u)
