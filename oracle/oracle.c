@@ -57,6 +57,7 @@ typedef struct {
     int32_t q[2];
     int32_t param;     /* index into theta, -1 = fixed */
     int32_t n_kraus;
+    int32_t pmask;     /* FSIM: bit k set = parameter k is variational (theta[param + rank]) */
     double fixed[5];
     double data[32];   /* complex (re, im) pairs, row-major; KRAUS: n_kraus 2x2 blocks */
 } orc_op;
@@ -68,6 +69,17 @@ static int is_channel(int kind) { return kind >= O_DEPOL; }
 static double op_angle(const orc_op *op, const double *theta)
 {
     return op->param >= 0 ? theta[op->param] : op->fixed[0];
+}
+
+/* The five FSIM parameters (theta, phi, d_plus, d_minus, d_minus_off): the variational
+ * ones (bits of pmask, in increasing k) read consecutive entries of theta from param. */
+static void fsim_values(const orc_op *op, const double *theta, double v[5])
+{
+    int k, r = 0;
+    for (k = 0; k < 5; k++) {
+        v[k] = op->fixed[k];
+        if (op->param >= 0 && ((op->pmask >> k) & 1)) v[k] = theta[op->param + r++];
+    }
 }
 
 /* Fill the row-major matrix of a unitary op; returns its qubit count k. */
@@ -117,9 +129,10 @@ static int gate_matrix(const orc_op *op, const double *theta, cplx *M)
     case O_CZ: M[0] = 1; M[5] = 1; M[10] = 1; M[15] = -1; return 2;
     case O_SWAP: M[0] = 1; M[1 * 4 + 2] = 1; M[2 * 4 + 1] = 1; M[15] = 1; return 2;
     case O_ISWAP: M[0] = 1; M[1 * 4 + 2] = I; M[2 * 4 + 1] = I; M[15] = 1; return 2;
-    case O_FSIM: { /* Eq. (FSIM): fixed = (theta, phi, d_plus, d_minus, d_minus_off) */
-        double th = op->fixed[0], ph = op->fixed[1], dp = op->fixed[2];
-        double dm = op->fixed[3], dmo = op->fixed[4];
+    case O_FSIM: { /* Eq. (FSIM): (theta, phi, d_plus, d_minus, d_minus_off) */
+        double v[5];
+        fsim_values(op, theta, v);
+        double th = v[0], ph = v[1], dp = v[2], dm = v[3], dmo = v[4];
         M[0] = 1;
         M[1 * 4 + 1] = cexp(I * (dp + dm)) * cos(th);
         M[1 * 4 + 2] = -I * cexp(I * (dp - dmo)) * sin(th);
@@ -156,6 +169,36 @@ static int gate_derivative(const orc_op *op, const double *theta, cplx *D)
     case O_RY: D[0] = -s / 2; D[1] = -c / 2; D[2] = c / 2; D[3] = -s / 2; return 1;
     case O_RZ: D[0] = -I / 2 * cexp(-I * t / 2); D[3] = I / 2 * cexp(I * t / 2); return 1;
     default: return -1;
+    }
+}
+
+/* Derivative of the FSIM matrix of Eq. (FSIM) with respect to its parameter k (entry by
+ * entry: d/dtheta turns cos into -sin and sin into cos; a phase parameter multiplies each
+ * entry by i times its coefficient in that entry's exponent). */
+static void fsim_derivative(const orc_op *op, const double *theta, int k, cplx *D)
+{
+    double v[5];
+    cplx M[16];
+    int i;
+    fsim_values(op, theta, v);
+    gate_matrix(op, theta, M);
+    for (i = 0; i < 16; i++) D[i] = 0;
+    switch (k) {
+    case 0: {
+        const double th = v[0], dp = v[2], dm = v[3], dmo = v[4];
+        D[1 * 4 + 1] = -cexp(I * (dp + dm)) * sin(th);
+        D[1 * 4 + 2] = -I * cexp(I * (dp - dmo)) * cos(th);
+        D[2 * 4 + 1] = -I * cexp(I * (dp + dmo)) * cos(th);
+        D[2 * 4 + 2] = -cexp(I * (dp - dm)) * sin(th);
+        break;
+    }
+    case 1: D[15] = -I * M[15]; break;
+    case 2:
+        D[5] = I * M[5]; D[6] = I * M[6]; D[9] = I * M[9]; D[10] = I * M[10];
+        D[15] = 2 * I * M[15];
+        break;
+    case 3: D[5] = I * M[5]; D[10] = -I * M[10]; break;
+    default: D[6] = -I * M[6]; D[9] = I * M[9]; break;
     }
 }
 
@@ -391,7 +434,16 @@ int orc_adjoint_grad(int n, const orc_op *ops, int n_ops, const double *theta, i
         int k = gate_matrix(&ops[j], theta, M);
         if (invert(1 << k, M, Minv) != 0) { rc = -3; goto done; }
         apply_k(phi, n, k, ops[j].q, Minv);
-        if (ops[j].param >= 0) {
+        if (ops[j].param >= 0 && ops[j].kind == O_FSIM) {  /* one term per variational parameter */
+            int b, r = 0;
+            for (b = 0; b < 5; b++) {
+                if (!((ops[j].pmask >> b) & 1)) continue;
+                fsim_derivative(&ops[j], theta, b, D);
+                memcpy(tmp, phi, sizeof(cplx) * (size_t)dim);
+                apply_k(tmp, n, 2, ops[j].q, D);
+                grad[ops[j].param + r++] += 2 * creal(inner(psi, tmp, dim));
+            }
+        } else if (ops[j].param >= 0) {
             int kd = gate_derivative(&ops[j], theta, D);
             if (kd < 0) { rc = -4; goto done; }
             memcpy(tmp, phi, sizeof(cplx) * (size_t)dim);

@@ -25,7 +25,7 @@ _KIND = {name: i for i, name in enumerate(
 
 class OrcOp(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("nq", ctypes.c_int32), ("q", ctypes.c_int32 * 2),
-                ("param", ctypes.c_int32), ("n_kraus", ctypes.c_int32),
+                ("param", ctypes.c_int32), ("n_kraus", ctypes.c_int32), ("pmask", ctypes.c_int32),
                 ("fixed", ctypes.c_double * 5), ("data", ctypes.c_double * 32)]
 
 
@@ -84,6 +84,7 @@ def _ops(ops) -> ctypes.Array:
         for t, q in enumerate(op.qubits):
             o.q[t] = q
         o.param = op.param
+        o.pmask = getattr(op, "pmask", 0)
         for t, v in enumerate(op.fixed):
             o.fixed[t] = v
         if op.data is not None:

@@ -36,10 +36,14 @@ class Op:
 
     name   : a name from ALL_NAMES.
     qubits : logical qubits; first listed = least significant bit of the matrix index.
-    param  : index into the parameter vector theta for a variational rotation, -1 if fixed.
+    param  : index into the parameter vector theta for a variational rotation, -1 if fixed;
+             for a variational FSIM the index of its first variational parameter.
     fixed  : fixed parameters: the angle of a fixed RX/RY/RZ, (theta, phi, d_plus,
              d_minus, d_minus_off) of FSIM (missing trailing entries are 0), the strength
              p or gamma of a channel.
+    pmask  : FSIM with param >= 0: bit k set = parameter k of (theta, phi, d_plus,
+             d_minus, d_minus_off) is variational (the paper's `isparas` array); the
+             variational ones read theta[param], theta[param + 1], ... in increasing k.
     data   : complex matrix for DENSE1 (2x2), DENSE2 (4x4), CONTROL (2x2 target block),
              or a list of 2x2 Kraus operators for KRAUS; row-major [row][col].
     """
@@ -48,6 +52,7 @@ class Op:
     param: int = -1
     fixed: Tuple[float, ...] = ()
     data: Optional[object] = None
+    pmask: int = 0
 
 
 @dataclass
@@ -120,6 +125,20 @@ def plain_10q(seed: int = 0) -> Workload:
     return hea_rx_rz_rx(10, 4, seed, 0.5, name="plain_10q_hea4")
 
 
+def _couplers(rows: int, cols: int, kind: int) -> List[Tuple[int, int]]:
+    """Coupler pattern kind of a rows x cols grid (qubit = cols*r + c):
+    A (0): (r,c)-(r,c+1), c even; B (1): c odd; C (2): (r,c)-(r+1,c), r even; D (3): r odd."""
+    pairs = []
+    for r in range(rows):
+        for c in range(cols):
+            q = cols * r + c
+            if kind < 2 and c + 1 < cols and c % 2 == kind:
+                pairs.append((q, q + 1))
+            if kind >= 2 and r + 1 < rows and r % 2 == kind - 2:
+                pairs.append((q, q + cols))
+    return pairs
+
+
 def grid_rqc(rows: int, cols: int, cycles: int, seed: int) -> Workload:
     """Random circuit on a rows x cols grid (qubit = cols*r + c).
 
@@ -134,17 +153,7 @@ def grid_rqc(rows: int, cols: int, cycles: int, seed: int) -> Workload:
     ops: List[Op] = []
     last = [-1] * n
     names = ("SX", "SY", "SW")
-    patterns = []
-    for kind in range(4):
-        pairs = []
-        for r in range(rows):
-            for c in range(cols):
-                q = cols * r + c
-                if kind < 2 and c + 1 < cols and c % 2 == kind:
-                    pairs.append((q, q + 1))
-                if kind >= 2 and r + 1 < rows and r % 2 == kind - 2:
-                    pairs.append((q, q + cols))
-        patterns.append(pairs)
+    patterns = [_couplers(rows, cols, kind) for kind in range(4)]
     for t in range(cycles):
         for q in range(n):
             choices = [i for i in range(3) if i != last[q]]
@@ -217,6 +226,40 @@ def heisenberg_20q(seed: int = 6) -> Workload:
     """20 qubits, 10 layers of random rotations + CNOT brick, 200 angles, Heisenberg H
     (20 Z terms + 57 XX/YY/ZZ terms)."""
     return random_rotation_heisenberg(20, 10, seed, name="heisenberg_20q_rand10")
+
+
+def fsim_grid_vqe(rows: int, cols: int, cycles: int, seed: int, pmask: int = 0b00011,
+                  name: str = "fsim_vqe") -> Workload:
+    """Grid circuit of the random-circuit construction (sqrt(X/Y/W) per qubit, never the
+    same twice in a row, then FSIM on the cycle's coupler pattern) whose FSIM parameters
+    selected by pmask are variational (initial values: theta ~ pi/2 + N(0, .05),
+    phi ~ pi/6 + N(0, .05), the Delta's ~ N(0, .1)); H = sum Z_iZ_i+1 + 0.5 sum X_i over
+    the qubit index chain."""
+    rng = _rng(seed)
+    n = rows * cols
+    names = ("SX", "SY", "SW")
+    last = [-1] * n
+    ops: List[Op] = []
+    theta: List[float] = []
+    p = 0
+    for t in range(cycles):
+        for q in range(n):
+            choices = [i for i in range(3) if i != last[q]]
+            g = choices[int(rng.integers(0, len(choices)))]
+            last[q] = g
+            ops.append(Op(names[g], (q,)))
+        for (a, b) in _couplers(rows, cols, t % 4):
+            vals = [math.pi / 2 + rng.normal(0, 0.05), math.pi / 6 + rng.normal(0, 0.05),
+                    rng.normal(0, 0.1), rng.normal(0, 0.1), rng.normal(0, 0.1)]
+            if pmask:
+                ops.append(Op("FSIM", (a, b), param=p, fixed=tuple(vals), pmask=pmask))
+                for k in range(5):
+                    if (pmask >> k) & 1:
+                        theta.append(vals[k])
+                        p += 1
+            else:
+                ops.append(Op("FSIM", (a, b), fixed=tuple(vals)))
+    return Workload(name, Circuit(n, ops, p), np.array(theta), ising_chain(n, [0.5] * n))
 
 
 def ry_rz_cnot_instance(n: int, depth: int, rng: np.random.Generator) -> Workload:

@@ -18,8 +18,8 @@ from tests.dense_ref import PAULI, embed, pauli_operator
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def op(name, qubits, param=-1, fixed=(), data=None):
-    return I.Op(name, tuple(qubits), param, tuple(fixed), data)
+def op(name, qubits, param=-1, fixed=(), data=None, pmask=0):
+    return I.Op(name, tuple(qubits), param, tuple(fixed), data, pmask)
 
 
 # ----------------------------------------------------------------- gate matrices
@@ -336,3 +336,60 @@ def test_measure_density_matches_pure():
         assert np.all(post[((idx >> q) & 1) != k1] == 0)
         kept = ((idx >> q) & 1) == k1
         np.testing.assert_allclose(post[kept] * math.sqrt(p1), psi[kept], atol=1e-13)
+
+
+# ----------------------------------------------------- variational FSIM (five parameters)
+
+def test_fsim_derivative_matches_matrix_differences():
+    """The oracle's analytic dFSIM/dp_k against central differences of the matrix."""
+    vals = [1.1, 0.7, 0.3, -0.2, 0.45]
+    for k in range(5):
+        c = I.Circuit(2, [op("FSIM", (0, 1), param=0, fixed=tuple(vals), pmask=1 << k)], 1)
+        h = 1e-6
+        Mp = O.gate_matrix(I.Op("FSIM", (0, 1), fixed=tuple(v + (h if i == k else 0) for i, v in enumerate(vals))))
+        Mm = O.gate_matrix(I.Op("FSIM", (0, 1), fixed=tuple(v - (h if i == k else 0) for i, v in enumerate(vals))))
+        # gradient of <psi|H|psi> for a single FSIM on a fixed input, two ways
+        psi0 = I.random_state(2, 3 + k)
+        terms = [(0.8, ((0, "X"), (1, "Y"))), (-0.3, ((1, "Z"),)), (0.5, ((0, "Y"),))]
+        Hm = pauli_operator(terms, 2)
+        fd = ((Mp @ psi0).conj() @ Hm @ (Mp @ psi0) - (Mm @ psi0).conj() @ Hm @ (Mm @ psi0)).real / (2 * h)
+        prep = [op("DENSE2", (0, 1), data=_prep_unitary(psi0))]
+        c2 = I.Circuit(2, prep + c.ops, 1)
+        _, g = O.adjoint_grad(c2, [vals[k]], terms)
+        assert g[0] == pytest.approx(fd, abs=1e-7)
+
+
+def _prep_unitary(psi0):
+    """A unitary whose first column is psi0 (Householder-style via QR)."""
+    A = np.random.default_rng(0).normal(size=(4, 4)) + 1j * np.random.default_rng(1).normal(size=(4, 4))
+    A[:, 0] = psi0
+    Q, R = np.linalg.qr(A)
+    Q[:, 0] *= R[0, 0] / abs(R[0, 0])
+    assert np.allclose(Q[:, 0], psi0)
+    return Q
+
+
+def test_fsim_grad_shift_rules_and_fd():
+    """Variational FSIM on a 3x3 grid circuit.  theta: its generator (XX+YY)/2 has
+    eigenvalues -1, 0, 0, 1, so the loss holds frequencies 1 and 2 in theta and the exact
+    four-term rule f' = (1 - sqrt2)/2 [f(+pi/2) - f(-pi/2)] + [f(+pi/4) - f(-pi/4)] applies
+    (solving 2 c1 sin(w s1) + 2 c2 sin(w s2) = w for w = 1, 2); phi: generator |11><11|
+    (eigenvalues 0, 1), the two-term +-pi/2 rule; the Delta's by central differences."""
+    w = I.fsim_grid_vqe(3, 3, 4, 7, pmask=0b11111)
+    e, g = O.adjoint_grad(w.circuit, w.theta, w.observable)
+    assert e == pytest.approx(O.energy(w.circuit, w.theta, w.observable), abs=1e-12)
+    L = lambda th: O.energy(w.circuit, th, w.observable)
+    for j in range(0, w.circuit.n_params, 3):
+        comp = j % 5  # parameters of a gate are consecutive: k = j mod 5 with all bits set
+        t = np.array(w.theta, dtype=float)
+        if comp == 0:
+            def shift(s):
+                tp, tm = t.copy(), t.copy(); tp[j] += s; tm[j] -= s
+                return L(tp) - L(tm)
+            ref = (1 - math.sqrt(2)) / 2 * shift(np.pi / 2) + shift(np.pi / 4)
+        elif comp == 1:
+            tp, tm = t.copy(), t.copy(); tp[j] += np.pi / 2; tm[j] -= np.pi / 2
+            ref = 0.5 * (L(tp) - L(tm))
+        else:
+            ref = O.finite_difference_grad(w.circuit, t, w.observable, [j], h=1e-5)[0]
+        assert g[j] == pytest.approx(ref, abs=1e-8 if comp < 2 else 1e-7)
