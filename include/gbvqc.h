@@ -68,9 +68,16 @@ typedef struct gbvqc_op {
     int32_t kind;          /* GBVQC_X .. GBVQC_KRAUS                                    */
     int32_t qubits[2];     /* logical qubits; qubits[1] unused for one-qubit kinds      */
     int32_t param_index;   /* RX/RY/RZ: index into theta (the paper's isparas=true);
-                              -1 = fixed angle params[0].  Must be -1 for other kinds.  */
+                              -1 = fixed angle params[0].  FSIM: index of the first
+                              variational parameter (see param_mask).  Must be -1 for
+                              other kinds.                                              */
     int32_t n_kraus;       /* KRAUS only: number of 2x2 operators in data (1..4)        */
-    int32_t reserved;      /* must be 0                                                 */
+    int32_t param_mask;    /* FSIM with param_index >= 0 (pure-state circuits): bit k set
+                              = parameter k of (theta, phi, d_plus, d_minus, d_minus_off)
+                              is variational (the paper's isparas array, Sec. II.B); the
+                              variational ones read theta[param_index], [param_index + 1],
+                              ... in increasing k, the others params[k].  Ignored by
+                              other kinds.                                              */
     double  params[5];     /* fixed angle / FSIM angles / channel strength              */
     double  data[32];      /* DENSE1 (2x2), DENSE2 (4x4), CONTROL (2x2 target block),
                               KRAUS (n_kraus 2x2 blocks): row-major (re, im) pairs      */
@@ -126,10 +133,12 @@ gbvqc_status sv_info(sv_handle sv, int *n_qubits, int *dtype, int *is_density, v
 
 /* Build a circuit over n_qubits logical qubits from n_ops operations (copied; the caller
  * keeps ownership of ops).  n_params = length of the theta vectors passed later; every
- * param_index must lie in [0, n_params).  is_density = 1 allows channels and makes
- * every unitary act as U rho U^dag (Sec. III.D).  Builds and caches the execution plans
- * (per-gate records and the fused tile schedule).  Errors: ERR_ARG (bad kind, qubit,
- * param index, Kraus count), ERR_NOT_DENSITY (channel with is_density = 0). */
+ * param_index must lie in [0, n_params) (a variational FSIM: all of its parameter
+ * indices).  is_density = 1 allows channels and makes every unitary act as U rho U^dag
+ * (Sec. III.D).  Builds and caches the execution plans (per-gate records and the fused
+ * tile schedule).  Errors: ERR_ARG (bad kind, qubit, param index, FSIM param_mask outside
+ * [1, 31], Kraus count), ERR_NOT_DENSITY (channel with is_density = 0), ERR_UNSUPPORTED
+ * (variational FSIM in a density circuit). */
 gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qubits, int n_params,
                             int is_density, circuit_handle *out);
 gbvqc_status circuit_free(circuit_handle c);

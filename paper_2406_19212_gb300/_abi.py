@@ -37,7 +37,7 @@ class GbvqcError(RuntimeError):
 class Op(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("qubits", ctypes.c_int32 * 2),
                 ("param_index", ctypes.c_int32), ("n_kraus", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("params", ctypes.c_double * 5),
+                ("param_mask", ctypes.c_int32), ("params", ctypes.c_double * 5),
                 ("data", ctypes.c_double * 32)]
 
 
@@ -133,6 +133,7 @@ def ops_array(ops) -> ctypes.Array:
         for t, q in enumerate(op.qubits):
             o.qubits[t] = int(q)
         o.param_index = int(op.param)
+        o.param_mask = int(getattr(op, "pmask", 0))
         for t, v in enumerate(op.fixed):
             o.params[t] = float(v)
         if op.data is not None:

@@ -108,6 +108,7 @@ static double ftype_flops(int ft)
     case FT_DENSE2: return 30;
     case FT_CTRL2: return 7;
     case FT_BLOCK2: return 10;
+    case FT_PROBE2: return 34;
     default: return 6;  // real / imaginary / anti-diagonal / diagonal
     }
 }
@@ -377,6 +378,9 @@ struct PlainGate {
     int param;
     double gscale;
     int slot;
+    // further derivatives of the same gate (variational FSIM parameters after the first)
+    int n_extra = 0;
+    int ex_rec[4] = {-1, -1, -1, -1}, ex_param[4] = {-1, -1, -1, -1}, ex_slot[4] = {-1, -1, -1, -1};
 };
 
 struct Workspace {
@@ -776,23 +780,63 @@ static int add_dyn(gbvqc_circuit *c, int param, int rot, int variant, int domain
     d.rot = rot;
     d.variant = variant;
     d.domain = domain;
-    MatRec r{};               // zero: materialisation writes only the entries a matrix uses
-    materialize(d, 0.0, &r);  // placeholder, refreshed from theta before every use
+    MatRec r{};  // zero: materialisation writes only the entries a matrix uses
+    const double zero[5] = {0, 0, 0, 0, 0};
+    materialize(d, zero, &r);  // placeholder, refreshed from theta before every use
     c->recs.push_back(r);
     c->dyn.push_back(d);
     return d.rec;
 }
 
-// Records of one unitary op in a domain: forward, inverse, derivative (or -1), and shape.
+static bool is_var_fsim(const gbvqc_op &op) { return op.kind == GBVQC_FSIM && op.param_index >= 0; }
+
+// theta-dependent FSIM record (variant FWD / INV / DER / GEN; comp = FSIM parameter)
+static int add_dyn_fsim(gbvqc_circuit *c, const gbvqc_op &op, int variant, int comp)
+{
+    DynRec d{};
+    d.rec = (int)c->recs.size();
+    d.param = op.param_index;
+    d.rot = ROT_FSIM;
+    d.variant = variant;
+    d.domain = DOM_KET;
+    d.comp = comp;
+    d.mask = op.param_mask;
+    for (int k = 0; k < 5; k++) d.fixed[k] = op.params[k];
+    MatRec r{};
+    const double zero[5] = {0, 0, 0, 0, 0};
+    materialize(d, zero, &r);
+    c->recs.push_back(r);
+    c->dyn.push_back(d);
+    return d.rec;
+}
+
+// Records of one unitary op in a domain: forward, inverse, derivative (or -1), and shape;
+// a variational FSIM lists per variational parameter its derivative record (dU/dp), its
+// generator record ((dU/dp) U^dag) and its theta index.
+struct OpComp {
+    int der, gen, param;
+};
 struct OpRecs {
     int f, i, d, shape, dshape;
     Mat Mf, Mi;
+    std::vector<OpComp> comps;
 };
 
 static OpRecs op_records(gbvqc_circuit *c, const gbvqc_op &op, int domain)
 {
     OpRecs o{};
     o.d = -1;
+    if (is_var_fsim(op)) {  // pure states only (checked by circuit_create)
+        o.f = add_dyn_fsim(c, op, VAR_FWD, 0);
+        o.i = add_dyn_fsim(c, op, VAR_INV, 0);
+        o.shape = SH_BLOCK2;  // every FSIM has the block structure
+        o.dshape = SH_DENSE2;
+        for (int k = 0, j = 0; k < 5; k++)
+            if ((op.param_mask >> k) & 1)
+                o.comps.push_back(OpComp{add_dyn_fsim(c, op, VAR_DER, k), add_dyn_fsim(c, op, VAR_GEN, k),
+                                         op.param_index + j++});
+        return o;
+    }
     if (is_rotation(op.kind) && op.param_index >= 0) {
         int rot = op.kind - GBVQC_RX;
         o.f = add_dyn(c, op.param_index, rot, VAR_FWD, domain);
@@ -986,6 +1030,21 @@ static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGa
                 g.param = op.param_index;
             }
             out.push_back(g);
+            // variational FSIM: one gradient probe per parameter, right after the gate
+            // (the reverse sweep reads 2 Re <Psi| (dU/dp) U^dag |Phi> before uncomputing U)
+            for (const OpComp &cp : r.comps) {
+                PGate pr = g;
+                pr.ftype = FT_PROBE2;
+                pr.diag = false;
+                pr.rec_f = pr.rec_i = pr.rec_a = cp.gen;
+                pr.perm_f = pr.perm_r = 0;
+                pr.gen = GEN_M2;
+                pr.gq = op.qubits[0];
+                pr.coef = 2.0f;
+                pr.param = cp.param;
+                pr.cz = false;
+                out.push_back(pr);
+            }
             continue;
         }
         if (is_channel(op.kind)) {
@@ -1067,8 +1126,16 @@ extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qub
             if (op.qubits[u] < 0 || op.qubits[u] >= n_qubits)
                 return fail(GBVQC_ERR_ARG, "op %d: qubit %d out of range", j, op.qubits[u]);
         if (k == 2 && op.qubits[0] == op.qubits[1]) return fail(GBVQC_ERR_ARG, "op %d: repeated qubit", j);
-        if (op.param_index >= 0 && (!is_rotation(op.kind) || op.param_index >= n_params))
+        if (op.param_index >= 0 && op.kind == GBVQC_FSIM) {
+            if (op.param_mask < 1 || op.param_mask > 31)
+                return fail(GBVQC_ERR_ARG, "op %d: FSIM param_mask %d", j, op.param_mask);
+            if (op.param_index + __builtin_popcount(op.param_mask) > n_params)
+                return fail(GBVQC_ERR_ARG, "op %d: FSIM parameters beyond n_params", j);
+            if (is_density)
+                return fail(GBVQC_ERR_UNSUPPORTED, "op %d: variational FSIM on a density matrix", j);
+        } else if (op.param_index >= 0 && (!is_rotation(op.kind) || op.param_index >= n_params)) {
             return fail(GBVQC_ERR_ARG, "op %d: bad param_index %d", j, op.param_index);
+        }
         if (op.param_index < -1) return fail(GBVQC_ERR_ARG, "op %d: bad param_index %d", j, op.param_index);
         if (is_channel(op.kind)) {
             if (!is_density) return fail(GBVQC_ERR_NOT_DENSITY, "op %d: channel in a pure-state circuit", j);
@@ -1089,7 +1156,8 @@ extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qub
     c->n_params = n_params;
     c->density = is_density ? 1 : 0;
     c->ops.assign(ops, ops + n_ops);
-    for (const gbvqc_op &op : c->ops) c->n_param_ops += op.param_index >= 0 ? 1 : 0;
+    for (const gbvqc_op &op : c->ops)
+        c->n_param_ops += op.param_index < 0 ? 0 : is_var_fsim(op) ? __builtin_popcount(op.param_mask) : 1;
     // per-gate schedule in the standard layout
     for (const gbvqc_op &op : c->ops) {
         int k = kind_qubits(op.kind);
@@ -1097,6 +1165,17 @@ extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qub
             OpRecs r = op_records(c, op, DOM_KET);
             PlainGate g{r.shape, op.qubits[0], k == 2 ? op.qubits[1] : 0, r.f, r.i, r.i, 1, op.qubits[0], 0,
                         r.d, op.param_index, 2.0, -1};
+            if (!r.comps.empty()) {  // variational FSIM: dU/dp on both qubits per parameter
+                g.der_k = 2;
+                g.dq1 = op.qubits[1];
+                g.rec_d = r.comps[0].der;
+                g.param = r.comps[0].param;
+                for (size_t e = 1; e < r.comps.size(); e++) {
+                    g.ex_rec[g.n_extra] = r.comps[e].der;
+                    g.ex_param[g.n_extra] = r.comps[e].param;
+                    g.n_extra++;
+                }
+            }
             c->plain.push_back(g);
         } else if (is_channel(op.kind)) {
             Mat S = superop(channel_kraus(op.kind, op.params[0], op.data, op.n_kraus)), Si;
@@ -1121,11 +1200,16 @@ extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qub
         }
     }
     std::vector<int> slot_param;  // parameter of each per-gate gradient slot
-    for (PlainGate &g : c->plain)
+    for (PlainGate &g : c->plain) {
         if (g.param >= 0 && g.rec_d >= 0) {
             g.slot = (int)slot_param.size();
             slot_param.push_back(g.param);
         }
+        for (int e = 0; e < g.n_extra; e++) {
+            g.ex_slot[e] = (int)slot_param.size();
+            slot_param.push_back(g.ex_param[e]);
+        }
+    }
     c->plain_slots = (int)slot_param.size();
     c->map_std = standard_map(n_qubits);
     c->map_grad = interleaved_map(n_qubits);
@@ -1510,6 +1594,11 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
                                  return launch_dot_matrix(dtype, w.psi, w.phi, c->n_phys, g.der_k, g.dq0, g.dq1,
                                                           c->d_recs + g.rec_d, g.gscale, red, w.d_slot_grad + g.slot, s);
                              }));
+            for (int e = 0; e < g.n_extra; e++)
+                ST_TRY(run_k("dot_derivative", (shape_flops(SH_DENSE2) + 4) * amps, 2 * sb, s, [&] {
+                    return launch_dot_matrix(dtype, w.psi, w.phi, c->n_phys, g.der_k, g.dq0, g.dq1,
+                                             c->d_recs + g.ex_rec[e], g.gscale, red, w.d_slot_grad + g.ex_slot[e], s);
+                }));
             ST_TRY(plain_gate(c, dtype, w.psi, g, g.rec_a, s));
         }
         ST_TRY(run_k("accumulate", 0, 0, s, [&] {
@@ -1837,7 +1926,7 @@ static gbvqc_status batch_build(gbvqc_batch *b)
         chunks += ((int64_t(1) << c->n_phys) + (1 << kPauliChunkBits) - 1) >> kPauliChunkBits;
         max_passes = std::max(max_passes, (int)P.fwd.size());
         for (const DynRec &d : c->dyn)
-            dyn.push_back(BatchDyn{c->d_recs + d.rec, b->param_off[i] + d.param, d.rot, d.variant, d.domain});
+            dyn.push_back(BatchDyn{c->d_recs + d.rec, b->param_off[i] + d.param, 0, d});
     }
     b->state_bytes = (size_t)amps * amp;
     ST_TRY(dev_alloc((unsigned char **)&b->phi_all, b->state_bytes));

@@ -37,15 +37,20 @@ inline __host__ __device__ int shape_qubits(int sh) { return sh >= SH_DENSE2 && 
 // and of its two diagonal phases (rows 0 and 3).
 #define GBVQC_BLOCK2_U(m) {(m)[10], (m)[11], (m)[12], (m)[13], (m)[18], (m)[19], (m)[20], (m)[21]}
 
-enum Rot : int32_t { ROT_X = 0, ROT_Y = 1, ROT_Z = 2 };
-enum Variant : int32_t { VAR_FWD = 0, VAR_INV = 1, VAR_DER = 2 };
+enum Rot : int32_t { ROT_X = 0, ROT_Y = 1, ROT_Z = 2, ROT_FSIM = 3 };
+// FWD: U; INV: U^-1 (= U^dag); DER: dU/dp; GEN: (dU/dp) U^dag, the derivative read from
+// the state after the gate (FSIM parameter p = comp).
+enum Variant : int32_t { VAR_FWD = 0, VAR_INV = 1, VAR_DER = 2, VAR_GEN = 3 };
 // KET: U on the ket (or pure) qubit; BRA: conj(U) on the bra qubit q+n;
 // SUPER: the 4x4 U (x) conj(U) on (q, q+n) of the vectorised density matrix (Eq. channel2).
 enum Domain : int32_t { DOM_KET = 0, DOM_BRA = 1, DOM_SUPER = 2 };
 
-// A matrix record whose entries depend on theta[param].
+// A matrix record whose entries depend on theta[param] (FSIM: on theta[param + j] for
+// the j-th set bit of mask; the parameters outside mask take their values from fixed).
 struct DynRec {
-    int32_t rec, param, rot, variant, domain, pad;
+    int32_t rec, param, rot, variant, domain, comp;
+    int32_t mask, pad;
+    double fixed[5];
 };
 
 // 2x2 rotation exp(-i t P / 2) for P = X, Y, Z (Sec. II.B: Rx, Ry with the unitary sign,
@@ -96,11 +101,122 @@ inline __host__ __device__ void kron_conj(const double *A, const double *B, doub
                 }
 }
 
-// Fill a record for a theta-dependent matrix.
-inline __host__ __device__ void materialize(const DynRec &r, double t, MatRec *out)
+inline __host__ __device__ void cis(double a, double &c, double &s)
+{
+#ifdef __CUDA_ARCH__
+    sincos(a, &s, &c);
+#else
+    s = sin(a);
+    c = cos(a);
+#endif
+}
+
+// FSIM of Eq. (FSIM) with v = (theta, phi, d_plus, d_minus, d_minus_off), row-major re/im
+// (first qubit = matrix bit 0; the 2x2 block sits on rows/columns 1 and 2), or with
+// comp >= 0 its derivative with respect to v[comp]: d/dtheta turns cos into -sin and sin
+// into cos; a phase parameter multiplies each entry by i times its coefficient.
+inline __host__ __device__ void fsim_matrix(const double *v, int comp, double *m)
+{
+    double ct, st, c11, s11, c12, s12, c21, s21, c22, s22, c33, s33;
+    cis(v[0], ct, st);
+    cis(v[2] + v[3], c11, s11);
+    cis(v[2] - v[4], c12, s12);
+    cis(v[2] + v[4], c21, s21);
+    cis(v[2] - v[3], c22, s22);
+    cis(2.0 * v[2] - v[1], c33, s33);
+    for (int i = 0; i < 32; i++) m[i] = 0.0;
+    // entries as (amplitude a, phase cis(x)): 11 = cos(th) cis, 12 = -i sin(th) cis,
+    // 21 = -i sin(th) cis, 22 = cos(th) cis, 33 = cis
+    double a11 = ct, a12 = st, a22 = ct;           // real amplitudes (12, 21 carry the -i)
+    double f00 = 1, f11 = 1, f12 = 1, f21 = 1, f22 = 1, f33 = 1;  // i-multipliers (real part)
+    double g11 = 0, g12 = 0, g21 = 0, g22 = 0, g33 = 0;            // (imaginary part)
+    if (comp == 0) {
+        a11 = -st; a12 = ct; a22 = -st;
+        f33 = 0; f00 = 0;
+    } else if (comp >= 1) {
+        // d/dv_k: entry * (i * coefficient of v_k in the entry's exponent)
+        const double k11 = comp == 2 ? 1 : comp == 3 ? 1 : 0;
+        const double k12 = comp == 2 ? 1 : comp == 4 ? -1 : 0;
+        const double k21 = comp == 2 ? 1 : comp == 4 ? 1 : 0;
+        const double k22 = comp == 2 ? 1 : comp == 3 ? -1 : 0;
+        const double k33 = comp == 2 ? 2 : comp == 1 ? -1 : 0;
+        f00 = 0;
+        f11 = 0; g11 = k11;
+        f12 = 0; g12 = k12;
+        f21 = 0; g21 = k21;
+        f22 = 0; g22 = k22;
+        f33 = 0; g33 = k33;
+    }
+    // z = (f + i g) * amplitude * cis; the -i of entries 12 and 21 applied last
+    auto put = [&](int idx, double amp, double c, double s, double f, double g, bool minus_i) {
+        double re = amp * (f * c - g * s), im = amp * (f * s + g * c);
+        if (minus_i) {
+            const double t = re;
+            re = im;
+            im = -t;
+        }
+        m[2 * idx] = re;
+        m[2 * idx + 1] = im;
+    };
+    m[0] = f00;
+    put(5, a11, c11, s11, f11, g11, false);
+    put(6, a12, c12, s12, f12, g12, true);
+    put(9, a12, c21, s21, f21, g21, true);
+    put(10, a22, c22, s22, f22, g22, false);
+    put(15, 1.0, c33, s33, f33, g33, false);
+}
+
+// c = a * b^dag for 4x4 complex row-major re/im matrices.
+inline __host__ __device__ void mul_dag4(const double *a, const double *b, double *c)
+{
+    for (int r = 0; r < 4; r++)
+        for (int col = 0; col < 4; col++) {
+            double re = 0, im = 0;
+            for (int k = 0; k < 4; k++) {
+                const double ar = a[2 * (4 * r + k)], ai = a[2 * (4 * r + k) + 1];
+                const double br = b[2 * (4 * col + k)], bi = -b[2 * (4 * col + k) + 1];  // conj(b[col][k])
+                re += ar * br - ai * bi;
+                im += ar * bi + ai * br;
+            }
+            c[2 * (4 * r + col)] = re;
+            c[2 * (4 * r + col) + 1] = im;
+        }
+}
+
+// Fill a record for a theta-dependent matrix; th points at theta[r.param].
+inline __host__ __device__ void materialize(const DynRec &r, const double *th, MatRec *out)
 {
     double m[32];
     for (int i = 0; i < 32; i++) m[i] = 0.0;
+    if (r.rot == ROT_FSIM) {
+        double v[5];
+        for (int k = 0, j = 0; k < 5; k++) v[k] = ((r.mask >> k) & 1) ? th[j++] : r.fixed[k];
+        if (r.variant == VAR_FWD) {
+            fsim_matrix(v, -1, m);
+        } else if (r.variant == VAR_DER) {
+            fsim_matrix(v, r.comp, m);
+        } else {
+            double u[32];
+            fsim_matrix(v, -1, u);
+            if (r.variant == VAR_INV) {  // U^dag
+                for (int a = 0; a < 4; a++)
+                    for (int b = 0; b < 4; b++) {
+                        m[2 * (4 * a + b)] = u[2 * (4 * b + a)];
+                        m[2 * (4 * a + b) + 1] = -u[2 * (4 * b + a) + 1];
+                    }
+            } else {  // VAR_GEN: (dU/dv) U^dag
+                double d[32];
+                fsim_matrix(v, r.comp, d);
+                mul_dag4(d, u, m);
+            }
+        }
+        for (int i = 0; i < 32; i++) {
+            out->d[i] = m[i];
+            out->f[i] = (float)m[i];
+        }
+        return;
+    }
+    const double t = th[0];
     if (r.domain == DOM_SUPER) {
         double U[8], dU[8];
         if (r.variant == VAR_DER) {
@@ -138,11 +254,13 @@ enum FType : int32_t {
     FT_LAYER1 = 9,  // one-qubit non-diagonal gates on distinct register slots (DEnt list):
                     // a = slot mask; entry k = Shape, ca = slot, cls = GenType
     FT_BLOCK2 = 10,  // SH_BLOCK2 on two register slots
-    FT_IMAG1 = 11    // SH_IMAG1 on one register slot
+    FT_IMAG1 = 11,   // SH_IMAG1 on one register slot
+    FT_PROBE2 = 12   // reverse only: gradient read 2 Re <Psi| K |Phi> with the 4x4 K on two
+                     // register slots; the states are not changed
 };
 // Generator of a variational gate for the fused reverse sweep: the gradient term is
 // coef * Im <Psi| P |Phi> with both states taken right after the gate.
-enum GenType : int32_t { GEN_NONE = 0, GEN_X = 1, GEN_Y = 2, GEN_Z = 3 };
+enum GenType : int32_t { GEN_NONE = 0, GEN_X = 1, GEN_Y = 2, GEN_Z = 3, GEN_M2 = 4 /* FT_PROBE2 */ };
 
 // Matrices of a pass are staged in shared memory in units of 8 elements (a 2x2 matrix is
 // one unit, a 4x4 matrix four); unit u copies elements 8*part .. 8*part+7 of record rec.

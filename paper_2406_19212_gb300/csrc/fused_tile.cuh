@@ -133,6 +133,47 @@ __device__ __forceinline__ void rg2_dispatch(int k0, int k1, typename CT<R>::T *
 #undef GBVQC_RG2
 }
 
+// Gradient probe: sum over the register quadruples of Re sum_r conj(p_r) (K f)_r with the
+// 4x4 K (row-major re/im; K0 = matrix bit 0, K1 = matrix bit 1), f = Phi, p = Psi.
+template <typename R, int NR, int K0, int K1>
+__device__ __forceinline__ R probe2(const typename CT<R>::T *f, const typename CT<R>::T *p, const R *m)
+{
+    typedef typename CT<R>::T T;
+    R s = 0;
+#pragma unroll
+    for (int j = 0; j < (1 << NR); j++) {
+        if (j & ((1 << K0) | (1 << K1))) continue;
+        const int idx[4] = {j, j | (1 << K0), j | (1 << K1), j | (1 << K0) | (1 << K1)};
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            T w = cmul<T, R>(m[8 * r], m[8 * r + 1], f[idx[0]]);
+#pragma unroll
+            for (int c = 1; c < 4; c++) cfma<T, R>(m[8 * r + 2 * c], m[8 * r + 2 * c + 1], f[idx[c]], w);
+            s += p[idx[r]].x * w.x + p[idx[r]].y * w.y;
+        }
+    }
+    return s;
+}
+
+template <typename R, int NR>
+__device__ __forceinline__ R probe2_dispatch(int k0, int k1, const typename CT<R>::T *f, const typename CT<R>::T *p,
+                                             const R *m)
+{
+#define GBVQC_PR2(K0, K1) \
+    case K0 * 8 + K1:     \
+        if constexpr (K0 < NR && K1 < NR) return probe2<R, NR, K0, K1>(f, p, m); \
+        break;
+    switch (k0 * 8 + k1) {
+        GBVQC_PR2(0, 1) GBVQC_PR2(0, 2) GBVQC_PR2(0, 3) GBVQC_PR2(0, 4)
+        GBVQC_PR2(1, 0) GBVQC_PR2(1, 2) GBVQC_PR2(1, 3) GBVQC_PR2(1, 4)
+        GBVQC_PR2(2, 0) GBVQC_PR2(2, 1) GBVQC_PR2(2, 3) GBVQC_PR2(2, 4)
+        GBVQC_PR2(3, 0) GBVQC_PR2(3, 1) GBVQC_PR2(3, 2) GBVQC_PR2(3, 4)
+        GBVQC_PR2(4, 0) GBVQC_PR2(4, 1) GBVQC_PR2(4, 2) GBVQC_PR2(4, 3)
+    }
+#undef GBVQC_PR2
+    return 0;
+}
+
 // Bit of a non-register position code (constant over the thread's amplitudes).
 template <int NR>
 __device__ __forceinline__ int const_bit(int code, int base, int64_t tilebase)
@@ -770,6 +811,12 @@ __device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, 
                     phase_block<R, NR>(ents, g.perm, smat, false, cst[0], cst[1], a, nullptr, base, tilebase);
                 }
                 continue;
+            }
+            if constexpr (REV && TWOQ) {
+                if (g.type == FT_PROBE2) {  // gradient read only: the states stay as they are
+                    emit_partial<R>(rc, g.slot, probe2_dispatch<R, NR>(g.a, g.b, a, b, smat + 8 * g.mat) * (R)g.coef);
+                    continue;
+                }
             }
             if constexpr (REV) {
                 if (g.gen == GEN_X)

@@ -153,7 +153,8 @@ struct SlotBatchEntry {
 struct BatchDyn {            // theta-dependent record of a batch member
     MatRec *rec;
     int theta_index;         // into the concatenated parameter vector
-    int rot, variant, domain;
+    int pad;
+    DynRec r;                // the member's record description (r.param unused)
 };
 cudaError_t fused_batch_prepare();
 cudaError_t launch_fused_batch(int dtype, bool reverse, bool two_q, int t, const FusedBatchEntry *entries,

@@ -226,11 +226,7 @@ __global__ void k_materialize_batch(const BatchDyn *__restrict__ dyn, int n_dyn,
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_dyn) return;
     const BatchDyn d = dyn[i];
-    DynRec r{};
-    r.rot = d.rot;
-    r.variant = d.variant;
-    r.domain = d.domain;
-    materialize(r, theta[d.theta_index], d.rec);
+    materialize(d.r, theta + d.theta_index, d.rec);
 }
 
 // psi_i = |0...0> for every instance of a contiguous batch buffer.

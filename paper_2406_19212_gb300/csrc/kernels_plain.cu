@@ -223,7 +223,7 @@ __global__ void k_materialize(const DynRec *__restrict__ dyn, int n_dyn,
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_dyn) return;
     DynRec r = dyn[i];
-    materialize(r, theta[r.param], &recs[r.rec]);
+    materialize(r, theta + r.param, &recs[r.rec]);
 }
 
 cudaError_t launch_materialize(const DynRec *dyn, int n_dyn, const double *theta, MatRec *recs,

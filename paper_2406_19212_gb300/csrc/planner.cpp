@@ -45,6 +45,7 @@ double ftype_flops(int ft)
     case FT_DENSE2: return 30;
     case FT_CTRL2: return 7;
     case FT_BLOCK2: return 10;   // FT_REAL1 / FT_IMAG1 / FT_ANTI1 / FT_DIAG*: 6
+    case FT_PROBE2: return 34;   // K Phi (dense 4x4: 30) and Re conj(Psi) . K Phi (4)
     default: return 6;
     }
 }
@@ -315,6 +316,7 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
                         continue;
                     }
                     flush_layer();
+                    if (g.ftype == FT_PROBE2 && !E.reverse) continue;  // gradient reads only
                     if (g.k == 2) E.has_2q = true;
                     FGate f{};
                     f.type = (int8_t)g.ftype;

@@ -161,3 +161,20 @@ def test_gradient_layout_cuts_passes_of_a_ladder(lib):
     apply_passes = c.plan_stats(gb.C64, for_grad=False)["passes"]
     assert grad_passes < apply_passes
     assert grad_passes <= 20
+
+
+def test_variational_fsim_validation(lib):
+    ok = I.Circuit(2, [I.Op("FSIM", (0, 1), param=0, fixed=(1.0, 0.5), pmask=0b11)], 2)
+    gb.circuit_create(ok)
+    bad_mask = I.Circuit(2, [I.Op("FSIM", (0, 1), param=0, fixed=(1.0, 0.5), pmask=0)], 2)
+    too_few = I.Circuit(2, [I.Op("FSIM", (0, 1), param=0, fixed=(1.0, 0.5), pmask=0b111)], 2)
+    density = I.Circuit(2, [I.Op("FSIM", (0, 1), param=0, fixed=(1.0, 0.5), pmask=0b11)], 2, density=True)
+    for circ, status in ((bad_mask, 1), (too_few, 1), (density, 6)):
+        with pytest.raises(gb.GbvqcError) as ex:
+            gb.circuit_create(circ)
+        assert ex.value.status == status
+    # the gradient plan of a variational FSIM circuit carries one slot per parameter
+    w = I.fsim_grid_vqe(3, 3, 3, 5, pmask=0b11111)
+    c = gb.circuit_create(w.circuit)
+    st = c.plan_stats(gb.C64, for_grad=True)
+    assert st["grad_slots"] == w.circuit.n_params

@@ -394,3 +394,33 @@ def test_measure_rejects_bad_arguments():
     for q, u in ((3, 0.5), (-1, 0.5), (0, 1.0), (0, -0.1), (0, float("nan"))):
         with pytest.raises(gb.GbvqcError):
             gb.measure(sv, q, u)
+
+
+# ----------------------------------------------------------------- variational FSIM
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("pmask", [0b00011, 0b11111, 0b10100])
+def test_fsim_parameter_gradients(dtype, mode, pmask):
+    """Grid circuit whose FSIM couplers carry variational parameters (the paper's isparas
+    mask over theta, phi and the three Delta's): energy and every gradient vs the oracle."""
+    w = I.fsim_grid_vqe(3, 4, 6, 17, pmask=pmask)
+    c = gb.circuit_create(w.circuit)
+    if mode == gb.FUSED:
+        c.set_tiling(8, 2)
+    o = gb.obs_create(w.observable, 12)
+    e, g = gb.grad(c, w.theta, o, dtype, mode)
+    e_ref, g_ref = O.adjoint_grad(w.circuit, w.theta, w.observable)
+    check_energy(e, e_ref, dtype)
+    check_grad(g, g_ref, dtype)
+
+
+def test_fsim_parameter_gradients_batched():
+    ws = [I.fsim_grid_vqe(3, 3 + i, 4 + i, 30 + i, pmask=(0b00011, 0b11111, 0b01001)[i]) for i in range(3)]
+    circs = [gb.circuit_create(w.circuit) for w in ws]
+    obss = [gb.obs_create(w.observable, w.circuit.n_qubits) for w in ws]
+    energies, grads = gb.batch_create(circs, obss, gb.C128).grad([w.theta for w in ws])
+    for w, e, g in zip(ws, energies, grads):
+        e_ref, g_ref = O.adjoint_grad(w.circuit, w.theta, w.observable)
+        check_energy(e, e_ref, gb.C128)
+        check_grad(g, g_ref, gb.C128)
