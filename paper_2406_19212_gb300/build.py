@@ -18,6 +18,8 @@ LIB = os.path.join(HERE, "libgbvqc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "planner.cpp", "kernels_plain.cu", "kernels_reduce.cu", "kernels_fused.cu",
            "kernels_batch.cu", "noalloc.cu"]
+# sources compiled as several objects (GBVQC_PART = 0 .. parts-1), one per kernel instance
+PARTS = {"kernels_fused.cu": 9, "kernels_batch.cu": 9}
 
 
 def nvcc() -> str:
@@ -37,11 +39,14 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(p) for p in paths)
 
 
-def _compile(src: str, verbose: bool) -> str:
-    out = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc()] + _flags() + ["-c", os.path.join(CSRC, src), "-o", out]
+def _compile(job, verbose: bool) -> str:
+    src, part = job
+    stem = os.path.splitext(src)[0] + (f".p{part}" if part is not None else "")
+    out = os.path.join(BUILD, stem + ".o")
+    defs = [f"-DGBVQC_PART={part}"] if part is not None else []
+    cmd = [nvcc()] + _flags() + defs + ["-c", os.path.join(CSRC, src), "-o", out]
     if src.endswith(".cpp"):
-        cmd = [nvcc(), "-x", "cu"] + _flags() + ["-c", os.path.join(CSRC, src), "-o", out]
+        cmd = [nvcc(), "-x", "cu"] + _flags() + defs + ["-c", os.path.join(CSRC, src), "-o", out]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     res = subprocess.run(cmd, capture_output=True, text=True)
@@ -57,9 +62,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
-    with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
+    jobs = []
+    for s in SOURCES:
+        if os.path.exists(os.path.join(CSRC, s)):
+            jobs += [(s, p) for p in range(PARTS[s])] if s in PARTS else [(s, None)]
+    # the longest compiles (the kernel instances) first
+    jobs.sort(key=lambda j: j[1] is None)
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), max(4, os.cpu_count() or 4))) as ex:
+        objs = list(ex.map(lambda j: _compile(j, verbose), jobs))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-lpthread", "-ldl"]
     res = subprocess.run(cmd, capture_output=True, text=True)

@@ -1234,6 +1234,20 @@ static gbvqc_status ensure_device(gbvqc_circuit *c)
 }
 
 static int default_tile(int dtype) { return 12; }
+
+static int ilog2(int x)
+{
+    int r = 0;
+    while ((1 << (r + 1)) <= x) r++;
+    return r;
+}
+
+// Largest tile: 2^(t - NR) threads per CTA within both fused kernels' launch bounds.
+static int max_tile(int dtype)
+{
+    const int nf = fused_nr(dtype, false), nr = fused_nr(dtype, true);
+    return std::min(nf + ilog2(fused_max_threads(nf, false)), nr + ilog2(fused_max_threads(nr, true)));
+}
 static int default_low(int dtype) { return dtype == GBVQC_C64 ? 4 : 3; }
 
 // Fused plan for (dtype, layout); built on first use (host only).
@@ -1321,8 +1335,7 @@ static gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout,
     opt.low = c->low_qubits ? c->low_qubits : default_low(dtype);
     opt.nr_f = fused_nr(dtype, false);
     opt.nr_r = fused_nr(dtype, true);
-    // at most 256 threads per CTA: 2^(t - NR) <= 256 for both the forward and reverse kernels
-    opt.t = std::min(opt.t, std::min(opt.nr_f, opt.nr_r) + 8);
+    opt.t = std::min(opt.t, max_tile(dtype));
     opt.elem_bytes = dtype == GBVQC_C64 ? 4 : 8;
     opt.max_slots = 128;
     opt.gate_smem = 40 * 1024;
@@ -1794,7 +1807,7 @@ extern "C" gbvqc_status circuit_autotune(circuit_handle c, const double *theta, 
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     const int nr_max = std::max(fused_nr(dtype, false), fused_nr(dtype, true));
-    const int t_hi = std::min(c->n_phys, std::min(fused_nr(dtype, false), fused_nr(dtype, true)) + 8);
+    const int t_hi = std::min(c->n_phys, max_tile(dtype));
     double best = 1e30;
     int bt = 0, bl = 0;
     gbvqc_status st = GBVQC_OK;

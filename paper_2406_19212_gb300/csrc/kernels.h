@@ -117,6 +117,10 @@ struct FusedArgs {
 cudaError_t launch_gather_units(int dtype, const MatUnit *fu, int nf, void *img_f, const MatUnit *ru, int nr,
                                 void *img_r, const MatRec *recs, cudaStream_t s);
 int fused_nr(int dtype, bool reverse);           // register qubits per sub-run
+// Threads per CTA the fused kernels are compiled for (launch bounds): 2^(t - NR) must
+// not exceed it.  Two CTAs per SM for the reverse kernels, three for the forward ones.
+constexpr int fused_max_threads(int nr, bool reverse) { return reverse && nr < 5 ? 256 : 128; }
+constexpr int fused_min_blocks(bool reverse) { return reverse ? 2 : 3; }
 cudaError_t fused_prepare();                     // shared-memory opt-in, outside capture
 cudaError_t launch_fused_forward(int dtype, void *psi, const FusedDev &fd, int pass,
                                  const PassDesc &pass_host, size_t smem, cudaStream_t s);

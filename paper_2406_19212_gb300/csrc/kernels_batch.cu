@@ -22,8 +22,8 @@ __device__ __forceinline__ int find_entry(const E *entries, int n, int64_t cta)
 // ------------------------------------------------------------------- fused passes
 
 template <typename R, int NR, bool REV, bool TWOQ>
-__global__ void __launch_bounds__(REV ? 256 : 128, REV ? 2 : 3) k_fused_batch(const FusedBatchEntry *__restrict__ entries,
-                                                                              int n_entries)
+__global__ void __launch_bounds__(fused_max_threads(NR, REV), fused_min_blocks(REV))
+    k_fused_batch(const FusedBatchEntry *__restrict__ entries, int n_entries)
 {
     typedef typename CT<R>::T T;
     __shared__ int s_e;
@@ -33,18 +33,75 @@ __global__ void __launch_bounds__(REV ? 256 : 128, REV ? 2 : 3) k_fused_batch(co
     fused_tile<R, NR, REV, TWOQ>((T *)e.phi, (T *)e.psi, e.args, (int64_t)blockIdx.x - e.begin);
 }
 
+// Per-instance launch and shared-memory opt-in, compiled in separate objects like the
+// single-circuit kernels (GBVQC_PART 0..7; 8 = everything else).
+template <typename R, int NR, bool REV, bool TWOQ>
+cudaError_t fused_batch_launch_t(unsigned grid, int threads, size_t smem, const FusedBatchEntry *entries,
+                                 int n_entries, cudaStream_t s)
+{
+    k_fused_batch<R, NR, REV, TWOQ><<<grid, threads, smem, s>>>(entries, n_entries);
+    return cudaGetLastError();
+}
+
+template <typename R, int NR, bool REV, bool TWOQ>
+cudaError_t fused_batch_prepare_t()
+{
+    return cudaFuncSetAttribute(k_fused_batch<R, NR, REV, TWOQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024);
+}
+
+#define GBVQC_BATCH_INST(EXT, R, NR, REV, TQ)                                                                \
+    EXT template cudaError_t fused_batch_launch_t<R, NR, REV, TQ>(unsigned, int, size_t, const FusedBatchEntry *, \
+                                                                  int, cudaStream_t);                       \
+    EXT template cudaError_t fused_batch_prepare_t<R, NR, REV, TQ>();
+
+#if !defined(GBVQC_PART) || GBVQC_PART == 0
+GBVQC_BATCH_INST(, float, 5, false, false)
+#endif
+#if !defined(GBVQC_PART) || GBVQC_PART == 1
+GBVQC_BATCH_INST(, float, 5, false, true)
+#endif
+#if !defined(GBVQC_PART) || GBVQC_PART == 2
+GBVQC_BATCH_INST(, float, 4, true, false)
+#endif
+#if !defined(GBVQC_PART) || GBVQC_PART == 3
+GBVQC_BATCH_INST(, float, 4, true, true)
+#endif
+#if !defined(GBVQC_PART) || GBVQC_PART == 4
+GBVQC_BATCH_INST(, double, 4, false, false)
+#endif
+#if !defined(GBVQC_PART) || GBVQC_PART == 5
+GBVQC_BATCH_INST(, double, 4, false, true)
+#endif
+#if !defined(GBVQC_PART) || GBVQC_PART == 6
+GBVQC_BATCH_INST(, double, 3, true, false)
+#endif
+#if !defined(GBVQC_PART) || GBVQC_PART == 7
+GBVQC_BATCH_INST(, double, 3, true, true)
+#endif
+
+#if !defined(GBVQC_PART) || GBVQC_PART == 8
+#if defined(GBVQC_PART)
+GBVQC_BATCH_INST(extern, float, 5, false, false)
+GBVQC_BATCH_INST(extern, float, 5, false, true)
+GBVQC_BATCH_INST(extern, float, 4, true, false)
+GBVQC_BATCH_INST(extern, float, 4, true, true)
+GBVQC_BATCH_INST(extern, double, 4, false, false)
+GBVQC_BATCH_INST(extern, double, 4, false, true)
+GBVQC_BATCH_INST(extern, double, 3, true, false)
+GBVQC_BATCH_INST(extern, double, 3, true, true)
+#endif
+
 cudaError_t fused_batch_prepare()
 {
-    const int bytes = 200 * 1024;
-    cudaError_t e = cudaSuccess;
-#define GBVQC_PREP(R, NR, REV, TQ) \
-    if (e == cudaSuccess)         \
-        e = cudaFuncSetAttribute(k_fused_batch<R, NR, REV, TQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    GBVQC_PREP(float, 5, false, false) GBVQC_PREP(float, 5, false, true)
-    GBVQC_PREP(float, 4, true, false) GBVQC_PREP(float, 4, true, true)
-    GBVQC_PREP(double, 4, false, false) GBVQC_PREP(double, 4, false, true)
-    GBVQC_PREP(double, 3, true, false) GBVQC_PREP(double, 3, true, true)
-#undef GBVQC_PREP
+    cudaError_t e = fused_batch_prepare_t<float, 5, false, false>();
+    if (e == cudaSuccess) e = fused_batch_prepare_t<float, 5, false, true>();
+    if (e == cudaSuccess) e = fused_batch_prepare_t<float, 4, true, false>();
+    if (e == cudaSuccess) e = fused_batch_prepare_t<float, 4, true, true>();
+    if (e == cudaSuccess) e = fused_batch_prepare_t<double, 4, false, false>();
+    if (e == cudaSuccess) e = fused_batch_prepare_t<double, 4, false, true>();
+    if (e == cudaSuccess) e = fused_batch_prepare_t<double, 3, true, false>();
+    if (e == cudaSuccess) e = fused_batch_prepare_t<double, 3, true, true>();
     return e;
 }
 
@@ -53,19 +110,17 @@ cudaError_t launch_fused_batch(int dtype, bool reverse, bool two_q, int t, const
 {
     const int nr = fused_nr(dtype, reverse);
     const int threads = 1 << (t - nr);
-    const unsigned grid = (unsigned)total_tiles;
+    const unsigned g = (unsigned)total_tiles;
 #define GBVQC_LB(R, NR, REV)                                                                          \
-    {                                                                                                 \
-        if (two_q) k_fused_batch<R, NR, REV, true><<<grid, threads, smem, s>>>(entries, n_entries);   \
-        else k_fused_batch<R, NR, REV, false><<<grid, threads, smem, s>>>(entries, n_entries);        \
-    }
+    return two_q ? fused_batch_launch_t<R, NR, REV, true>(g, threads, smem, entries, n_entries, s)    \
+                 : fused_batch_launch_t<R, NR, REV, false>(g, threads, smem, entries, n_entries, s);
     if (dtype == 0) {
-        if (reverse) GBVQC_LB(float, 4, true) else GBVQC_LB(float, 5, false)
-    } else {
-        if (reverse) GBVQC_LB(double, 3, true) else GBVQC_LB(double, 4, false)
+        if (reverse) GBVQC_LB(float, 4, true)
+        GBVQC_LB(float, 5, false)
     }
+    if (reverse) GBVQC_LB(double, 3, true)
+    GBVQC_LB(double, 4, false)
 #undef GBVQC_LB
-    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------- Pauli expectation
@@ -251,5 +306,7 @@ cudaError_t launch_batch_init(const BatchDyn *dyn, int n_dyn, const double *thet
     k_zero_ones<<<(n_inst + 127) / 128, 128, 0, s>>>(phi_all, offsets, n_inst, dtype);
     return cudaGetLastError();
 }
+
+#endif  // part 8
 
 }  // namespace gbvqc

@@ -4,15 +4,74 @@
 
 namespace gbvqc {
 
-// Forward kernels run 2^(t-NR) <= 128 threads (three CTAs per SM), reverse kernels
-// <= 256 threads (two CTAs per SM).
+// Launch bounds from fused_max_threads / fused_min_blocks.
 template <typename R, int NR, bool REV, bool TWOQ>
-__global__ void __launch_bounds__(REV ? 256 : 128, REV ? 2 : 3) k_fused(typename CT<R>::T *__restrict__ phi,
-                                                                        typename CT<R>::T *__restrict__ psi,
-                                                                        FusedArgs args)
+__global__ void __launch_bounds__(fused_max_threads(NR, REV), fused_min_blocks(REV))
+    k_fused(typename CT<R>::T *__restrict__ phi, typename CT<R>::T *__restrict__ psi, FusedArgs args)
 {
     fused_tile<R, NR, REV, TWOQ>(phi, psi, args, blockIdx.x);
 }
+
+// One launch / shared-memory opt-in per kernel instance.  The instances are compiled in
+// separate objects (GBVQC_PART 0..7, one per precision x direction x two-qubit flavour;
+// 8 = the dispatchers and small kernels) so the build runs them in parallel; without
+// GBVQC_PART everything is compiled in one object.
+template <typename R, int NR, bool REV, bool TWOQ>
+cudaError_t fused_launch_t(void *phi, void *psi, unsigned tiles, int threads, size_t smem, FusedArgs args,
+                           cudaStream_t s)
+{
+    typedef typename CT<R>::T T;
+    k_fused<R, NR, REV, TWOQ><<<tiles, threads, smem, s>>>((T *)phi, (T *)psi, args);
+    return cudaGetLastError();
+}
+
+template <typename R, int NR, bool REV, bool TWOQ>
+cudaError_t fused_prepare_t()  // large dynamic shared memory (call outside stream capture)
+{
+    return cudaFuncSetAttribute(k_fused<R, NR, REV, TWOQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+#define GBVQC_FUSED_INST(EXT, R, NR, REV, TQ)                                                           \
+    EXT template cudaError_t fused_launch_t<R, NR, REV, TQ>(void *, void *, unsigned, int, size_t, FusedArgs, \
+                                                            cudaStream_t);                              \
+    EXT template cudaError_t fused_prepare_t<R, NR, REV, TQ>();
+
+#if !defined(GBVQC_PART) || GBVQC_PART == 0
+GBVQC_FUSED_INST(, float, 5, false, false)
+#endif
+#if !defined(GBVQC_PART) || GBVQC_PART == 1
+GBVQC_FUSED_INST(, float, 5, false, true)
+#endif
+#if !defined(GBVQC_PART) || GBVQC_PART == 2
+GBVQC_FUSED_INST(, float, 4, true, false)
+#endif
+#if !defined(GBVQC_PART) || GBVQC_PART == 3
+GBVQC_FUSED_INST(, float, 4, true, true)
+#endif
+#if !defined(GBVQC_PART) || GBVQC_PART == 4
+GBVQC_FUSED_INST(, double, 4, false, false)
+#endif
+#if !defined(GBVQC_PART) || GBVQC_PART == 5
+GBVQC_FUSED_INST(, double, 4, false, true)
+#endif
+#if !defined(GBVQC_PART) || GBVQC_PART == 6
+GBVQC_FUSED_INST(, double, 3, true, false)
+#endif
+#if !defined(GBVQC_PART) || GBVQC_PART == 7
+GBVQC_FUSED_INST(, double, 3, true, true)
+#endif
+
+#if !defined(GBVQC_PART) || GBVQC_PART == 8
+#if defined(GBVQC_PART)
+GBVQC_FUSED_INST(extern, float, 5, false, false)
+GBVQC_FUSED_INST(extern, float, 5, false, true)
+GBVQC_FUSED_INST(extern, float, 4, true, false)
+GBVQC_FUSED_INST(extern, float, 4, true, true)
+GBVQC_FUSED_INST(extern, double, 4, false, false)
+GBVQC_FUSED_INST(extern, double, 4, false, true)
+GBVQC_FUSED_INST(extern, double, 3, true, false)
+GBVQC_FUSED_INST(extern, double, 3, true, true)
+#endif
 
 // -------------------------------------------------------------------------- launchers
 
@@ -22,23 +81,16 @@ int fused_nr(int dtype, bool reverse)
     return reverse ? 3 : 4;
 }
 
-// Opt the fused kernels in to large dynamic shared memory (call outside stream capture).
-template <typename R, int NR, bool REV>
-static cudaError_t prepare_pair()
-{
-    const int bytes = 200 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_fused<R, NR, REV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fused<R, NR, REV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return e;
-}
-
 cudaError_t fused_prepare()
 {
-    cudaError_t e = prepare_pair<float, 5, false>();
-    if (e == cudaSuccess) e = prepare_pair<float, 4, true>();
-    if (e == cudaSuccess) e = prepare_pair<double, 4, false>();
-    if (e == cudaSuccess) e = prepare_pair<double, 3, true>();
+    cudaError_t e = fused_prepare_t<float, 5, false, false>();
+    if (e == cudaSuccess) e = fused_prepare_t<float, 5, false, true>();
+    if (e == cudaSuccess) e = fused_prepare_t<float, 4, true, false>();
+    if (e == cudaSuccess) e = fused_prepare_t<float, 4, true, true>();
+    if (e == cudaSuccess) e = fused_prepare_t<double, 4, false, false>();
+    if (e == cudaSuccess) e = fused_prepare_t<double, 4, false, true>();
+    if (e == cudaSuccess) e = fused_prepare_t<double, 3, true, false>();
+    if (e == cudaSuccess) e = fused_prepare_t<double, 3, true, true>();
     return e;
 }
 
@@ -46,14 +98,10 @@ template <typename R, int NR, bool REV>
 static cudaError_t fused_launch(void *phi, void *psi, const PassDesc &ph, size_t smem, FusedArgs args,
                                 cudaStream_t s)
 {
-    typedef typename CT<R>::T T;
     const int threads = 1 << (ph.t - NR);
-    const int64_t tiles = int64_t(1) << (ph.n - ph.t);
-    if (ph.has_2q)
-        k_fused<R, NR, REV, true><<<(unsigned)tiles, threads, smem, s>>>((T *)phi, (T *)psi, args);
-    else
-        k_fused<R, NR, REV, false><<<(unsigned)tiles, threads, smem, s>>>((T *)phi, (T *)psi, args);
-    return cudaGetLastError();
+    const unsigned tiles = (unsigned)(int64_t(1) << (ph.n - ph.t));
+    if (ph.has_2q) return fused_launch_t<R, NR, REV, true>(phi, psi, tiles, threads, smem, args, s);
+    return fused_launch_t<R, NR, REV, false>(phi, psi, tiles, threads, smem, args, s);
 }
 
 cudaError_t launch_fused_forward(int dtype, void *psi, const FusedDev &fd, int pass, const PassDesc &ph,
@@ -123,5 +171,7 @@ cudaError_t launch_reduce_slots(const double *slot_partials, int n_slots, int n_
     k_reduce_slots<<<n_slots, 256, 0, s>>>(slot_partials, n_tiles, stride, slot_grad);
     return cudaGetLastError();
 }
+
+#endif  // part 8
 
 }  // namespace gbvqc
