@@ -48,7 +48,7 @@ typedef double complex cplx;
 enum {
     O_X, O_Y, O_Z, O_H, O_S, O_T, O_SX, O_SY, O_SW, O_RX, O_RY, O_RZ,
     O_CNOT, O_CZ, O_SWAP, O_ISWAP, O_FSIM, O_CONTROL, O_DENSE1, O_DENSE2,
-    O_DEPOL, O_AMPDAMP, O_PHASEDAMP, O_KRAUS
+    O_DEPOL, O_AMPDAMP, O_PHASEDAMP, O_KRAUS, O_DEPOL2, O_KRAUS2
 };
 
 typedef struct {
@@ -60,6 +60,7 @@ typedef struct {
     int32_t pmask;     /* FSIM: bit k set = parameter k is variational (theta[param + rank]) */
     double fixed[5];
     double data[32];   /* complex (re, im) pairs, row-major; KRAUS: n_kraus 2x2 blocks */
+    const double *kraus; /* KRAUS2: n_kraus 4x4 blocks, (re, im) row-major */
 } orc_op;
 
 static int is_channel(int kind) { return kind >= O_DEPOL; }
@@ -202,13 +203,35 @@ static void fsim_derivative(const orc_op *op, const double *theta, int k, cplx *
     }
 }
 
-/* Kraus operators of a single-qubit channel (Sec. II.B); returns their count. */
-static int channel_kraus(const orc_op *op, cplx *K /* up to 4 x 4 entries */)
+/* Kraus operators of a channel (Sec. II.B, QuantumMap): returns their count and sets *k
+ * to the channel's qubit count (K holds count blocks of 2^k x 2^k entries). */
+static int channel_kraus_k(const orc_op *op, cplx *K /* up to 256 entries */, int *k)
 {
     double g = op->fixed[0];
     int i;
-    for (i = 0; i < 16; i++) K[i] = 0;
+    for (i = 0; i < 256; i++) K[i] = 0;
+    *k = 1;
     switch (op->kind) {
+    case O_DEPOL2: { /* sqrt(1 - 15p/16) I, sqrt(p/16) s_a (x) s_b for the 15 other Paulis */
+        const cplx P[4][4] = {{1, 0, 0, 1}, {0, 1, 1, 0}, {0, -I, I, 0}, {1, 0, 0, -1}};
+        int a, b, r0, r1, c0, c1;
+        *k = 2;
+        for (a = 0; a < 4; a++)       /* Pauli on the first qubit (matrix bit 0) */
+            for (b = 0; b < 4; b++) { /* Pauli on the second qubit (matrix bit 1) */
+                const double w = (a == 0 && b == 0) ? sqrt(1 - 15 * g / 16) : sqrt(g / 16);
+                cplx *M = K + 16 * (4 * b + a);
+                for (r0 = 0; r0 < 2; r0++)
+                    for (r1 = 0; r1 < 2; r1++)
+                        for (c0 = 0; c0 < 2; c0++)
+                            for (c1 = 0; c1 < 2; c1++)
+                                M[(r0 + 2 * r1) * 4 + (c0 + 2 * c1)] = w * P[a][2 * r0 + c0] * P[b][2 * r1 + c1];
+            }
+        return 16;
+    }
+    case O_KRAUS2:
+        *k = 2;
+        for (i = 0; i < 16 * op->n_kraus; i++) K[i] = op->kraus[2 * i] + I * op->kraus[2 * i + 1];
+        return op->n_kraus;
     case O_AMPDAMP:
         K[0] = 1; K[3] = sqrt(1 - g);
         K[4 + 1] = sqrt(g);
@@ -231,6 +254,12 @@ static int channel_kraus(const orc_op *op, cplx *K /* up to 4 x 4 entries */)
     default:
         return -1;
     }
+}
+
+static int channel_kraus(const orc_op *op, cplx *K)
+{
+    int k;
+    return channel_kraus_k(op, K, &k);
 }
 
 /* ------------------------------------------------------------ state evolution */
@@ -330,12 +359,14 @@ int orc_gate_matrix(const orc_op *op, const double *theta, double *out /* 32 dou
     return k;
 }
 
-int orc_kraus(const orc_op *op, double *out /* 32 doubles */)
+/* Kraus operators of a channel op: count returned, *k = its qubit count, out = count
+ * blocks of 2^k x 2^k (re, im) entries, row-major (up to 512 doubles). */
+int orc_kraus(const orc_op *op, double *out, int *k)
 {
-    cplx K[16];
-    int m = channel_kraus(op, K), i;
+    cplx K[256];
+    int m = channel_kraus_k(op, K, k), i;
     if (m < 0) return -1;
-    for (i = 0; i < 4 * m; i++) { out[2 * i] = creal(K[i]); out[2 * i + 1] = cimag(K[i]); }
+    for (i = 0; i < (1 << (2 * *k)) * m; i++) { out[2 * i] = creal(K[i]); out[2 * i + 1] = cimag(K[i]); }
     return m;
 }
 
@@ -491,14 +522,14 @@ int orc_rho_apply_circuit(double *rho_, int n, const orc_op *ops, int n_ops, con
             if (k < 0) return -1;
             rho_sandwich(rho, n, k, ops[j].q, M);
         } else {
-            cplx K[16];
-            int m = channel_kraus(&ops[j], K), s;
+            cplx K[256];
+            int kq, m = channel_kraus_k(&ops[j], K, &kq), s;
             cplx *acc = (cplx *)calloc((size_t)len, sizeof(cplx));
             cplx *tmp = (cplx *)malloc(sizeof(cplx) * (size_t)len);
             if (m < 0) { free(acc); free(tmp); return -1; }
             for (s = 0; s < m; s++) {
                 memcpy(tmp, rho, sizeof(cplx) * (size_t)len);
-                rho_sandwich(tmp, n, 1, ops[j].q, K + 4 * s);
+                rho_sandwich(tmp, n, kq, ops[j].q, K + (1 << (2 * kq)) * s);
                 for (i = 0; i < len; i++) acc[i] += tmp[i];
             }
             memcpy(rho, acc, sizeof(cplx) * (size_t)len);
@@ -537,11 +568,10 @@ int orc_rho_expect(const double *rho_, int n, const double *coeff, const char *p
  * acting on the 2k physical qubits (q..., q+n...).  A unitary has the single K = U. */
 static int superop(const orc_op *op, const double *theta, int n, cplx *S, int *pq)
 {
-    cplx K[16];
+    cplx K[256];
     int m, k, s, a, b, c, d;
     if (is_channel(op->kind)) {
-        m = channel_kraus(op, K);
-        k = 1;
+        m = channel_kraus_k(op, K, &k);
     } else {
         k = gate_matrix(op, theta, K);
         m = 1;

@@ -20,13 +20,14 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _KIND = {name: i for i, name in enumerate(
     ["X", "Y", "Z", "H", "S", "T", "SX", "SY", "SW", "RX", "RY", "RZ",
      "CNOT", "CZ", "SWAP", "ISWAP", "FSIM", "CONTROL", "DENSE1", "DENSE2",
-     "DEPOL", "AMPDAMP", "PHASEDAMP", "KRAUS"])}
+     "DEPOL", "AMPDAMP", "PHASEDAMP", "KRAUS", "DEPOL2", "KRAUS2"])}
 
 
 class OrcOp(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("nq", ctypes.c_int32), ("q", ctypes.c_int32 * 2),
                 ("param", ctypes.c_int32), ("n_kraus", ctypes.c_int32), ("pmask", ctypes.c_int32),
-                ("fixed", ctypes.c_double * 5), ("data", ctypes.c_double * 32)]
+                ("fixed", ctypes.c_double * 5), ("data", ctypes.c_double * 32),
+                ("kraus", ctypes.c_void_p)]
 
 
 def build(force: bool = False) -> str:
@@ -52,7 +53,7 @@ def lib():
         ip = ctypes.POINTER(ctypes.c_int32)
         op_p = ctypes.POINTER(OrcOp)
         L.orc_gate_matrix.argtypes = [op_p, dp, dp]
-        L.orc_kraus.argtypes = [op_p, dp]
+        L.orc_kraus.argtypes = [op_p, dp, ctypes.POINTER(ctypes.c_int)]
         L.orc_apply_matrix.argtypes = [dp, ctypes.c_int, ctypes.c_int, ip, dp]
         L.orc_apply_circuit.argtypes = [dp, ctypes.c_int, op_p, ctypes.c_int, dp]
         L.orc_apply_hamiltonian.argtypes = [dp, dp, ctypes.c_int, dp, ctypes.c_char_p, ctypes.c_int]
@@ -77,6 +78,7 @@ def _dp(a: np.ndarray):
 
 def _ops(ops) -> ctypes.Array:
     arr = (OrcOp * max(1, len(ops)))()
+    arr._keep = []  # KRAUS2 operator buffers referenced by pointer
     for i, op in enumerate(ops):
         o = arr[i]
         o.kind = _KIND[op.name]
@@ -87,7 +89,13 @@ def _ops(ops) -> ctypes.Array:
         o.pmask = getattr(op, "pmask", 0)
         for t, v in enumerate(op.fixed):
             o.fixed[t] = v
-        if op.data is not None:
+        if op.name == "KRAUS2":
+            ks = [np.asarray(k, dtype=np.complex128).reshape(4, 4) for k in op.data]
+            o.n_kraus = len(ks)
+            buf = np.ascontiguousarray(np.concatenate([k.reshape(-1) for k in ks])).view(np.float64)
+            arr._keep.append(buf)
+            o.kraus = buf.ctypes.data
+        elif op.data is not None:
             if op.name == "KRAUS":
                 ks = [np.asarray(k, dtype=np.complex128) for k in op.data]
                 o.n_kraus = len(ks)
@@ -124,12 +132,14 @@ def gate_matrix(op, theta=()) -> np.ndarray:
 
 
 def kraus(op) -> List[np.ndarray]:
-    out = np.zeros(32)
-    m = lib().orc_kraus(_ops([op]), _dp(out))
+    out = np.zeros(512)
+    k = ctypes.c_int()
+    m = lib().orc_kraus(_ops([op]), _dp(out), ctypes.byref(k))
     if m < 0:
         raise ValueError(op.name)
+    d = 1 << k.value
     c = out[0::2] + 1j * out[1::2]
-    return [c[4 * s:4 * s + 4].reshape(2, 2) for s in range(m)]
+    return [c[d * d * s:d * d * (s + 1)].reshape(d, d) for s in range(m)]
 
 
 def apply_matrix(psi: np.ndarray, n: int, qubits: Sequence[int], mat: np.ndarray) -> np.ndarray:

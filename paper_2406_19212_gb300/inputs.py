@@ -26,8 +26,9 @@ ONE_QUBIT_FIXED = ("X", "Y", "Z", "H", "S", "T", "SX", "SY", "SW")
 ROTATIONS = ("RX", "RY", "RZ")
 TWO_QUBIT_FIXED = ("CNOT", "CZ", "SWAP", "ISWAP")
 CHANNELS = ("DEPOL", "AMPDAMP", "PHASEDAMP", "KRAUS")
+CHANNELS2 = ("DEPOL2", "KRAUS2")  # two-qubit QuantumMap: depolarising, general Kraus list
 ALL_NAMES = ONE_QUBIT_FIXED + ROTATIONS + TWO_QUBIT_FIXED + (
-    "FSIM", "CONTROL", "DENSE1", "DENSE2") + CHANNELS
+    "FSIM", "CONTROL", "DENSE1", "DENSE2") + CHANNELS + CHANNELS2
 
 
 @dataclass(frozen=True)
@@ -45,7 +46,8 @@ class Op:
              d_minus, d_minus_off) is variational (the paper's `isparas` array); the
              variational ones read theta[param], theta[param + 1], ... in increasing k.
     data   : complex matrix for DENSE1 (2x2), DENSE2 (4x4), CONTROL (2x2 target block),
-             or a list of 2x2 Kraus operators for KRAUS; row-major [row][col].
+             a list of 2x2 Kraus operators for KRAUS or of 4x4 ones for KRAUS2;
+             row-major [row][col].
     """
     name: str
     qubits: Tuple[int, ...]
@@ -328,6 +330,14 @@ def random_unitary(k: int, rng: np.random.Generator) -> np.ndarray:
     z = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
     q, r = np.linalg.qr(z)
     return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def random_kraus2(rng: np.random.Generator, count: int = 3) -> List[np.ndarray]:
+    """A random two-qubit channel: count 4x4 Kraus operators cut from a random isometry
+    (orthonormal columns of a 4 count x 4 matrix), so sum K^dag K = I."""
+    A = rng.normal(size=(4 * count, 4)) + 1j * rng.normal(size=(4 * count, 4))
+    Q, _ = np.linalg.qr(A)
+    return [Q[4 * s:4 * s + 4, :] for s in range(count)]
 
 
 def random_kraus(rng: np.random.Generator, count: int = 3) -> List[np.ndarray]:

@@ -393,3 +393,71 @@ def test_fsim_grad_shift_rules_and_fd():
         else:
             ref = O.finite_difference_grad(w.circuit, t, w.observable, [j], h=1e-5)[0]
         assert g[j] == pytest.approx(ref, abs=1e-8 if comp < 2 else 1e-7)
+
+
+# ------------------------------------------------------------- two-qubit channels
+
+def _partial_trace_pair(rho, n, qa, qb):
+    """Tr over qubits qa, qb of a 2^n x 2^n matrix, embedded back as X (x) I_{qa,qb}/... :
+    returns sum_{s} (<s| on qa,qb) rho (|s>) expanded with the identity on qa, qb."""
+    d = 1 << n
+    out = np.zeros_like(rho)
+    idx = np.arange(d)
+    mask = (1 << qa) | (1 << qb)
+    for a in range(d):
+        for b in range(d):
+            if (a & mask) != (b & mask):
+                continue
+            # (Tr_{qa,qb} rho)[a without qa,qb; b without qa,qb] = sum over s of rho[a|s, b|s]
+            s = 0.0
+            for t in range(4):
+                bits = ((t & 1) << qa) | (((t >> 1) & 1) << qb)
+                s += rho[(a & ~mask) | bits, (b & ~mask) | bits]
+            out[a, b] = s
+    return out
+
+
+def test_depol2_closed_form():
+    """Two-qubit depolarising (reading: K0 = sqrt(1-15p/16) I, the 15 others sqrt(p/16)
+    s_a (x) s_b) gives (1-p) rho + p/4 Tr_{q0 q1}(rho) (x) I on the pair."""
+    n, p = 3, 0.23
+    rho = I.random_density(n, 4).reshape(1 << n, 1 << n, order="F")
+    c = I.Circuit(n, [op("DEPOL2", (0, 2), fixed=(p,))], 0, True)
+    out = O.rho_apply_circuit(c, [], rho.reshape(-1, order="F")).reshape(1 << n, 1 << n, order="F")
+    ref = (1 - p) * rho + p / 4 * _partial_trace_pair(rho, n, 0, 2)
+    np.testing.assert_allclose(out, ref, atol=1e-14)
+    ks = O.kraus(op("DEPOL2", (0, 2), fixed=(p,)))
+    assert len(ks) == 16 and ks[0].shape == (4, 4)
+    np.testing.assert_allclose(sum(k.conj().T @ k for k in ks), np.eye(4), atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_kraus2_density_against_dense_and_superoperator(seed):
+    """General two-qubit Kraus channels inside a noisy circuit: the Kraus-sum evolution
+    equals dense K rho K^dag products, and the superoperator evolution equals both."""
+    n = 3
+    rng = np.random.default_rng(seed)
+    ops = [op("RY", (0,), param=0), op("CNOT", (0, 1)), op("KRAUS2", (1, 2), data=I.random_kraus2(rng, 3)),
+           op("RX", (2,), param=1), op("DEPOL2", (2, 0), fixed=(0.1,)), op("KRAUS2", (0, 1), data=I.random_kraus2(rng, 2))]
+    circ = I.Circuit(n, ops, 2, True)
+    theta = [0.7, -1.3]
+    for o in ops:
+        if o.name == "KRAUS2":
+            np.testing.assert_allclose(sum(k.conj().T @ k for k in O.kraus(o)), np.eye(4), atol=1e-13)
+    rho = I.random_density(n, seed).reshape(1 << n, 1 << n, order="F")
+    ref = rho.copy()
+    for o in ops:
+        if o.name in I.CHANNELS + I.CHANNELS2:
+            ks = [embed(k, o.qubits, n) for k in O.kraus(o)]
+            ref = sum(k @ ref @ k.conj().T for k in ks)
+        else:
+            U = embed(O.gate_matrix(o, theta), o.qubits, n)
+            ref = U @ ref @ U.conj().T
+    out = O.rho_apply_circuit(circ, theta, rho.reshape(-1, order="F"))
+    np.testing.assert_allclose(out, ref.reshape(-1, order="F"), atol=1e-13)
+    vec = O.vec_apply_circuit(circ, theta, rho.reshape(-1, order="F"))
+    np.testing.assert_allclose(vec, ref.reshape(-1, order="F"), atol=1e-13)
+    # noisy Algorithm 2 through two-qubit channels vs parameter shift (exact for Rx, Ry)
+    terms = [(0.6, ((0, "Z"), (2, "X"))), (-0.4, ((1, "Y"),)), (0.3, ((2, "Z"),))]
+    e, g = O.noisy_adjoint_grad(circ, theta, terms)
+    np.testing.assert_allclose(g, O.parameter_shift_grad(circ, theta, terms), atol=1e-12)
