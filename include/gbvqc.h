@@ -60,7 +60,11 @@ enum {
     GBVQC_X = 0, GBVQC_Y, GBVQC_Z, GBVQC_H, GBVQC_S, GBVQC_T, GBVQC_SX, GBVQC_SY,
     GBVQC_SW, GBVQC_RX, GBVQC_RY, GBVQC_RZ, GBVQC_CNOT, GBVQC_CZ, GBVQC_SWAP,
     GBVQC_ISWAP, GBVQC_FSIM, GBVQC_CONTROL, GBVQC_DENSE1, GBVQC_DENSE2,
-    GBVQC_DEPOL, GBVQC_AMPDAMP, GBVQC_PHASEDAMP, GBVQC_KRAUS, GBVQC_NUM_KINDS
+    GBVQC_DEPOL, GBVQC_AMPDAMP, GBVQC_PHASEDAMP, GBVQC_KRAUS,
+    GBVQC_DEPOL2,          /* two-qubit depolarising: sqrt(1 - 15p/16) I and sqrt(p/16) for
+                              the 15 other two-qubit Paulis, i.e. (1-p) rho + p/4 Tr(rho) I */
+    GBVQC_KRAUS2,          /* two-qubit QuantumMap: n_kraus 4x4 operators in `kraus`      */
+    GBVQC_NUM_KINDS
 };
 
 /* One circuit element (QuantumGate / QuantumMap, Sec. II.B-C). */
@@ -81,6 +85,9 @@ typedef struct gbvqc_op {
     double  params[5];     /* fixed angle / FSIM angles / channel strength              */
     double  data[32];      /* DENSE1 (2x2), DENSE2 (4x4), CONTROL (2x2 target block),
                               KRAUS (n_kraus 2x2 blocks): row-major (re, im) pairs      */
+    const double *kraus;   /* KRAUS2 only: n_kraus (1..16) 4x4 operators, row-major (re, im)
+                              pairs, 32 doubles each, host memory, copied by
+                              circuit_create; NULL for every other kind                 */
 } gbvqc_op;
 
 /* One Pauli term coeff * P (Sec. II.E, QubitsTerm): qubit q carries X if only bit q of

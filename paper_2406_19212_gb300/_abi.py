@@ -22,7 +22,8 @@ PTR_HOST, PTR_DEVICE = 0, 1
 
 KIND = {name: i for i, name in enumerate(
     ["X", "Y", "Z", "H", "S", "T", "SX", "SY", "SW", "RX", "RY", "RZ", "CNOT", "CZ", "SWAP",
-     "ISWAP", "FSIM", "CONTROL", "DENSE1", "DENSE2", "DEPOL", "AMPDAMP", "PHASEDAMP", "KRAUS"])}
+     "ISWAP", "FSIM", "CONTROL", "DENSE1", "DENSE2", "DEPOL", "AMPDAMP", "PHASEDAMP", "KRAUS",
+     "DEPOL2", "KRAUS2"])}
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT",
           5: "ERR_NOT_DENSITY", 6: "ERR_UNSUPPORTED"}
@@ -38,7 +39,7 @@ class Op(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("qubits", ctypes.c_int32 * 2),
                 ("param_index", ctypes.c_int32), ("n_kraus", ctypes.c_int32),
                 ("param_mask", ctypes.c_int32), ("params", ctypes.c_double * 5),
-                ("data", ctypes.c_double * 32)]
+                ("data", ctypes.c_double * 32), ("kraus", ctypes.c_void_p)]
 
 
 class KernelStat(ctypes.Structure):
@@ -127,6 +128,7 @@ def exported_symbols() -> List[str]:
 def ops_array(ops) -> ctypes.Array:
     """inputs.Op list -> gbvqc_op array."""
     arr = (Op * max(1, len(ops)))()
+    arr._keep = []  # KRAUS2 operator buffers referenced by pointer (copied by circuit_create)
     for i, op in enumerate(ops):
         o = arr[i]
         o.kind = KIND[op.name]
@@ -136,7 +138,13 @@ def ops_array(ops) -> ctypes.Array:
         o.param_mask = int(getattr(op, "pmask", 0))
         for t, v in enumerate(op.fixed):
             o.params[t] = float(v)
-        if op.data is not None:
+        if op.name == "KRAUS2":
+            mats = [np.asarray(k, dtype=np.complex128).reshape(4, 4) for k in op.data]
+            o.n_kraus = len(mats)
+            buf = np.ascontiguousarray(np.concatenate([m.reshape(-1) for m in mats])).view(np.float64)
+            arr._keep.append(buf)
+            o.kraus = buf.ctypes.data
+        elif op.data is not None:
             if op.name == "KRAUS":
                 mats = [np.asarray(k, dtype=np.complex128) for k in op.data]
                 o.n_kraus = len(mats)

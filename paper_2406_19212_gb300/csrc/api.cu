@@ -96,6 +96,7 @@ static double shape_flops(int sh)
     case SH_CTRL2: return 7;    // a dense 2x2 on half of the amplitudes
     case SH_BLOCK2: return 10;  // a dense 2x2 on half, one phase on each remaining quarter
     case SH_IMAG1: return 6;    // two real products and a sum per output
+    case SH_DENSE4: return 126; // sixteen complex products and fifteen sums per output
     case SH_REAL1: return 6;
     default: return 6;          // one complex product
     }
@@ -174,11 +175,12 @@ static bool mat_inverse(const Mat &A, int d, Mat &out)
     return true;
 }
 
-static bool is_channel(int kind) { return kind >= GBVQC_DEPOL && kind <= GBVQC_KRAUS; }
+static bool is_channel(int kind) { return kind >= GBVQC_DEPOL && kind <= GBVQC_KRAUS2; }
+static bool is_channel2(int kind) { return kind == GBVQC_DEPOL2 || kind == GBVQC_KRAUS2; }
 static bool is_rotation(int kind) { return kind == GBVQC_RX || kind == GBVQC_RY || kind == GBVQC_RZ; }
 static int kind_qubits(int kind)
 {
-    return (kind >= GBVQC_CNOT && kind <= GBVQC_CONTROL) || kind == GBVQC_DENSE2 ? 2 : 1;
+    return (kind >= GBVQC_CNOT && kind <= GBVQC_CONTROL) || kind == GBVQC_DENSE2 || is_channel2(kind) ? 2 : 1;
 }
 
 // Matrix of a unitary op with its fixed parameters (Sec. II.B); rotations use params[0].
@@ -254,6 +256,42 @@ static std::vector<Mat> channel_kraus(int kind, double g, const double *kraus, i
         return ks;
     }
     }
+}
+
+// Kraus operators (4x4, matrix bit 0 = the first qubit) of a two-qubit channel.
+static std::vector<Mat> channel_kraus2(int kind, double g, const double *kraus, int n_kraus)
+{
+    std::vector<Mat> ks;
+    if (kind == GBVQC_KRAUS2) {
+        for (int s = 0; s < n_kraus; s++) ks.push_back(mat_from(kraus + 32 * s, 4));
+        return ks;
+    }
+    const cd I(0, 1);
+    const cd P[4][4] = {{1, 0, 0, 1}, {0, 1, 1, 0}, {0, -I, I, 0}, {1, 0, 0, -1}};  // I, X, Y, Z
+    for (int b = 0; b < 4; b++)      // Pauli on the second qubit
+        for (int a = 0; a < 4; a++) {  // Pauli on the first qubit
+            const double w = (a == 0 && b == 0) ? std::sqrt(1 - 15 * g / 16) : std::sqrt(g / 16);
+            Mat K(16, 0);
+            for (int r = 0; r < 4; r++)
+                for (int c = 0; c < 4; c++)
+                    K[r * 4 + c] = w * P[a][2 * (r & 1) + (c & 1)] * P[b][2 * (r >> 1) + (c >> 1)];
+            ks.push_back(K);
+        }
+    return ks;
+}
+
+// Superoperator of a two-qubit channel on (ket q0, ket q1, bra q0, bra q1) (matrix bits
+// 0..3): S[(r + 4 r'), (c + 4 c')] = sum_s K[r][c] conj(K[r'][c']), 16 x 16.
+static Mat superop2(const std::vector<Mat> &ks)
+{
+    Mat S(256, 0);
+    for (const Mat &K : ks)
+        for (int r = 0; r < 4; r++)
+            for (int r2 = 0; r2 < 4; r2++)
+                for (int c = 0; c < 4; c++)
+                    for (int c2 = 0; c2 < 4; c2++)
+                        S[(r + 4 * r2) * 16 + (c + 4 * c2)] += K[r * 4 + c] * std::conj(K[r2 * 4 + c2]);
+    return S;
 }
 
 // Superoperator on (ket q, bra q): S[(r1 + 2 r2), (c1 + 2 c2)] = sum_s K[r1][c1] conj(K[r2][c2])
@@ -378,6 +416,8 @@ struct PlainGate {
     int param;
     double gscale;
     int slot;
+    // SH_DENSE4 (two-qubit channel superoperator): qubits 3 and 4 of the matrix
+    int q2 = 0, q3 = 0;
     // further derivatives of the same gate (variational FSIM parameters after the first)
     int n_extra = 0;
     int ex_rec[4] = {-1, -1, -1, -1}, ex_param[4] = {-1, -1, -1, -1}, ex_slot[4] = {-1, -1, -1, -1};
@@ -410,6 +450,7 @@ struct DevPlan {  // a FusedPlan and its device copies (uploaded on first launch
 struct gbvqc_circuit {
     int n_log = 0, n_phys = 0, n_params = 0, density = 0;
     std::vector<gbvqc_op> ops;
+    std::vector<std::vector<double>> kraus_store;  // copies of the KRAUS2 operator lists
     std::vector<MatRec> recs;
     std::vector<DynRec> dyn;
     MatRec *d_recs = nullptr;
@@ -737,6 +778,7 @@ extern "C" gbvqc_status apply_channel(sv_handle sv, int kind, int qubit, double 
     if (!sv) return fail(GBVQC_ERR_ARG, "NULL state");
     if (!sv->density) return fail(GBVQC_ERR_NOT_DENSITY, "apply_channel needs a density state");
     if (!is_channel(kind)) return fail(GBVQC_ERR_ARG, "kind %d is not a channel", kind);
+    if (is_channel2(kind)) return fail(GBVQC_ERR_ARG, "two-qubit channels run inside circuits");
     if (qubit < 0 || qubit >= sv->n_log) return fail(GBVQC_ERR_ARG, "qubit %d out of range", qubit);
     if (kind == GBVQC_KRAUS && (!kraus || n_kraus < 1 || n_kraus > 4))
         return fail(GBVQC_ERR_ARG, "KRAUS needs 1..4 operators");
@@ -770,6 +812,35 @@ static int add_rec(gbvqc_circuit *c, const Mat &M)
     }
     c->recs.push_back(r);
     return (int)c->recs.size() - 1;
+}
+
+// A 16 x 16 matrix as 16 consecutive records (record base + r holds row r); returns base.
+static int add_rec16(gbvqc_circuit *c, const Mat &M)
+{
+    const int base = (int)c->recs.size();
+    for (int r = 0; r < 16; r++) {
+        MatRec rec{};
+        for (int col = 0; col < 16; col++) {
+            rec.d[2 * col] = M[r * 16 + col].real();
+            rec.d[2 * col + 1] = M[r * 16 + col].imag();
+            rec.f[2 * col] = (float)rec.d[2 * col];
+            rec.f[2 * col + 1] = (float)rec.d[2 * col + 1];
+        }
+        c->recs.push_back(rec);
+    }
+    return base;
+}
+
+// Forward, inverse and adjoint superoperators of a two-qubit channel (records of 16 rows).
+struct Chan2Recs {
+    int f, i, a;
+};
+static Chan2Recs channel2_records(gbvqc_circuit *c, const gbvqc_op &op)
+{
+    const Mat S = superop2(channel_kraus2(op.kind, op.params[0], op.kraus, op.n_kraus));
+    Mat Si;
+    mat_inverse(S, 16, Si);  // invertibility checked by circuit_create
+    return Chan2Recs{add_rec16(c, S), add_rec16(c, Si), add_rec16(c, mat_dagger(S, 16))};
 }
 
 static int add_dyn(gbvqc_circuit *c, int param, int rot, int variant, int domain)
@@ -1047,6 +1118,23 @@ static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGa
             }
             continue;
         }
+        if (is_channel2(op.kind)) {  // a four-qubit superoperator: its own pass (barrier)
+            const Chan2Recs r = channel2_records(c, op);
+            PGate g{};
+            g.k = 4;
+            g.q[0] = map.ket[op.qubits[0]];
+            g.q[1] = map.ket[op.qubits[1]];
+            g.q[2] = map.bra[op.qubits[0]];
+            g.q[3] = map.bra[op.qubits[1]];
+            g.ftype = FT_DENSE4;
+            g.rec_f = r.f;
+            g.rec_i = r.i;
+            g.rec_a = r.a;
+            g.gen = GEN_NONE;
+            g.param = -1;
+            out.push_back(g);
+            continue;
+        }
         if (is_channel(op.kind)) {
             Mat S = superop(channel_kraus(op.kind, op.params[0], op.data, op.n_kraus)), Si;
             mat_inverse(S, 4, Si);
@@ -1137,7 +1225,16 @@ extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qub
             return fail(GBVQC_ERR_ARG, "op %d: bad param_index %d", j, op.param_index);
         }
         if (op.param_index < -1) return fail(GBVQC_ERR_ARG, "op %d: bad param_index %d", j, op.param_index);
-        if (is_channel(op.kind)) {
+        if (is_channel2(op.kind)) {
+            if (!is_density) return fail(GBVQC_ERR_NOT_DENSITY, "op %d: channel in a pure-state circuit", j);
+            if (op.kind == GBVQC_KRAUS2 && (!op.kraus || op.n_kraus < 1 || op.n_kraus > 16))
+                return fail(GBVQC_ERR_ARG, "op %d: KRAUS2 needs 1..16 operators", j);
+            if (op.kind == GBVQC_DEPOL2 && !(op.params[0] >= 0.0 && op.params[0] <= 1.0))
+                return fail(GBVQC_ERR_ARG, "op %d: channel strength %g", j, op.params[0]);
+            Mat Si;
+            if (!mat_inverse(superop2(channel_kraus2(op.kind, op.params[0], op.kraus, op.n_kraus)), 16, Si))
+                return fail(GBVQC_ERR_ARG, "op %d: channel superoperator is singular", j);
+        } else if (is_channel(op.kind)) {
             if (!is_density) return fail(GBVQC_ERR_NOT_DENSITY, "op %d: channel in a pure-state circuit", j);
             if (op.kind == GBVQC_KRAUS && (op.n_kraus < 1 || op.n_kraus > 4))
                 return fail(GBVQC_ERR_ARG, "op %d: n_kraus %d", j, op.n_kraus);
@@ -1156,6 +1253,15 @@ extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qub
     c->n_params = n_params;
     c->density = is_density ? 1 : 0;
     c->ops.assign(ops, ops + n_ops);
+    c->kraus_store.reserve(n_ops);
+    for (gbvqc_op &op : c->ops) {
+        if (op.kind == GBVQC_KRAUS2) {
+            c->kraus_store.emplace_back(op.kraus, op.kraus + 32 * op.n_kraus);
+            op.kraus = c->kraus_store.back().data();
+        } else {
+            op.kraus = nullptr;
+        }
+    }
     for (const gbvqc_op &op : c->ops)
         c->n_param_ops += op.param_index < 0 ? 0 : is_var_fsim(op) ? __builtin_popcount(op.param_mask) : 1;
     // per-gate schedule in the standard layout
@@ -1176,6 +1282,12 @@ extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qub
                     g.n_extra++;
                 }
             }
+            c->plain.push_back(g);
+        } else if (is_channel2(op.kind)) {
+            const Chan2Recs r = channel2_records(c, op);
+            PlainGate g{SH_DENSE4, op.qubits[0], op.qubits[1], r.f, r.i, r.a, 0, 0, 0, -1, -1, 1.0, -1};
+            g.q2 = op.qubits[0] + n_qubits;
+            g.q3 = op.qubits[1] + n_qubits;
             c->plain.push_back(g);
         } else if (is_channel(op.kind)) {
             Mat S = superop(channel_kraus(op.kind, op.params[0], op.data, op.n_kraus)), Si;
@@ -1470,9 +1582,22 @@ static gbvqc_status stage_theta(gbvqc_circuit *c, const double *theta, int n_the
 
 static double state_bytes(const gbvqc_circuit *c, int dtype) { return double(size_t(1) << c->n_phys) * amp_size(dtype); }
 
+// Four-qubit superoperator (16 rows from record rec) on physical qubits q[0..3].
+static gbvqc_status gate4(gbvqc_circuit *c, int dtype, void *psi, const int *q, int rec, cudaStream_t s)
+{
+    const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
+    return run_k("gate4q", shape_flops(SH_DENSE4) * amps, 2.0 * sb, s, [&] {
+        return launch_gate4(dtype, psi, c->n_phys, q[0], q[1], q[2], q[3], c->d_recs + rec, s);
+    });
+}
+
 static gbvqc_status plain_gate(gbvqc_circuit *c, int dtype, void *psi, const PlainGate &g, int rec, cudaStream_t s)
 {
     const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
+    if (g.shape == SH_DENSE4) {
+        const int q[4] = {g.q0, g.q1, g.q2, g.q3};
+        return gate4(c, dtype, psi, q, rec, s);
+    }
     const bool one = shape_qubits(g.shape) == 1;
     return run_k(one ? "gate1q" : "gate2q", shape_flops(g.shape) * amps, (g.shape == SH_CTRL2 ? 1.0 : 2.0) * sb, s,
                  [&] { return launch_gate(dtype, psi, c->n_phys, g.shape, g.q0, g.q1, c->d_recs + rec, s); });
@@ -1497,10 +1622,16 @@ static gbvqc_status run_fused_forward(gbvqc_circuit *c, DevPlan *p, int dtype, v
 {
     const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
     const FusedDev fd{p->d_fwd, p->d_fsubs, p->d_fgates, p->d_fents, p->d_funits, c->d_recs, p->d_fimg};
-    for (size_t i = 0; i < p->p.fwd.size(); i++)
+    for (size_t i = 0; i < p->p.fwd.size(); i++) {
+        if (p->p.barrier[i] >= 0) {  // two-qubit channel between the tile passes
+            const PGate &g = p->p.barrier_gates[p->p.barrier[i]];
+            ST_TRY(gate4(c, dtype, psi, g.q, g.rec_f, s));
+            continue;
+        }
         ST_TRY(run_k("fused_forward", p->p.fwd_flops[i] * amps, 2 * sb, s, [&] {
             return launch_fused_forward(dtype, psi, fd, (int)i, p->p.fwd[i], p->fwd_smem[i], s);
         }));
+    }
     return GBVQC_OK;
 }
 
@@ -1585,11 +1716,18 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
     if (fused) {
         const int tiles = 1 << (c->n_phys - p->p.t);
         const FusedDev fd{p->d_rev, p->d_rsubs, p->d_rgates, p->d_rents, p->d_runits, c->d_recs, p->d_rimg};
-        for (int i = (int)p->p.rev.size() - 1; i >= 0; i--)
+        for (int i = (int)p->p.rev.size() - 1; i >= 0; i--) {
+            if (p->p.barrier[i] >= 0) {  // Phi <- S^-1 Phi, Psi <- S^dag Psi (no parameters)
+                const PGate &g = p->p.barrier_gates[p->p.barrier[i]];
+                ST_TRY(gate4(c, dtype, w.phi, g.q, g.rec_i, s));
+                ST_TRY(gate4(c, dtype, w.psi, g.q, g.rec_a, s));
+                continue;
+            }
             ST_TRY(run_k("fused_reverse", p->p.rev_flops[i] * amps, 4 * sb, s, [&] {
                 return launch_fused_reverse(dtype, w.phi, w.psi, fd, i, p->p.rev[i], p->rev_smem[i],
                                             w.d_slot_partials, tiles, s);
             }));
+        }
         ST_TRY(run_k("reduce_slots", 0, 0, s, [&] {
             return launch_reduce_slots(w.d_slot_partials, p->p.n_slots, tiles, tiles, w.d_slot_grad, s);
         }));
@@ -1928,6 +2066,8 @@ static gbvqc_status batch_build(gbvqc_batch *b)
         ST_TRY(ensure_device(c));
         ST_TRY(ensure_obs(b->obs[i]));
         ST_TRY(get_plan(c, dtype, true, &plans[i]));
+        for (int bi : plans[i]->p.barrier)
+            if (bi >= 0) return fail(GBVQC_ERR_UNSUPPORTED, "batch member %d holds a two-qubit channel", i);
         const FusedPlan &P = plans[i]->p;
         amp_off[i] = amps;
         amps += int64_t(1) << c->n_phys;

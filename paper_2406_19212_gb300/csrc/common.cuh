@@ -27,11 +27,15 @@ enum Shape : int32_t {
     SH_PERM2 = 6,   // one non-zero per row (SWAP, iSWAP)
     SH_CTRL2 = 7,   // identity unless the first qubit is 1, then a 2x2 on the second
     SH_BLOCK2 = 8,  // phase on |00>, a 2x2 on {|01>, |10>}, phase on |11> (FSIM, iSWAP-like)
-    SH_IMAG1 = 9    // real diagonal, imaginary off-diagonal 2x2 (Rx; sqrt(X) up to a phase)
+    SH_IMAG1 = 9,   // real diagonal, imaginary off-diagonal 2x2 (Rx; sqrt(X) up to a phase)
+    SH_DENSE4 = 10  // general 16x16 (two-qubit channel superoperator), 16 records of one row
 };
 
 inline __host__ __device__ bool shape_is_diag(int sh) { return sh == SH_DIAG1 || sh == SH_DIAG2; }
-inline __host__ __device__ int shape_qubits(int sh) { return sh >= SH_DENSE2 && sh <= SH_BLOCK2 ? 2 : 1; }
+inline __host__ __device__ int shape_qubits(int sh)
+{
+    return sh == SH_DENSE4 ? 4 : sh >= SH_DENSE2 && sh <= SH_BLOCK2 ? 2 : 1;
+}
 
 // Row-major re/im offsets of the 2x2 block of an SH_BLOCK2 matrix (rows/columns 1 and 2)
 // and of its two diagonal phases (rows 0 and 3).
@@ -255,8 +259,10 @@ enum FType : int32_t {
                     // a = slot mask; entry k = Shape, ca = slot, cls = GenType
     FT_BLOCK2 = 10,  // SH_BLOCK2 on two register slots
     FT_IMAG1 = 11,   // SH_IMAG1 on one register slot
-    FT_PROBE2 = 12   // reverse only: gradient read 2 Re <Psi| K |Phi> with the 4x4 K on two
+    FT_PROBE2 = 12,  // reverse only: gradient read 2 Re <Psi| K |Phi> with the 4x4 K on two
                      // register slots; the states are not changed
+    FT_DENSE4 = 13   // a two-qubit channel's superoperator: never in a tile pass (the planner
+                     // makes it a pass of its own, run by the per-gate kernel)
 };
 // Generator of a variational gate for the fused reverse sweep: the gradient term is
 // coef * Im <Psi| P |Phi> with both states taken right after the gate.

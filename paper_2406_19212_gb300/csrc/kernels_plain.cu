@@ -193,6 +193,67 @@ cudaError_t launch_gate(int dtype, void *psi, int n, int shape, int q0, int q1, 
                       : gate_dispatch<double>(psi, n, shape, q0, q1, rec, s);
 }
 
+// ------------------------------------------------------------------ four-qubit gates
+
+// One thread per group of 16 amplitudes: gather, 16 x 16 complex product from the matrix
+// staged in shared memory, scatter (a two-qubit channel's superoperator on (ket q0, ket q1,
+// bra q0, bra q1), Eq. channel2).
+template <typename R>
+__global__ void __launch_bounds__(128) k_gate4(typename CT<R>::T *__restrict__ psi, int64_t ngroups, int4 q,
+                                               const MatRec *__restrict__ rows)
+{
+    typedef typename CT<R>::T T;
+    __shared__ R m[512];
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) m[i] = mat_of<R>(&rows[i >> 5])[i & 31];
+    __syncthreads();
+    const int qs[4] = {q.x, q.y, q.z, q.w};
+    int srt[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = a + 1; b < 4; b++)
+            if (srt[b] < srt[a]) {
+                const int x = srt[a];
+                srt[a] = srt[b];
+                srt[b] = x;
+            }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+        int64_t base = g;
+#pragma unroll
+        for (int u = 0; u < 4; u++) base = insert_zero(base, srt[u]);
+        int64_t idx[16];
+        T v[16];
+#pragma unroll
+        for (int l = 0; l < 16; l++) {
+            int64_t ix = base;
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if ((l >> u) & 1) ix |= int64_t(1) << qs[u];
+            idx[l] = ix;
+            v[l] = psi[ix];
+        }
+#pragma unroll
+        for (int r = 0; r < 16; r++) {
+            T acc = cmul<T, R>(m[32 * r], m[32 * r + 1], v[0]);
+#pragma unroll
+            for (int c = 1; c < 16; c++) cfma<T, R>(m[32 * r + 2 * c], m[32 * r + 2 * c + 1], v[c], acc);
+            psi[idx[r]] = acc;  // v holds the old values, so rows can be written as they finish
+        }
+    }
+}
+
+cudaError_t launch_gate4(int dtype, void *psi, int n, int q0, int q1, int q2, int q3, const MatRec *rows,
+                         cudaStream_t s)
+{
+    const int64_t ng = int64_t(1) << (n - 4);
+    const int gr = grid_for(ng, 128);
+    const int4 q = make_int4(q0, q1, q2, q3);
+    if (dtype == 0) k_gate4<float><<<gr, 128, 0, s>>>((float2 *)psi, ng, q, rows);
+    else k_gate4<double><<<gr, 128, 0, s>>>((double2 *)psi, ng, q, rows);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ small helpers
 
 template <typename T>

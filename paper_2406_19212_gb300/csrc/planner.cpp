@@ -28,8 +28,8 @@ namespace {
 
 inline uint64_t qmask(const PGate &g)
 {
-    uint64_t m = uint64_t(1) << g.q[0];
-    if (g.k == 2) m |= uint64_t(1) << g.q[1];
+    uint64_t m = 0;
+    for (int u = 0; u < g.k; u++) m |= uint64_t(1) << g.q[u];
     return m;
 }
 
@@ -436,7 +436,8 @@ size_t pass_smem_bytes(const FusedPlan &plan, const PassDesc &d, bool reverse, i
 // Greedy pass selection: scan the remaining gates in circuit order; a gate joins the pass
 // if every earlier remaining gate on its qubits joined (no qubit of it is blocked), its
 // non-diagonal qubits fit in the t tile qubits (the `low` lowest physical qubits are
-// always in the tile), and the pass's slot and shared-memory budgets allow it.
+// always in the tile), and the pass's slot and shared-memory budgets allow it.  A ready
+// four-qubit gate met by an empty pass becomes a pass of its own; met later, it blocks.
 bool select_passes(const std::vector<PGate> &G, int n, int t, int low, const PlanOptions &opt,
                    std::vector<PassSel> &passes, std::string &err)
 {
@@ -455,6 +456,15 @@ bool select_passes(const std::vector<PGate> &G, int n, int t, int low, const Pla
             const PGate &g = G[i];
             const uint64_t qm = qmask(g);
             if (qm & blocked) {
+                blocked |= qm;
+                continue;
+            }
+            if (g.k == 4) {
+                if (pb.gates.empty()) {
+                    pb.barrier = i;
+                    pb.gates.push_back(i);
+                    break;
+                }
                 blocked |= qm;
                 continue;
             }
@@ -483,6 +493,10 @@ bool select_passes(const std::vector<PGate> &G, int n, int t, int low, const Pla
         }
         for (int i : pb.gates) applied[i] = 1;
         done += (int)pb.gates.size();
+        if (pb.barrier >= 0) {
+            passes.push_back(std::move(pb));
+            continue;
+        }
         for (int q = 0; q < n && cnt < t; q++)
             if (!((pb.S >> q) & 1)) {
                 pb.S |= uint64_t(1) << q;
@@ -531,6 +545,12 @@ bool build_fused_plan(const std::vector<PGate> &G, int n, const PlanOptions &opt
     out.rev.resize(P);
     out.fwd_flops.assign(P, 0.0);
     out.rev_flops.assign(P, 0.0);
+    out.barrier.assign(P, -1);
+    for (size_t p = 0; p < P; p++)
+        if (passes[p].barrier >= 0) {
+            out.barrier[p] = (int)out.barrier_gates.size();
+            out.barrier_gates.push_back(G[passes[p].barrier]);
+        }
     std::vector<std::vector<int>> local_of(P, std::vector<int>(64, -1));
     for (size_t p = 0; p < P; p++) {
         PassDesc d{};
@@ -554,6 +574,10 @@ bool build_fused_plan(const std::vector<PGate> &G, int n, const PlanOptions &opt
         for (size_t pi = 0; pi < P; pi++) {
             const size_t p = rev ? P - 1 - pi : pi;   // reverse passes in launch order
             PassDesc &d = rev ? out.rev[p] : out.fwd[p];
+            if (passes[p].barrier >= 0) {  // not a tile pass: empty ranges, no slots
+                d.slot_begin = rev ? slot_counter : 0;
+                continue;
+            }
             std::vector<int> order = passes[p].gates;
             if (rev) std::reverse(order.begin(), order.end());
             Emitter E{G, local_of[p].data(), t, rev ? opt.nr_r : opt.nr_f, opt.elem_bytes, rev,

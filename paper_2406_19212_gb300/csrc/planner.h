@@ -13,8 +13,8 @@ namespace gbvqc {
 
 // One physical gate as the planner sees it.
 struct PGate {
-    int k;            // 1 or 2 physical qubits
-    int q[2];         // physical qubits (q[0] = matrix bit 0)
+    int k;            // 1, 2 or 4 physical qubits (4: a two-qubit channel's superoperator)
+    int q[4];         // physical qubits (q[0] = matrix bit 0)
     bool diag;        // diagonal matrix (commutes with other diagonal gates)
     int ftype;        // FType
     int rec_f;        // forward matrix record
@@ -50,15 +50,21 @@ struct FusedPlan {
     int max_pass_slots = 0;
     // algorithmic flops per amplitude of every pass (forward / reverse)
     std::vector<double> fwd_flops, rev_flops;
+    // passes that are one four-qubit gate (a two-qubit channel), run by the per-gate
+    // kernel between the tile passes: index into barrier_gates, -1 for a tile pass
+    std::vector<int> barrier;
+    std::vector<PGate> barrier_gates;
 };
 
 bool build_fused_plan(const std::vector<PGate> &gates, int n, const PlanOptions &opt, FusedPlan &out,
                       std::string &err);
 
-// The tile qubit set and the gates of one pass, from the greedy pass selection.
+// The tile qubit set and the gates of one pass, from the greedy pass selection; a
+// four-qubit gate is a pass of its own (barrier >= 0: its gate index).
 struct PassSel {
     uint64_t S = 0;
     std::vector<int> gates;
+    int barrier = -1;
 };
 bool select_passes(const std::vector<PGate> &gates, int n, int t, int low, const PlanOptions &opt,
                    std::vector<PassSel> &passes, std::string &err);

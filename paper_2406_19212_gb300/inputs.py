@@ -332,12 +332,17 @@ def random_unitary(k: int, rng: np.random.Generator) -> np.ndarray:
     return q * (np.diag(r) / np.abs(np.diag(r)))
 
 
-def random_kraus2(rng: np.random.Generator, count: int = 3) -> List[np.ndarray]:
+def random_kraus2(rng: np.random.Generator, count: int = 3, weight: Optional[float] = None) -> List[np.ndarray]:
     """A random two-qubit channel: count 4x4 Kraus operators cut from a random isometry
-    (orthonormal columns of a 4 count x 4 matrix), so sum K^dag K = I."""
+    (orthonormal columns of a 4 count x 4 matrix), so sum K^dag K = I.  With weight w the
+    channel is mixed with the identity: sqrt(1-w) I followed by sqrt(w) K_s (weak noise,
+    whose superoperator inverse stays well conditioned)."""
     A = rng.normal(size=(4 * count, 4)) + 1j * rng.normal(size=(4 * count, 4))
     Q, _ = np.linalg.qr(A)
-    return [Q[4 * s:4 * s + 4, :] for s in range(count)]
+    ks = [Q[4 * s:4 * s + 4, :] for s in range(count)]
+    if weight is None:
+        return ks
+    return [math.sqrt(1.0 - weight) * np.eye(4, dtype=complex)] + [math.sqrt(weight) * k for k in ks]
 
 
 def random_kraus(rng: np.random.Generator, count: int = 3) -> List[np.ndarray]:

@@ -178,3 +178,23 @@ def test_variational_fsim_validation(lib):
     c = gb.circuit_create(w.circuit)
     st = c.plan_stats(gb.C64, for_grad=True)
     assert st["grad_slots"] == w.circuit.n_params
+
+
+def test_two_qubit_channel_validation_and_barrier_passes(lib):
+    pure = I.Circuit(3, [I.Op("DEPOL2", (0, 1), fixed=(0.1,))], 0)
+    with pytest.raises(gb.GbvqcError) as ex:
+        gb.circuit_create(pure)
+    assert ex.value.status == 5  # ERR_NOT_DENSITY
+    bad_p = I.Circuit(3, [I.Op("DEPOL2", (0, 1), fixed=(1.5,))], 0, density=True)
+    with pytest.raises(gb.GbvqcError):
+        gb.circuit_create(bad_p)
+    singular = I.Circuit(3, [I.Op("KRAUS2", (0, 2), data=[np.zeros((4, 4))])], 0, density=True)
+    with pytest.raises(gb.GbvqcError):
+        gb.circuit_create(singular)
+    rng = np.random.default_rng(2)
+    ops = [I.Op("RY", (0,), param=0), I.Op("KRAUS2", (0, 2), data=I.random_kraus2(rng, 3)),
+           I.Op("RX", (1,), param=1), I.Op("DEPOL2", (1, 2), fixed=(0.05,)), I.Op("RZ", (2,), param=2)]
+    c = gb.circuit_create(I.Circuit(4, ops, 3, density=True))
+    c.set_tiling(6, 2)
+    st = c.plan_stats(gb.C64, for_grad=True)
+    assert st["passes"] >= 3  # the two channels are passes of their own between tile passes

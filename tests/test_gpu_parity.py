@@ -424,3 +424,54 @@ def test_fsim_parameter_gradients_batched():
         e_ref, g_ref = O.adjoint_grad(w.circuit, w.theta, w.observable)
         check_energy(e, e_ref, gb.C128)
         check_grad(g, g_ref, gb.C128)
+
+
+# ----------------------------------------------------------------- two-qubit channels
+
+def _noisy_two_qubit_channels(n, seed):
+    """Rx.Rz layers with CNOTs followed by two-qubit depolarising, plus random two-qubit
+    Kraus channels (QuantumMap on two positions) of weak strength: the reverse sweep
+    uncomputes with the superoperator inverse, whose norm grows with the noise, so strong
+    random channels amplify complex64 rounding beyond the gradient tolerance."""
+    rng = np.random.default_rng(seed)
+    ops, p = [], 0
+    for layer in range(3):
+        for q in range(n):
+            ops += [I.Op("RX", (q,), param=p), I.Op("RZ", (q,), param=p + 1)]
+            p += 2
+        for q in range(layer % 2, n - 1, 2):
+            ops += [I.Op("CNOT", (q, q + 1)), I.Op("DEPOL2", (q, q + 1), fixed=(0.02,))]
+        a, b = rng.choice(n, 2, replace=False)
+        ops.append(I.Op("KRAUS2", (int(a), int(b)), data=I.random_kraus2(rng, 2 + layer, weight=0.05)))
+    theta = rng.uniform(0, 2 * math.pi, p)
+    obs = I.ising_chain(n, [0.5] * n) + [(0.3, ((0, "Y"), (n - 1, "X")))]
+    return I.Circuit(n, ops, p, density=True), theta, obs
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", MODES)
+def test_two_qubit_channels_apply_and_grad(dtype, mode):
+    n = 5
+    circ, theta, obs = _noisy_two_qubit_channels(n, 3)
+    ref = O.rho_apply_circuit(circ, theta)
+    got = run_apply(circ, theta, dtype, mode, tiling=(7, 2) if mode == gb.FUSED else None)
+    np.testing.assert_allclose(got, ref, atol=AMP_TOL[dtype] * 4, rtol=0)
+    c = gb.circuit_create(circ)
+    if mode == gb.FUSED:
+        c.set_tiling(7, 2)
+    o = gb.obs_create(obs, n)
+    e, g = gb.grad(c, theta, o, dtype, mode)
+    e_ref, g_ref = O.noisy_adjoint_grad(circ, theta, obs)
+    check_energy(e, e_ref, dtype)
+    check_grad(g, g_ref, dtype)
+
+
+def test_two_qubit_channels_rejected_by_batches():
+    """Batches take pure-state circuits only (a density circuit is refused before its
+    plan, so a two-qubit channel never reaches the batched kernels)."""
+    circ, theta, obs = _noisy_two_qubit_channels(4, 9)
+    c = gb.circuit_create(circ)
+    o = gb.obs_create(obs, 4)
+    with pytest.raises(gb.GbvqcError) as ex:
+        gb.batch_create([c], [o], gb.C64)
+    assert ex.value.status == 1
