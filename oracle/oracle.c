@@ -22,7 +22,8 @@
  *     conjugate on the bra index);
  *   - measure!(state, i) of Sec. II.D: the probability of each outcome of qubit i, the
  *     outcome picked by a caller-supplied uniform u (0 if u < P(0)), and the collapsed,
- *     renormalised state (pure or density).
+ *     renormalised state (pure or density); and sampling of all qubits (the index where
+ *     the cumulative probability first exceeds u times the total).
  *
  * Readings of the paper taken here (each also listed in the design notes):
  *   - the printed Ry matrix [[c,-s],[-s,c]] is not unitary: Ry = [[c,-s],[s,c]];
@@ -714,6 +715,38 @@ int orc_measure(double *state_, int n, int density, int q, double u, int *outcom
                 }
         }
     }
+    return 0;
+}
+
+/* Sampling (repeated measurement of every qubit on fresh copies of the state): with
+ * w_a = |psi_a|^2 (pure) or rho_aa (density) and the total W, shot s returns the least
+ * index a with u_s W < w_0 + ... + w_a (sums in FP64 in index order); u_s in [0, 1) are
+ * the caller's uniform draws. */
+int orc_sample(const double *state_, int n, int density, const double *u, int n_shots, int64_t *out)
+{
+    const cplx *st = (const cplx *)state_;
+    const int64_t dim = (int64_t)1 << n;
+    double *cdf = (double *)malloc(sizeof(double) * (size_t)dim);
+    double acc = 0.0;
+    int64_t a;
+    int s;
+    if (!cdf) return -1;
+    for (a = 0; a < dim; a++) {
+        const cplx v = density ? st[a + dim * a] : st[a];
+        acc += density ? creal(v) : creal(v) * creal(v) + cimag(v) * cimag(v);
+        cdf[a] = acc;
+    }
+    for (s = 0; s < n_shots; s++) {
+        const double target = u[s] * acc;
+        int64_t lo = 0, hi = dim - 1;  /* least a with target < cdf[a] */
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (target < cdf[mid]) hi = mid;
+            else lo = mid + 1;
+        }
+        out[s] = lo;
+    }
+    free(cdf);
     return 0;
 }
 

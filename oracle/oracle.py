@@ -67,6 +67,8 @@ def lib():
         L.orc_vec_apply_circuit.argtypes = [dp, ctypes.c_int, op_p, ctypes.c_int, dp]
         L.orc_measure.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                   ctypes.POINTER(ctypes.c_int), dp]
+        L.orc_sample.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_int64)]
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -295,3 +297,15 @@ def measure(state: np.ndarray, n: int, qubit: int, u: float, density: bool = Fal
     if r != 0:
         raise ValueError("orc_measure failed")
     return outcome.value, prob.value, st
+
+
+def sample(state: np.ndarray, n: int, u, density: bool = False) -> np.ndarray:
+    """Basis indices sampled from |psi_a|^2 (or rho_aa) with the uniform draws u."""
+    st = np.ascontiguousarray(np.array(state, dtype=np.complex128).reshape(-1))
+    uu = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1))
+    out = np.zeros(max(1, uu.size), dtype=np.int64)
+    r = lib().orc_sample(_dp(st.view(np.float64)), n, int(bool(density)), _dp(uu), uu.size,
+                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    if r != 0:
+        raise ValueError("orc_sample failed")
+    return out[:uu.size]

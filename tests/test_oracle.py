@@ -461,3 +461,34 @@ def test_kraus2_density_against_dense_and_superoperator(seed):
     terms = [(0.6, ((0, "Z"), (2, "X"))), (-0.4, ((1, "Y"),)), (0.3, ((2, "Z"),))]
     e, g = O.noisy_adjoint_grad(circ, theta, terms)
     np.testing.assert_allclose(g, O.parameter_shift_grad(circ, theta, terms), atol=1e-12)
+
+
+# ----------------------------------------------------------------- sampling
+
+def test_sample_quantiles_of_a_product_state():
+    """Ry(t_q) on every qubit of |0...0> gives P(a) = prod_q (cos^2 or sin^2)(t_q/2); with
+    the quantile grid u_i = (i + 1/2)/N the number of shots returning a equals the number
+    of grid points inside [CDF(a-1), CDF(a)) of that closed form."""
+    n, N = 4, 2000
+    ts = [0.3, 1.1, 2.0, 2.9]
+    ops = [op("RY", (q,), fixed=(ts[q],)) for q in range(n)]
+    psi = O.apply_circuit(I.Circuit(n, ops, 0), [])
+    P = np.array([np.prod([(math.sin(ts[q] / 2) ** 2) if (a >> q) & 1 else (math.cos(ts[q] / 2) ** 2)
+                           for q in range(n)]) for a in range(1 << n)])
+    u = (np.arange(N) + 0.5) / N
+    got = O.sample(psi, n, u)
+    cdf = np.cumsum(P)
+    lo = np.concatenate([[0.0], cdf[:-1]])
+    expect = [int(np.sum((u >= lo[a]) & (u < cdf[a]))) for a in range(1 << n)]
+    assert np.bincount(got, minlength=1 << n).tolist() == expect
+
+
+def test_sample_basis_state_ghz_and_density():
+    n = 5
+    psi = np.zeros(1 << n, complex)
+    psi[19] = 1
+    assert set(O.sample(psi, n, [0.0, 0.3, 0.999999]).tolist()) == {19}
+    ghz = O.apply_circuit(I.Circuit(n, [op("H", (0,))] + [op("CNOT", (i, i + 1)) for i in range(n - 1)], 0), [])
+    assert O.sample(ghz, n, [0.2, 0.49, 0.51, 0.97]).tolist() == [0, 0, 31, 31]
+    rho = np.outer(ghz, ghz.conj()).T.reshape(-1)
+    assert O.sample(rho, n, [0.2, 0.49, 0.51, 0.97], density=True).tolist() == [0, 0, 31, 31]
