@@ -202,6 +202,15 @@ gbvqc_status apply_channel(sv_handle sv, int kind, int qubit, double strength,
  * [0, n_qubits), u outside [0, 1) or a state of zero norm; ERR_CUDA if a launch fails. */
 gbvqc_status measure(sv_handle sv, int qubit, double u, int *outcome, double *prob);
 
+/* Sampling: measurement of every qubit on n_shots fresh copies of the state (the state is
+ * not changed).  With weights w_a = |psi_a|^2 (pure) or rho_aa (density) and their total
+ * W, shot s returns in out[s] the least basis index a with u[s] W < w_0 + ... + w_a (FP64
+ * partial sums over chunks of the index range, then within the chunk).  u: n_shots
+ * uniform draws in [0, 1) (host), out: n_shots int64 (host).  Synchronises the state's
+ * stream; allocates and frees scratch of about 2^(n-cbits) doubles.  Errors: ERR_ARG for
+ * NULL pointers or u outside [0, 1); ERR_OOM; ERR_CUDA. */
+gbvqc_status sample(sv_handle sv, const double *u, int n_shots, int64_t *out);
+
 /* ---------------------------------------------------------- observables (Sec. II.E) */
 
 /* Pauli sum H = sum_t terms[t].coeff P_t over n_qubits logical qubits (QubitsOperator).

@@ -25,7 +25,7 @@ from ._abi import C64, C128, FUSED, PLAIN, GbvqcError
 __all__ = ["C64", "C128", "PLAIN", "FUSED", "GbvqcError", "StateVector", "CircuitHandle",
            "Observable", "sv_alloc", "sv_wrap", "sv_set", "sv_get", "sv_reset",
            "circuit_create", "apply_circuit", "apply_channel", "obs_create", "expect", "grad",
-           "grad_profile", "grad_batch", "batch_create", "BatchHandle", "expect_noalloc", "measure",
+           "grad_profile", "grad_batch", "batch_create", "BatchHandle", "expect_noalloc", "measure", "sample",
            "VQEEnergy",
            "load"]
 
@@ -242,6 +242,16 @@ def measure(sv: StateVector, qubit: int, u: float) -> Tuple[int, float]:
     p = ctypes.c_double()
     _abi.check(_abi.lib().measure(sv.handle, int(qubit), float(u), ctypes.byref(k), ctypes.byref(p)))
     return k.value, p.value
+
+
+def sample(sv: StateVector, u) -> np.ndarray:
+    """Basis indices of len(u) shots (every qubit measured on fresh copies of the state,
+    which is left unchanged); u are the caller's uniform draws in [0, 1)."""
+    uu = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1))
+    out = np.zeros(max(1, uu.size), dtype=np.int64)
+    _abi.check(_abi.lib().sample(sv.handle, uu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), uu.size,
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return out[:uu.size]
 
 
 def expect_noalloc(psi, n_qubits: int, terms, out, stream=None) -> None:

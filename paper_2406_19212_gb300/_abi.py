@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
         "obs_free": [vp],
         "expect": [vp, vp, dp],
         "measure": [vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int), dp],
+        "sample": [vp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
         "grad": [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp],
         "grad_profile": [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp,
                          ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
@@ -120,7 +121,7 @@ def exported_symbols() -> List[str]:
             "sv_set", "sv_get", "sv_info", "circuit_create", "circuit_free", "circuit_set_tiling",
             "circuit_plan_info", "circuit_plan_stats", "circuit_autotune", "apply_circuit", "apply_channel", "obs_create", "obs_free",
             "expect", "grad", "grad_profile", "grad_batch", "batch_create", "batch_free",
-            "batch_grad", "expect_noalloc", "measure"]
+            "batch_grad", "expect_noalloc", "measure", "sample"]
 
 
 # ------------------------------------------------------------------ marshalling

@@ -755,6 +755,36 @@ extern "C" gbvqc_status measure(sv_handle sv, int qubit, double u, int *outcome,
     return GBVQC_OK;
 }
 
+extern "C" gbvqc_status sample(sv_handle sv, const double *u, int n_shots, int64_t *out)
+{
+    if (!sv || (n_shots > 0 && (!u || !out)) || n_shots < 0) return fail(GBVQC_ERR_ARG, "bad arguments");
+    for (int i = 0; i < n_shots; i++)
+        if (!(u[i] >= 0.0 && u[i] < 1.0)) return fail(GBVQC_ERR_ARG, "u[%d] = %g outside [0, 1)", i, u[i]);
+    if (n_shots == 0) return GBVQC_OK;
+    const int n = sv->n_log;  // the weights live on the 2^n diagonal (density) or amplitudes
+    const int cbits = std::min(n, std::max(5, n - 16));
+    const size_t m = size_t(1) << (n - cbits);
+    double *d_buf = nullptr;
+    ST_TRY(dev_alloc(&d_buf, 2 * m + (size_t)n_shots));
+    int64_t *d_out = nullptr;
+    gbvqc_status st = dev_alloc(&d_out, (size_t)n_shots);
+    cudaError_t e = cudaSuccess;
+    if (st == GBVQC_OK) {
+        e = cudaMemcpyAsync(d_buf + 2 * m, u, sizeof(double) * n_shots, cudaMemcpyHostToDevice, sv->stream);
+        if (e == cudaSuccess)
+            e = launch_sample(sv->dtype, sv->data, n, sv->density, cbits, d_buf, d_buf + m, d_buf + 2 * m, n_shots,
+                              d_out, sv->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out, d_out, sizeof(int64_t) * n_shots, cudaMemcpyDeviceToHost, sv->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(sv->stream);
+    }
+    cudaFree(d_buf);
+    cudaFree(d_out);
+    if (st != GBVQC_OK) return st;
+    CUDA_TRY(e);
+    return GBVQC_OK;
+}
+
 extern "C" gbvqc_status expect(sv_handle sv, obs_handle h, double *out_energy)
 {
     if (!sv || !h || !out_energy) return fail(GBVQC_ERR_ARG, "NULL argument");

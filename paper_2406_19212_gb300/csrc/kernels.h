@@ -89,6 +89,10 @@ cudaError_t launch_measure_sums(int dtype, const void *st, int n, int density, i
                                 int max_blocks, double *out, cudaStream_t s);
 cudaError_t launch_collapse(int dtype, void *st, int n, int density, int q, int k, double scale,
                             cudaStream_t s);
+// Sampling: chunk sums (2^(n - cbits) doubles), their inclusive prefix, then out[s] = the
+// least index a with u[s] * total < w_0 + ... + w_a (device buffers; 5 <= cbits <= n).
+cudaError_t launch_sample(int dtype, const void *st, int n, int density, int cbits, double *chunk_sum,
+                          double *incl, const double *u, int n_shots, int64_t *out, cudaStream_t s);
 cudaError_t launch_density_seed(int dtype, void *psi, int n, DensMap map, ObsDev obs,
                                 cudaStream_t s);
 

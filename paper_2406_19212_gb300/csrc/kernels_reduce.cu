@@ -444,4 +444,116 @@ cudaError_t launch_collapse(int dtype, void *st, int n, int density, int q, int 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ sampling
+
+template <typename R>
+__device__ __forceinline__ double sample_weight(const typename CTr<R>::T *st, int64_t dim, int density, int64_t a)
+{
+    if (density) return (double)st[a + dim * a].x;
+    const double x = (double)st[a].x, y = (double)st[a].y;
+    return x * x + y * y;
+}
+
+// chunk_sum[m] = sum of the weights of indices [m C, (m+1) C), C = 2^cbits, in FP64 (a
+// fixed tree per block).
+template <typename R>
+__global__ void __launch_bounds__(256) k_chunk_sums(const typename CTr<R>::T *__restrict__ st, int n, int density,
+                                                    int cbits, double *chunk_sum)
+{
+    __shared__ double sh[256];
+    const int64_t dim = int64_t(1) << n, a0 = (int64_t)blockIdx.x << cbits, C = int64_t(1) << cbits;
+    double acc = 0.0;
+    for (int64_t a = a0 + threadIdx.x; a < a0 + C; a += blockDim.x) acc += sample_weight<R>(st, dim, density, a);
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) chunk_sum[blockIdx.x] = sh[0];
+}
+
+// incl[m] = chunk_sum[0] + ... + chunk_sum[m] (one block: per-thread runs, then a scan of
+// the run totals in thread order).
+__global__ void __launch_bounds__(1024) k_chunk_prefix(const double *__restrict__ chunk_sum, int m_chunks, double *incl)
+{
+    __shared__ double run[1024];
+    const int per = (m_chunks + blockDim.x - 1) / blockDim.x;
+    const int b = threadIdx.x * per, e = min(m_chunks, b + per);
+    double t = 0.0;
+    for (int m = b; m < e; m++) t += chunk_sum[m];
+    run[threadIdx.x] = t;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = 1; i < (int)blockDim.x; i++) run[i] += run[i - 1];
+    __syncthreads();
+    double acc = threadIdx.x ? run[threadIdx.x - 1] : 0.0;
+    for (int m = b; m < e; m++) {
+        acc += chunk_sum[m];
+        incl[m] = acc;
+    }
+}
+
+// One warp per shot: the chunk holding u*total by binary search of incl, then the index
+// inside it by a warp scan of the chunk's weights in steps of 32.
+template <typename R>
+__global__ void __launch_bounds__(256) k_sample_shots(const typename CTr<R>::T *__restrict__ st, int n, int density,
+                                                      int cbits, const double *__restrict__ incl, int m_chunks,
+                                                      const double *__restrict__ u, int n_shots, int64_t *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int shot = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (shot >= n_shots) return;  // whole warps leave together
+    const int64_t dim = int64_t(1) << n, C = int64_t(1) << cbits;
+    const double total = incl[m_chunks - 1];
+    const double target = u[shot] * total;
+    int lo = 0, hi = m_chunks - 1;  // least chunk with target < incl[m]
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (target < incl[mid]) hi = mid;
+        else lo = mid + 1;
+    }
+    double run = lo ? incl[lo - 1] : 0.0;
+    const int64_t a0 = (int64_t)lo << cbits;
+    int64_t found = a0 + C - 1, last_nz = -1;
+    for (int64_t base = a0; base < a0 + C; base += 32) {
+        const double w = base + lane < a0 + C ? sample_weight<R>(st, dim, density, base + lane) : 0.0;
+        double x = w;  // inclusive warp scan
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const unsigned hit = __ballot_sync(0xffffffffu, target < run + x && w > 0.0);
+        const unsigned nzm = __ballot_sync(0xffffffffu, w > 0.0);
+        if (nzm) last_nz = base + 31 - __clz(nzm);
+        if (hit) {
+            found = base + __ffs(hit) - 1;
+            last_nz = -2;
+            break;
+        }
+        run += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (last_nz >= 0) found = last_nz;  // rounding pushed u*total past the chunk's end
+    if (lane == 0) out[shot] = found;
+}
+
+cudaError_t launch_sample(int dtype, const void *st, int n, int density, int cbits, double *chunk_sum, double *incl,
+                          const double *u, int n_shots, int64_t *out, cudaStream_t s)
+{
+    const int m = 1 << (n - cbits);
+    if (dtype == 0) k_chunk_sums<float><<<m, 256, 0, s>>>((const float2 *)st, n, density, cbits, chunk_sum);
+    else k_chunk_sums<double><<<m, 256, 0, s>>>((const double2 *)st, n, density, cbits, chunk_sum);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_chunk_prefix<<<1, 1024, 0, s>>>(chunk_sum, m, incl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int blocks = (int)((32 * (int64_t)n_shots + 255) / 256);
+    if (dtype == 0)
+        k_sample_shots<float><<<blocks, 256, 0, s>>>((const float2 *)st, n, density, cbits, incl, m, u, n_shots, out);
+    else
+        k_sample_shots<double><<<blocks, 256, 0, s>>>((const double2 *)st, n, density, cbits, incl, m, u, n_shots, out);
+    return cudaGetLastError();
+}
+
 }  // namespace gbvqc

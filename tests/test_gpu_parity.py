@@ -475,3 +475,48 @@ def test_two_qubit_channels_rejected_by_batches():
     with pytest.raises(gb.GbvqcError) as ex:
         gb.batch_create([c], [o], gb.C64)
     assert ex.value.status == 1
+
+
+# ----------------------------------------------------------------- sampling
+
+def _check_samples(got, weights, u):
+    """Equal to the oracle's sequential-CDF answer, except that within rounding of a CDF
+    boundary either neighbouring index is valid."""
+    cdf = np.cumsum(weights)
+    total = cdf[-1]
+    for g, uu in zip(got, u):
+        t = uu * total
+        lo = cdf[g - 1] if g > 0 else 0.0
+        assert weights[g] > 0
+        assert lo - 1e-12 * total <= t <= cdf[g] + 1e-12 * total
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("density", [False, True])
+def test_sample_matches_oracle(dtype, density):
+    n = 5 if density else 13
+    if density:
+        state = I.random_density(n, 12)
+    else:
+        state = I.random_state(n, 12)
+    sv = gb.sv_alloc(n, dtype, density)
+    gb.sv_set(sv, state)
+    stored = gb.sv_get(sv).astype(np.complex128)  # the amplitudes the GPU sampled from
+    u = np.random.default_rng(3).uniform(0, 1, 3000)
+    got = gb.sample(sv, u)
+    ref = O.sample(stored, n, u, density=density)
+    d = 1 << n
+    w = (stored[np.arange(d) * (d + 1)].real if density else np.abs(stored) ** 2)
+    _check_samples(got, w, u)
+    assert np.mean(got == ref) > 0.999
+    np.testing.assert_array_equal(gb.sv_get(sv), stored.astype(gb.sv_get(sv).dtype))  # unchanged
+
+
+def test_sample_small_register_and_ghz():
+    n = 3  # smaller than one warp's scan step
+    c = I.Circuit(n, [I.Op("H", (0,)), I.Op("CNOT", (0, 1)), I.Op("CNOT", (1, 2))], 0)
+    sv = gb.sv_alloc(n, gb.C128)
+    gb.apply_circuit(sv, gb.circuit_create(c), [], gb.PLAIN)
+    assert gb.sample(sv, [0.0, 0.2, 0.49, 0.51, 0.999]).tolist() == [0, 0, 0, 7, 7]
+    with pytest.raises(gb.GbvqcError):
+        gb.sample(sv, [1.0])
