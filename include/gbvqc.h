@@ -42,7 +42,7 @@ typedef enum {
     GBVQC_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed      */
     GBVQC_ERR_TIMEOUT = 4,      /* a bounded device wait ran out                    */
     GBVQC_ERR_NOT_DENSITY = 5,  /* channel applied to a pure state                  */
-    GBVQC_ERR_UNSUPPORTED = 6   /* valid request this build does not implement      */
+    GBVQC_ERR_UNSUPPORTED = 6   /* valid request the library does not implement     */
 } gbvqc_status;
 
 enum { GBVQC_C64 = 0, GBVQC_C128 = 1 };            /* amplitude dtype                */

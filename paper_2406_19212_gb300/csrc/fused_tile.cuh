@@ -182,47 +182,6 @@ __device__ __forceinline__ int const_bit(int code, int base, int64_t tilebase)
     return (base >> (code - NR)) & 1;
 }
 
-// Bit of a position code for register amplitude j (j compile-time after unrolling).
-template <int NR>
-__device__ __forceinline__ int code_bit(int code, int j, int base, int64_t tilebase)
-{
-    if (code >= 0 && code < NR) return (j >> code) & 1;
-    return const_bit<NR>(code, base, tilebase);
-}
-
-// Diagonal one-qubit gate on a position code.
-template <typename R, int NR>
-__device__ __forceinline__ void dg1(typename CT<R>::T *a, const R *m, int code, int base,
-                                    int64_t tilebase)
-{
-    typedef typename CT<R>::T T;
-    if (code >= 0 && code < NR) {
-        rg1_dispatch<R, NR, SH_DIAG1>(code, a, m);
-        return;
-    }
-    const int bit = const_bit<NR>(code, base, tilebase);
-    const R pr = bit ? m[6] : m[0], pi = bit ? m[7] : m[1];
-#pragma unroll
-    for (int j = 0; j < (1 << NR); j++) cmul_ip<T, R>(pr, pi, a[j]);
-}
-
-// Diagonal two-qubit gate on two position codes (matrix bit 0 = code ca).
-template <typename R, int NR>
-__device__ __forceinline__ void dg2(typename CT<R>::T *a, const R *m, int ca, int cb, int base,
-                                    int64_t tilebase)
-{
-    typedef typename CT<R>::T T;
-    const R p0r = m[0], p0i = m[1], p1r = m[10], p1i = m[11];
-    const R p2r = m[20], p2i = m[21], p3r = m[30], p3i = m[31];
-#pragma unroll
-    for (int j = 0; j < (1 << NR); j++) {
-        const int idx = code_bit<NR>(ca, j, base, tilebase) | (code_bit<NR>(cb, j, base, tilebase) << 1);
-        const R pr = idx == 0 ? p0r : idx == 1 ? p1r : idx == 2 ? p2r : p3r;
-        const R pi = idx == 0 ? p0i : idx == 1 ? p1i : idx == 2 ? p2i : p3i;
-        cmul_ip<T, R>(pr, pi, a[j]);
-    }
-}
-
 // Non-diagonal gate on register slots.  Kernels compiled without TWOQ never see
 // two-qubit gates (the planner flags every pass that holds one), which keeps their
 // code paths out of the common one-qubit loop.
