@@ -1976,8 +1976,28 @@ extern "C" gbvqc_status circuit_autotune(circuit_handle c, const double *theta, 
     CUDA_TRY(cudaEventCreate(&e1));
     const int nr_max = std::max(fused_nr(dtype, false), fused_nr(dtype, true));
     const int t_hi = std::min(c->n_phys, max_tile(dtype));
-    double best = 1e30;
-    int bt = 0, bl = 0;
+    // median over `batches` timed batches of `per` gradient evaluations
+    auto time_grad = [&](int batches, int per, double *out_ms) -> gbvqc_status {
+        std::vector<double> runs;
+        for (int r = 0; r < batches; r++) {
+            cudaEventRecord(e0, s);
+            for (int k = 0; k < per; k++)
+                ST_TRY(grad(c, theta, n_theta, h, dtype, GBVQC_MODE_FUSED, GBVQC_PTR_HOST, s, &e, g.data()));
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            runs.push_back(ms / per);
+        }
+        std::sort(runs.begin(), runs.end());
+        *out_ms = runs[runs.size() / 2];
+        return GBVQC_OK;
+    };
+    struct Cand {
+        double ms;
+        int t, lo;
+    };
+    std::vector<Cand> cands;
     gbvqc_status st = GBVQC_OK;
     for (int t = std::max(8, nr_max + 1); t <= t_hi && st == GBVQC_OK; t++) {
         for (int lo = 2; lo <= 4 && st == GBVQC_OK; lo++) {
@@ -1988,25 +2008,23 @@ extern "C" gbvqc_status circuit_autotune(circuit_handle c, const double *theta, 
                 if (st == GBVQC_ERR_UNSUPPORTED) st = GBVQC_OK;  // e.g. a plan exceeding shared memory
                 continue;
             }
-            // a few timed replays, median of three batches of two
-            double ms_runs[3];
-            for (int r = 0; r < 3 && st == GBVQC_OK; r++) {
-                cudaEventRecord(e0, s);
-                for (int k = 0; k < 2 && st == GBVQC_OK; k++)
-                    st = grad(c, theta, n_theta, h, dtype, GBVQC_MODE_FUSED, GBVQC_PTR_HOST, s, &e, g.data());
-                cudaEventRecord(e1, s);
-                cudaEventSynchronize(e1);
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ms_runs[r] = ms / 2;
-            }
-            if (st != GBVQC_OK) break;
-            std::sort(ms_runs, ms_runs + 3);
-            if (ms_runs[1] < best) {
-                best = ms_runs[1];
-                bt = t;
-                bl = lo;
-            }
+            double ms = 0;
+            st = time_grad(3, 2, &ms);  // coarse: median of three batches of two
+            if (st == GBVQC_OK) cands.push_back(Cand{ms, t, lo});
+        }
+    }
+    // refine the three fastest with longer measurements (close candidates differ by ~1%)
+    std::sort(cands.begin(), cands.end(), [](const Cand &x, const Cand &y) { return x.ms < y.ms; });
+    double best = 1e30;
+    int bt = 0, bl = 0;
+    for (size_t i = 0; i < cands.size() && i < 3 && st == GBVQC_OK; i++) {
+        st = circuit_set_tiling(c, cands[i].t, cands[i].lo);
+        double ms = 0;
+        if (st == GBVQC_OK) st = time_grad(7, 6, &ms);
+        if (st == GBVQC_OK && ms < best) {
+            best = ms;
+            bt = cands[i].t;
+            bl = cands[i].lo;
         }
     }
     cudaEventDestroy(e0);

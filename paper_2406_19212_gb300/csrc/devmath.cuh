@@ -47,16 +47,28 @@ template <typename R, int SH>
 __device__ __forceinline__ void apply2(const R *m, typename CT<R>::T &a, typename CT<R>::T &b)
 {
     if (SH == SH_DENSE1) {
-        // contributions of the old a to a' and b'
-        const R a1x = fma(m[0], a.x, -m[1] * a.y), a1y = fma(m[0], a.y, m[1] * a.x);
-        const R b1x = fma(m[4], a.x, -m[5] * a.y), b1y = fma(m[4], a.y, m[5] * a.x);
-        // a' = a1 + m01 b
-        a.x = fma(m[2], b.x, fma(-m[3], b.y, a1x));
-        a.y = fma(m[2], b.y, fma(m[3], b.x, a1y));
-        // b' = b1 + m11 b
-        const R bx = fma(-m[7], b.y, b1x), by = fma(m[7], b.x, b1y);
-        b.x = fma(m[6], b.x, bx);
-        b.y = fma(m[6], b.y, by);
+        if constexpr (sizeof(R) == 4) {
+            // packed FP32x2: z x = (zr, zr) * x + (-zi, zi) * swap(x) for complex z, so each
+            // output takes one packed multiply and three packed fmas
+            const float2 sa = make_float2(a.y, a.x), sb = make_float2(b.y, b.x);
+            const float2 na = __ffma2_rn(make_float2(m[0], m[0]), a,
+                                         __fmul2_rn(make_float2(-m[1], m[1]), sa));
+            const float2 nb = __ffma2_rn(make_float2(m[4], m[4]), a,
+                                         __fmul2_rn(make_float2(-m[5], m[5]), sa));
+            a = __ffma2_rn(make_float2(-m[3], m[3]), sb, __ffma2_rn(make_float2(m[2], m[2]), b, na));
+            b = __ffma2_rn(make_float2(-m[7], m[7]), sb, __ffma2_rn(make_float2(m[6], m[6]), b, nb));
+        } else {
+            // contributions of the old a to a' and b'
+            const R a1x = fma(m[0], a.x, -m[1] * a.y), a1y = fma(m[0], a.y, m[1] * a.x);
+            const R b1x = fma(m[4], a.x, -m[5] * a.y), b1y = fma(m[4], a.y, m[5] * a.x);
+            // a' = a1 + m01 b
+            a.x = fma(m[2], b.x, fma(-m[3], b.y, a1x));
+            a.y = fma(m[2], b.y, fma(m[3], b.x, a1y));
+            // b' = b1 + m11 b
+            const R bx = fma(-m[7], b.y, b1x), by = fma(m[7], b.x, b1y);
+            b.x = fma(m[6], b.x, bx);
+            b.y = fma(m[6], b.y, by);
+        }
     } else if (SH == SH_DIAG1) {
         cmul_ip(m[0], m[1], a);
         cmul_ip(m[6], m[7], b);
