@@ -593,6 +593,28 @@ static int superop(const orc_op *op, const double *theta, int n, cplx *S, int *p
     return 2 * k;
 }
 
+/* Derivative of the superoperator U (x) conj(U) of a variational FSIM with respect to
+ * its parameter comp: dS = dU (x) conj(U) + U (x) conj(dU), 16 x 16 on (ket q0, ket q1,
+ * bra q0, bra q1). */
+static int superop_derivative_fsim(const orc_op *op, const double *theta, int n, int comp, cplx *dS, int *pq)
+{
+    cplx U[16], dU[16];
+    int a, b, c, d;
+    gate_matrix(op, theta, U);
+    fsim_derivative(op, theta, comp, dU);
+    for (a = 0; a < 4; a++)
+        for (b = 0; b < 4; b++)
+            for (c = 0; c < 4; c++)
+                for (d = 0; d < 4; d++)
+                    dS[(a + 4 * b) * 16 + (c + 4 * d)] =
+                        dU[a * 4 + c] * conj(U[b * 4 + d]) + U[a * 4 + c] * conj(dU[b * 4 + d]);
+    pq[0] = op->q[0];
+    pq[1] = op->q[1];
+    pq[2] = op->q[0] + n;
+    pq[3] = op->q[1] + n;
+    return 4;
+}
+
 /* Derivative of U (x) conj(U) for a variational single-qubit rotation:
  * dS = dU (x) conj(U) + U (x) conj(dU). */
 static int superop_derivative(const orc_op *op, const double *theta, int n, cplx *dS, int *pq)
@@ -651,7 +673,16 @@ int orc_noisy_adjoint_grad(int n, const orc_op *ops, int n_ops, const double *th
         for (r = 0; r < D; r++)
             for (c = 0; c < D; c++) Sdag[r * D + c] = conj(S[c * D + r]);
         apply_k(phi, N, k2, pq, Sinv);
-        if (ops[j].param >= 0) {
+        if (ops[j].param >= 0 && ops[j].kind == O_FSIM) {  /* one term per variational parameter */
+            int b2, r = 0, dq[4];
+            for (b2 = 0; b2 < 5; b2++) {
+                if (!((ops[j].pmask >> b2) & 1)) continue;
+                superop_derivative_fsim(&ops[j], theta, n, b2, S, dq);  /* S reused as scratch */
+                memcpy(tmp, phi, sizeof(cplx) * (size_t)len);
+                apply_k(tmp, N, 4, dq, S);
+                grad[ops[j].param + r++] += creal(inner(psi, tmp, len));
+            }
+        } else if (ops[j].param >= 0) {
             cplx dS[16];
             int dq[2];
             if (superop_derivative(&ops[j], theta, n, dS, dq) < 0) { rc = -4; goto done; }

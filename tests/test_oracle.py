@@ -492,3 +492,32 @@ def test_sample_basis_state_ghz_and_density():
     assert O.sample(ghz, n, [0.2, 0.49, 0.51, 0.97]).tolist() == [0, 0, 31, 31]
     rho = np.outer(ghz, ghz.conj()).T.reshape(-1)
     assert O.sample(rho, n, [0.2, 0.49, 0.51, 0.97], density=True).tolist() == [0, 0, 31, 31]
+
+
+def test_noisy_fsim_gradient_matches_shift_rules():
+    """Variational FSIM inside a noisy density circuit: the noisy Algorithm 2 with the
+    16x16 superoperator derivative vs the exact shift rules (theta: four-term, phi:
+    two-term) and FP64 differences (Delta's)."""
+    n = 3
+    ops = [op("RX", (0,), param=0), op("FSIM", (0, 1), param=1, fixed=(1.0, 0.6, 0.2, -0.3, 0.4), pmask=0b11111),
+           op("DEPOL", (1,), fixed=(0.05,)), op("AMPDAMP", (0,), fixed=(0.1,)), op("RY", (2,), param=6),
+           op("FSIM", (1, 2), param=7, fixed=(0.5, 1.1), pmask=0b00011)]
+    circ = I.Circuit(n, ops, 9, True)
+    theta = np.array([0.4, 1.0, 0.6, 0.2, -0.3, 0.4, 0.9, 0.5, 1.1])
+    terms = [(0.7, ((0, "Z"), (1, "Z"))), (-0.5, ((2, "X"),)), (0.3, ((1, "Y"), (2, "Y")))]
+    e, g = O.noisy_adjoint_grad(circ, theta, terms)
+    L = lambda th: O.energy(circ, th, terms)
+
+    def shift(j, s):
+        tp, tm = theta.copy(), theta.copy()
+        tp[j] += s
+        tm[j] -= s
+        return L(tp) - L(tm)
+    for j in (1, 7):   # theta of each FSIM
+        assert g[j] == pytest.approx((1 - math.sqrt(2)) / 2 * shift(j, np.pi / 2) + shift(j, np.pi / 4), abs=1e-11)
+    for j in (2, 8):   # phi
+        assert g[j] == pytest.approx(0.5 * shift(j, np.pi / 2), abs=1e-11)
+    for j in (3, 4, 5):
+        assert g[j] == pytest.approx(O.finite_difference_grad(circ, theta, terms, [j], h=1e-5)[0], abs=1e-8)
+    for j in (0, 6):   # the rotations, by the two-term rule
+        assert g[j] == pytest.approx(0.5 * shift(j, np.pi / 2), abs=1e-11)
