@@ -76,7 +76,7 @@ typedef struct gbvqc_op {
                               variational parameter (see param_mask).  Must be -1 for
                               other kinds.                                              */
     int32_t n_kraus;       /* KRAUS only: number of 2x2 operators in data (1..4)        */
-    int32_t param_mask;    /* FSIM with param_index >= 0 (pure-state circuits): bit k set
+    int32_t param_mask;    /* FSIM with param_index >= 0: bit k set
                               = parameter k of (theta, phi, d_plus, d_minus, d_minus_off)
                               is variational (the paper's isparas array, Sec. II.B); the
                               variational ones read theta[param_index], [param_index + 1],
@@ -144,8 +144,7 @@ gbvqc_status sv_info(sv_handle sv, int *n_qubits, int *dtype, int *is_density, v
  * indices).  is_density = 1 allows channels and makes every unitary act as U rho U^dag
  * (Sec. III.D).  Builds and caches the execution plans (per-gate records and the fused
  * tile schedule).  Errors: ERR_ARG (bad kind, qubit, param index, FSIM param_mask outside
- * [1, 31], Kraus count), ERR_NOT_DENSITY (channel with is_density = 0), ERR_UNSUPPORTED
- * (variational FSIM in a density circuit). */
+ * [1, 31], Kraus count), ERR_NOT_DENSITY (channel with is_density = 0). */
 gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qubits, int n_params,
                             int is_density, circuit_handle *out);
 gbvqc_status circuit_free(circuit_handle c);

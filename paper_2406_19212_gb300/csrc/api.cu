@@ -891,15 +891,16 @@ static int add_dyn(gbvqc_circuit *c, int param, int rot, int variant, int domain
 
 static bool is_var_fsim(const gbvqc_op &op) { return op.kind == GBVQC_FSIM && op.param_index >= 0; }
 
-// theta-dependent FSIM record (variant FWD / INV / DER / GEN; comp = FSIM parameter)
-static int add_dyn_fsim(gbvqc_circuit *c, const gbvqc_op &op, int variant, int comp)
+// theta-dependent FSIM record (variant FWD / INV / DER / GEN; comp = FSIM parameter;
+// domain BRA: the complex conjugate, for the bra qubits of a density matrix)
+static int add_dyn_fsim(gbvqc_circuit *c, const gbvqc_op &op, int variant, int comp, int domain = DOM_KET)
 {
     DynRec d{};
     d.rec = (int)c->recs.size();
     d.param = op.param_index;
     d.rot = ROT_FSIM;
     d.variant = variant;
-    d.domain = DOM_KET;
+    d.domain = domain;
     d.comp = comp;
     d.mask = op.param_mask;
     for (int k = 0; k < 5; k++) d.fixed[k] = op.params[k];
@@ -927,15 +928,15 @@ static OpRecs op_records(gbvqc_circuit *c, const gbvqc_op &op, int domain)
 {
     OpRecs o{};
     o.d = -1;
-    if (is_var_fsim(op)) {  // pure states only (checked by circuit_create)
-        o.f = add_dyn_fsim(c, op, VAR_FWD, 0);
-        o.i = add_dyn_fsim(c, op, VAR_INV, 0);
-        o.shape = SH_BLOCK2;  // every FSIM has the block structure
+    if (is_var_fsim(op)) {  // ket or bra side (a density matrix applies U and conj(U))
+        o.f = add_dyn_fsim(c, op, VAR_FWD, 0, domain);
+        o.i = add_dyn_fsim(c, op, VAR_INV, 0, domain);
+        o.shape = SH_BLOCK2;  // every FSIM (and its conjugate) has the block structure
         o.dshape = SH_DENSE2;
         for (int k = 0, j = 0; k < 5; k++)
             if ((op.param_mask >> k) & 1)
-                o.comps.push_back(OpComp{add_dyn_fsim(c, op, VAR_DER, k), add_dyn_fsim(c, op, VAR_GEN, k),
-                                         op.param_index + j++});
+                o.comps.push_back(OpComp{add_dyn_fsim(c, op, VAR_DER, k, domain),
+                                         add_dyn_fsim(c, op, VAR_GEN, k, domain), op.param_index + j++});
         return o;
     }
     if (is_rotation(op.kind) && op.param_index >= 0) {
@@ -1213,6 +1214,21 @@ static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGa
                 g.param = op.param_index;
             }
             out.push_back(g);
+            // variational FSIM: Re <<Psi| (dU/dp) U^-1 |Phi>> on this side (K conjugated on
+            // the bra side) per parameter, read after the side's gate
+            for (const OpComp &cp : r.comps) {
+                PGate pr = g;
+                pr.ftype = FT_PROBE2;
+                pr.diag = false;
+                pr.rec_f = pr.rec_i = pr.rec_a = cp.gen;
+                pr.perm_f = pr.perm_r = 0;
+                pr.gen = GEN_M2;
+                pr.gq = g.q[0];
+                pr.coef = 1.0f;
+                pr.param = cp.param;
+                pr.cz = false;
+                out.push_back(pr);
+            }
         }
     }
     const double ph = std::remainder(phase, 2.0 * M_PI);
@@ -1249,8 +1265,6 @@ extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qub
                 return fail(GBVQC_ERR_ARG, "op %d: FSIM param_mask %d", j, op.param_mask);
             if (op.param_index + __builtin_popcount(op.param_mask) > n_params)
                 return fail(GBVQC_ERR_ARG, "op %d: FSIM parameters beyond n_params", j);
-            if (is_density)
-                return fail(GBVQC_ERR_UNSUPPORTED, "op %d: variational FSIM on a density matrix", j);
         } else if (op.param_index >= 0 && (!is_rotation(op.kind) || op.param_index >= n_params)) {
             return fail(GBVQC_ERR_ARG, "op %d: bad param_index %d", j, op.param_index);
         }
@@ -1337,6 +1351,18 @@ extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qub
                 OpRecs r = op_records(c, op, side == 0 ? DOM_KET : DOM_BRA);
                 int off = side == 0 ? 0 : n_qubits;
                 PlainGate g{r.shape, op.qubits[0] + off, op.qubits[1] + off, r.f, r.i, r.i, 1, 0, 0, -1, -1, 1.0, -1};
+                if (!r.comps.empty()) {  // variational FSIM: Re <<Psi| dU (side) |Phi>> per parameter
+                    g.der_k = 2;
+                    g.dq0 = op.qubits[0] + off;
+                    g.dq1 = op.qubits[1] + off;
+                    g.rec_d = r.comps[0].der;
+                    g.param = r.comps[0].param;
+                    for (size_t e = 1; e < r.comps.size(); e++) {
+                        g.ex_rec[g.n_extra] = r.comps[e].der;
+                        g.ex_param[g.n_extra] = r.comps[e].param;
+                        g.n_extra++;
+                    }
+                }
                 c->plain.push_back(g);
             }
         }

@@ -214,6 +214,8 @@ inline __host__ __device__ void materialize(const DynRec &r, const double *th, M
                 mul_dag4(d, u, m);
             }
         }
+        if (r.domain == DOM_BRA)  // conj(U), and correspondingly conjugated inverse / derivatives
+            for (int i = 1; i < 32; i += 2) m[i] = -m[i];
         for (int i = 0; i < 32; i++) {
             out->d[i] = m[i];
             out->f[i] = (float)m[i];

@@ -520,3 +520,29 @@ def test_sample_small_register_and_ghz():
     assert gb.sample(sv, [0.0, 0.2, 0.49, 0.51, 0.999]).tolist() == [0, 0, 0, 7, 7]
     with pytest.raises(gb.GbvqcError):
         gb.sample(sv, [1.0])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", MODES)
+def test_fsim_parameter_gradients_density(dtype, mode):
+    """Variational FSIM couplers inside a noisy density circuit (the ket gate U and the bra
+    gate conj(U) each contribute Re <<Psi| dS |Phi>>) against the noisy oracle."""
+    n = 4
+    ops = [I.Op("RX", (q,), param=q) for q in range(n)]
+    p = n
+    for (a, b), mask in (((0, 1), 0b11111), ((2, 3), 0b00011), ((1, 2), 0b10101)):
+        vals = (1.0 + 0.1 * a, 0.5, 0.2, -0.1, 0.3)
+        ops.append(I.Op("FSIM", (a, b), param=p, fixed=vals, pmask=mask))
+        p += bin(mask).count("1")
+        ops += [I.Op("DEPOL", (a,), fixed=(0.02,)), I.Op("AMPDAMP", (b,), fixed=(0.03,))]
+    circ = I.Circuit(n, ops, p, density=True)
+    theta = np.random.default_rng(5).uniform(-1, 1, p)
+    obs = I.ising_chain(n, [0.6] * n) + [(0.4, ((1, "Y"), (3, "X")))]
+    c = gb.circuit_create(circ)
+    if mode == gb.FUSED:
+        c.set_tiling(7, 2)
+    o = gb.obs_create(obs, n)
+    e, g = gb.grad(c, theta, o, dtype, mode)
+    e_ref, g_ref = O.noisy_adjoint_grad(circ, theta, obs)
+    check_energy(e, e_ref, dtype)
+    check_grad(g, g_ref, dtype)
