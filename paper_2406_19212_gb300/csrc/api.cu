@@ -97,6 +97,7 @@ static double shape_flops(int sh)
     case SH_BLOCK2: return 10;  // a dense 2x2 on half, one phase on each remaining quarter
     case SH_IMAG1: return 6;    // two real products and a sum per output
     case SH_DENSE4: return 126; // sixteen complex products and fifteen sums per output
+    case SH_PAR2: return 14;    // a dense 2x2 on every amplitude pair
     case SH_REAL1: return 6;
     default: return 6;          // one complex product
     }
@@ -109,6 +110,7 @@ static double ftype_flops(int ft)
     case FT_DENSE2: return 30;
     case FT_CTRL2: return 7;
     case FT_BLOCK2: return 10;
+    case FT_PAR2: return 14;
     case FT_PROBE2: return 34;
     default: return 6;  // real / imaginary / anti-diagonal / diagonal
     }
@@ -348,7 +350,17 @@ static int classify(const Mat &M)
             const bool inside = (r == c && (r == 0 || r == 3)) || ((r == 1 || r == 2) && (c == 1 || c == 2));
             if (!inside && nz(M[r * 4 + c])) block = false;
         }
-    return block ? SH_BLOCK2 : SH_DENSE2;
+    if (block) return SH_BLOCK2;
+    // parity-preserving: entry (r, c) is zero unless r ^ c is 0 or 3, i.e. |00> couples
+    // only to |11> and |01> only to |10>
+    bool par = true, real = true;
+    for (int r = 0; r < 4; r++)
+        for (int c = 0; c < 4; c++) {
+            if (((r ^ c) == 1 || (r ^ c) == 2) && nz(M[r * 4 + c])) par = false;
+            real = real && M[r * 4 + c].imag() == 0.0;
+        }
+    if (par) return real ? SH_RPAR2 : SH_PAR2;
+    return SH_DENSE2;
 }
 
 static int perm_bits(const Mat &M)
@@ -364,7 +376,9 @@ static int perm_bits(const Mat &M)
 static int join_shape(int a, int b)
 {
     if (a == b) return a;
-    return shape_qubits(a) == 1 ? SH_DENSE1 : SH_DENSE2;
+    if (shape_qubits(a) == 1) return SH_DENSE1;
+    auto par = [](int s) { return s == SH_DIAG2 || s == SH_BLOCK2 || s == SH_PAR2 || s == SH_RPAR2; };
+    return par(a) && par(b) ? SH_PAR2 : SH_DENSE2;
 }
 
 static int ftype_of(int sh)
@@ -379,6 +393,8 @@ static int ftype_of(int sh)
     case SH_PERM2: return FT_PERM2;
     case SH_BLOCK2: return FT_BLOCK2;
     case SH_IMAG1: return FT_IMAG1;
+    case SH_PAR2: return FT_PAR2;
+    case SH_RPAR2: return FT_RPAR2;
     default: return FT_CTRL2;
     }
 }
@@ -1108,6 +1124,7 @@ static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGa
             const bool fixed = !(is_rotation(op.kind) && op.param_index >= 0) && !r.Mf.empty() &&
                                op.kind != GBVQC_CZ;
             const bool scalable = r.shape == SH_DENSE1 || r.shape == SH_DENSE2 || r.shape == SH_BLOCK2 ||
+                                  r.shape == SH_PAR2 ||
                                   r.shape == SH_DIAG1 || r.shape == SH_DIAG2 || r.shape == SH_PERM2 ||
                                   r.shape == SH_ANTI1;
             if (fold < 0 && fixed && scalable) fold = (int)out.size(), fold_f = r.Mf, fold_i = r.Mi;

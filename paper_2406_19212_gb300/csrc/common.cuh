@@ -28,18 +28,23 @@ enum Shape : int32_t {
     SH_CTRL2 = 7,   // identity unless the first qubit is 1, then a 2x2 on the second
     SH_BLOCK2 = 8,  // phase on |00>, a 2x2 on {|01>, |10>}, phase on |11> (FSIM, iSWAP-like)
     SH_IMAG1 = 9,   // real diagonal, imaginary off-diagonal 2x2 (Rx; sqrt(X) up to a phase)
-    SH_DENSE4 = 10  // general 16x16 (two-qubit channel superoperator), 16 records of one row
+    SH_DENSE4 = 10, // general 16x16 (two-qubit channel superoperator), 16 records of one row
+    SH_PAR2 = 11,   // parity-preserving 4x4: a 2x2 on {|00>, |11>} and a 2x2 on {|01>, |10>}
+                    // (superoperator of a phase-covariant one-qubit channel on (ket, bra))
+    SH_RPAR2 = 12   // SH_PAR2 with real entries (depolarising, amplitude and phase damping)
 };
 
 inline __host__ __device__ bool shape_is_diag(int sh) { return sh == SH_DIAG1 || sh == SH_DIAG2; }
 inline __host__ __device__ int shape_qubits(int sh)
 {
-    return sh == SH_DENSE4 ? 4 : sh >= SH_DENSE2 && sh <= SH_BLOCK2 ? 2 : 1;
+    return sh == SH_DENSE4 ? 4 : (sh >= SH_DENSE2 && sh <= SH_BLOCK2) || sh == SH_PAR2 || sh == SH_RPAR2 ? 2 : 1;
 }
 
 // Row-major re/im offsets of the 2x2 block of an SH_BLOCK2 matrix (rows/columns 1 and 2)
 // and of its two diagonal phases (rows 0 and 3).
 #define GBVQC_BLOCK2_U(m) {(m)[10], (m)[11], (m)[12], (m)[13], (m)[18], (m)[19], (m)[20], (m)[21]}
+// ... and of the 2x2 on rows/columns 0 and 3 (the other block of an SH_PAR2 matrix).
+#define GBVQC_OUTER_U(m) {(m)[0], (m)[1], (m)[6], (m)[7], (m)[24], (m)[25], (m)[30], (m)[31]}
 
 enum Rot : int32_t { ROT_X = 0, ROT_Y = 1, ROT_Z = 2, ROT_FSIM = 3 };
 // FWD: U; INV: U^-1 (= U^dag); DER: dU/dp; GEN: (dU/dp) U^dag, the derivative read from
@@ -263,8 +268,10 @@ enum FType : int32_t {
     FT_IMAG1 = 11,   // SH_IMAG1 on one register slot
     FT_PROBE2 = 12,  // reverse only: gradient read 2 Re <Psi| K |Phi> with the 4x4 K on two
                      // register slots; the states are not changed
-    FT_DENSE4 = 13   // a two-qubit channel's superoperator: never in a tile pass (the planner
+    FT_DENSE4 = 13,  // a two-qubit channel's superoperator: never in a tile pass (the planner
                      // makes it a pass of its own, run by the per-gate kernel)
+    FT_PAR2 = 14,    // SH_PAR2 on two register slots
+    FT_RPAR2 = 15    // SH_RPAR2 on two register slots
 };
 // Generator of a variational gate for the fused reverse sweep: the gradient term is
 // coef * Im <Psi| P |Phi> with both states taken right after the gate.

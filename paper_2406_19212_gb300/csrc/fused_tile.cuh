@@ -91,6 +91,12 @@ __device__ __forceinline__ void rg2(typename CT<R>::T *a, const R *m, int perm)
             cmul_ip<T, R>(m[30], m[31], a[i3]);
             continue;
         }
+        if (SH == SH_PAR2 || SH == SH_RPAR2) {
+            R o[8] = GBVQC_OUTER_U(m), u[8] = GBVQC_BLOCK2_U(m);
+            apply2<R, SH == SH_PAR2 ? SH_DENSE1 : SH_REAL1>(o, a[j], a[i3]);
+            apply2<R, SH == SH_PAR2 ? SH_DENSE1 : SH_REAL1>(u, a[i1], a[i2]);
+            continue;
+        }
         T v[4] = {a[j], a[i1], a[i2], a[i3]}, w[4];
         if (SH == SH_DENSE2) {
 #pragma unroll
@@ -200,6 +206,8 @@ __device__ __forceinline__ void apply_fgate(int type, int ga, int gb, int perm, 
             case FT_DENSE2: rg2_dispatch<R, NR, SH_DENSE2>(ga, gb, a, m, 0); break;
             case FT_PERM2: rg2_dispatch<R, NR, SH_PERM2>(ga, gb, a, m, perm); break;
             case FT_BLOCK2: rg2_dispatch<R, NR, SH_BLOCK2>(ga, gb, a, m, 0); break;
+            case FT_RPAR2: rg2_dispatch<R, NR, SH_RPAR2>(ga, gb, a, m, 0); break;
+            case FT_PAR2: rg2_dispatch<R, NR, SH_PAR2>(ga, gb, a, m, 0); break;
             default: rg2_dispatch<R, NR, SH_CTRL2>(ga, gb, a, m, 0); break;
             }
         }

@@ -112,6 +112,18 @@ __global__ void __launch_bounds__(256) k_gate2(typename CT<R>::T *__restrict__ p
             psi[i3] = d;
             continue;
         }
+        if (SH == SH_PAR2 || SH == SH_RPAR2) {  // 2x2 on |00>, |11>; 2x2 on |01>, |10>
+            const int64_t i1 = base | b0, i2 = base | b1, i3 = base | b0 | b1;
+            T a = psi[base], d = psi[i3], b = psi[i1], c = psi[i2];
+            R o[8] = GBVQC_OUTER_U(m), u[8] = GBVQC_BLOCK2_U(m);
+            apply2<R, SH == SH_PAR2 ? SH_DENSE1 : SH_REAL1>(o, a, d);
+            apply2<R, SH == SH_PAR2 ? SH_DENSE1 : SH_REAL1>(u, b, c);
+            psi[base] = a;
+            psi[i1] = b;
+            psi[i2] = c;
+            psi[i3] = d;
+            continue;
+        }
         int64_t idx[4] = {base, base | b0, base | b1, base | b0 | b1};
         T v[4], w[4];
 #pragma unroll
@@ -167,6 +179,8 @@ static cudaError_t gate_dispatch(void *psi_, int n, int shape, int q0, int q1, c
         case SH_DIAG2: k_gate2<R, SH_DIAG2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
         case SH_PERM2: k_gate2<R, SH_PERM2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
         case SH_BLOCK2: k_gate2<R, SH_BLOCK2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
+        case SH_PAR2: k_gate2<R, SH_PAR2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
+        case SH_RPAR2: k_gate2<R, SH_RPAR2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
         default: k_gate2<R, SH_CTRL2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
         }
     }

@@ -44,7 +44,8 @@ double ftype_flops(int ft)
     case FT_DENSE1: return 14;
     case FT_DENSE2: return 30;
     case FT_CTRL2: return 7;
-    case FT_BLOCK2: return 10;   // FT_REAL1 / FT_IMAG1 / FT_ANTI1 / FT_DIAG*: 6
+    case FT_BLOCK2: return 10;   // FT_REAL1 / FT_IMAG1 / FT_ANTI1 / FT_DIAG* / FT_RPAR2: 6
+    case FT_PAR2: return 14;     // a dense 2x2 on every amplitude pair
     case FT_PROBE2: return 34;   // K Phi (dense 4x4: 30) and Re conj(Psi) . K Phi (4)
     default: return 6;
     }

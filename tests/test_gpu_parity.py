@@ -546,3 +546,49 @@ def test_fsim_parameter_gradients_density(dtype, mode):
     e_ref, g_ref = O.noisy_adjoint_grad(circ, theta, obs)
     check_energy(e, e_ref, dtype)
     check_grad(g, g_ref, dtype)
+
+
+def _phase_covariant_kraus(p, angles):
+    """Kraus operators that are each diagonal or anti-diagonal: the superoperator couples
+    |00> only with |11> and |01> only with |10> (Eq. channel; complex entries)."""
+    a, b, c = angles
+    k0 = np.sqrt(1 - p) * np.diag([1.0, np.exp(1j * a)])
+    k1 = np.sqrt(p) * np.array([[0, np.exp(1j * b)], [np.exp(1j * c), 0]])
+    return [k0, k1]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", MODES)
+def test_parity_preserving_channels(dtype, mode):
+    """Channels whose superoperators keep (ket xor bra) of a qubit: the real ones
+    (depolarising, amplitude and phase damping, a bit flip) and complex ones (phased
+    Kraus operators), inside a variational density circuit, state and gradient."""
+    n = 4
+    rng = np.random.default_rng(11)
+    ops, p = [], 0
+    for layer in range(2):
+        for q in range(n):
+            ops.append(I.Op("RY", (q,), param=p)); p += 1
+            ops.append(I.Op("RZ", (q,), param=p)); p += 1
+        for q in range(layer % 2, n - 1, 2):
+            ops.append(I.Op("CNOT", (q, q + 1)))
+        ops += [I.Op("DEPOL", (0,), fixed=(0.05,)), I.Op("AMPDAMP", (1,), fixed=(0.1,)),
+                I.Op("PHASEDAMP", (2,), fixed=(0.2,)),
+                I.Op("KRAUS", (3,), data=_phase_covariant_kraus(0.1, rng.uniform(-3, 3, 3))),
+                I.Op("KRAUS", (layer,), data=_phase_covariant_kraus(0.05, (0.0, 0.0, 0.0))),
+                I.Op("KRAUS", (2,), data=[np.sqrt(0.9) * np.eye(2), np.sqrt(0.1) * np.array([[0, 1], [1, 0]])])]
+    circ = I.Circuit(n, ops, p, density=True)
+    theta = rng.uniform(0, 2 * np.pi, p)
+    obs = I.ising_chain(n, [0.7] * n) + [(0.3, ((0, "Y"), (2, "Y")))]
+    start = I.random_density(n, 12)
+    tiling = (6, 2) if mode == gb.FUSED else None
+    check_amps(run_apply(circ, theta, dtype, mode, start=start, tiling=tiling),
+               O.rho_apply_circuit(circ, theta, start), dtype)
+    c = gb.circuit_create(circ)
+    if mode == gb.FUSED:
+        c.set_tiling(6, 2)
+    o = gb.obs_create(obs, n)
+    e, g = gb.grad(c, theta, o, dtype, mode)
+    e_ref, g_ref = O.noisy_adjoint_grad(circ, theta, obs)
+    check_energy(e, e_ref, dtype)
+    check_grad(g, g_ref, dtype)
