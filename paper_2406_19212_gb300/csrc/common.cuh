@@ -262,8 +262,10 @@ enum FType : int32_t {
     FT_DENSE1 = 0, FT_REAL1 = 1, FT_ANTI1 = 2, FT_DIAG1 = 3,
     FT_DENSE2 = 4, FT_DIAG2 = 5, FT_PERM2 = 6, FT_CTRL2 = 7,
     FT_DIAGB = 8,  // a run of commuting diagonal gates (DEnt list) fused into one phase table
-    FT_LAYER1 = 9,  // one-qubit non-diagonal gates on distinct register slots (DEnt list):
-                    // a = slot mask; entry k = Shape, ca = slot, cls = GenType
+    FT_LAYER1 = 9,  // one-qubit non-diagonal gates on distinct register slots: a = slot
+                    // mask, b = entries, perm = per-slot shape code, forward: mat = first
+                    // of the entries' consecutive units; DEnt list (slot order): entry =
+                    // Shape, ca = slot, cls = GenType, mat / mat2, gradient slot and weight
     FT_BLOCK2 = 10,  // SH_BLOCK2 on two register slots
     FT_IMAG1 = 11,   // SH_IMAG1 on one register slot
     FT_PROBE2 = 12,  // reverse only: gradient read 2 Re <Psi| K |Phi> with the 4x4 K on two

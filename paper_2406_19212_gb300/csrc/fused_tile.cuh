@@ -459,12 +459,6 @@ struct RedCtx {
     unsigned lanemask;
 };
 
-// FT_LAYER1: one-qubit gates on distinct register slots, slot loop unrolled at compile
-// time (no per-gate dispatch on the slot).  Reverse: generator, then Phi and Psi.
-template <typename R, int NR, bool REV>
-__device__ __forceinline__ void apply_layer(int mask, const DEnt *le, const R *smat, typename CT<R>::T *a,
-                                            typename CT<R>::T *b, const RedCtx<R> &rc);
-
 // Sum a per-thread partial over the warp (shuffles in the state's precision: FP32 for
 // complex64, FP64 for complex128) and store it for its slot.
 template <typename R>
@@ -476,9 +470,41 @@ __device__ __forceinline__ void emit_partial(const RedCtx<R> &c, int slot, R v)
     if (c.lane == 0) c.sgrad[(slot - c.slot_begin) * c.nwarps + c.warp] = v;
 }
 
+// A 2x2 matrix unit (8 reals) from shared memory as 16-byte vector loads.
+template <typename R>
+__device__ __forceinline__ void load_unit(const R *p, R (&m)[8])
+{
+    if constexpr (sizeof(R) == 4) {
+        const float4 x = reinterpret_cast<const float4 *>(p)[0], y = reinterpret_cast<const float4 *>(p)[1];
+        m[0] = x.x; m[1] = x.y; m[2] = x.z; m[3] = x.w; m[4] = y.x; m[5] = y.y; m[6] = y.z; m[7] = y.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const double2 v = reinterpret_cast<const double2 *>(p)[i];
+            m[2 * i] = v.x;
+            m[2 * i + 1] = v.y;
+        }
+    }
+}
+
+// One-qubit gate of layer shape code sh (0 dense, 1 real, 2 imaginary off-diagonal,
+// 3 anti-diagonal) on register slot K.
+template <typename R, int NR, int K>
+__device__ __forceinline__ void layer_gate(int sh, const R *m, typename CT<R>::T *a)
+{
+    if (sh == 1) rg1<R, NR, K, SH_REAL1>(a, m);
+    else if (sh == 2) rg1<R, NR, K, SH_IMAG1>(a, m);
+    else if (sh == 0) rg1<R, NR, K, SH_DENSE1>(a, m);
+    else rg1<R, NR, K, SH_ANTI1>(a, m);
+}
+
+// FT_LAYER1: one-qubit gates on distinct register slots, slot loop unrolled at compile
+// time (no per-gate dispatch on the slot).  Entry-driven form: each entry names its
+// shape, generator class, gradient slot and matrix units.  Reverse: generator read, then
+// Phi and Psi.
 template <typename R, int NR, bool REV, int K>
-__device__ __forceinline__ void layer_slot(int mask, const DEnt *le, int &idx, const R *smat, typename CT<R>::T *a,
-                                           typename CT<R>::T *b, const RedCtx<R> &rc)
+__device__ __forceinline__ void layer_slot_ent(int mask, const DEnt *le, int &idx, const R *smat, typename CT<R>::T *a,
+                                               typename CT<R>::T *b, const RedCtx<R> &rc)
 {
     if constexpr (K < NR) {
         if ((mask >> K) & 1) {
@@ -503,16 +529,45 @@ __device__ __forceinline__ void layer_slot(int mask, const DEnt *le, int &idx, c
                 if constexpr (REV) rg1<R, NR, K, SH_ANTI1>(b, m2);
             }
         }
-        layer_slot<R, NR, REV, K + 1>(mask, le, idx, smat, a, b, rc);
+        layer_slot_ent<R, NR, REV, K + 1>(mask, le, idx, smat, a, b, rc);
     }
 }
 
-template <typename R, int NR, bool REV>
-__device__ __forceinline__ void apply_layer(int mask, const DEnt *le, const R *smat, typename CT<R>::T *a,
+// Forward form for kernels without two-qubit gates: the record carries each slot's shape
+// (codes, 2 bits per slot) and the first of the layer's consecutive matrix units, so no
+// matrix address waits for an entry load, and the next entry's matrix is loaded into
+// registers while the current one is applied.
+template <typename R, int NR, int K>
+__device__ __forceinline__ void layer_slot_pf(int mask, int codes, const R *mp, int last, int &idx, R (&cur)[8],
+                                              typename CT<R>::T *a)
+{
+    if constexpr (K < NR) {
+        if ((mask >> K) & 1) {
+            R nxt[8];
+            load_unit<R>(mp + 8 * (idx + 1 < last ? idx + 1 : last), nxt);
+            layer_gate<R, NR, K>((codes >> (2 * K)) & 3, cur, a);
+#pragma unroll
+            for (int i = 0; i < 8; i++) cur[i] = nxt[i];
+            idx++;
+        }
+        layer_slot_pf<R, NR, K + 1>(mask, codes, mp, last, idx, cur, a);
+    }
+}
+
+// PF: the prefetching forward form (the other kernels are at their register bound)
+template <typename R, int NR, bool REV, bool PF>
+__device__ __forceinline__ void apply_layer(const FGate &g, const DEnt *le, const R *smat, typename CT<R>::T *a,
                                             typename CT<R>::T *b, const RedCtx<R> &rc)
 {
     int idx = 0;
-    layer_slot<R, NR, REV, 0>(mask, le, idx, smat, a, b, rc);
+    if constexpr (!REV && PF) {
+        R cur[8];
+        const R *mp = smat + 8 * g.mat;
+        load_unit<R>(mp, cur);
+        layer_slot_pf<R, NR, 0>(g.a, g.perm, mp, g.b - 1, idx, cur, a);
+    } else {
+        layer_slot_ent<R, NR, REV, 0>(g.a, le, idx, smat, a, b, rc);
+    }
 }
 
 // ----------------------------------------------------------------------- the kernel
@@ -736,7 +791,7 @@ __device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, 
             const FGate g = gn;
             if (gi + 1 < sr.g_end) gn = sgates[gi + 1];  // prefetch the next record
             if (g.type == FT_LAYER1) {
-                apply_layer<R, NR, REV>(g.a, sents + g.ent, smat, a, b, rc);
+                apply_layer<R, NR, REV, !TWOQ>(g, sents + g.ent, smat, a, b, rc);
                 continue;
             }
             if (g.type == FT_DIAGB) {

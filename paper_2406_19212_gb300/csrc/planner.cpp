@@ -96,6 +96,13 @@ struct Emitter {
     bool has_2q = false;     // a non-diagonal two-qubit gate was emitted
     bool overflow = false;   // a phase block class with more than 255 entries
 
+    // a unit of its own (no sharing): layers take runs of consecutive units
+    int fresh_unit(int rec)
+    {
+        units.push_back(MatUnit{rec, 0});
+        return (int)units.size() - 1 - unit_base;
+    }
+
     int unit(int rec, int k)
     {
         auto it = unit_of_rec.find(rec);
@@ -272,11 +279,21 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
                     std::sort(layer.begin(), layer.end(), [&](int x, int y) {
                         return slot_of(E.local_of[G[order[x]].q[0]]) < slot_of(E.local_of[G[order[y]].q[0]]);
                     });
+                    // record: a = slot mask, b = entries, perm = per slot K the shape code
+                    // (bits 2K: 0 dense, 1 real, 2 imaginary off-diagonal, 3 anti-diagonal);
+                    // forward: mat = first of the entries' consecutive units (slot order)
                     FGate f{};
                     f.type = FT_LAYER1;
                     f.slot = -1;
                     f.ent = (int16_t)((int)E.ents.size() - E.ent_base);
-                    int mask = 0;
+                    int first = -1;
+                    if (!E.reverse)
+                        for (int pos : layer) {
+                            const int u = E.fresh_unit(G[order[pos]].rec_f);
+                            if (first < 0) first = u;
+                        }
+                    f.mat = f.mat2 = (int16_t)first;
+                    int mask = 0, codes = 0, i_ent = 0;
                     for (int pos : layer) {
                         const PGate &g = G[order[pos]];
                         DEnt d{};
@@ -286,9 +303,11 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
                                        : g.ftype == FT_ANTI1 ? SH_ANTI1
                                        : g.ftype == FT_IMAG1 ? SH_IMAG1
                                                              : SH_DENSE1);
+                        codes |= (g.ftype == FT_REAL1 ? 1 : g.ftype == FT_IMAG1 ? 2 : g.ftype == FT_ANTI1 ? 3 : 0) << (2 * k);
                         d.ca = (int8_t)k;
-                        d.mat = (int16_t)E.unit(E.reverse ? g.rec_i : g.rec_f, 1);
+                        d.mat = (int16_t)(E.reverse ? E.unit(g.rec_i, 1) : first + i_ent);
                         d.mat2 = (int16_t)(E.reverse ? E.unit(g.rec_a, 1) : d.mat);
+                        i_ent++;
                         d.cls = GEN_NONE;
                         d.slot = -1;
                         E.flops += st * ftype_flops(g.ftype);
@@ -302,6 +321,8 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
                         E.ents.push_back(d);
                     }
                     f.a = (int8_t)mask;
+                    f.b = (int8_t)layer.size();
+                    f.perm = codes;
                     f.n_ent = (int16_t)layer.size();
                     E.gates.push_back(f);
                     layer.clear();
