@@ -504,14 +504,15 @@ __device__ __forceinline__ void layer_gate(int sh, const R *m, typename CT<R>::T
 // Phi and Psi.
 template <typename R, int NR, bool REV, int K>
 __device__ __forceinline__ void layer_slot_ent(int mask, const DEnt *le, int &idx, const R *smat, typename CT<R>::T *a,
-                                               typename CT<R>::T *b, const RedCtx<R> &rc)
+                                               typename CT<R>::T *b, R (&gv)[NR], int (&gs)[NR])
 {
     if constexpr (K < NR) {
         if ((mask >> K) & 1) {
             const DEnt d = le[idx++];
-            if constexpr (REV) {
-                if (d.cls == GEN_X) emit_partial<R>(rc, d.slot, gen_xy<R, NR, K, GEN_X>(a, b) * (R)d.coef);
-                else if (d.cls == GEN_Y) emit_partial<R>(rc, d.slot, gen_xy<R, NR, K, GEN_Y>(a, b) * (R)d.coef);
+            if constexpr (REV) {  // the read is reduced over the warp after the layer
+                gs[K] = d.cls == GEN_NONE ? -1 : d.slot;
+                if (d.cls == GEN_X) gv[K] = gen_xy<R, NR, K, GEN_X>(a, b) * (R)d.coef;
+                else if (d.cls == GEN_Y) gv[K] = gen_xy<R, NR, K, GEN_Y>(a, b) * (R)d.coef;
             }
             const R *m = smat + 8 * d.mat;
             const R *m2 = smat + 8 * d.mat2;
@@ -529,7 +530,7 @@ __device__ __forceinline__ void layer_slot_ent(int mask, const DEnt *le, int &id
                 if constexpr (REV) rg1<R, NR, K, SH_ANTI1>(b, m2);
             }
         }
-        layer_slot_ent<R, NR, REV, K + 1>(mask, le, idx, smat, a, b, rc);
+        layer_slot_ent<R, NR, REV, K + 1>(mask, le, idx, smat, a, b, gv, gs);
     }
 }
 
@@ -566,7 +567,25 @@ __device__ __forceinline__ void apply_layer(const FGate &g, const DEnt *le, cons
         load_unit<R>(mp, cur);
         layer_slot_pf<R, NR, 0>(g.a, g.perm, mp, g.b - 1, idx, cur, a);
     } else {
-        layer_slot_ent<R, NR, REV, 0>(g.a, le, idx, smat, a, b, rc);
+        R gv[NR];
+        int gs[NR];
+#pragma unroll
+        for (int k = 0; k < NR; k++) {
+            gv[k] = R(0);
+            gs[k] = -1;
+        }
+        layer_slot_ent<R, NR, REV, 0>(g.a, le, idx, smat, a, b, gv, gs);
+        if constexpr (REV) {
+            // the layer's generator reads: NR independent warp reductions, interleaved
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int k = 0; k < NR; k++)
+                    if (o < rc.lanes) gv[k] += __shfl_xor_sync(rc.lanemask, gv[k], o);
+#pragma unroll
+            for (int k = 0; k < NR; k++)
+                if (gs[k] >= 0 && rc.lane == 0) rc.sgrad[(gs[k] - rc.slot_begin) * rc.nwarps + rc.warp] = gv[k];
+        }
     }
 }
 
