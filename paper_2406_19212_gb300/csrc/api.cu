@@ -1506,9 +1506,12 @@ static std::vector<int8_t> choose_grad_layout(const std::vector<PGate> &pg, int 
     return perm;
 }
 
-static gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out)
+// batch: the plan a batch member runs with (launches shared by all members take the
+// largest member's shared memory, so its passes keep the smaller slot budget that leaves
+// two CTAs per SM; a single circuit takes larger passes, fewer tile loads and stores).
+static gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out, bool batch = false)
 {
-    int key = dtype * 2 + (grad_layout ? 1 : 0);
+    int key = dtype * 2 + (grad_layout ? 1 : 0) + (batch ? 4 : 0);
     auto it = c->plans.find(key);
     if (it != c->plans.end()) {
         *out = it->second.get();
@@ -1522,7 +1525,7 @@ static gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout,
     opt.nr_r = fused_nr(dtype, true);
     opt.t = std::min(opt.t, max_tile(dtype));
     opt.elem_bytes = dtype == GBVQC_C64 ? 4 : 8;
-    opt.max_slots = 128;
+    opt.max_slots = batch ? 128 : 256;
     opt.gate_smem = 40 * 1024;
     std::vector<int8_t> perm;
     std::vector<PGate> permuted;
@@ -1554,10 +1557,10 @@ static gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout,
 }
 
 // Fused plan with its device copies.
-static gbvqc_status get_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out)
+static gbvqc_status get_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out, bool batch = false)
 {
     DevPlan *dp = nullptr;
-    ST_TRY(get_host_plan(c, dtype, grad_layout, &dp));
+    ST_TRY(get_host_plan(c, dtype, grad_layout, &dp, batch));
     if (!dp->uploaded) {
         CUDA_TRY(fused_prepare());
         ST_TRY(upload(&dp->d_fwd, dp->p.fwd));
@@ -2156,7 +2159,7 @@ static gbvqc_status batch_build(gbvqc_batch *b)
         gbvqc_circuit *c = b->circs[i];
         ST_TRY(ensure_device(c));
         ST_TRY(ensure_obs(b->obs[i]));
-        ST_TRY(get_plan(c, dtype, true, &plans[i]));
+        ST_TRY(get_plan(c, dtype, true, &plans[i], true));
         for (int bi : plans[i]->p.barrier)
             if (bi >= 0) return fail(GBVQC_ERR_UNSUPPORTED, "batch member %d holds a two-qubit channel", i);
         const FusedPlan &P = plans[i]->p;
