@@ -1506,6 +1506,10 @@ static std::vector<int8_t> choose_grad_layout(const std::vector<PGate> &pg, int 
     return perm;
 }
 
+// Shared memory per CTA that still leaves two reverse-pass CTAs on one SM (228 KB per SM,
+// 1 KB reserved per CTA), less a margin for alignment and the phase-block constants.
+constexpr int kTwoCtaSmem = 110 * 1024;
+
 // batch: the plan a batch member runs with (launches shared by all members take the
 // largest member's shared memory, so its passes keep the smaller slot budget that leaves
 // two CTAs per SM; a single circuit takes larger passes, fewer tile loads and stores).
@@ -1525,8 +1529,8 @@ static gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout,
     opt.nr_r = fused_nr(dtype, true);
     opt.t = std::min(opt.t, max_tile(dtype));
     opt.elem_bytes = dtype == GBVQC_C64 ? 4 : 8;
-    opt.max_slots = batch ? 128 : 256;
-    opt.gate_smem = 40 * 1024;
+    opt.max_slots = batch ? 128 : 512;
+    opt.gate_smem = batch ? 40 * 1024 : 64 * 1024;
     std::vector<int8_t> perm;
     std::vector<PGate> permuted;
     if (grad_layout && !c->density) perm = choose_grad_layout(pg0, c->n_phys, opt);
@@ -1543,10 +1547,23 @@ static gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout,
     dp->elem = opt.elem_bytes;
     dp->perm = perm;
     std::string err;
-    if (!build_fused_plan(pg, c->n_phys, opt, dp->p, err))
-        return fail(GBVQC_ERR_UNSUPPORTED, "fused plan: %s", err.c_str());
-    for (const PassDesc &d : dp->p.fwd) dp->fwd_smem.push_back(pass_smem_bytes(dp->p, d, false, opt.elem_bytes));
-    for (const PassDesc &d : dp->p.rev) dp->rev_smem.push_back(pass_smem_bytes(dp->p, d, true, opt.elem_bytes));
+    for (int attempt = 0;; attempt++) {
+        dp->p = FusedPlan();
+        dp->fwd_smem.clear();
+        dp->rev_smem.clear();
+        if (!build_fused_plan(pg, c->n_phys, opt, dp->p, err))
+            return fail(GBVQC_ERR_UNSUPPORTED, "fused plan: %s", err.c_str());
+        size_t worst = 0;
+        for (const PassDesc &d : dp->p.fwd) dp->fwd_smem.push_back(pass_smem_bytes(dp->p, d, false, opt.elem_bytes));
+        for (const PassDesc &d : dp->p.rev) {
+            dp->rev_smem.push_back(pass_smem_bytes(dp->p, d, true, opt.elem_bytes));
+            worst = std::max(worst, dp->rev_smem.back());
+        }
+        // larger passes only while every reverse pass still fits two CTAs per SM
+        if (batch || worst <= (size_t)kTwoCtaSmem || opt.gate_smem <= 24 * 1024 || attempt >= 4) break;
+        opt.gate_smem = opt.gate_smem * 3 / 4;
+        opt.max_slots = std::max(128, opt.max_slots / 2);
+    }
     for (size_t b : dp->fwd_smem)
         if (b > 200 * 1024) return fail(GBVQC_ERR_UNSUPPORTED, "fused pass needs %zu bytes of shared memory", b);
     for (size_t b : dp->rev_smem)
