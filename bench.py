@@ -359,18 +359,19 @@ def run_ours(args, world, rank, local):
     return 0
 
 
-def gate_sweep(gb, I, torch, dev, stream, pk):
-    """28-qubit random circuit (4x7 grid, 20 cycles) applied in complex64: fused tile
-    passes vs one launch per gate; GB/s = algorithmic bytes (one read + one write of the
-    state per pass or per gate) / time."""
-    w = I.precision_28q()
+def gate_sweep(gb, I, torch, dev, stream, pk, rows=4, cols=7):
+    """Random circuit on a rows x cols grid (20 cycles; 4x7 = 28 qubits) applied in
+    complex64: fused tile passes vs one launch per gate; GB/s = algorithmic bytes (one
+    read + one write of the state per pass or per gate) / time."""
+    n = rows * cols
+    w = I.grid_rqc(rows, cols, 20, 1)
     circ = gb.circuit_create(w.circuit)
     passes, _, tq = circ.plan_info()
-    state = torch.zeros(1 << 28, dtype=torch.complex64, device=dev)
+    state = torch.zeros(1 << n, dtype=torch.complex64, device=dev)
     state[0] = 1
-    sv = gb.sv_wrap(state, 28, stream=stream)
-    res = {"workload": "rqc_4x7_c20: 28 qubits, 20 cycles of sqrt(X/Y/W) + FSIM couplers, "
-                       "785 gates, complex64 (2 GiB state, inputs larger than L2)",
+    sv = gb.sv_wrap(state, n, stream=stream)
+    res = {"workload": f"rqc_{rows}x{cols}_c20: {n} qubits, 20 cycles of sqrt(X/Y/W) + FSIM couplers, "
+                       f"{len(w.circuit.ops)} gates, complex64 ({(8 << n) >> 20} MiB state)",
            "tile_qubits": tq, "fused_passes": passes}
     for mode, key in ((gb.FUSED, "fused"), (gb.PLAIN, "plain")):
         gb.apply_circuit(sv, circ, (), mode)
@@ -385,14 +386,14 @@ def gate_sweep(gb, I, torch, dev, stream, pk):
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / reps
         sweeps = passes if mode == gb.FUSED else len(w.circuit.ops)
-        byts = sweeps * 2 * (8 << 28)
+        byts = sweeps * 2 * (8 << n)
         res[f"{key}_ms"] = ms
         res[f"{key}_sweeps"] = sweeps
         res[f"{key}_gbs"] = byts / (ms / 1e3) / 1e9
         res[f"{key}_frac_hbm"] = res[f"{key}_gbs"] / pk["hbm_gbs"]
     res["speedup_fused_vs_plain"] = res["plain_ms"] / res["fused_ms"]
     # per-gate sweep bytes the fused passes stand in for, over the fused time
-    res["fused_effective_gbs"] = len(w.circuit.ops) * 2 * (8 << 28) / (res["fused_ms"] / 1e3) / 1e9
+    res["fused_effective_gbs"] = len(w.circuit.ops) * 2 * (8 << n) / (res["fused_ms"] / 1e3) / 1e9
     sv.free()
     del state
     torch.cuda.empty_cache()
@@ -472,6 +473,19 @@ def heisenberg_rate(gb, I, torch, dev, stream):
             "ms_per_eval": ms, "gradient_evals_per_s": 1e3 / ms, "l2": "warm (16 MiB states)"}
 
 
+def run_sweep_only(args) -> int:
+    """The gate-sweep leg alone on one GPU (profiling entry point)."""
+    import torch
+    import paper_2406_19212_gb300 as gb
+    from paper_2406_19212_gb300 import inputs as I
+    rows, cols = (int(x) for x in args.sweep_grid.lower().split("x"))
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    res = gate_sweep(gb, I, torch, dev, stream, peaks()[0], rows, cols)
+    print(json.dumps(res))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -481,7 +495,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary legs (plain complex128, 28q sweep, batch, noisy)")
+    ap.add_argument("--only-sweep", action="store_true",
+                    help="run only the gate-sweep leg (fused vs per-gate) and print its JSON; "
+                         "for kernel profiles on a chosen size")
+    ap.add_argument("--sweep-grid", default="4x7", help="grid of the gate-sweep circuit, ROWSxCOLS")
     args = ap.parse_args()
+    if args.only_sweep:
+        return run_sweep_only(args)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         rc = run_reference(args, world, rank)
