@@ -473,6 +473,52 @@ def heisenberg_rate(gb, I, torch, dev, stream):
             "ms_per_eval": ms, "gradient_evals_per_s": 1e3 / ms, "l2": "warm (16 MiB states)"}
 
 
+def gate_micro(gb, I, torch, n, pk):
+    """Single-gate sweeps (H, Rx, CNOT, CZ) on qubit positions 0, 5, 11, 20 and n - 1 of an
+    n-qubit state, one kernel per gate (per-gate path) and one tile pass (fused path):
+    GB/s = algorithmic bytes / event-timed duration, the algorithmic bytes being one read
+    and one write of the amplitudes the gate changes (the whole state; for CNOT the half
+    with the control set and for CZ the quarter |11>, by the per-gate kernel) or of the
+    whole state (tile pass).  The
+    state is larger than L2 for n >= 25, so no flush is needed."""
+    stream = torch.cuda.current_stream()
+    rows = []
+    for dtype, dname, s in ((gb.C64, "c64", 8), (gb.C128, "c128", 16)):
+        sv = gb.sv_alloc(n, dtype)
+        full = 2.0 * s * (1 << n)
+        for gate in ("H", "RX", "CNOT", "CZ"):
+            for q in sorted({0, 5, 11, 20, n - 1}):
+                if q >= n:
+                    continue
+                if gate in ("CNOT", "CZ"):
+                    op = I.Op(gate, (q, q + 1 if q + 1 < n else q - 1))
+                else:
+                    op = I.Op(gate, (q,), fixed=(0.3,) if gate == "RX" else ())
+                c = gb.circuit_create(I.Circuit(n, [op], 0))
+                row = {"dtype": dname, "gate": gate, "qubit": q}
+                for mode, key in ((gb.PLAIN, "plain"), (gb.FUSED, "fused")):
+                    byts = full / {"CNOT": 2, "CZ": 4}.get(gate, 1) if mode == gb.PLAIN else full
+                    for _ in range(3):
+                        gb.apply_circuit(sv, c, (), mode)
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    reps = 20
+                    a.record(stream)
+                    for _ in range(reps):
+                        gb.apply_circuit(sv, c, (), mode)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    ms = a.elapsed_time(b) / reps
+                    row[f"{key}_us"] = round(ms * 1e3, 1)
+                    row[f"{key}_gbs"] = round(byts / (ms / 1e3) / 1e9, 1)
+                    row[f"{key}_frac_hbm"] = round(byts / (ms / 1e3) / 1e9 / pk["hbm_gbs"], 3)
+                rows.append(row)
+                c.free()
+        sv.free()
+    return {"workload": f"single-gate sweeps on a {n}-qubit state (H, Rx(0.3), CNOT, CZ; qubits 0, 5, 11, 20, n-1)",
+            "hbm_peak_gbs": pk["hbm_gbs"], "rows": rows}
+
+
 def run_sweep_only(args) -> int:
     """The gate-sweep leg alone on one GPU (profiling entry point)."""
     import torch
@@ -499,9 +545,18 @@ def main():
                     help="run only the gate-sweep leg (fused vs per-gate) and print its JSON; "
                          "for kernel profiles on a chosen size")
     ap.add_argument("--sweep-grid", default="4x7", help="grid of the gate-sweep circuit, ROWSxCOLS")
+    ap.add_argument("--gate-micro", type=int, default=0, metavar="N",
+                    help="run only the single-gate sweep microbenchmark on N qubits and print its JSON")
     args = ap.parse_args()
     if args.only_sweep:
         return run_sweep_only(args)
+    if args.gate_micro:
+        import torch
+        import paper_2406_19212_gb300 as gb
+        from paper_2406_19212_gb300 import inputs as I
+        torch.cuda.set_device(0)
+        print(json.dumps(gate_micro(gb, I, torch, args.gate_micro, peaks()[0])))
+        return 0
     world, rank, local = dist_setup()
     if args.impl == "reference":
         rc = run_reference(args, world, rank)

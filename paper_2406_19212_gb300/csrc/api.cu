@@ -98,6 +98,8 @@ static double shape_flops(int sh)
     case SH_IMAG1: return 6;    // two real products and a sum per output
     case SH_DENSE4: return 126; // sixteen complex products and fifteen sums per output
     case SH_PAR2: return 14;    // a dense 2x2 on every amplitude pair
+    case SH_CX: return 0;      // data movement only
+    case SH_CZ: return 0.5;    // a sign on a quarter of the amplitudes
     case SH_REAL1: return 6;
     default: return 6;          // one complex product
     }
@@ -327,7 +329,13 @@ static int classify(const Mat &M)
     for (int r = 0; r < 4; r++)
         for (int c = 0; c < 4; c++)
             if (r != c && nz(M[r * 4 + c])) diag = false;
-    if (diag) return SH_DIAG2;
+    if (diag) return M[0] == cd(1) && M[5] == cd(1) && M[10] == cd(1) && M[15] == cd(-1) ? SH_CZ : SH_DIAG2;
+    // exactly CNOT with the first qubit as control (rows 1 and 3 swapped, unit entries)
+    if (M[0] == cd(1) && M[10] == cd(1) && M[7] == cd(1) && M[13] == cd(1)) {
+        int others = 0;
+        for (int i = 0; i < 16; i++) others += nz(M[i]);
+        if (others == 4) return SH_CX;
+    }
     // controlled: identity on the q0 = 0 block (indices 0, 2), no coupling to 1, 3
     bool ctrl = M[0] == cd(1) && M[10] == cd(1) && !nz(M[2]) && !nz(M[8]);
     for (int r : {0, 2})
@@ -393,6 +401,7 @@ static int ftype_of(int sh)
     case SH_PERM2: return FT_PERM2;
     case SH_BLOCK2: return FT_BLOCK2;
     case SH_IMAG1: return FT_IMAG1;
+    case SH_CZ: return FT_DIAG2;
     case SH_PAR2: return FT_PAR2;
     case SH_RPAR2: return FT_RPAR2;
     default: return FT_CTRL2;
@@ -1192,7 +1201,8 @@ static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGa
             g.q[0] = map.ket[op.qubits[0]];
             g.q[1] = map.bra[op.qubits[0]];
             int sh = join_shape(join_shape(classify(S), classify(Si)), classify(Sa));
-            if (sh == SH_PERM2 || sh == SH_CTRL2) sh = SH_DENSE2;
+            if (sh == SH_PERM2 || sh == SH_CTRL2 || sh == SH_CX) sh = SH_DENSE2;
+            if (sh == SH_CZ) sh = SH_DIAG2;
             g.diag = sh == SH_DIAG2;
             g.ftype = ftype_of(sh);
             g.rec_f = add_rec(c, S);
@@ -1692,7 +1702,9 @@ static gbvqc_status plain_gate(gbvqc_circuit *c, int dtype, void *psi, const Pla
         return gate4(c, dtype, psi, q, rec, s);
     }
     const bool one = shape_qubits(g.shape) == 1;
-    return run_k(one ? "gate1q" : "gate2q", shape_flops(g.shape) * amps, (g.shape == SH_CTRL2 ? 1.0 : 2.0) * sb, s,
+    // complex64 runs CNOT through the controlled-2x2 kernel (launch_gate)
+    const int fsh = g.shape == SH_CX && dtype == GBVQC_C64 ? SH_CTRL2 : g.shape;
+    return run_k(one ? "gate1q" : "gate2q", shape_flops(fsh) * amps, (g.shape == SH_CTRL2 || g.shape == SH_CX ? 1.0 : g.shape == SH_CZ ? 0.5 : 2.0) * sb, s,
                  [&] { return launch_gate(dtype, psi, c->n_phys, g.shape, g.q0, g.q1, c->d_recs + rec, s); });
 }
 

@@ -31,13 +31,15 @@ enum Shape : int32_t {
     SH_DENSE4 = 10, // general 16x16 (two-qubit channel superoperator), 16 records of one row
     SH_PAR2 = 11,   // parity-preserving 4x4: a 2x2 on {|00>, |11>} and a 2x2 on {|01>, |10>}
                     // (superoperator of a phase-covariant one-qubit channel on (ket, bra))
-    SH_RPAR2 = 12   // SH_PAR2 with real entries (depolarising, amplitude and phase damping)
+    SH_RPAR2 = 12,  // SH_PAR2 with real entries (depolarising, amplitude and phase damping)
+    SH_CX = 13,     // exactly CNOT (control = first qubit): a swap, no arithmetic
+    SH_CZ = 14      // exactly CZ: the sign of |11>, no arithmetic
 };
 
-inline __host__ __device__ bool shape_is_diag(int sh) { return sh == SH_DIAG1 || sh == SH_DIAG2; }
+inline __host__ __device__ bool shape_is_diag(int sh) { return sh == SH_DIAG1 || sh == SH_DIAG2 || sh == SH_CZ; }
 inline __host__ __device__ int shape_qubits(int sh)
 {
-    return sh == SH_DENSE4 ? 4 : (sh >= SH_DENSE2 && sh <= SH_BLOCK2) || sh == SH_PAR2 || sh == SH_RPAR2 ? 2 : 1;
+    return sh == SH_DENSE4 ? 4 : (sh >= SH_DENSE2 && sh <= SH_BLOCK2) || (sh >= SH_PAR2 && sh <= SH_CZ) ? 2 : 1;
 }
 
 // Row-major re/im offsets of the 2x2 block of an SH_BLOCK2 matrix (rows/columns 1 and 2)

@@ -112,6 +112,21 @@ __global__ void __launch_bounds__(256) k_gate2(typename CT<R>::T *__restrict__ p
             psi[i3] = d;
             continue;
         }
+        if (SH == SH_CX) {  // CNOT: the two amplitudes with the control set trade places
+            const int64_t i1 = base | b0, i3 = base | b0 | b1;
+            const T t = psi[i1];
+            psi[i1] = psi[i3];
+            psi[i3] = t;
+            continue;
+        }
+        if (SH == SH_CZ) {  // CZ: the |11> amplitude changes sign
+            const int64_t i3 = base | b0 | b1;
+            T t = psi[i3];
+            t.x = -t.x;
+            t.y = -t.y;
+            psi[i3] = t;
+            continue;
+        }
         if (SH == SH_PAR2 || SH == SH_RPAR2) {  // 2x2 on |00>, |11>; 2x2 on |01>, |10>
             const int64_t i1 = base | b0, i2 = base | b1, i3 = base | b0 | b1;
             T a = psi[base], d = psi[i3], b = psi[i1], c = psi[i2];
@@ -181,6 +196,12 @@ static cudaError_t gate_dispatch(void *psi_, int n, int shape, int q0, int q1, c
         case SH_BLOCK2: k_gate2<R, SH_BLOCK2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
         case SH_PAR2: k_gate2<R, SH_PAR2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
         case SH_RPAR2: k_gate2<R, SH_RPAR2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
+        case SH_CX:  // measured: the swap wins in complex128 (no FP64 arithmetic), the
+                     // controlled 2x2 in complex64 (87-97% of HBM against 55-60% for the swap)
+            if constexpr (sizeof(R) == 8) k_gate2<R, SH_CX><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec);
+            else k_gate2<R, SH_CTRL2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec);
+            break;
+        case SH_CZ: k_gate2<R, SH_CZ><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
         default: k_gate2<R, SH_CTRL2><<<gr, th, 0, s>>>(psi, nq, q0, q1, rec); break;
         }
     }
