@@ -122,6 +122,26 @@ def test_planner_invariants_host(lib, dtype):
         assert st["fwd_gates"] <= st["phys_gates"]
 
 
+def test_passes_leave_two_ctas_per_sm_host(lib):
+    # single-circuit plans take passes as large as 110 KiB of reverse-pass shared memory
+    # allows (two CTAs per SM); the 20-qubit step then needs 5 passes at tile 12
+    cases = [I.diff_20q(), I.noisy_hea(6, 2, 1), I.precision_24q(), I.heisenberg_20q(),
+             I.random_circuit(14, 300, 3, param_share=True)]
+    for w in cases:
+        c = gb.circuit_create(w.circuit)
+        for dtype in (gb.C64, gb.C128):
+            for t, lo in ((10, 2), (11, 3), (12, 4)):
+                try:
+                    c.set_tiling(t, lo)
+                    st = c.plan_stats(dtype, for_grad=True)
+                except gb.GbvqcError:
+                    continue  # tile above the precision's thread cap
+                assert st["rev_smem_max"] <= 110 * 1024
+    c = gb.circuit_create(I.diff_20q().circuit)
+    c.set_tiling(12, 4)
+    assert c.plan_stats(gb.C64, for_grad=True)["passes"] == 5
+
+
 def test_tiling_options_host(lib):
     w = I.random_circuit(14, 200, 5)
     c = gb.circuit_create(w.circuit)
