@@ -257,7 +257,6 @@ __global__ void __launch_bounds__(128) k_gate4(typename CT<R>::T *__restrict__ p
         int64_t base = g;
 #pragma unroll
         for (int u = 0; u < 4; u++) base = insert_zero(base, srt[u]);
-        int64_t idx[16];
         T v[16];
 #pragma unroll
         for (int l = 0; l < 16; l++) {
@@ -265,15 +264,20 @@ __global__ void __launch_bounds__(128) k_gate4(typename CT<R>::T *__restrict__ p
 #pragma unroll
             for (int u = 0; u < 4; u++)
                 if ((l >> u) & 1) ix |= int64_t(1) << qs[u];
-            idx[l] = ix;
             v[l] = psi[ix];
         }
-#pragma unroll
+        // the rows in a loop (fully unrolled, the 16 x 16 product put the amplitudes in
+        // local memory), each row's index recomputed rather than kept in an array
+#pragma unroll 1
         for (int r = 0; r < 16; r++) {
             T acc = cmul<T, R>(m[32 * r], m[32 * r + 1], v[0]);
 #pragma unroll
             for (int c = 1; c < 16; c++) cfma<T, R>(m[32 * r + 2 * c], m[32 * r + 2 * c + 1], v[c], acc);
-            psi[idx[r]] = acc;  // v holds the old values, so rows can be written as they finish
+            int64_t ix = base;
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if ((r >> u) & 1) ix |= int64_t(1) << qs[u];
+            psi[ix] = acc;  // v holds the old values, so rows can be written as they finish
         }
     }
 }
