@@ -174,6 +174,30 @@ gbvqc_status circuit_plan_info(circuit_handle c, int *n_passes, int *n_gates, in
  * physical gate list.  Fills min(n_stats, 10) entries. */
 gbvqc_status circuit_plan_stats(circuit_handle c, int dtype, int for_grad, int64_t *stats, int n_stats);
 
+/* Kernel structure the library uses for a one- or two-qubit matrix (a diagnostic query:
+ * host only, needs no GPU).  matrix: dim x dim complex entries, row-major, interleaved
+ * (re, im) doubles, dim 2 or 4 (first qubit = matrix bit 0).  *shape receives one of the
+ * GBVQC_SHAPE_* codes: which sweep a gate or a one-qubit channel's superoperator takes
+ * (exact zeros, ones and real parts decide; no tolerance).  Errors: ERR_ARG (NULL
+ * pointer, dim not 2 or 4). */
+enum {
+    GBVQC_SHAPE_DENSE1 = 0,  /* general 2x2 */
+    GBVQC_SHAPE_DIAG1 = 1,   /* diagonal 2x2 */
+    GBVQC_SHAPE_ANTI1 = 2,   /* anti-diagonal 2x2 */
+    GBVQC_SHAPE_REAL1 = 3,   /* real 2x2 */
+    GBVQC_SHAPE_DENSE2 = 4,  /* general 4x4 */
+    GBVQC_SHAPE_DIAG2 = 5,   /* diagonal 4x4 */
+    GBVQC_SHAPE_PERM2 = 6,   /* one non-zero per row and column */
+    GBVQC_SHAPE_CTRL2 = 7,   /* identity unless the first qubit is 1 */
+    GBVQC_SHAPE_BLOCK2 = 8,  /* phases on |00>, |11> and a 2x2 on |01>, |10> (FSIM) */
+    GBVQC_SHAPE_IMAG1 = 9,   /* real diagonal, imaginary off-diagonal 2x2 (Rx) */
+    GBVQC_SHAPE_PAR2 = 11,   /* a 2x2 on |00>, |11> and a 2x2 on |01>, |10> */
+    GBVQC_SHAPE_RPAR2 = 12,  /* the same with real entries */
+    GBVQC_SHAPE_CX = 13,     /* exactly CNOT, the first qubit the control */
+    GBVQC_SHAPE_CZ = 14      /* exactly CZ */
+};
+gbvqc_status gate_shape(const double *matrix, int dim, int *shape);
+
 /* ------------------------------------------------------------ execution (Sec. II.D) */
 
 /* psi <- C(theta) psi in place (apply!, Eq. circuitevolve; Eq. channel for density

@@ -26,6 +26,7 @@ __all__ = ["C64", "C128", "PLAIN", "FUSED", "GbvqcError", "StateVector", "Circui
            "Observable", "sv_alloc", "sv_wrap", "sv_set", "sv_get", "sv_reset",
            "circuit_create", "apply_circuit", "apply_channel", "obs_create", "expect", "grad",
            "grad_profile", "grad_batch", "batch_create", "BatchHandle", "expect_noalloc", "measure", "sample",
+           "gate_shape",
            "VQEEnergy",
            "load"]
 
@@ -232,6 +233,22 @@ def expect(sv: StateVector, obs: Observable) -> float:
     out = ctypes.c_double()
     _abi.check(_abi.lib().expect(sv.handle, obs.handle, ctypes.byref(out)))
     return out.value
+
+
+SHAPE_NAMES = {0: "DENSE1", 1: "DIAG1", 2: "ANTI1", 3: "REAL1", 4: "DENSE2", 5: "DIAG2", 6: "PERM2",
+               7: "CTRL2", 8: "BLOCK2", 9: "IMAG1", 11: "PAR2", 12: "RPAR2", 13: "CX", 14: "CZ"}
+
+
+def gate_shape(matrix) -> str:
+    """Name of the kernel structure the library picks for a 2x2 or 4x4 matrix (host only)."""
+    m = np.ascontiguousarray(np.asarray(matrix, dtype=np.complex128))
+    if m.ndim != 2 or m.shape[0] != m.shape[1]:
+        raise ValueError("a square matrix is required")
+    flat = np.ascontiguousarray(m.reshape(-1).view(np.float64))
+    out = ctypes.c_int()
+    _abi.check(_abi.lib().gate_shape(flat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), m.shape[0],
+                                     ctypes.byref(out)))
+    return SHAPE_NAMES[out.value]
 
 
 def measure(sv: StateVector, qubit: int, u: float) -> Tuple[int, float]:

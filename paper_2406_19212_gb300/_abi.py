@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
         "circuit_autotune": [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)],
         "circuit_plan_stats": [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
+        "gate_shape": [dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
         "apply_circuit": [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
         "apply_channel": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, ctypes.c_int],
         "obs_create": [ctypes.POINTER(Pauli), ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)],
@@ -121,7 +122,7 @@ def exported_symbols() -> List[str]:
             "sv_set", "sv_get", "sv_info", "circuit_create", "circuit_free", "circuit_set_tiling",
             "circuit_plan_info", "circuit_plan_stats", "circuit_autotune", "apply_circuit", "apply_channel", "obs_create", "obs_free",
             "expect", "grad", "grad_profile", "grad_batch", "batch_create", "batch_free",
-            "batch_grad", "expect_noalloc", "measure", "sample"]
+            "batch_grad", "expect_noalloc", "measure", "sample", "gate_shape"]
 
 
 # ------------------------------------------------------------------ marshalling

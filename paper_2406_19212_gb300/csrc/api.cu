@@ -1615,6 +1615,22 @@ static bool fused_supported(const gbvqc_circuit *c, int dtype)
     return c->n_phys >= std::max(fused_nr(dtype, false), fused_nr(dtype, true)) + 1;
 }
 
+static_assert(GBVQC_SHAPE_DENSE1 == SH_DENSE1 && GBVQC_SHAPE_DIAG1 == SH_DIAG1 && GBVQC_SHAPE_ANTI1 == SH_ANTI1 &&
+                  GBVQC_SHAPE_REAL1 == SH_REAL1 && GBVQC_SHAPE_DENSE2 == SH_DENSE2 && GBVQC_SHAPE_DIAG2 == SH_DIAG2 &&
+                  GBVQC_SHAPE_PERM2 == SH_PERM2 && GBVQC_SHAPE_CTRL2 == SH_CTRL2 && GBVQC_SHAPE_BLOCK2 == SH_BLOCK2 &&
+                  GBVQC_SHAPE_IMAG1 == SH_IMAG1 && GBVQC_SHAPE_PAR2 == SH_PAR2 && GBVQC_SHAPE_RPAR2 == SH_RPAR2 &&
+                  GBVQC_SHAPE_CX == SH_CX && GBVQC_SHAPE_CZ == SH_CZ,
+              "public shape codes follow the kernels' shapes");
+
+extern "C" gbvqc_status gate_shape(const double *matrix, int dim, int *shape)
+{
+    if (!matrix || !shape || (dim != 2 && dim != 4)) return fail(GBVQC_ERR_ARG, "gate_shape: matrix, dim 2 or 4, shape");
+    Mat M(dim * dim);
+    for (int i = 0; i < dim * dim; i++) M[i] = cd(matrix[2 * i], matrix[2 * i + 1]);
+    *shape = classify(M);
+    return GBVQC_OK;
+}
+
 extern "C" gbvqc_status circuit_set_tiling(circuit_handle c, int tile_qubits, int low_qubits)
 {
     if (!c) return fail(GBVQC_ERR_ARG, "NULL circuit");

@@ -219,3 +219,50 @@ def test_two_qubit_channel_validation_and_barrier_passes(lib):
     c.set_tiling(6, 2)
     st = c.plan_stats(gb.C64, for_grad=True)
     assert st["passes"] >= 3  # the two channels are passes of their own between tile passes
+
+
+def _superop(kraus):
+    """sum_s K_s (ket, matrix bit 0) x conj(K_s) (bra, matrix bit 1), Eq. channel2."""
+    return sum(np.kron(np.conj(k), k) for k in kraus)
+
+
+def test_gate_shape_classification_host(lib):
+    # the sweep a matrix takes: exact structure decides (textbook gates and channels)
+    s2, c, s = np.sqrt(0.5), np.cos(0.15), np.sin(0.15)
+    cases = {
+        "DIAG1": np.diag([1, 1j]),
+        "ANTI1": np.array([[0, 1], [1, 0]]),
+        "REAL1": s2 * np.array([[1, 1], [1, -1]]),
+        "IMAG1": np.array([[c, -1j * s], [-1j * s, c]]),
+        "DENSE1": 0.5 * np.array([[1 + 1j, 1 - 1j], [1 - 1j, 1 + 1j]]),  # sqrt(X)
+        "CX": np.array([[1, 0, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0], [0, 1, 0, 0]]),  # control = first qubit
+        "CZ": np.diag([1, 1, 1, -1]),
+        "DIAG2": np.diag([1, 1, 1, np.exp(0.3j)]),
+        "PERM2": np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]]),  # SWAP
+        "CTRL2": np.array([[1, 0, 0, 0], [0, c, 0, -1j * s], [0, 0, 1, 0], [0, -1j * s, 0, c]]),
+        "BLOCK2": np.array([[1, 0, 0, 0], [0, c, -1j * s, 0], [0, -1j * s, c, 0], [0, 0, 0, np.exp(-0.2j)]]),
+        "DENSE2": np.eye(4) + 0.1 * np.arange(16).reshape(4, 4),
+    }
+    for name, m in cases.items():
+        assert gb.gate_shape(m) == name, name
+    # CNOT with the second qubit as control is a permutation; a CZ off by one rounding
+    # step is a general diagonal
+    assert gb.gate_shape(np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]])) == "PERM2"
+    assert gb.gate_shape(np.diag([1, 1, 1, -1 + 2.0 ** -52])) == "DIAG2"
+    # one-qubit channel superoperators (Sec. II.B channels, completeness-corrected)
+    p, g = 0.1, 0.2
+    paulis = [np.eye(2), np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.diag([1, -1])]
+    depol = [np.sqrt(1 - 3 * p / 4) * paulis[0]] + [np.sqrt(p / 4) * q for q in paulis[1:]]
+    ampdamp = [np.array([[1, 0], [0, np.sqrt(1 - g)]]), np.array([[0, np.sqrt(g)], [0, 0]])]
+    phasedamp = [np.array([[1, 0], [0, np.sqrt(1 - g)]]), np.array([[0, 0], [0, np.sqrt(g)]])]
+    phased = [np.sqrt(0.9) * np.diag([1, np.exp(0.4j)]), np.sqrt(0.1) * np.array([[0, np.exp(0.3j)], [np.exp(-1.1j), 0]])]
+    assert gb.gate_shape(_superop(depol)) == "RPAR2"
+    assert gb.gate_shape(_superop(ampdamp)) == "RPAR2"
+    assert gb.gate_shape(_superop(phasedamp)) == "DIAG2"
+    assert gb.gate_shape(_superop(phased)) == "PAR2"
+    rng = np.random.default_rng(1)
+    assert gb.gate_shape(_superop(I.random_kraus(rng, 3))) == "DENSE2"
+    with pytest.raises(ValueError):
+        gb.gate_shape(np.zeros((2, 3)))
+    with pytest.raises(gb.GbvqcError):
+        gb.gate_shape(np.eye(8))
