@@ -257,12 +257,6 @@ static int channel_kraus_k(const orc_op *op, cplx *K /* up to 256 entries */, in
     }
 }
 
-static int channel_kraus(const orc_op *op, cplx *K)
-{
-    int k;
-    return channel_kraus_k(op, K, &k);
-}
-
 /* ------------------------------------------------------------ state evolution */
 
 /* Eq. (3) / Eq. (twoqubitgate) / Algorithm 1 for k qubits: psi <- M acting on qs. */

@@ -105,19 +105,6 @@ static double shape_flops(int sh)
     }
 }
 
-static double ftype_flops(int ft)
-{
-    switch (ft) {
-    case FT_DENSE1: return 14;
-    case FT_DENSE2: return 30;
-    case FT_CTRL2: return 7;
-    case FT_BLOCK2: return 10;
-    case FT_PAR2: return 14;
-    case FT_PROBE2: return 34;
-    default: return 6;  // real / imaginary / anti-diagonal / diagonal
-    }
-}
-
 // ------------------------------------------------------------------ host matrices
 
 typedef std::vector<cd> Mat;  // row-major d x d
@@ -1428,7 +1415,7 @@ static gbvqc_status ensure_device(gbvqc_circuit *c)
     return GBVQC_OK;
 }
 
-static int default_tile(int dtype) { return 12; }
+static int default_tile(int) { return 12; }
 
 static int ilog2(int x)
 {
@@ -1615,12 +1602,16 @@ static bool fused_supported(const gbvqc_circuit *c, int dtype)
     return c->n_phys >= std::max(fused_nr(dtype, false), fused_nr(dtype, true)) + 1;
 }
 
-static_assert(GBVQC_SHAPE_DENSE1 == SH_DENSE1 && GBVQC_SHAPE_DIAG1 == SH_DIAG1 && GBVQC_SHAPE_ANTI1 == SH_ANTI1 &&
-                  GBVQC_SHAPE_REAL1 == SH_REAL1 && GBVQC_SHAPE_DENSE2 == SH_DENSE2 && GBVQC_SHAPE_DIAG2 == SH_DIAG2 &&
-                  GBVQC_SHAPE_PERM2 == SH_PERM2 && GBVQC_SHAPE_CTRL2 == SH_CTRL2 && GBVQC_SHAPE_BLOCK2 == SH_BLOCK2 &&
-                  GBVQC_SHAPE_IMAG1 == SH_IMAG1 && GBVQC_SHAPE_PAR2 == SH_PAR2 && GBVQC_SHAPE_RPAR2 == SH_RPAR2 &&
-                  GBVQC_SHAPE_CX == SH_CX && GBVQC_SHAPE_CZ == SH_CZ,
+#define GBVQC_SAME(a, b) ((int)(a) == (int)(b))
+static_assert(GBVQC_SAME(GBVQC_SHAPE_DENSE1, SH_DENSE1) && GBVQC_SAME(GBVQC_SHAPE_DIAG1, SH_DIAG1) &&
+                  GBVQC_SAME(GBVQC_SHAPE_ANTI1, SH_ANTI1) && GBVQC_SAME(GBVQC_SHAPE_REAL1, SH_REAL1) &&
+                  GBVQC_SAME(GBVQC_SHAPE_DENSE2, SH_DENSE2) && GBVQC_SAME(GBVQC_SHAPE_DIAG2, SH_DIAG2) &&
+                  GBVQC_SAME(GBVQC_SHAPE_PERM2, SH_PERM2) && GBVQC_SAME(GBVQC_SHAPE_CTRL2, SH_CTRL2) &&
+                  GBVQC_SAME(GBVQC_SHAPE_BLOCK2, SH_BLOCK2) && GBVQC_SAME(GBVQC_SHAPE_IMAG1, SH_IMAG1) &&
+                  GBVQC_SAME(GBVQC_SHAPE_PAR2, SH_PAR2) && GBVQC_SAME(GBVQC_SHAPE_RPAR2, SH_RPAR2) &&
+                  GBVQC_SAME(GBVQC_SHAPE_CX, SH_CX) && GBVQC_SAME(GBVQC_SHAPE_CZ, SH_CZ),
               "public shape codes follow the kernels' shapes");
+#undef GBVQC_SAME
 
 extern "C" gbvqc_status gate_shape(const double *matrix, int dim, int *shape)
 {
@@ -1780,7 +1771,7 @@ extern "C" gbvqc_status apply_circuit(sv_handle sv, circuit_handle c, const doub
 
 // ------------------------------------------------------------------------ gradient
 
-static gbvqc_status ensure_workspace(gbvqc_circuit *c, int dtype, size_t slot_partials)
+static gbvqc_status ensure_workspace(gbvqc_circuit *c, int dtype)
 {
     Workspace &w = c->ws;
     if (w.dtype != dtype) {
@@ -1899,7 +1890,7 @@ extern "C" gbvqc_status grad(circuit_handle c, const double *theta, int n_theta,
         ObsDev od;
         ST_TRY(obs_dev_perm(h, p->perm, &od));
     }
-    ST_TRY(ensure_workspace(c, dtype, 0));
+    ST_TRY(ensure_workspace(c, dtype));
     Workspace &w = c->ws;
     // a gradient slot per variational physical gate: at most two per op (ket and bra)
     if (!w.d_slot_grad) ST_TRY(dev_alloc(&w.d_slot_grad, (size_t)2 * c->n_param_ops + 1));
