@@ -107,6 +107,15 @@ const char *gbvqc_last_error(void);
 /* Library version: major*10000 + minor*100 + patch. */
 int gbvqc_version(void);
 
+/* The library's own device memory (a diagnostic, not a paper operation): bytes it holds
+ * now (states, plans, work buffers, scratch of handles) and the number of device
+ * allocations it has made since the process started (either pointer may be NULL).  Every
+ * allocation of the library is counted; memory of sv_wrap'ed states is the caller's and
+ * is not.  The environment variable GBVQC_DEVICE_ALLOC_LIMIT (read once, a byte count)
+ * caps the live bytes: a request that would exceed it fails with GBVQC_ERR_OOM as a
+ * failed cudaMalloc does (host-side fault injection).  Never fails. */
+gbvqc_status gbvqc_mem_info(int64_t *live_bytes, int64_t *allocations);
+
 /* ---------------------------------------------------------------- states (Sec. II.A) */
 
 /* Allocate a state of n_qubits logical qubits (a density matrix holds 2^(2n) amplitudes)

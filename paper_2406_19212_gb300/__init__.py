@@ -25,7 +25,7 @@ from ._abi import C64, C128, FUSED, PLAIN, GbvqcError
 __all__ = ["C64", "C128", "PLAIN", "FUSED", "GbvqcError", "StateVector", "CircuitHandle",
            "Observable", "sv_alloc", "sv_wrap", "sv_set", "sv_get", "sv_reset",
            "circuit_create", "apply_circuit", "apply_channel", "obs_create", "expect", "grad",
-           "grad_profile", "grad_batch", "batch_create", "BatchHandle", "expect_noalloc", "measure", "sample",
+           "grad_profile", "grad_batch", "batch_create", "BatchHandle", "expect_noalloc", "mem_info", "measure", "sample",
            "gate_shape",
            "VQEEnergy",
            "load"]
@@ -81,14 +81,39 @@ def sv_alloc(n_qubits: int, dtype: int = C64, is_density: bool = False, stream=N
     return StateVector(h.value, n_qubits, dtype, bool(is_density))
 
 
-def sv_wrap(tensor, n_qubits: int, is_density: bool = False, stream=None) -> StateVector:
-    """Wrap a CUDA torch.complex64/complex128 tensor (the library never frees it)."""
+def _check_cuda_amplitudes(tensor, n_amps: int, what: str):
+    """A contiguous CUDA complex64/complex128 tensor of exactly n_amps elements (the kernels
+    index 2^n amplitudes from its data pointer: a shorter or strided tensor would be read
+    out of bounds)."""
     import torch
-    dtype = {torch.complex64: C64, torch.complex128: C128}[tensor.dtype]
+    if not (isinstance(tensor, torch.Tensor) and tensor.is_cuda):
+        raise GbvqcError(_abi.ERR_ARG, f"{what} must be a CUDA tensor")
+    if tensor.dtype not in (torch.complex64, torch.complex128):
+        raise GbvqcError(_abi.ERR_ARG, f"{what} must be complex64 or complex128, not {tensor.dtype}")
+    if not tensor.is_contiguous():
+        raise GbvqcError(_abi.ERR_ARG, f"{what} must be contiguous")
+    if tensor.numel() != n_amps:
+        raise GbvqcError(_abi.ERR_ARG, f"{what} holds {tensor.numel()} amplitudes, expected {n_amps}")
+    return C64 if tensor.dtype == torch.complex64 else C128
+
+
+def sv_wrap(tensor, n_qubits: int, is_density: bool = False, stream=None) -> StateVector:
+    """Wrap a contiguous CUDA torch.complex64/complex128 tensor of 2^n (density: 2^(2n))
+    amplitudes (the library never frees it)."""
+    if not 1 <= n_qubits <= 34:
+        raise GbvqcError(_abi.ERR_ARG, f"qubit count {n_qubits}")
+    dtype = _check_cuda_amplitudes(tensor, 1 << (2 * n_qubits if is_density else n_qubits), "state tensor")
     h = ctypes.c_void_p()
     _abi.check(_abi.lib().sv_wrap(tensor.data_ptr(), n_qubits, dtype, int(is_density),
                                   _stream_ptr(stream), ctypes.byref(h)))
     return StateVector(h.value, n_qubits, dtype, bool(is_density), keep=tensor)
+
+
+def mem_info() -> Tuple[int, int]:
+    """(bytes of device memory the library holds now, device allocations it has made)."""
+    live, count = ctypes.c_int64(), ctypes.c_int64()
+    _abi.check(_abi.lib().gbvqc_mem_info(ctypes.byref(live), ctypes.byref(count)))
+    return live.value, count.value
 
 
 def _np_dtype(dtype: int):
@@ -274,17 +299,27 @@ def sample(sv: StateVector, u) -> np.ndarray:
 def expect_noalloc(psi, n_qubits: int, terms, out, stream=None) -> None:
     """<psi|H|psi> of a CUDA complex64/complex128 tensor without any device allocation.
 
-    For callers that cannot allocate (inside stream capture, under a framework that owns
-    the memory budget): `out` is a caller-provided CUDA float64 tensor of one element,
-    written asynchronously on `stream` (default: torch's current stream).  At most 64
-    terms.  Calls share one fixed scratch array in the library, so calls that overlap on
-    the GPU race; keep them on one stream."""
+    For callers that cannot allocate device memory themselves or through the library
+    (a framework that owns the whole device memory budget through its own pool, a loop
+    that cannot take the device-wide synchronisation of cudaMalloc / cudaFree): `psi` is
+    a contiguous CUDA tensor of 2^n_qubits amplitudes, `out` a caller-provided CUDA
+    float64 tensor (one element is written) on the same device, written asynchronously
+    on `stream` (default: torch's current stream of psi's device).  At most 64 terms.
+    Calls share one fixed scratch array in the library, so calls that overlap on the GPU
+    race; keep them on one stream."""
     import torch
-    dtype = {torch.complex64: C64, torch.complex128: C128}[psi.dtype]
+    if not 1 <= n_qubits <= 34:
+        raise GbvqcError(_abi.ERR_ARG, f"qubit count {n_qubits}")
+    dtype = _check_cuda_amplitudes(psi, 1 << n_qubits, "psi")
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64 and out.numel() >= 1):
+        raise GbvqcError(_abi.ERR_ARG, "out must be a CUDA float64 tensor with at least one element")
+    if out.device != psi.device:
+        raise GbvqcError(_abi.ERR_ARG, f"out is on {out.device}, psi on {psi.device}")
     arr = _abi.pauli_array(terms)
-    s = _stream_ptr(stream if stream is not None else torch.cuda.current_stream(psi.device))
-    _abi.check(_abi.lib().expect_noalloc(psi.data_ptr(), n_qubits, dtype, arr, len(terms), s,
-                                         out.data_ptr()))
+    with torch.cuda.device(psi.device):
+        s = _stream_ptr(stream if stream is not None else torch.cuda.current_stream(psi.device))
+        _abi.check(_abi.lib().expect_noalloc(psi.data_ptr(), n_qubits, dtype, arr, len(terms), s,
+                                             out.data_ptr()))
 
 
 def grad(circ: CircuitHandle, theta, obs: Observable, dtype: int = C64, mode: int = FUSED,

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libgbvqc.so")
 C64, C128 = 0, 1
 PLAIN, FUSED = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT = 1, 2, 3, 4
 
 KIND = {name: i for i, name in enumerate(
     ["X", "Y", "Z", "H", "S", "T", "SX", "SY", "SW", "RX", "RY", "RZ", "CNOT", "CZ", "SWAP",
@@ -103,6 +104,7 @@ def lib() -> ctypes.CDLL:
         "batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)],
         "batch_free": [vp],
         "batch_grad": [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp],
+        "gbvqc_mem_info": [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -122,7 +124,7 @@ def exported_symbols() -> List[str]:
             "sv_set", "sv_get", "sv_info", "circuit_create", "circuit_free", "circuit_set_tiling",
             "circuit_plan_info", "circuit_plan_stats", "circuit_autotune", "apply_circuit", "apply_channel", "obs_create", "obs_free",
             "expect", "grad", "grad_profile", "grad_batch", "batch_create", "batch_free",
-            "batch_grad", "expect_noalloc", "measure", "sample", "gate_shape"]
+            "batch_grad", "expect_noalloc", "measure", "sample", "gate_shape", "gbvqc_mem_info"]
 
 
 # ------------------------------------------------------------------ marshalling

@@ -16,7 +16,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbvqc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "planner.cpp", "kernels_plain.cu", "kernels_reduce.cu", "kernels_fused.cu",
+SOURCES = ["api_state.cu", "api_matrices.cu", "api_circuit.cu", "api_grad.cu", "api_tune.cu",
+           "api_batch.cu", "planner.cpp", "kernels_plain.cu", "kernels_reduce.cu", "kernels_fused.cu",
            "kernels_batch.cu", "noalloc.cu"]
 # sources compiled as several objects (GBVQC_PART = 0 .. parts-1), one per kernel instance
 PARTS = {"kernels_fused.cu": 9, "kernels_batch.cu": 9}

@@ -1,0 +1,311 @@
+// C ABI: apply_circuit (Eq. circuitevolve) and the gradient of Algorithm 2, with
+// CUDA-graph replay of the launch sequence and per-launch profiling.
+#include "api_internal.h"
+
+// ------------------------------------------------------------------- execution
+
+static gbvqc_status ensure_theta(gbvqc_circuit *c)
+{
+    if (!c->ws.d_theta) ST_TRY(dev_alloc(&c->ws.d_theta, c->n_params + 1));
+    return GBVQC_OK;
+}
+
+static gbvqc_status stage_theta(gbvqc_circuit *c, const double *theta, int n_theta, int loc, cudaStream_t s)
+{
+    if (n_theta != c->n_params) return fail(GBVQC_ERR_ARG, "expected %d parameters, got %d", c->n_params, n_theta);
+    if (n_theta > 0 && !theta) return fail(GBVQC_ERR_ARG, "theta is NULL");
+    ST_TRY(ensure_theta(c));
+    if (n_theta > 0)
+        CUDA_TRY(cudaMemcpyAsync(c->ws.d_theta, theta, sizeof(double) * n_theta,
+                                 loc == GBVQC_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    return GBVQC_OK;
+}
+
+double state_bytes(const gbvqc_circuit *c, int dtype) { return double(size_t(1) << c->n_phys) * amp_size(dtype); }
+
+// Four-qubit superoperator (16 rows from record rec) on physical qubits q[0..3].
+static gbvqc_status gate4(gbvqc_circuit *c, int dtype, void *psi, const int *q, int rec, cudaStream_t s)
+{
+    const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
+    return run_k("gate4q", shape_flops(SH_DENSE4) * amps, 2.0 * sb, s, [&] {
+        return launch_gate4(dtype, psi, c->n_phys, q[0], q[1], q[2], q[3], c->d_recs + rec, s);
+    });
+}
+
+static gbvqc_status plain_gate(gbvqc_circuit *c, int dtype, void *psi, const PlainGate &g, int rec, cudaStream_t s)
+{
+    const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
+    if (g.shape == SH_DENSE4) {
+        const int q[4] = {g.q0, g.q1, g.q2, g.q3};
+        return gate4(c, dtype, psi, q, rec, s);
+    }
+    const bool one = shape_qubits(g.shape) == 1;
+    // complex64 runs CNOT through the controlled-2x2 kernel (launch_gate)
+    const int fsh = g.shape == SH_CX && dtype == GBVQC_C64 ? SH_CTRL2 : g.shape;
+    return run_k(one ? "gate1q" : "gate2q", shape_flops(fsh) * amps, (g.shape == SH_CTRL2 || g.shape == SH_CX ? 1.0 : g.shape == SH_CZ ? 0.5 : 2.0) * sb, s,
+                 [&] { return launch_gate(dtype, psi, c->n_phys, g.shape, g.q0, g.q1, c->d_recs + rec, s); });
+}
+
+static gbvqc_status run_plain_forward(gbvqc_circuit *c, int dtype, void *psi, cudaStream_t s)
+{
+    for (const PlainGate &g : c->plain) ST_TRY(plain_gate(c, dtype, psi, g, g.rec_f, s));
+    return GBVQC_OK;
+}
+
+// Matrix images of the plan's forward (and reverse) unit lists from this step's records.
+static gbvqc_status gather_images(gbvqc_circuit *c, DevPlan *p, int dtype, bool with_rev, cudaStream_t s)
+{
+    return run_k("gather_units", 0, 0, s, [&] {
+        return launch_gather_units(dtype, p->d_funits, (int)p->p.funits.size(), p->d_fimg, p->d_runits,
+                                   with_rev ? (int)p->p.runits.size() : 0, p->d_rimg, c->d_recs, s);
+    });
+}
+
+static gbvqc_status run_fused_forward(gbvqc_circuit *c, DevPlan *p, int dtype, void *psi, cudaStream_t s)
+{
+    const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
+    const FusedDev fd{p->d_fwd, p->d_fsubs, p->d_fgates, p->d_fents, p->d_funits, c->d_recs, p->d_fimg};
+    for (size_t i = 0; i < p->p.fwd.size(); i++) {
+        if (p->p.barrier[i] >= 0) {  // two-qubit channel between the tile passes
+            const PGate &g = p->p.barrier_gates[p->p.barrier[i]];
+            ST_TRY(gate4(c, dtype, psi, g.q, g.rec_f, s));
+            continue;
+        }
+        ST_TRY(run_k("fused_forward", p->p.fwd_flops[i] * amps, 2 * sb, s, [&] {
+            return launch_fused_forward(dtype, psi, fd, (int)i, p->p.fwd[i], p->fwd_smem[i], s);
+        }));
+    }
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status apply_circuit(sv_handle sv, circuit_handle c, const double *theta, int n_theta, int theta_loc,
+                                      int mode)
+{
+    if (!sv || !c) return fail(GBVQC_ERR_ARG, "NULL argument");
+    if (sv->n_log != c->n_log || sv->density != c->density)
+        return fail(GBVQC_ERR_ARG, "state (%d qubits, density %d) does not match circuit (%d, %d)", sv->n_log,
+                    sv->density, c->n_log, c->density);
+    if (mode != GBVQC_MODE_PLAIN && mode != GBVQC_MODE_FUSED) return fail(GBVQC_ERR_ARG, "mode %d", mode);
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t s = sv->stream;
+    ST_TRY(ensure_device(c));
+    ST_TRY(stage_theta(c, theta, n_theta, theta_loc, s));
+    CUDA_TRY(launch_materialize(c->d_dyn, (int)c->dyn.size(), c->ws.d_theta, c->d_recs, s));
+    if (mode == GBVQC_MODE_FUSED && fused_supported(c, sv->dtype)) {
+        DevPlan *p = nullptr;
+        ST_TRY(get_plan(c, sv->dtype, false, &p));
+        ST_TRY(gather_images(c, p, sv->dtype, false, s));
+        return run_fused_forward(c, p, sv->dtype, sv->data, s);
+    }
+    return run_plain_forward(c, sv->dtype, sv->data, s);
+}
+
+// ------------------------------------------------------------------------ gradient
+
+static gbvqc_status ensure_workspace(gbvqc_circuit *c, int dtype)
+{
+    Workspace &w = c->ws;
+    if (w.dtype != dtype) {
+        free_graphs(c);
+        dev_free(w.phi);
+        dev_free(w.psi);
+        w.phi = w.psi = nullptr;
+        size_t bytes = (size_t(1) << c->n_phys) * amp_size(dtype);
+        ST_TRY(dev_alloc((unsigned char **)&w.phi, bytes));
+        ST_TRY(dev_alloc((unsigned char **)&w.psi, bytes));
+        w.dtype = dtype;
+    }
+    ST_TRY(ensure_theta(c));
+    if (!w.d_energy) ST_TRY(dev_alloc(&w.d_energy, 1));
+    if (!w.d_grad) ST_TRY(dev_alloc(&w.d_grad, c->n_params + 1));
+    if (!w.d_red) ST_TRY(dev_alloc(&w.d_red, kMaxRedBlocks));
+    if (!w.d_counter) {
+        ST_TRY(dev_alloc(&w.d_counter, 1));
+        CUDA_TRY(cudaMemset(w.d_counter, 0, sizeof(unsigned)));
+    }
+    return GBVQC_OK;
+}
+
+// The whole gradient evaluation as a stream-ordered launch sequence (capturable).
+static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int mode, DevPlan *p, cudaStream_t s)
+{
+    Workspace &w = c->ws;
+    RedScratch red{w.d_red, w.d_counter};
+    const bool fused = mode == GBVQC_MODE_FUSED && p;
+    const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
+    ST_TRY(run_k("materialize", 0, 0, s, [&] {
+        return launch_materialize(c->d_dyn, (int)c->dyn.size(), w.d_theta, c->d_recs, s);
+    }));
+    if (fused) ST_TRY(gather_images(c, p, dtype, true, s));
+    ST_TRY(run_k("zero_state", 0, sb, s, [&] { return launch_zero_state(dtype, w.phi, c->n_phys, s); }));
+    if (fused) ST_TRY(run_fused_forward(c, p, dtype, w.phi, s));
+    else ST_TRY(run_plain_forward(c, dtype, w.phi, s));
+    // energy and adjoint seed
+    if (c->density) {
+        const DensMap &m = fused ? c->map_grad : c->map_std;
+        ST_TRY(run_k("density_expect", 0, 0, s, [&] {
+            return launch_density_expect(dtype, w.phi, c->n_log, m, h->dev(), red, w.d_energy, s);
+        }));
+        ST_TRY(run_k("density_seed", 0, sb, s, [&] {
+            return launch_density_seed(dtype, w.psi, c->n_log, m, h->dev(), s);
+        }));
+    } else {
+        ObsDev od;  // in the plan's gradient layout (copies made before any capture)
+        ST_TRY(obs_dev_perm(h, fused ? p->perm : std::vector<int8_t>(), &od));
+        ST_TRY(run_k("pauli_expect_seed", (8.0 * h->groups.size() + 4) * amps, 2 * sb, s, [&] {
+            return launch_pauli_expect(dtype, w.phi, w.psi, c->n_phys, od, red, w.d_energy, s);
+        }));
+    }
+    if (fused) {
+        const int tiles = 1 << (c->n_phys - p->p.t);
+        const FusedDev fd{p->d_rev, p->d_rsubs, p->d_rgates, p->d_rents, p->d_runits, c->d_recs, p->d_rimg};
+        for (int i = (int)p->p.rev.size() - 1; i >= 0; i--) {
+            if (p->p.barrier[i] >= 0) {  // Phi <- S^-1 Phi, Psi <- S^dag Psi (no parameters)
+                const PGate &g = p->p.barrier_gates[p->p.barrier[i]];
+                ST_TRY(gate4(c, dtype, w.phi, g.q, g.rec_i, s));
+                ST_TRY(gate4(c, dtype, w.psi, g.q, g.rec_a, s));
+                continue;
+            }
+            ST_TRY(run_k("fused_reverse", p->p.rev_flops[i] * amps, 4 * sb, s, [&] {
+                return launch_fused_reverse(dtype, w.phi, w.psi, fd, i, p->p.rev[i], p->rev_smem[i],
+                                            w.d_slot_partials, tiles, s);
+            }));
+        }
+        ST_TRY(run_k("reduce_slots", 0, 0, s, [&] {
+            return launch_reduce_slots(w.d_slot_partials, p->p.n_slots, tiles, tiles, w.d_slot_grad, s);
+        }));
+        ST_TRY(run_k("accumulate", 0, 0, s, [&] {
+            return launch_accumulate(w.d_slot_grad, p->d_csr_ptr, p->d_csr_slots, c->n_params, w.d_grad, s);
+        }));
+    } else {
+        // Algorithm 2: Phi <- Q^-1 Phi; g = scale Re <Psi|dQ|Phi>; Psi <- Q^-1 Psi (Q^dag for channels)
+        for (int j = (int)c->plain.size() - 1; j >= 0; j--) {
+            const PlainGate &g = c->plain[j];
+            ST_TRY(plain_gate(c, dtype, w.phi, g, g.rec_i, s));
+            if (g.slot >= 0)
+                ST_TRY(run_k("dot_derivative", (shape_flops(g.der_k == 1 ? SH_DENSE1 : SH_DENSE2) + 4) * amps, 2 * sb, s,
+                             [&] {
+                                 return launch_dot_matrix(dtype, w.psi, w.phi, c->n_phys, g.der_k, g.dq0, g.dq1,
+                                                          c->d_recs + g.rec_d, g.gscale, red, w.d_slot_grad + g.slot, s);
+                             }));
+            for (int e = 0; e < g.n_extra; e++)
+                ST_TRY(run_k("dot_derivative", (shape_flops(SH_DENSE2) + 4) * amps, 2 * sb, s, [&] {
+                    return launch_dot_matrix(dtype, w.psi, w.phi, c->n_phys, g.der_k, g.dq0, g.dq1,
+                                             c->d_recs + g.ex_rec[e], g.gscale, red, w.d_slot_grad + g.ex_slot[e], s);
+                }));
+            ST_TRY(plain_gate(c, dtype, w.psi, g, g.rec_a, s));
+        }
+        ST_TRY(run_k("accumulate", 0, 0, s, [&] {
+            return launch_accumulate(w.d_slot_grad, c->d_plain_ptr, c->d_plain_slots, c->n_params, w.d_grad, s);
+        }));
+    }
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status grad(circuit_handle c, const double *theta, int n_theta, obs_handle h, int dtype, int mode,
+                             int ptr_loc, void *stream, double *energy, double *grad_out)
+{
+    if (!c || !h || !energy || (!grad_out && c->n_params > 0)) return fail(GBVQC_ERR_ARG, "NULL argument");
+    if (dtype != GBVQC_C64 && dtype != GBVQC_C128) return fail(GBVQC_ERR_ARG, "dtype %d", dtype);
+    if (mode != GBVQC_MODE_PLAIN && mode != GBVQC_MODE_FUSED) return fail(GBVQC_ERR_ARG, "mode %d", mode);
+    if (ptr_loc != GBVQC_PTR_HOST && ptr_loc != GBVQC_PTR_DEVICE) return fail(GBVQC_ERR_ARG, "ptr_loc %d", ptr_loc);
+    if (h->n_qubits != c->n_log) return fail(GBVQC_ERR_ARG, "observable has %d qubits, circuit %d", h->n_qubits, c->n_log);
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    ST_TRY(ensure_device(c));
+    ST_TRY(ensure_obs(h));
+    DevPlan *p = nullptr;
+    if (mode == GBVQC_MODE_FUSED && fused_supported(c, dtype)) ST_TRY(get_plan(c, dtype, true, &p));
+    else mode = GBVQC_MODE_PLAIN;
+    if (p && !c->density) {
+        ObsDev od;
+        ST_TRY(obs_dev_perm(h, p->perm, &od));
+    }
+    ST_TRY(ensure_workspace(c, dtype));
+    Workspace &w = c->ws;
+    // a gradient slot per variational physical gate: at most two per op (ket and bra)
+    if (!w.d_slot_grad) ST_TRY(dev_alloc(&w.d_slot_grad, (size_t)2 * c->n_param_ops + 1));
+    if (p) {
+        size_t need = (size_t)p->p.n_slots * (size_t(1) << (c->n_phys - p->p.t));
+        if (need > c->partials_cap) {
+            free_graphs(c);
+            dev_free(w.d_slot_partials);
+            w.d_slot_partials = nullptr;
+            ST_TRY(dev_alloc(&w.d_slot_partials, std::max<size_t>(need, 1)));
+            c->partials_cap = std::max<size_t>(need, 1);
+        }
+    }
+    ST_TRY(stage_theta(c, theta, n_theta, ptr_loc, s));
+    if (g_prof) {  // grad_profile: plain stream launches with events
+        ST_TRY(enqueue_grad(c, h, dtype, mode, p, s));
+        cudaMemcpyKind k = ptr_loc == GBVQC_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        CUDA_TRY(cudaMemcpyAsync(energy, w.d_energy, sizeof(double), k, s));
+        if (c->n_params > 0) CUDA_TRY(cudaMemcpyAsync(grad_out, w.d_grad, sizeof(double) * c->n_params, k, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return GBVQC_OK;
+    }
+    // replay the captured launch sequence
+    if ((const void *)h != c->graph_obs) {
+        free_graphs(c);
+        c->graph_obs = h;
+    }
+    const int gkey = dtype * 2 + mode;
+    auto it = c->graphs.find(gkey);
+    if (it == c->graphs.end()) {
+        cudaGraph_t graph = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        gbvqc_status st = enqueue_grad(c, h, dtype, mode, p, c->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (st != GBVQC_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        CUDA_TRY(e);
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CUDA_TRY(e);
+        it = c->graphs.emplace(gkey, exec).first;
+    }
+    CUDA_TRY(cudaGraphLaunch(it->second, s));
+    cudaMemcpyKind kind = ptr_loc == GBVQC_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CUDA_TRY(cudaMemcpyAsync(energy, w.d_energy, sizeof(double), kind, s));
+    if (c->n_params > 0) CUDA_TRY(cudaMemcpyAsync(grad_out, w.d_grad, sizeof(double) * c->n_params, kind, s));
+    if (ptr_loc == GBVQC_PTR_HOST) CUDA_TRY(cudaStreamSynchronize(s));
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status grad_profile(circuit_handle c, const double *theta, int n_theta, obs_handle h, int dtype,
+                                     int mode, void *stream, gbvqc_kernel_stat *stats, int max_stats, int *n_stats)
+{
+    if (!stats || !n_stats || max_stats < 0) return fail(GBVQC_ERR_ARG, "NULL argument");
+    std::vector<ProfRec> recs;
+    std::vector<double> g(c ? std::max(c->n_params, 1) : 1);
+    double e = 0;
+    g_prof = &recs;
+    gbvqc_status st = grad(c, theta, n_theta, h, dtype, mode, GBVQC_PTR_HOST, stream, &e, g.data());
+    g_prof = nullptr;
+    std::vector<gbvqc_kernel_stat> agg;
+    for (ProfRec &r : recs) {
+        float ms = 0;
+        if (st == GBVQC_OK && cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+            st = fail(GBVQC_ERR_CUDA, "event timing failed");
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+        size_t i = 0;
+        while (i < agg.size() && r.name != agg[i].name) i++;
+        if (i == agg.size()) {
+            gbvqc_kernel_stat k{};
+            snprintf(k.name, sizeof k.name, "%s", r.name.c_str());
+            agg.push_back(k);
+        }
+        agg[i].launches++;
+        agg[i].ms += ms;
+        agg[i].alg_flops += r.flops;
+        agg[i].alg_bytes += r.bytes;
+    }
+    if (st != GBVQC_OK) return st;
+    *n_stats = (int)std::min<size_t>(agg.size(), (size_t)max_stats);
+    for (int i = 0; i < *n_stats; i++) stats[i] = agg[i];
+    return GBVQC_OK;
+}

@@ -506,6 +506,10 @@ __global__ void __launch_bounds__(256) k_sample_shots(const typename CTr<R>::T *
     if (shot >= n_shots) return;  // whole warps leave together
     const int64_t dim = int64_t(1) << n, C = int64_t(1) << cbits;
     const double total = incl[m_chunks - 1];
+    // u < 1 makes target < total in round-to-nearest (u <= 1 - 2^-53, and the rounding error
+    // of the product is below half an ulp of total), so the search below always finds a
+    // chunk with target < incl[m]; that chunk has non-zero weight (a zero-weight chunk
+    // repeats incl[m - 1], which would then have satisfied the test already).
     const double target = u[shot] * total;
     int lo = 0, hi = m_chunks - 1;  // least chunk with target < incl[m]
     while (lo < hi) {

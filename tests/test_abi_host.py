@@ -266,3 +266,54 @@ def test_gate_shape_classification_host(lib):
         gb.gate_shape(np.zeros((2, 3)))
     with pytest.raises(gb.GbvqcError):
         gb.gate_shape(np.eye(8))
+
+
+# ------------------------------------------------- status codes and fault injection
+
+def _run_child(code, env_extra):
+    import subprocess
+    import sys
+    env = dict(os.environ)
+    env.update(env_extra)
+    return subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                          timeout=300)
+
+
+def test_allocation_cap_returns_oom(lib):
+    """GBVQC_DEVICE_ALLOC_LIMIT caps the library's device memory: with a cap of 0 bytes
+    every allocation fails with ERR_OOM before any CUDA call (so this runs without a
+    GPU), and the message names the cap."""
+    code = ("import paper_2406_19212_gb300 as gb\n"
+            "from paper_2406_19212_gb300 import inputs as I\n"
+            "try:\n    gb.sv_alloc(4)\nexcept gb.GbvqcError as e:\n    print('sv_alloc', e.status, e)\n"
+            "w = I.plain_10q()\n"
+            "c = gb.circuit_create(w.circuit)\n"
+            "o = gb.obs_create(w.observable, 10)\n"
+            "try:\n    gb.grad(c, w.theta, o)\nexcept gb.GbvqcError as e:\n    print('grad', e.status)\n"
+            "print('mem', gb.mem_info())\n")
+    res = _run_child(code, {"GBVQC_DEVICE_ALLOC_LIMIT": "0"})
+    assert res.returncode == 0, res.stderr
+    lines = res.stdout.splitlines()
+    assert lines[0].startswith("sv_alloc 2 ") and "GBVQC_DEVICE_ALLOC_LIMIT" in lines[0], res.stdout
+    assert "grad 2" in lines, res.stdout
+    assert "mem (0, 0)" in lines, res.stdout
+
+
+def test_no_device_returns_cuda_error(lib):
+    """Without a usable GPU the first device allocation fails inside CUDA: ERR_CUDA."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    expect_status(3, gb.sv_alloc, 4)
+
+
+def test_wrappers_reject_host_tensors(lib):
+    """sv_wrap and expect_noalloc take CUDA tensors only: a host tensor, or anything
+    else, is refused before the library sees a pointer."""
+    import torch
+    psi = torch.zeros(16, dtype=torch.complex64)
+    out = torch.zeros(1, dtype=torch.float64)
+    expect_status(1, gb.sv_wrap, psi, 4)
+    expect_status(1, gb.sv_wrap, np.zeros(16, np.complex64), 4)
+    expect_status(1, gb.expect_noalloc, psi, 4, [(1.0, ((0, "Z"),))], out)
+    expect_status(1, gb.sv_wrap, psi, 0)

@@ -100,6 +100,43 @@ def test_fsim_special_cases():
     np.testing.assert_allclose(F, scipy.linalg.expm(-0.5j * th * XXYY), atol=1e-14)
 
 
+def _zphase_layer(a0, a1):
+    """exp(i (a0 n0 + a1 n1)) on two qubits, n_k the excitation number of qubit k
+    (basis index = bit(q0) + 2 bit(q1)): a single-qubit Z rotation on each qubit, up to
+    a global phase."""
+    return np.diag([1.0, np.exp(1j * a0), np.exp(1j * a1), np.exp(1j * (a0 + a1))])
+
+
+def test_fsim_delta_entries_from_single_qubit_phases():
+    """Pin of the Delta entries of Eq. (FSIM), built from physics rather than from the
+    printed entries.  The five-parameter FSIM is the (theta, phi) core
+    C = exp(-i theta (XX+YY)/2) diag(1, 1, 1, e^{-i phi}) between two layers of single-qubit
+    Z phases, D(a) C D(b) with D(a) = exp(i (a0 n0 + a1 n1)).  In the single-excitation
+    block D(a) C D(b) carries the phases a_i + b_j on entry (i, j) (i, j = 0 for |10>, 1
+    for |01>):
+      - Delta_+ is their mean over the diagonal, (a0 + b0 + a1 + b1) / 2;
+      - Delta_- is half the difference of the two diagonal phases, ((a0 + b0) - (a1 + b1)) / 2;
+      - Delta_-,off is half the difference of the two off-diagonal phases,
+        ((a1 + b0) - (a0 + b1)) / 2;
+    and |11> collects a0 + a1 + b0 + b1 = 2 Delta_+ on top of the core's e^{-i phi}.
+    So, for random a, b, theta, phi, the oracle's FSIM at those Deltas must equal
+    D(a) C D(b) exactly: a sign slip between the off-diagonal entries, between the
+    diagonal ones, or Delta_+ in place of 2 Delta_+ on |11> fails here."""
+    rng = np.random.default_rng(11)
+    XXYY = np.kron(PAULI["X"], PAULI["X"]) + np.kron(PAULI["Y"], PAULI["Y"])
+    for _ in range(8):
+        th, ph = rng.uniform(-3, 3, 2)
+        a0, a1, b0, b1 = rng.uniform(-3, 3, 4)
+        core = scipy.linalg.expm(-0.5j * th * XXYY) @ np.diag([1, 1, 1, np.exp(-1j * ph)])
+        want = _zphase_layer(a0, a1) @ core @ _zphase_layer(b0, b1)
+        dp = (a0 + b0 + a1 + b1) / 2
+        dm = ((a0 + b0) - (a1 + b1)) / 2
+        dmo = ((a1 + b0) - (a0 + b1)) / 2
+        assert len({round(v, 6) for v in (th, ph, dp, dm, dmo)}) == 5
+        F = O.gate_matrix(op("FSIM", (0, 1), fixed=(th, ph, dp, dm, dmo)))
+        np.testing.assert_allclose(F, want, atol=1e-14, rtol=0)
+
+
 @pytest.mark.parametrize("name,strength", [("DEPOL", 0.13), ("AMPDAMP", 0.21),
                                            ("PHASEDAMP", 0.4)])
 def test_kraus_completeness(name, strength):
@@ -521,3 +558,16 @@ def test_noisy_fsim_gradient_matches_shift_rules():
         assert g[j] == pytest.approx(O.finite_difference_grad(circ, theta, terms, [j], h=1e-5)[0], abs=1e-8)
     for j in (0, 6):   # the rotations, by the two-term rule
         assert g[j] == pytest.approx(0.5 * shift(j, np.pi / 2), abs=1e-11)
+
+
+def test_sample_largest_draw_never_returns_zero_weight():
+    """The largest draw u = nextafter(1, 0) with zero-weight amplitudes at the end of the
+    index range returns the last index of non-zero weight: u W stays below W in
+    round-to-nearest, so the least index with u W < CDF(a) exists and has weight."""
+    n = 6
+    rng = np.random.default_rng(4)
+    for last in (0, 5, 37, 62):
+        psi = np.zeros(1 << n, complex)
+        psi[: last + 1] = rng.normal(size=last + 1) + 1j * rng.normal(size=last + 1)
+        got = O.sample(psi, n, [np.nextafter(1.0, 0.0), 0.0])
+        assert got.tolist() == [last, 0]

@@ -4,8 +4,9 @@ It serves callers that cannot allocate device memory (inside CUDA-graph stream c
 or under a framework that owns the memory budget).  The test calls it through the C ABI
 on caller-owned CUDA tensors and checks it against the handle-based `expect`, within
 the tolerances of the other parity tests, on two calls in a row (the fixed scratch
-array is reused, so the second call must see a clean counter), and checks that inputs
-beyond its stated maximum are rejected with an error.
+array is reused, so the second call must see a clean counter), checks that the library
+makes no device allocation during those calls (its allocation counter is unchanged), and
+checks that inputs beyond its stated maximum are rejected with an error.
 """
 import numpy as np
 import pytest
@@ -29,8 +30,10 @@ def test_expect_noalloc_matches_expect(dtype, n):
     out = torch.empty(1, dtype=torch.float64, device="cuda")
     for _ in range(2):
         out.fill_(float("nan"))
+        before = gb.mem_info()
         gb.expect_noalloc(psi, n, terms, out)
         torch.cuda.synchronize()
+        assert gb.mem_info() == before   # the library made no device allocation
         got = float(out.item())
         if dtype == gb.C64:
             assert abs(got - ref) <= 1e-5 * max(1.0, abs(ref))
