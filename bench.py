@@ -5,13 +5,18 @@ One step = one energy + full gradient evaluation (800 parameters) of the 20-qubi
 20-layer Ry.Rz + CZ-brick ansatz with the 39-term transverse-field Ising Hamiltonian:
 gate materialisation, state initialisation, fused forward tile passes, expectation
 fused with the adjoint seed, fused reverse passes (Algorithm 2) and the gradient
-reduction, in complex64 with FP64 reductions.  Inputs (parameters) are resident on
-the device; L2 (129 MB) is flushed by writing a 256 MiB buffer between timed steps.
+reduction, in complex64 with FP64 reductions.  The tile passes are the circuit's
+specialised kernels (GBVQC_MODE_JIT, compiled during set-up, outside the timed region).
+Inputs (parameters) are resident on the device; L2 (129 MB) is flushed by writing a
+256 MiB buffer between timed steps.
 
-Also reported: the end-to-end rate through the host-pointer C-ABI call, the plain
-per-gate complex128 path on the same workload, the gate-sweep HBM bandwidth of the
-28-qubit random circuit (fused tile passes vs one launch per gate), the dominant
-kernel's roofline, clocks sampled during the timed region, and the FP64 CPU oracle.
+Also reported: the end-to-end rate through the host-pointer C-ABI call, the record
+interpreter (GBVQC_MODE_FUSED) and complex128 on the same workload, the plain per-gate
+complex128 path, the 10-qubit plain complex128 configuration, the gate-sweep HBM
+bandwidth of the 28-qubit random circuit (tile passes vs one launch per gate, both
+precisions), the 512-instance batch, the 13-qubit noisy density matrix (both
+precisions), the dominant kernel's roofline, clocks sampled during the timed region,
+and the FP64 CPU oracle.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU (torchrun): every rank runs an independent replica (the single-state path
@@ -51,9 +56,10 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def alu_peak_tflops(sm_mhz: float) -> float:
-    """FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x SM clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def alu_peak_tflops(sm_mhz: float, sms: int) -> float:
+    """FP32 CUDA-core peak: SMs (read from the device) x 128 FP32 lanes x 2 flops (FMA) x
+    SM clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -135,7 +141,7 @@ def max_over_ranks(world, x: float) -> float:
     return float(t.item())
 
 
-KERNEL_SOURCES = ("fused_tile.cuh", "devmath.cuh", "common.cuh", "kernels_fused.cu")
+KERNEL_SOURCES = ("fused_tile.cuh", "devmath.cuh", "common.cuh", "kernels_fused.cu", "jit.cpp")
 
 
 def kernel_src_sha() -> str:
@@ -235,21 +241,28 @@ def run_ours(args, world, rank, local):
     os.environ.setdefault("GBVQC_TUNE_CACHE", "off")
     tile, low, tune_ms = circ.autotune(w.theta, obs, gb.C64)   # set-up, outside the timed region
     dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     stream = torch.cuda.current_stream(dev)
     theta = torch.tensor(w.theta, dtype=torch.float64, device=dev)
     e_out = torch.empty(1, dtype=torch.float64, device=dev)
     g_out = torch.empty(w.circuit.n_params, dtype=torch.float64, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    t0 = time.perf_counter()
+    spec = circ.specialize(gb.C64, True)   # compile the specialised passes (set-up)
+    gb.grad(circ, theta, obs, gb.C64, gb.JIT, stream=stream, out=(e_out, g_out))   # load them
+    torch.cuda.synchronize()
+    spec["setup_s"] = time.perf_counter() - t0
+    MODE = gb.JIT
 
     def step():
-        gb.grad(circ, theta, obs, gb.C64, gb.FUSED, stream=stream, out=(e_out, g_out))
+        gb.grad(circ, theta, obs, gb.C64, MODE, stream=stream, out=(e_out, g_out))
 
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
 
     # kernel-level profile of one evaluation (CUDA events on the launching stream)
-    prof = gb.grad_profile(circ, w.theta, obs, gb.C64, gb.FUSED, stream=stream)
+    prof = gb.grad_profile(circ, w.theta, obs, gb.C64, MODE, stream=stream)
     launches_per_step = sum(v[0] for v in prof.values())
 
     # timed region: per-step events, L2 flushed between steps outside the events
@@ -281,11 +294,11 @@ def run_ours(args, world, rank, local):
     theta_host = torch.from_numpy(np.ascontiguousarray(w.theta)).pin_memory().numpy()
     e_host = torch.empty(1, dtype=torch.float64).pin_memory().numpy()
     g_host = torch.empty(w.circuit.n_params, dtype=torch.float64).pin_memory().numpy()
-    gb.grad(circ, theta_host, obs, gb.C64, gb.FUSED, out=(e_host, g_host))
+    gb.grad(circ, theta_host, obs, gb.C64, MODE, out=(e_host, g_host))
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(n_e2e):
-        gb.grad(circ, theta_host, obs, gb.C64, gb.FUSED, out=(e_host, g_host))
+        gb.grad(circ, theta_host, obs, gb.C64, MODE, out=(e_host, g_host))
     e2e_s = max_over_ranks(world, time.perf_counter() - t0)
     e2e = {"value": n_e2e * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": 8 * w.circuit.n_params,
@@ -297,7 +310,7 @@ def run_ours(args, world, rank, local):
         name, (nl, ms, fl, by) = max(prof.items(), key=lambda kv: kv[1][1])
         avg_s = ms / nl / 1e3
         sm_mhz = pk.get("sm_max_mhz", 2070.0)
-        alu = alu_peak_tflops(sm_mhz)
+        alu = alu_peak_tflops(sm_mhz, sms)
         hbm = pk["hbm_gbs"]
         intensity = fl / by if by else 0.0
         ridge = alu * 1e12 / (hbm * 1e9)
@@ -305,7 +318,7 @@ def run_ours(args, world, rank, local):
         if intensity > ridge:
             roof = {"bound": "alu", "achieved": fl / nl / avg_s / 1e12, "peak": alu,
                     "unit": "TFLOP/s"}
-            roof["peak_note"] = (f"FP32 CUDA cores: 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz "
+            roof["peak_note"] = (f"FP32 CUDA cores: {sms} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz "
                                  f"(derived; HBM {hbm:.0f} GB/s {pk_kind})")
         else:
             roof = {"bound": "hbm", "achieved": by / nl / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
@@ -322,18 +335,24 @@ def run_ours(args, world, rank, local):
         out["kernels"] = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items()}
 
     if rank == 0 and not args.no_extra:
-        # plain per-gate complex128 path on the same workload (the reference mode)
-        gb.grad(circ, w.theta, obs, gb.C128, gb.PLAIN)
-        torch.cuda.synchronize()
-        n_plain = 3
-        t0 = time.perf_counter()
-        for _ in range(n_plain):
-            gb.grad(circ, theta, obs, gb.C128, gb.PLAIN, stream=stream, out=(e_out, g_out))
-        torch.cuda.synchronize()
-        plain_rate = n_plain / (time.perf_counter() - t0)
+        def rate(dtype, mode, reps):
+            gb.grad(circ, theta, obs, dtype, mode, stream=stream, out=(e_out, g_out))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                gb.grad(circ, theta, obs, dtype, mode, stream=stream, out=(e_out, g_out))
+            torch.cuda.synchronize()
+            return reps / (time.perf_counter() - t0)
+        # the same workload through the record interpreter, in complex128, and per gate
+        out["interpreter_c64"] = {"value": rate(gb.C64, gb.FUSED, 50), "unit": UNIT,
+                                  "mode": "fused tile passes, record interpreter (GBVQC_MODE_FUSED)"}
+        circ.specialize(gb.C128, True)
+        out["jit_c128"] = {"value": rate(gb.C128, gb.JIT, 20), "unit": UNIT,
+                           "mode": "specialised tile passes, complex128 sweeps"}
+        plain_rate = rate(gb.C128, gb.PLAIN, 3)
         out["plain_c128"] = {"value": plain_rate, "unit": UNIT,
                              "speedup_fused_c64": value / world / plain_rate}
-
+        out["plain_10q"] = plain10_rate(gb, I, torch, dev, stream)
         out["sweep"] = gate_sweep(gb, I, torch, dev, stream, pk)
         out["batch"] = batch_rate(gb, I, torch)
         out["noisy"] = noisy_rate(gb, I, torch)
@@ -349,7 +368,9 @@ def run_ours(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "qubits": 20, "params": w.circuit.n_params,
-                       "mode": "fused tile passes, CUDA-graph replay, device pointers",
+                       "mode": "specialised fused tile passes (GBVQC_MODE_JIT), CUDA-graph replay, "
+                               "device pointers",
+                       "specialised": spec,
                        "tiling": {"tile_qubits": tile, "low_qubits": low, "autotuned": True},
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
@@ -361,42 +382,80 @@ def run_ours(args, world, rank, local):
 
 def gate_sweep(gb, I, torch, dev, stream, pk, rows=4, cols=7):
     """Random circuit on a rows x cols grid (20 cycles; 4x7 = 28 qubits) applied in
-    complex64: fused tile passes vs one launch per gate; GB/s = algorithmic bytes (one
-    read + one write of the state per pass or per gate) / time."""
+    complex64 and complex128: specialised tile passes, the record interpreter's tile
+    passes and one launch per gate; GB/s = algorithmic bytes (one read + one write of the
+    state per pass or per gate) / time."""
     n = rows * cols
     w = I.grid_rqc(rows, cols, 20, 1)
     circ = gb.circuit_create(w.circuit)
-    passes, _, tq = circ.plan_info()
-    state = torch.zeros(1 << n, dtype=torch.complex64, device=dev)
-    state[0] = 1
-    sv = gb.sv_wrap(state, n, stream=stream)
     res = {"workload": f"rqc_{rows}x{cols}_c20: {n} qubits, 20 cycles of sqrt(X/Y/W) + FSIM couplers, "
-                       f"{len(w.circuit.ops)} gates, complex64 ({(8 << n) >> 20} MiB state)",
-           "tile_qubits": tq, "fused_passes": passes}
-    for mode, key in ((gb.FUSED, "fused"), (gb.PLAIN, "plain")):
-        gb.apply_circuit(sv, circ, (), mode)
+                       f"{len(w.circuit.ops)} gates, complex64 ({(8 << n) >> 20} MiB state) and complex128 "
+                       f"({(16 << n) >> 20} MiB)"}
+    for dtype, dname, tdt, amp in ((gb.C64, "", torch.complex64, 8), (gb.C128, "c128_", torch.complex128, 16)):
+        stats = circ.plan_stats(dtype, False)
+        passes, tq = stats["passes"], stats["tile_qubits"]
+        res[f"{dname}tile_qubits"] = tq
+        res[f"{dname}fused_passes"] = passes
+        circ.specialize(dtype, False)
+        state = torch.zeros(1 << n, dtype=tdt, device=dev)
+        state[0] = 1
+        sv = gb.sv_wrap(state, n, stream=stream)
+        modes = [(gb.JIT, "fused"), (gb.FUSED, "interp"), (gb.PLAIN, "plain")]
+        for mode, key in modes:
+            gb.apply_circuit(sv, circ, (), mode)
+            torch.cuda.synchronize()
+            reps = 3 if mode != gb.PLAIN else 1
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                gb.apply_circuit(sv, circ, (), mode)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            sweeps = passes if mode != gb.PLAIN else len(w.circuit.ops)
+            byts = sweeps * 2 * (amp << n)
+            res[f"{dname}{key}_ms"] = ms
+            res[f"{dname}{key}_sweeps"] = sweeps
+            res[f"{dname}{key}_gbs"] = byts / (ms / 1e3) / 1e9
+            res[f"{dname}{key}_frac_hbm"] = res[f"{dname}{key}_gbs"] / pk["hbm_gbs"]
+        res[f"{dname}speedup_fused_vs_plain"] = res[f"{dname}plain_ms"] / res[f"{dname}fused_ms"]
+        # per-gate sweep bytes the fused passes stand in for, over the fused time
+        res[f"{dname}fused_effective_gbs"] = len(w.circuit.ops) * 2 * (amp << n) / (res[f"{dname}fused_ms"] / 1e3) / 1e9
+        sv.free()
+        del state
+        torch.cuda.empty_cache()
+    res["mode"] = "fused = specialised tile passes (GBVQC_MODE_JIT); interp = record interpreter"
+    return res
+
+
+def plain10_rate(gb, I, torch, dev, stream):
+    """The 10-qubit plain configuration: Rx.Rz.Rx + CNOT ladder, 4 layers, 120 angles,
+    energy + full gradient in complex128 through the per-gate path (one launch per gate)
+    and through the specialised tile passes."""
+    w = I.plain_10q()
+    c = gb.circuit_create(w.circuit)
+    obs = gb.obs_create(w.observable, 10)
+    theta = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+    e = torch.empty(1, dtype=torch.float64, device=dev)
+    g = torch.empty(w.circuit.n_params, dtype=torch.float64, device=dev)
+    res = {"workload": "plain_10q: 10 qubits, 4 layers Rx.Rz.Rx + CNOT ladder, 120 angles, "
+                       "H = sum Z_iZ_i+1 + 0.5 sum X_i (19 terms), complex128"}
+    for mode, key in ((gb.PLAIN, "plain"), (gb.JIT, "fused")):
+        for _ in range(3):
+            gb.grad(c, theta, obs, gb.C128, mode, stream=stream, out=(e, g))
         torch.cuda.synchronize()
-        reps = 3 if mode == gb.FUSED else 1
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
+        reps = 50
         a.record(stream)
         for _ in range(reps):
-            gb.apply_circuit(sv, circ, (), mode)
+            gb.grad(c, theta, obs, gb.C128, mode, stream=stream, out=(e, g))
         b.record(stream)
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / reps
-        sweeps = passes if mode == gb.FUSED else len(w.circuit.ops)
-        byts = sweeps * 2 * (8 << n)
         res[f"{key}_ms"] = ms
-        res[f"{key}_sweeps"] = sweeps
-        res[f"{key}_gbs"] = byts / (ms / 1e3) / 1e9
-        res[f"{key}_frac_hbm"] = res[f"{key}_gbs"] / pk["hbm_gbs"]
-    res["speedup_fused_vs_plain"] = res["plain_ms"] / res["fused_ms"]
-    # per-gate sweep bytes the fused passes stand in for, over the fused time
-    res["fused_effective_gbs"] = len(w.circuit.ops) * 2 * (8 << n) / (res["fused_ms"] / 1e3) / 1e9
-    sv.free()
-    del state
-    torch.cuda.empty_cache()
+        res[f"{key}_evals_per_s"] = 1e3 / ms
     return res
 
 
@@ -429,16 +488,18 @@ def batch_rate(gb, I, torch):
 
 
 def noisy_rate(gb, I, torch):
-    """13-qubit noisy density matrix (26 vectorised qubits): energy + 312-parameter gradient."""
+    """13-qubit noisy density matrix (26 vectorised qubits): energy + 312-parameter gradient
+    with specialised tile passes in complex64 and complex128, and per gate in complex128."""
     w = I.noisy_13q()
     c = gb.circuit_create(w.circuit)
     obs = gb.obs_create(w.observable, 13)
     res = {"workload": "noisy_13q_hea8: density matrix, 8 layers Rx.Rz.Rx + CNOT, depolarising + amplitude "
                        "damping, 312 parameters, 2^26 amplitudes"}
-    for dtype, mode, key in ((gb.C64, gb.FUSED, "fused_c64"), (gb.C128, gb.PLAIN, "plain_c128")):
+    for dtype, mode, key in ((gb.C64, gb.JIT, "fused_c64"), (gb.C128, gb.JIT, "fused_c128"),
+                             (gb.C128, gb.PLAIN, "plain_c128")):
         gb.grad(c, w.theta, obs, dtype, mode)
         torch.cuda.synchronize()
-        reps = 3 if mode == gb.FUSED else 1
+        reps = 3 if mode != gb.PLAIN else 1
         t0 = time.perf_counter()
         for _ in range(reps):
             gb.grad(c, w.theta, obs, dtype, mode)
@@ -454,17 +515,18 @@ def heisenberg_rate(gb, I, torch, dev, stream):
     c = gb.circuit_create(w.circuit)
     obs = gb.obs_create(w.observable, 20)
     c.autotune(w.theta, obs, gb.C64)
+    c.specialize(gb.C64, True)
     theta = torch.tensor(w.theta, dtype=torch.float64, device=dev)
     e = torch.empty(1, dtype=torch.float64, device=dev)
     g = torch.empty(w.circuit.n_params, dtype=torch.float64, device=dev)
     for _ in range(3):
-        gb.grad(c, theta, obs, gb.C64, gb.FUSED, stream=stream, out=(e, g))
+        gb.grad(c, theta, obs, gb.C64, gb.JIT, stream=stream, out=(e, g))
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     reps = 20
     a.record(stream)
     for _ in range(reps):
-        gb.grad(c, theta, obs, gb.C64, gb.FUSED, stream=stream, out=(e, g))
+        gb.grad(c, theta, obs, gb.C64, gb.JIT, stream=stream, out=(e, g))
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps

@@ -46,7 +46,12 @@ typedef enum {
 } gbvqc_status;
 
 enum { GBVQC_C64 = 0, GBVQC_C128 = 1 };            /* amplitude dtype                */
-enum { GBVQC_MODE_PLAIN = 0, GBVQC_MODE_FUSED = 1 }; /* one launch per gate / tiled  */
+enum { GBVQC_MODE_PLAIN = 0,  /* one launch per gate                                     */
+       GBVQC_MODE_FUSED = 1,  /* tile passes run by the record interpreter                */
+       GBVQC_MODE_JIT = 2     /* tile passes specialised to the circuit: the first call per
+                                 circuit, dtype and tiling compiles them (NVRTC, seconds;
+                                 cached on disk, see grad), later calls only launch      */
+};
 enum { GBVQC_PTR_HOST = 0, GBVQC_PTR_DEVICE = 1 };   /* where theta/outputs live      */
 
 /* Operation kinds (paper Sec. II.B).  Rotations: Rx = [[c,-is],[-is,c]],
@@ -172,6 +177,19 @@ gbvqc_status circuit_set_tiling(circuit_handle c, int tile_qubits, int low_qubit
  * re-timed (*best_ms is then the cached time).  theta (host) only feeds the timing runs. */
 gbvqc_status circuit_autotune(circuit_handle c, const double *theta, int n_theta, obs_handle h, int dtype,
                               void *stream, int *best_tile, int *best_low, double *best_ms);
+
+/* Specialise the fused tile passes of the circuit to its structure (GBVQC_MODE_JIT) ahead
+ * of time: generate the CUDA source of every pass of the plan for dtype (the gradient plan
+ * and both sweeps with for_grad = 1, else the forward passes of apply_circuit's plan) and
+ * compile it with NVRTC for sm_103a into the on-disk cache, so that the first JIT-mode call
+ * only loads the modules.  Host only: needs no GPU.  The cache is the directory named by
+ * GBVQC_JIT_CACHE (default $HOME/.cache/gbvqc/jit; "off" disables it, and then this call
+ * only checks that the sources compile).  *n_kernels = passes specialised, *n_cached = of
+ * them found in the cache, *seconds = compile wall time (any pointer may be NULL).
+ * Errors: ERR_ARG; ERR_UNSUPPORTED (too few qubits for tiles); ERR_CUDA if NVRTC cannot be
+ * loaded or a source fails to compile (the message carries NVRTC's log). */
+gbvqc_status circuit_specialize(circuit_handle c, int dtype, int for_grad, int *n_kernels, int *n_cached,
+                                double *seconds);
 
 /* Report the fused schedule: number of tile passes and of gate records it holds. */
 gbvqc_status circuit_plan_info(circuit_handle c, int *n_passes, int *n_gates, int *tile_qubits);

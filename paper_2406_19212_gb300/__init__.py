@@ -20,9 +20,9 @@ from typing import Optional, Sequence, Tuple
 import numpy as np
 
 from . import _abi
-from ._abi import C64, C128, FUSED, PLAIN, GbvqcError
+from ._abi import C64, C128, FUSED, JIT, PLAIN, GbvqcError
 
-__all__ = ["C64", "C128", "PLAIN", "FUSED", "GbvqcError", "StateVector", "CircuitHandle",
+__all__ = ["C64", "C128", "PLAIN", "FUSED", "JIT", "GbvqcError", "StateVector", "CircuitHandle",
            "Observable", "sv_alloc", "sv_wrap", "sv_set", "sv_get", "sv_reset",
            "circuit_create", "apply_circuit", "apply_channel", "obs_create", "expect", "grad",
            "grad_profile", "grad_batch", "batch_create", "BatchHandle", "expect_noalloc", "mem_info", "measure", "sample",
@@ -166,6 +166,14 @@ class CircuitHandle:
 
     STAT_NAMES = ("tile_qubits", "passes", "fwd_subruns", "fwd_gates", "fwd_phase_blocks",
                   "rev_subruns", "grad_slots", "fwd_smem_max", "rev_smem_max", "phys_gates")
+
+    def specialize(self, dtype: int = C64, for_grad: bool = True) -> dict:
+        """Compile the plan's specialised tile passes (mode JIT) into the on-disk cache
+        (host only); returns the number of kernels, how many were cached, and seconds."""
+        nk, nc, sec = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _abi.check(_abi.lib().circuit_specialize(self.handle, dtype, int(for_grad), ctypes.byref(nk),
+                                                 ctypes.byref(nc), ctypes.byref(sec)))
+        return {"kernels": nk.value, "cached": nc.value, "seconds": sec.value}
 
     def plan_stats(self, dtype: int = C64, for_grad: bool = False) -> dict:
         """Host-only statistics of the fused schedule (no GPU needed)."""

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgbvqc.so")
 
 C64, C128 = 0, 1
-PLAIN, FUSED = 0, 1
+PLAIN, FUSED, JIT = 0, 1, 2
 PTR_HOST, PTR_DEVICE = 0, 1
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT = 1, 2, 3, 4
 
@@ -88,6 +88,8 @@ def lib() -> ctypes.CDLL:
         "circuit_autotune": [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)],
         "circuit_plan_stats": [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
+        "circuit_specialize": [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_double)],
         "gate_shape": [dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
         "apply_circuit": [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
         "apply_channel": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, ctypes.c_int],
@@ -124,7 +126,7 @@ def exported_symbols() -> List[str]:
             "sv_set", "sv_get", "sv_info", "circuit_create", "circuit_free", "circuit_set_tiling",
             "circuit_plan_info", "circuit_plan_stats", "circuit_autotune", "apply_circuit", "apply_channel", "obs_create", "obs_free",
             "expect", "grad", "grad_profile", "grad_batch", "batch_create", "batch_free",
-            "batch_grad", "expect_noalloc", "measure", "sample", "gate_shape", "gbvqc_mem_info"]
+            "batch_grad", "expect_noalloc", "measure", "sample", "gate_shape", "gbvqc_mem_info", "circuit_specialize"]
 
 
 # ------------------------------------------------------------------ marshalling

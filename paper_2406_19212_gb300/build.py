@@ -17,8 +17,12 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbvqc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api_state.cu", "api_matrices.cu", "api_circuit.cu", "api_grad.cu", "api_tune.cu",
-           "api_batch.cu", "planner.cpp", "kernels_plain.cu", "kernels_reduce.cu", "kernels_fused.cu",
-           "kernels_batch.cu", "noalloc.cu"]
+           "api_batch.cu", "planner.cpp", "jit.cpp", "kernels_plain.cu", "kernels_reduce.cu",
+           "kernels_fused.cu", "kernels_batch.cu", "noalloc.cu"]
+# device headers the specialised tile passes are compiled from at run time (NVRTC), embedded
+# into the library as strings
+JIT_HEADERS = ["common.cuh", "devmath.cuh", "kernels.h", "fused_tile.cuh"]
+JIT_DELIM = "GBVQC_JIT_SRC"
 # sources compiled as several objects (GBVQC_PART = 0 .. parts-1), one per kernel instance
 PARTS = {"kernels_fused.cu": 9, "kernels_batch.cu": 9}
 
@@ -40,14 +44,36 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(p) for p in paths)
 
 
+def _write_jit_headers() -> str:
+    """_build/jit_headers.cpp: the JIT_HEADERS as raw string literals (rewritten only when
+    their contents change)."""
+    parts = ["// generated by build.py: device headers of the specialised tile passes",
+             "namespace gbvqc {", f"extern const int kJitHeaderCount = {len(JIT_HEADERS)};",
+             "extern const char *const kJitHeaderNames[] = {" + ", ".join(f'"{h}"' for h in JIT_HEADERS) + "};",
+             "extern const char *const kJitHeaderSources[] = {"]
+    for h in JIT_HEADERS:
+        text = open(os.path.join(CSRC, h)).read()
+        if f"){JIT_DELIM}\"" in text:
+            raise RuntimeError(f"{h} contains the raw-string delimiter")
+        parts.append(f'R"{JIT_DELIM}({text}){JIT_DELIM}",')
+    parts += ["};", "}  // namespace gbvqc", ""]
+    out = os.path.join(BUILD, "jit_headers.cpp")
+    body = "\n".join(parts)
+    if not os.path.exists(out) or open(out).read() != body:
+        with open(out, "w") as f:
+            f.write(body)
+    return out
+
+
 def _compile(job, verbose: bool) -> str:
     src, part = job
-    stem = os.path.splitext(src)[0] + (f".p{part}" if part is not None else "")
+    stem = os.path.splitext(os.path.basename(src))[0] + (f".p{part}" if part is not None else "")
     out = os.path.join(BUILD, stem + ".o")
     defs = [f"-DGBVQC_PART={part}"] if part is not None else []
-    cmd = [nvcc()] + _flags() + defs + ["-c", os.path.join(CSRC, src), "-o", out]
+    path = src if os.path.isabs(src) else os.path.join(CSRC, src)
+    cmd = [nvcc()] + _flags() + defs + ["-c", path, "-o", out]
     if src.endswith(".cpp"):
-        cmd = [nvcc(), "-x", "cu"] + _flags() + defs + ["-c", os.path.join(CSRC, src), "-o", out]
+        cmd = [nvcc(), "-x", "cu"] + _flags() + defs + ["-c", path, "-o", out]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     res = subprocess.run(cmd, capture_output=True, text=True)
@@ -63,7 +89,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    jobs = []
+    jobs = [(_write_jit_headers(), None)]
     for s in SOURCES:
         if os.path.exists(os.path.join(CSRC, s)):
             jobs += [(s, p) for p in range(PARTS[s])] if s in PARTS else [(s, None)]

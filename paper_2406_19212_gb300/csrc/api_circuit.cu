@@ -150,6 +150,9 @@ static void free_plan(DevPlan *p)
     dev_free(p->d_fgates); dev_free(p->d_rgates); dev_free(p->d_fents); dev_free(p->d_rents);
     dev_free(p->d_funits); dev_free(p->d_runits); dev_free(p->d_csr_ptr); dev_free(p->d_csr_slots);
     dev_free(p->d_fimg); dev_free(p->d_rimg);
+    dev_free(p->d_ftabs); dev_free(p->d_rtabs); dev_free(p->d_ftabents); dev_free(p->d_rtabents);
+    if (p->jit) jit_free(*p->jit);
+    p->jit.reset();
 }
 
 void free_graphs(gbvqc_circuit *c)
@@ -671,7 +674,7 @@ constexpr int kTwoCtaSmem = 110 * 1024;
 // batch: the plan a batch member runs with (launches shared by all members take the
 // largest member's shared memory, so its passes keep the smaller slot budget that leaves
 // two CTAs per SM; a single circuit takes larger passes, fewer tile loads and stores).
-static gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out, bool batch = false)
+gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out, bool batch)
 {
     int key = dtype * 2 + (grad_layout ? 1 : 0) + (batch ? 4 : 0);
     auto it = c->plans.find(key);
@@ -689,6 +692,7 @@ static gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout,
     opt.elem_bytes = dtype == GBVQC_C64 ? 4 : 8;
     opt.max_slots = batch ? 128 : 512;
     opt.gate_smem = batch ? 40 * 1024 : 64 * 1024;
+    opt.phase_tables = !batch;  // batch members stage matrices without a per-step image
     std::vector<int8_t> perm;
     std::vector<PGate> permuted;
     if (grad_layout && !c->density) perm = choose_grad_layout(pg0, c->n_phys, opt);
@@ -748,6 +752,10 @@ gbvqc_status get_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **o
         ST_TRY(upload(&dp->d_rents, dp->p.rents));
         ST_TRY(upload(&dp->d_funits, dp->p.funits));
         ST_TRY(upload(&dp->d_runits, dp->p.runits));
+        ST_TRY(upload(&dp->d_ftabs, dp->p.ftabs));
+        ST_TRY(upload(&dp->d_rtabs, dp->p.rtabs));
+        ST_TRY(upload(&dp->d_ftabents, dp->p.ftabents));
+        ST_TRY(upload(&dp->d_rtabents, dp->p.rtabents));
         const size_t eb = dtype == GBVQC_C64 ? 4 : 8;
         ST_TRY(dev_alloc((unsigned char **)&dp->d_fimg, std::max<size_t>(1, 8 * eb * dp->p.funits.size())));
         ST_TRY(dev_alloc((unsigned char **)&dp->d_rimg, std::max<size_t>(1, 8 * eb * dp->p.runits.size())));
@@ -829,5 +837,27 @@ extern "C" gbvqc_status circuit_plan_stats(circuit_handle c, int dtype, int for_
                      (int64_t)*std::max_element(p->rev_smem.begin(), p->rev_smem.end()),
                      (int64_t)((for_grad && c->density) ? c->pg_grad.size() : c->pg_std.size())};
     for (int i = 0; i < n_stats && i < 10; i++) stats[i] = v[i];
+    return GBVQC_OK;
+}
+
+extern "C" gbvqc_status circuit_specialize(circuit_handle c, int dtype, int for_grad, int *n_kernels, int *n_cached,
+                                          double *seconds)
+{
+    if (!c) return fail(GBVQC_ERR_ARG, "NULL circuit");
+    if (dtype != GBVQC_C64 && dtype != GBVQC_C128) return fail(GBVQC_ERR_ARG, "dtype %d", dtype);
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!fused_supported(c, dtype)) return fail(GBVQC_ERR_UNSUPPORTED, "too few qubits for tiles");
+    DevPlan *p = nullptr;
+    ST_TRY(get_host_plan(c, dtype, for_grad != 0, &p));
+    std::vector<JitModule> mods;
+    double secs = 0;
+    std::string err;
+    if (!jit_compile(p->p, dtype, for_grad != 0, mods, secs, err))
+        return fail(GBVQC_ERR_CUDA, "specialising the tile passes: %s", err.c_str());
+    int cached = 0;
+    for (const JitModule &m : mods) cached += m.from_cache ? 1 : 0;
+    if (n_kernels) *n_kernels = (int)mods.size();
+    if (n_cached) *n_cached = cached;
+    if (seconds) *seconds = secs;
     return GBVQC_OK;
 }

@@ -55,13 +55,29 @@ static gbvqc_status run_plain_forward(gbvqc_circuit *c, int dtype, void *psi, cu
 // Matrix images of the plan's forward (and reverse) unit lists from this step's records.
 static gbvqc_status gather_images(gbvqc_circuit *c, DevPlan *p, int dtype, bool with_rev, cudaStream_t s)
 {
-    return run_k("gather_units", 0, 0, s, [&] {
-        return launch_gather_units(dtype, p->d_funits, (int)p->p.funits.size(), p->d_fimg, p->d_runits,
-                                   with_rev ? (int)p->p.runits.size() : 0, p->d_rimg, c->d_recs, s);
-    });
+    GatherArgs g{p->d_funits, (int)p->p.funits.size(), p->d_runits, with_rev ? (int)p->p.runits.size() : 0,
+                 p->d_fimg, p->d_rimg, c->d_recs, p->d_ftabs, p->d_rtabs, p->d_ftabents, p->d_rtabents,
+                 (int)p->p.ftabs.size(), with_rev ? (int)p->p.rtabs.size() : 0, p->p.nr_f, p->p.nr_r};
+    return run_k("gather_units", 0, 0, s, [&] { return launch_gather_units(dtype, g, s); });
 }
 
-static gbvqc_status run_fused_forward(gbvqc_circuit *c, DevPlan *p, int dtype, void *psi, cudaStream_t s)
+// Specialised passes of plan p (GBVQC_MODE_JIT): compiled, or loaded from the cache, on
+// first use; with_rev adds the reverse sweep's passes.  Call outside stream capture.
+static gbvqc_status ensure_jit(DevPlan *p, int dtype, bool with_rev)
+{
+    if (p->jit && (!with_rev || !p->jit->rev.empty())) return GBVQC_OK;
+    if (p->jit) jit_free(*p->jit);
+    p->jit.reset(new JitPlan());
+    std::string err;
+    if (!jit_build(p->p, dtype, with_rev, *p->jit, err)) {
+        p->jit.reset();
+        return fail(GBVQC_ERR_CUDA, "specialising the tile passes: %s", err.c_str());
+    }
+    return GBVQC_OK;
+}
+
+static gbvqc_status run_fused_forward(gbvqc_circuit *c, DevPlan *p, int dtype, void *psi, cudaStream_t s,
+                                      bool jit = false)
 {
     const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
     const FusedDev fd{p->d_fwd, p->d_fsubs, p->d_fgates, p->d_fents, p->d_funits, c->d_recs, p->d_fimg};
@@ -69,6 +85,16 @@ static gbvqc_status run_fused_forward(gbvqc_circuit *c, DevPlan *p, int dtype, v
         if (p->p.barrier[i] >= 0) {  // two-qubit channel between the tile passes
             const PGate &g = p->p.barrier_gates[p->p.barrier[i]];
             ST_TRY(gate4(c, dtype, psi, g.q, g.rec_f, s));
+            continue;
+        }
+        if (jit) {
+            const PassDesc &d = p->p.fwd[i];
+            const FusedArgs args{p->d_fwd + i, p->d_fsubs, p->d_fgates, p->d_fents, p->d_funits, c->d_recs,
+                                 p->d_fimg, nullptr, 0};
+            ST_TRY(run_k("fused_forward", p->p.fwd_flops[i] * amps, 2 * sb, s, [&] {
+                return jit_launch(p->jit->fwd[i], psi, nullptr, args, 1u << (d.n - d.t), 1 << (d.t - p->p.nr_f),
+                                  p->fwd_smem[i], s);
+            }));
             continue;
         }
         ST_TRY(run_k("fused_forward", p->p.fwd_flops[i] * amps, 2 * sb, s, [&] {
@@ -85,17 +111,19 @@ extern "C" gbvqc_status apply_circuit(sv_handle sv, circuit_handle c, const doub
     if (sv->n_log != c->n_log || sv->density != c->density)
         return fail(GBVQC_ERR_ARG, "state (%d qubits, density %d) does not match circuit (%d, %d)", sv->n_log,
                     sv->density, c->n_log, c->density);
-    if (mode != GBVQC_MODE_PLAIN && mode != GBVQC_MODE_FUSED) return fail(GBVQC_ERR_ARG, "mode %d", mode);
+    if (mode != GBVQC_MODE_PLAIN && mode != GBVQC_MODE_FUSED && mode != GBVQC_MODE_JIT)
+        return fail(GBVQC_ERR_ARG, "mode %d", mode);
     std::lock_guard<std::mutex> lk(c->mu);
     cudaStream_t s = sv->stream;
     ST_TRY(ensure_device(c));
     ST_TRY(stage_theta(c, theta, n_theta, theta_loc, s));
     CUDA_TRY(launch_materialize(c->d_dyn, (int)c->dyn.size(), c->ws.d_theta, c->d_recs, s));
-    if (mode == GBVQC_MODE_FUSED && fused_supported(c, sv->dtype)) {
+    if (mode != GBVQC_MODE_PLAIN && fused_supported(c, sv->dtype)) {
         DevPlan *p = nullptr;
         ST_TRY(get_plan(c, sv->dtype, false, &p));
+        if (mode == GBVQC_MODE_JIT) ST_TRY(ensure_jit(p, sv->dtype, false));
         ST_TRY(gather_images(c, p, sv->dtype, false, s));
-        return run_fused_forward(c, p, sv->dtype, sv->data, s);
+        return run_fused_forward(c, p, sv->dtype, sv->data, s, mode == GBVQC_MODE_JIT);
     }
     return run_plain_forward(c, sv->dtype, sv->data, s);
 }
@@ -131,14 +159,14 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
 {
     Workspace &w = c->ws;
     RedScratch red{w.d_red, w.d_counter};
-    const bool fused = mode == GBVQC_MODE_FUSED && p;
+    const bool fused = mode != GBVQC_MODE_PLAIN && p, jit = mode == GBVQC_MODE_JIT && p;
     const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
     ST_TRY(run_k("materialize", 0, 0, s, [&] {
         return launch_materialize(c->d_dyn, (int)c->dyn.size(), w.d_theta, c->d_recs, s);
     }));
     if (fused) ST_TRY(gather_images(c, p, dtype, true, s));
     ST_TRY(run_k("zero_state", 0, sb, s, [&] { return launch_zero_state(dtype, w.phi, c->n_phys, s); }));
-    if (fused) ST_TRY(run_fused_forward(c, p, dtype, w.phi, s));
+    if (fused) ST_TRY(run_fused_forward(c, p, dtype, w.phi, s, jit));
     else ST_TRY(run_plain_forward(c, dtype, w.phi, s));
     // energy and adjoint seed
     if (c->density) {
@@ -164,6 +192,16 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
                 const PGate &g = p->p.barrier_gates[p->p.barrier[i]];
                 ST_TRY(gate4(c, dtype, w.phi, g.q, g.rec_i, s));
                 ST_TRY(gate4(c, dtype, w.psi, g.q, g.rec_a, s));
+                continue;
+            }
+            if (jit) {
+                const PassDesc &d = p->p.rev[i];
+                const FusedArgs args{p->d_rev + i, p->d_rsubs, p->d_rgates, p->d_rents, p->d_runits, c->d_recs,
+                                     p->d_rimg, w.d_slot_partials, tiles};
+                ST_TRY(run_k("fused_reverse", p->p.rev_flops[i] * amps, 4 * sb, s, [&] {
+                    return jit_launch(p->jit->rev[i], w.phi, w.psi, args, 1u << (d.n - d.t), 1 << (d.t - p->p.nr_r),
+                                      p->rev_smem[i], s);
+                }));
                 continue;
             }
             ST_TRY(run_k("fused_reverse", p->p.rev_flops[i] * amps, 4 * sb, s, [&] {
@@ -207,7 +245,8 @@ extern "C" gbvqc_status grad(circuit_handle c, const double *theta, int n_theta,
 {
     if (!c || !h || !energy || (!grad_out && c->n_params > 0)) return fail(GBVQC_ERR_ARG, "NULL argument");
     if (dtype != GBVQC_C64 && dtype != GBVQC_C128) return fail(GBVQC_ERR_ARG, "dtype %d", dtype);
-    if (mode != GBVQC_MODE_PLAIN && mode != GBVQC_MODE_FUSED) return fail(GBVQC_ERR_ARG, "mode %d", mode);
+    if (mode != GBVQC_MODE_PLAIN && mode != GBVQC_MODE_FUSED && mode != GBVQC_MODE_JIT)
+        return fail(GBVQC_ERR_ARG, "mode %d", mode);
     if (ptr_loc != GBVQC_PTR_HOST && ptr_loc != GBVQC_PTR_DEVICE) return fail(GBVQC_ERR_ARG, "ptr_loc %d", ptr_loc);
     if (h->n_qubits != c->n_log) return fail(GBVQC_ERR_ARG, "observable has %d qubits, circuit %d", h->n_qubits, c->n_log);
     std::lock_guard<std::mutex> lk(c->mu);
@@ -215,8 +254,12 @@ extern "C" gbvqc_status grad(circuit_handle c, const double *theta, int n_theta,
     ST_TRY(ensure_device(c));
     ST_TRY(ensure_obs(h));
     DevPlan *p = nullptr;
-    if (mode == GBVQC_MODE_FUSED && fused_supported(c, dtype)) ST_TRY(get_plan(c, dtype, true, &p));
-    else mode = GBVQC_MODE_PLAIN;
+    if (mode != GBVQC_MODE_PLAIN && fused_supported(c, dtype)) {
+        ST_TRY(get_plan(c, dtype, true, &p));
+        if (mode == GBVQC_MODE_JIT) ST_TRY(ensure_jit(p, dtype, true));
+    } else {
+        mode = GBVQC_MODE_PLAIN;
+    }
     if (p && !c->density) {
         ObsDev od;
         ST_TRY(obs_dev_perm(h, p->perm, &od));
@@ -249,7 +292,7 @@ extern "C" gbvqc_status grad(circuit_handle c, const double *theta, int n_theta,
         free_graphs(c);
         c->graph_obs = h;
     }
-    const int gkey = dtype * 2 + mode;
+    const int gkey = dtype * 4 + mode;
     auto it = c->graphs.find(gkey);
     if (it == c->graphs.end()) {
         cudaGraph_t graph = nullptr;

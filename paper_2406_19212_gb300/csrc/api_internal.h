@@ -18,6 +18,7 @@
 
 #include "gbvqc.h"
 #include "kernels.h"
+#include "jit.h"
 #include "planner.h"
 
 using namespace gbvqc;
@@ -184,7 +185,10 @@ struct DevPlan {  // a FusedPlan and its device copies (uploaded on first launch
     DEnt *d_fents = nullptr, *d_rents = nullptr;
     MatUnit *d_funits = nullptr, *d_runits = nullptr;
     void *d_fimg = nullptr, *d_rimg = nullptr;  // per-step matrix images of the unit lists
+    TabDesc *d_ftabs = nullptr, *d_rtabs = nullptr;     // register phase tables (table-mode blocks)
+    TabEnt *d_ftabents = nullptr, *d_rtabents = nullptr;
     int *d_csr_ptr = nullptr, *d_csr_slots = nullptr;
+    std::unique_ptr<JitPlan> jit;  // specialised passes (GBVQC_MODE_JIT), built on first use
 };
 
 struct gbvqc_circuit {
@@ -206,7 +210,7 @@ struct gbvqc_circuit {
     std::map<int, std::unique_ptr<DevPlan>> plans;  // key: dtype*2 + (grad layout)
     Workspace ws;
     cudaStream_t cap_stream = nullptr;
-    std::map<int, cudaGraphExec_t> graphs;           // key: dtype*2 + mode
+    std::map<int, cudaGraphExec_t> graphs;           // key: dtype*4 + mode
     const void *graph_obs = nullptr;                 // observable the graphs were captured with
     int n_param_ops = 0;                             // ops driven by a parameter
     size_t partials_cap = 0;                         // doubles in ws.d_slot_partials
@@ -232,7 +236,10 @@ gbvqc_status csr_upload(const std::vector<int> &slot_param, int n_params, int **
 gbvqc_status ensure_device(gbvqc_circuit *c);
 // Largest tile the fused kernels take for dtype.
 int max_tile(int dtype);
-// Fused plan for (dtype, layout) with its device copies; batch: the plan of a batch member.
+// Fused plan for (dtype, layout), host side only (no GPU needed); batch: the plan of a
+// batch member.
+gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out, bool batch = false);
+// The same with its device copies.
 gbvqc_status get_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out, bool batch = false);
 bool fused_supported(const gbvqc_circuit *c, int dtype);
 double state_bytes(const gbvqc_circuit *c, int dtype);

@@ -2,9 +2,21 @@
 // kernels, and materialisation of the theta-dependent rotation matrices (host + device).
 #pragma once
 
+#ifdef __CUDACC_RTC__
+// runtime compilation of specialised tile passes (NVRTC): no host headers
+typedef signed char int8_t;
+typedef short int16_t;
+typedef int int32_t;
+typedef long long int64_t;
+typedef unsigned char uint8_t;
+typedef unsigned short uint16_t;
+typedef unsigned int uint32_t;
+typedef unsigned long long uint64_t;
+#else
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#endif
 
 namespace gbvqc {
 
@@ -300,9 +312,10 @@ struct FGate {               // 32 bytes, staged in shared memory
     int32_t slot;            // X/Y generator: gradient slot (-1 if none); FT_DIAGB: pass-local
                              // block index (its tile-constant phase product in shared memory)
     float coef;              // gradient weight
-    int32_t perm;            // FT_PERM2: source column of output row r in bits 2r, 2r+1;
-                             // FT_DIAGB: entry counts per class after the Z entries:
+    int32_t perm;            // FT_DIAGB: entry counts per class after the Z entries:
                              // tile | local << 8 | register << 16 | pair << 24
+                             // (table mode: tile | local << 8 | mixed CZ << 16);
+                             // FT_PERM2: source column of output row r in bits 2r, 2r+1
     int32_t pad1;
 };
 
@@ -312,6 +325,30 @@ struct FGate {               // 32 bytes, staged in shared memory
 // constant: a factor pair on that register bit), PAIR (two register positions: factor
 // pairs plus a controlled phase on |11>), PAIR_CZ (the |11> sign flip of CZ).
 enum DClass : int8_t { DC_Z = 0, DC_TILE = 1, DC_LOCAL = 2, DC_REG = 3, DC_PAIR = 4, DC_PAIR_CZ = 5 };
+
+// Table mode of a phase block (FGate.flags bit 1): every entry on register positions
+// only (one-qubit phases on a register bit, two-qubit diagonals on two register bits) is
+// multiplied into one table over the 2^NR register indices, the same for every thread
+// of every tile; it is computed once per step (k_phase_tables, FP64 products of the FP64
+// records rounded once) into the pass's matrix image at unit FGate.mat (Psi: mat2), and
+// the kernel multiplies amplitude j by table[j].  The block's DEnt list after its Z
+// entries is then TILE, LOCAL, and MIXCZ entries: CZ between a register position and a
+// constant one, a sign flip of the amplitudes whose register bit is 1 in the threads
+// whose constant bit is 1.  Blocks with any other mixed entry keep the factor-pair form.
+constexpr int FLAG_SEPARATE = 1;  // Psi takes its own phases (a non-unitary block)
+constexpr int FLAG_TABLE = 2;     // table mode
+
+// One register phase table: 2^nbits complex entries at img[off .. off + 2^(nbits+1)) (reals)
+// of the direction's matrix image, the product of TabEnt [ent_begin, ent_begin + n_ent).
+struct TabDesc {
+    int32_t off, nbits, ent_begin, n_ent;
+};
+struct TabEnt {
+    int32_t rec;             // matrix record (its FP64 entries)
+    int8_t k;                // 1: diagonal 2x2 on register bit ca; 2: diagonal 4x4 on (ca, cb)
+    int8_t ca, cb;
+    int8_t pad;
+};
 
 struct DEnt {                // 16 bytes: one diagonal gate or Z generator of an FT_DIAGB
     int8_t k;                // 1 or 2 positions with phases; 3 = Z generator only

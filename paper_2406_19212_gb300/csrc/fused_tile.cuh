@@ -405,6 +405,67 @@ __device__ __forceinline__ void phase_block(const DEnt *ents, int counts, const 
     }
 }
 
+// Bit j of the result: parity of the register bits of j selected by sm (sign pattern of
+// the mixed CZ entries), for the 2^NR register indices.
+template <int NR>
+__device__ __forceinline__ uint32_t parity_bits(uint32_t sm)
+{
+    constexpr uint32_t col[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
+    uint32_t par = 0;
+#pragma unroll
+    for (int k = 0; k < NR; k++)
+        if ((sm >> k) & 1) par ^= col[k];
+    return par;
+}
+
+// Table-mode phase block (FLAG_TABLE): amplitude j is multiplied by c * table[j] * (-1)^(j . sm)
+// with c the product of the tile-constant (c0) and thread-local entries, table the block's
+// register phase table in shared memory (written per step by k_phase_tables) and sm the
+// register bits of the mixed CZ entries whose constant bit is 1 in this thread.  `ents`
+// points after the Z entries; b (if given) takes the same phases.
+template <typename R, int NR>
+__device__ __forceinline__ void phase_table(const DEnt *ents, int counts, const R *smat, int tab, bool second,
+                                            R c0r, R c0i, typename CT<R>::T *a, typename CT<R>::T *b, int base,
+                                            int64_t tilebase)
+{
+    typedef typename CT<R>::T T;
+    const int nt = counts & 255, nl = (counts >> 8) & 255, nm = (counts >> 16) & 255;
+    const DEnt *e = ents + nt;
+    R cr = c0r, ci = c0i;
+    for (int i = 0; i < nl; i++, e++) {  // thread-local constants
+        const R *m = smat + 8 * (second ? e->mat2 : e->mat);
+        const int idx = e->k == 1 ? const_bit<NR>(e->ca, base, tilebase)
+                                  : const_bit<NR>(e->ca, base, tilebase) | (const_bit<NR>(e->cb, base, tilebase) << 1);
+        R er, ei;
+        diag_elem<R>(m, e->k, idx, er, ei);
+        cmul_inplace<R>(cr, ci, er, ei);
+    }
+    uint32_t sm = 0;
+    for (int i = 0; i < nm; i++, e++) {  // mixed CZ: sign on register bit k where the constant bit is 1
+        const bool ra = e->ca >= 0 && e->ca < NR;
+        const int k = ra ? e->ca : e->cb, c = ra ? e->cb : e->ca;
+        sm ^= (uint32_t)const_bit<NR>(c, base, tilebase) << k;
+    }
+    const uint32_t par = parity_bits<NR>(sm);
+    const bool has_c = (nt | nl) != 0;
+    const T *tb = reinterpret_cast<const T *>(smat + 8 * tab);
+#pragma unroll
+    for (int j = 0; j < (1 << NR); j++) {
+        T t = tb[j];
+        if ((par >> j) & 1) {
+            t.x = -t.x;
+            t.y = -t.y;
+        }
+        if (has_c) {
+            const R x = cr * t.x - ci * t.y;
+            t.y = cr * t.y + ci * t.x;
+            t.x = x;
+        }
+        cmul_ip<T, R>(t.x, t.y, a[j]);
+        if (b) cmul_ip<T, R>(t.x, t.y, b[j]);
+    }
+}
+
 // ------------------------------------------------------------ generator inner products
 
 // Im <Psi| P_K |Phi> over the thread's register amplitudes, P = X or Y on slot K.
@@ -468,6 +529,21 @@ __device__ __forceinline__ void emit_partial(const RedCtx<R> &c, int slot, R v)
     for (int o = 16; o > 0; o >>= 1)
         if (o < c.lanes) v += __shfl_xor_sync(c.lanemask, v, o);
     if (c.lane == 0) c.sgrad[(slot - c.slot_begin) * c.nwarps + c.warp] = v;
+}
+
+// Several per-thread partials at once (specialised passes): N interleaved warp reductions,
+// lane 0 stores each for its pass-local slot.
+template <typename R, int N>
+__device__ __forceinline__ void emit_partials(const RedCtx<R> &c, const int (&local_slot)[N], R (&v)[N])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < N; k++)
+            if (o < c.lanes) v[k] += __shfl_xor_sync(c.lanemask, v[k], o);
+    if (c.lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; k++) c.sgrad[local_slot[k] * c.nwarps + c.warp] = v[k];
 }
 
 // A 2x2 matrix unit (8 reals) from shared memory as 16-byte vector loads.
@@ -652,11 +728,30 @@ __device__ __forceinline__ void tile_store(typename CT<R>::T *gmem, const typena
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// One tile of one pass: the body shared by the single-circuit kernel (tile = CTA index)
-// and the batched kernel (tile looked up from the CTA index).
-template <typename R, int NR, bool REV, bool TWOQ>
-__device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, typename CT<R>::T *__restrict__ psi,
-                                           const FusedArgs &args, const int64_t tile)
+// Shared-memory layout and per-CTA state of one tile pass, built by tile_begin and used
+// by the sub-runs (interpreted from the pass's records, or specialised code) and tile_end.
+template <typename R, int NR, bool REV>
+struct TileCtx {
+    typedef typename CT<R>::T T;
+    T *sphi, *spsi;
+    int64_t *hitab;
+    FGate *sgates;
+    DEnt *sents;
+    R *sconst;
+    R *smat;
+    int64_t tilebase;
+    int t, low, n_slots, slot_begin;
+    RedCtx<R> rc;
+};
+
+// Prologue of a tile pass: the tile's base offset and strided address table, the tile's
+// global loads (issued first), the staging of the pass's gate records, diagonal entries
+// and matrices, the tile into shared memory, and the tile-constant products of every
+// phase block.  Ends with the block synchronised.
+template <typename R, int NR, bool REV>
+__device__ __forceinline__ void tile_begin(const typename CT<R>::T *__restrict__ phi,
+                                           const typename CT<R>::T *__restrict__ psi, const FusedArgs &args,
+                                           const int64_t tile, TileCtx<R, NR, REV> &c)
 {
     typedef typename CT<R>::T T;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -750,7 +845,7 @@ __device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, 
         } else {
             for (int i = threadIdx.x; i < pd.n_units * 8; i += blockDim.x) {
                 const MatUnit u = args.units[pd.unit_begin + (i >> 3)];
-                smat[i] = mat_of<R>(&args.recs[u.rec])[8 * u.part + (i & 7)];
+                smat[i] = u.rec >= 0 ? mat_of<R>(&args.recs[u.rec])[8 * u.part + (i & 7)] : R(0);
             }
         }
     }
@@ -778,117 +873,202 @@ __device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, 
         sconst[4 * g.slot + 3] = i1;
     }
     __syncthreads();
+    c.sphi = sphi;
+    c.spsi = spsi;
+    c.hitab = hitab;
+    c.sgates = sgates;
+    c.sents = sents;
+    c.sconst = sconst;
+    c.smat = smat;
+    c.tilebase = tilebase;
+    c.t = t;
+    c.low = low;
+    c.n_slots = pd.n_slots;
+    c.slot_begin = pd.slot_begin;
+    c.rc = RedCtx<R>{sgrad, pd.slot_begin, nwarps, warp, lane, lanes, lanemask};
+}
 
-    RedCtx<R> rc{sgrad, pd.slot_begin, nwarps, warp, lane, lanes, lanemask};
-    T a[1 << NR], b[REV ? (1 << NR) : 1];
-    for (int s = 0; s < pd.n_sub; s++) {
-        const SubRun sr = args.subs[pd.sub_begin + s];
-        // thread bits -> tile positions outside R, ascending
-        int rmask = 0;
+// Gather a sub-run's register amplitudes: tile positions Rp[0..NR-1] are the register
+// bits, the thread index spells the other positions in ascending order (returned: the
+// thread's base position, off[k] = 1 << Rp[k]).
+template <typename R, int NR, bool REV>
+__device__ __forceinline__ int subrun_load(const TileCtx<R, NR, REV> &c, const int (&Rp)[NR], int (&off)[NR],
+                                           typename CT<R>::T *a, typename CT<R>::T *b)
+{
+    int rmask = 0;
 #pragma unroll
-        for (int k = 0; k < NR; k++) rmask |= 1 << sr.R[k];
-        int base = 0;
-        for (int q = 0, i = 0; q < t; q++) {
-            if ((rmask >> q) & 1) continue;
-            if ((threadIdx.x >> i) & 1) base |= 1 << q;
-            i++;
-        }
-        int off[NR];
-#pragma unroll
-        for (int k = 0; k < NR; k++) off[k] = 1 << sr.R[k];
-#pragma unroll
-        for (int j = 0; j < (1 << NR); j++) {
-            int l = base;
-#pragma unroll
-            for (int k = 0; k < NR; k++)
-                if ((j >> k) & 1) l |= off[k];
-            a[j] = sphi[swz<R>(l)];
-            if constexpr (REV) b[j] = spsi[swz<R>(l)];
-        }
-        FGate gn = sgates[sr.g_begin < sr.g_end ? sr.g_begin : 0];
-        for (int gi = sr.g_begin; gi < sr.g_end; gi++) {
-            const FGate g = gn;
-            if (gi + 1 < sr.g_end) gn = sgates[gi + 1];  // prefetch the next record
-            if (g.type == FT_LAYER1) {
-                apply_layer<R, NR, REV, !TWOQ>(g, sents + g.ent, smat, a, b, rc);
-                continue;
-            }
-            if (g.type == FT_DIAGB) {
-                const DEnt *ents = sents + g.ent;
-                const R *cst = sconst + 4 * g.slot;
-                if constexpr (REV) {
-                    if (g.nz > 0) {  // Z generators on the states after the block
-                        R tot = 0, dk[NR];
-#pragma unroll
-                        for (int k = 0; k < NR; k++) dk[k] = 0;
-#pragma unroll
-                        for (int j = 0; j < (1 << NR); j++) {
-                            const R v = b[j].x * a[j].y - b[j].y * a[j].x;  // Im(conj(Psi) Phi)
-                            tot += v;
-#pragma unroll
-                            for (int k = 0; k < NR; k++) dk[k] += ((j >> k) & 1) ? -v : v;
-                        }
-                        for (int e = 0; e < g.nz; e++) {
-                            const DEnt d = ents[e];
-                            R part;
-                            if (d.ca >= 0 && d.ca < NR) {
-                                part = dk[0];
-#pragma unroll
-                                for (int k = 1; k < NR; k++)
-                                    if (k == d.ca) part = dk[k];
-                            } else {
-                                part = const_bit<NR>(d.ca, base, tilebase) ? -tot : tot;
-                            }
-                            emit_partial<R>(rc, d.slot, part * (R)d.coef);
-                        }
-                    }
-                    if (g.flags & 1) {
-                        phase_block<R, NR>(ents + g.nz, g.perm, smat, false, cst[0], cst[1], a, nullptr, base, tilebase);
-                        phase_block<R, NR>(ents + g.nz, g.perm, smat, true, cst[2], cst[3], b, nullptr, base, tilebase);
-                    } else {
-                        phase_block<R, NR>(ents + g.nz, g.perm, smat, false, cst[0], cst[1], a, b, base, tilebase);
-                    }
-                } else {
-                    phase_block<R, NR>(ents, g.perm, smat, false, cst[0], cst[1], a, nullptr, base, tilebase);
-                }
-                continue;
-            }
-            if constexpr (REV && TWOQ) {
-                if (g.type == FT_PROBE2) {  // gradient read only: the states stay as they are
-                    emit_partial<R>(rc, g.slot, probe2_dispatch<R, NR>(g.a, g.b, a, b, smat + 8 * g.mat) * (R)g.coef);
-                    continue;
-                }
-            }
-            if constexpr (REV) {
-                if (g.gen == GEN_X)
-                    emit_partial<R>(rc, g.slot, gen_xy_dispatch<R, NR, GEN_X>(g.gpos, a, b) * (R)g.coef);
-                else if (g.gen == GEN_Y)
-                    emit_partial<R>(rc, g.slot, gen_xy_dispatch<R, NR, GEN_Y>(g.gpos, a, b) * (R)g.coef);
-            }
-            apply_fgate<R, NR, TWOQ>(g.type, g.a, g.b, g.perm, smat + 8 * g.mat, a);
-            if constexpr (REV) apply_fgate<R, NR, TWOQ>(g.type, g.a, g.b, g.perm, smat + 8 * g.mat2, b);
-        }
-#pragma unroll
-        for (int j = 0; j < (1 << NR); j++) {
-            int l = base;
-#pragma unroll
-            for (int k = 0; k < NR; k++)
-                if ((j >> k) & 1) l |= off[k];
-            sphi[swz<R>(l)] = a[j];
-            if constexpr (REV) spsi[swz<R>(l)] = b[j];
-        }
-        __syncthreads();
+    for (int k = 0; k < NR; k++) rmask |= 1 << Rp[k];
+    int base = 0;
+    for (int q = 0, i = 0; q < c.t; q++) {
+        if ((rmask >> q) & 1) continue;
+        if ((threadIdx.x >> i) & 1) base |= 1 << q;
+        i++;
     }
-    tile_store<R, CNT>(phi, sphi, low, tilebase, hitab);
+#pragma unroll
+    for (int k = 0; k < NR; k++) off[k] = 1 << Rp[k];
+#pragma unroll
+    for (int j = 0; j < (1 << NR); j++) {
+        int l = base;
+#pragma unroll
+        for (int k = 0; k < NR; k++)
+            if ((j >> k) & 1) l |= off[k];
+        a[j] = c.sphi[swz<R>(l)];
+        if constexpr (REV) b[j] = c.spsi[swz<R>(l)];
+    }
+    return base;
+}
+
+// Scatter the register amplitudes back and synchronise the block.
+template <typename R, int NR, bool REV>
+__device__ __forceinline__ void subrun_store(const TileCtx<R, NR, REV> &c, int base, const int (&off)[NR],
+                                             const typename CT<R>::T *a, const typename CT<R>::T *b)
+{
+#pragma unroll
+    for (int j = 0; j < (1 << NR); j++) {
+        int l = base;
+#pragma unroll
+        for (int k = 0; k < NR; k++)
+            if ((j >> k) & 1) l |= off[k];
+        c.sphi[swz<R>(l)] = a[j];
+        if constexpr (REV) c.spsi[swz<R>(l)] = b[j];
+    }
+    __syncthreads();
+}
+
+// Z-generator reads of a phase block (reverse): per register bit k the sum of
+// Im(conj(Psi) Phi) with sign (-1)^(bit k), and the total.
+template <typename R, int NR>
+__device__ __forceinline__ void z_sums(const typename CT<R>::T *a, const typename CT<R>::T *b, R &tot, R (&dk)[NR])
+{
+    tot = 0;
+#pragma unroll
+    for (int k = 0; k < NR; k++) dk[k] = 0;
+#pragma unroll
+    for (int j = 0; j < (1 << NR); j++) {
+        const R v = b[j].x * a[j].y - b[j].y * a[j].x;  // Im(conj(Psi) Phi)
+        tot += v;
+#pragma unroll
+        for (int k = 0; k < NR; k++) dk[k] += ((j >> k) & 1) ? -v : v;
+    }
+}
+
+// The record interpreter: gates [g_begin, g_end) of the pass on the register amplitudes.
+template <typename R, int NR, bool REV, bool TWOQ>
+__device__ __forceinline__ void run_records(const TileCtx<R, NR, REV> &c, int g_begin, int g_end, int base,
+                                            typename CT<R>::T *a, typename CT<R>::T *b)
+{
+    const FGate *sgates = c.sgates;
+    const DEnt *sents = c.sents;
+    const R *smat = c.smat;
+    const int64_t tilebase = c.tilebase;
+    const RedCtx<R> &rc = c.rc;
+    FGate gn = sgates[g_begin < g_end ? g_begin : 0];
+    for (int gi = g_begin; gi < g_end; gi++) {
+        const FGate g = gn;
+        if (gi + 1 < g_end) gn = sgates[gi + 1];  // prefetch the next record
+        if (g.type == FT_LAYER1) {
+            apply_layer<R, NR, REV, !TWOQ>(g, sents + g.ent, smat, a, b, rc);
+            continue;
+        }
+        if (g.type == FT_DIAGB) {
+            const DEnt *ents = sents + g.ent;
+            const R *cst = c.sconst + 4 * g.slot;
+            if constexpr (REV) {
+                if (g.nz > 0) {  // Z generators on the states after the block
+                    R tot, dk[NR];
+                    z_sums<R, NR>(a, b, tot, dk);
+                    for (int e = 0; e < g.nz; e++) {
+                        const DEnt d = ents[e];
+                        R part;
+                        if (d.ca >= 0 && d.ca < NR) {
+                            part = dk[0];
+#pragma unroll
+                            for (int k = 1; k < NR; k++)
+                                if (k == d.ca) part = dk[k];
+                        } else {
+                            part = const_bit<NR>(d.ca, base, tilebase) ? -tot : tot;
+                        }
+                        emit_partial<R>(rc, d.slot, part * (R)d.coef);
+                    }
+                }
+                if (g.flags & FLAG_TABLE) {
+                    if (g.flags & FLAG_SEPARATE) {
+                        phase_table<R, NR>(ents + g.nz, g.perm, smat, g.mat, false, cst[0], cst[1], a, nullptr, base, tilebase);
+                        phase_table<R, NR>(ents + g.nz, g.perm, smat, g.mat2, true, cst[2], cst[3], b, nullptr, base, tilebase);
+                    } else {
+                        phase_table<R, NR>(ents + g.nz, g.perm, smat, g.mat, false, cst[0], cst[1], a, b, base, tilebase);
+                    }
+                } else if (g.flags & FLAG_SEPARATE) {
+                    phase_block<R, NR>(ents + g.nz, g.perm, smat, false, cst[0], cst[1], a, nullptr, base, tilebase);
+                    phase_block<R, NR>(ents + g.nz, g.perm, smat, true, cst[2], cst[3], b, nullptr, base, tilebase);
+                } else {
+                    phase_block<R, NR>(ents + g.nz, g.perm, smat, false, cst[0], cst[1], a, b, base, tilebase);
+                }
+            } else if (g.flags & FLAG_TABLE) {
+                phase_table<R, NR>(ents, g.perm, smat, g.mat, false, cst[0], cst[1], a, nullptr, base, tilebase);
+            } else {
+                phase_block<R, NR>(ents, g.perm, smat, false, cst[0], cst[1], a, nullptr, base, tilebase);
+            }
+            continue;
+        }
+        if constexpr (REV && TWOQ) {
+            if (g.type == FT_PROBE2) {  // gradient read only: the states stay as they are
+                emit_partial<R>(rc, g.slot, probe2_dispatch<R, NR>(g.a, g.b, a, b, smat + 8 * g.mat) * (R)g.coef);
+                continue;
+            }
+        }
+        if constexpr (REV) {
+            if (g.gen == GEN_X)
+                emit_partial<R>(rc, g.slot, gen_xy_dispatch<R, NR, GEN_X>(g.gpos, a, b) * (R)g.coef);
+            else if (g.gen == GEN_Y)
+                emit_partial<R>(rc, g.slot, gen_xy_dispatch<R, NR, GEN_Y>(g.gpos, a, b) * (R)g.coef);
+        }
+        apply_fgate<R, NR, TWOQ>(g.type, g.a, g.b, g.perm, smat + 8 * g.mat, a);
+        if constexpr (REV) apply_fgate<R, NR, TWOQ>(g.type, g.a, g.b, g.perm, smat + 8 * g.mat2, b);
+    }
+}
+
+// Epilogue: the tile back to global memory and (reverse) the tile's FP64 partial of every
+// gradient slot of the pass, summed over the warps in fixed order.
+template <typename R, int NR, bool REV>
+__device__ __forceinline__ void tile_end(typename CT<R>::T *__restrict__ phi, typename CT<R>::T *__restrict__ psi,
+                                         const FusedArgs &args, const int64_t tile, const TileCtx<R, NR, REV> &c)
+{
+    typedef typename CT<R>::T T;
+    constexpr int CNT = sizeof(T) == 8 ? (1 << (NR - 1)) : (1 << NR);
+    tile_store<R, CNT>(phi, c.sphi, c.low, c.tilebase, c.hitab);
     if (REV) {
-        tile_store<R, CNT>(psi, spsi, low, tilebase, hitab);
-        for (int sl = threadIdx.x; sl < pd.n_slots; sl += blockDim.x) {
+        tile_store<R, CNT>(psi, c.spsi, c.low, c.tilebase, c.hitab);
+        const int nwarps = c.rc.nwarps;
+        for (int sl = threadIdx.x; sl < c.n_slots; sl += blockDim.x) {
             double acc = 0.0;
-            for (int w = 0; w < nwarps; w++) acc += (double)sgrad[sl * nwarps + w];
-            args.slot_partials[(int64_t)(pd.slot_begin + sl) * args.tiles_stride + tile] = acc;
+            for (int w = 0; w < nwarps; w++) acc += (double)c.rc.sgrad[sl * nwarps + w];
+            args.slot_partials[(int64_t)(c.slot_begin + sl) * args.tiles_stride + tile] = acc;
         }
     }
 }
 
+// One tile of one pass: the body shared by the single-circuit kernel (tile = CTA index)
+// and the batched kernel (tile looked up from the CTA index).
+template <typename R, int NR, bool REV, bool TWOQ>
+__device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, typename CT<R>::T *__restrict__ psi,
+                                           const FusedArgs &args, const int64_t tile)
+{
+    typedef typename CT<R>::T T;
+    TileCtx<R, NR, REV> c;
+    tile_begin<R, NR, REV>(phi, psi, args, tile, c);
+    const int n_sub = args.pd->n_sub, sub_begin = args.pd->sub_begin;
+    T a[1 << NR], b[REV ? (1 << NR) : 1];
+    for (int s = 0; s < n_sub; s++) {
+        const SubRun sr = args.subs[sub_begin + s];
+        int Rp[NR], off[NR];
+#pragma unroll
+        for (int k = 0; k < NR; k++) Rp[k] = sr.R[k];
+        const int base = subrun_load<R, NR, REV>(c, Rp, off, a, b);
+        run_records<R, NR, REV, TWOQ>(c, sr.g_begin, sr.g_end, base, a, b);
+        subrun_store<R, NR, REV>(c, base, off, a, b);
+    }
+    tile_end<R, NR, REV>(phi, psi, args, tile, c);
+}
 
 }  // namespace gbvqc

@@ -1,10 +1,12 @@
 // Host-side launchers of the CUDA kernels (implemented in kernels_*.cu).
 #pragma once
 
+#include "common.cuh"
+
+#ifndef __CUDACC_RTC__  // (runtime compilation: NVRTC's built-in definitions)
 #include <cuda_runtime.h>
 #include <stdint.h>
-
-#include "common.cuh"
+#endif
 
 namespace gbvqc {
 
@@ -122,8 +124,18 @@ struct FusedArgs {
 };
 // img_f / img_r [8 u + e] = element e of unit u of the forward / reverse unit list, in the
 // state's precision (after the step's matrices are materialised).
-cudaError_t launch_gather_units(int dtype, const MatUnit *fu, int nf, void *img_f, const MatUnit *ru, int nr,
-                                void *img_r, const MatRec *recs, cudaStream_t s);
+struct GatherArgs {
+    const MatUnit *fu;          // forward unit list (nf units) -> img_f
+    int nf;
+    const MatUnit *ru;          // reverse unit list (nr units) -> img_r
+    int nr;
+    void *img_f, *img_r;
+    const MatRec *recs;
+    const TabDesc *ftabs, *rtabs;   // register phase tables written into img_f / img_r
+    const TabEnt *ftabents, *rtabents;
+    int n_ftabs, n_rtabs, fbits, rbits;
+};
+cudaError_t launch_gather_units(int dtype, const GatherArgs &g, cudaStream_t s);
 int fused_nr(int dtype, bool reverse);           // register qubits per sub-run
 // Threads per CTA the fused kernels are compiled for (launch bounds): 2^(t - NR) must
 // not exceed it.  Two CTAs per SM for the reverse kernels, three for the forward ones.

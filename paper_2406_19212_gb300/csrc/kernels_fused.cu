@@ -122,29 +122,55 @@ cudaError_t launch_fused_reverse(int dtype, void *phi, void *psi, const FusedDev
     return fused_launch<double, 3, true>(phi, psi, ph, smem, args, s);
 }
 
+// Register phase table entry j of tab: the FP64 product of its entries' diagonal elements
+// at the register bits of j, rounded once to R.
 template <typename R>
-__global__ void k_gather_units(const MatUnit *__restrict__ fu, int nf, R *img_f, const MatUnit *__restrict__ ru,
-                               int nr, R *img_r, const MatRec *__restrict__ recs)
+__device__ __forceinline__ void phase_table_entry(const TabDesc &tab, int j, const TabEnt *__restrict__ ents,
+                                                  const MatRec *__restrict__ recs, R *img)
+{
+    double pr = 1.0, pi = 0.0;
+    for (int i = 0; i < tab.n_ent; i++) {
+        const TabEnt e = ents[tab.ent_begin + i];
+        const int r = e.k == 1 ? (j >> e.ca) & 1 : ((j >> e.ca) & 1) | (((j >> e.cb) & 1) << 1);
+        const double *m = recs[e.rec].d + (e.k == 1 ? 6 * r : 10 * r);
+        const double x = pr * m[0] - pi * m[1];
+        pi = pr * m[1] + pi * m[0];
+        pr = x;
+    }
+    img[tab.off + 2 * j] = (R)pr;
+    img[tab.off + 2 * j + 1] = (R)pi;
+}
+
+template <typename R>
+__global__ void k_gather_units(GatherArgs g)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int u = i >> 3, e = i & 7;
-    if (u < nf) {
-        const MatUnit m = fu[u];
-        img_f[i] = mat_of<R>(&recs[m.rec])[8 * m.part + e];
-    } else if (u < nf + nr) {
-        const MatUnit m = ru[u - nf];
-        img_r[i - 8 * nf] = mat_of<R>(&recs[m.rec])[8 * m.part + e];
+    R *img_f = (R *)g.img_f, *img_r = (R *)g.img_r;
+    if (u < g.nf) {
+        const MatUnit m = g.fu[u];
+        if (m.rec >= 0) img_f[i] = mat_of<R>(&g.recs[m.rec])[8 * m.part + e];  // rec < 0: a table's units
+    } else if (u < g.nf + g.nr) {
+        const MatUnit m = g.ru[u - g.nf];
+        if (m.rec >= 0) img_r[i - 8 * g.nf] = mat_of<R>(&g.recs[m.rec])[8 * m.part + e];
+    } else {
+        const int k = i - 8 * (g.nf + g.nr);
+        const int nfe = g.n_ftabs << g.fbits;
+        if (k < nfe) phase_table_entry<R>(g.ftabs[k >> g.fbits], k & ((1 << g.fbits) - 1), g.ftabents, g.recs, img_f);
+        else if (k - nfe < (g.n_rtabs << g.rbits)) {
+            const int kr = k - nfe;
+            phase_table_entry<R>(g.rtabs[kr >> g.rbits], kr & ((1 << g.rbits) - 1), g.rtabents, g.recs, img_r);
+        }
     }
 }
 
-cudaError_t launch_gather_units(int dtype, const MatUnit *fu, int nf, void *img_f, const MatUnit *ru, int nr,
-                                void *img_r, const MatRec *recs, cudaStream_t s)
+cudaError_t launch_gather_units(int dtype, const GatherArgs &g, cudaStream_t s)
 {
-    const int total = 8 * (nf + nr);
+    const int64_t total = 8 * (int64_t)(g.nf + g.nr) + ((int64_t)g.n_ftabs << g.fbits) + ((int64_t)g.n_rtabs << g.rbits);
     if (total == 0) return cudaSuccess;
-    const int blocks = (total + 255) / 256;
-    if (dtype == 0) k_gather_units<float><<<blocks, 256, 0, s>>>(fu, nf, (float *)img_f, ru, nr, (float *)img_r, recs);
-    else k_gather_units<double><<<blocks, 256, 0, s>>>(fu, nf, (double *)img_f, ru, nr, (double *)img_r, recs);
+    const int blocks = (int)((total + 255) / 256);
+    if (dtype == 0) k_gather_units<float><<<blocks, 256, 0, s>>>(g);
+    else k_gather_units<double><<<blocks, 256, 0, s>>>(g);
     return cudaGetLastError();
 }
 

@@ -89,6 +89,9 @@ struct Emitter {
     std::vector<FGate> &gates;
     std::vector<DEnt> &ents;
     std::vector<MatUnit> &units;
+    std::vector<TabDesc> &tabs;
+    std::vector<TabEnt> &tabents;
+    bool phase_tables;
     int gate_base, ent_base, unit_base;   // pass-local indices start here
     std::map<int, int> unit_of_rec;
     double flops = 0;
@@ -101,6 +104,18 @@ struct Emitter {
     {
         units.push_back(MatUnit{rec, 0});
         return (int)units.size() - 1 - unit_base;
+    }
+
+    // a register phase table over 2^NR indices from the given entries: reserves its units
+    // (placeholders the gather skips) and returns the first, pass-local
+    int table(const std::vector<TabEnt> &te)
+    {
+        const int n_units = std::max(1, (1 << NR) * 2 / 8);
+        const int first = (int)units.size();
+        for (int i = 0; i < n_units; i++) units.push_back(MatUnit{-1, 0});
+        tabs.push_back(TabDesc{8 * first, NR, (int)tabents.size(), (int)te.size()});
+        tabents.insert(tabents.end(), te.begin(), te.end());
+        return first - unit_base;
     }
 
     int unit(int rec, int k)
@@ -383,6 +398,63 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
                 E.slot_param.push_back(g.param);
                 E.ents.push_back(d);
             }
+            // table mode: every mixed entry (one register position, one constant) is a CZ
+            bool table = E.phase_tables;
+            if (table)
+                for (int pos : run) {
+                    const PGate &g = G[order[pos]];
+                    if (g.k != 2) continue;
+                    const int ca = code_of(g.q[0]), cb = code_of(g.q[1]);
+                    const bool ra = ca >= 0 && ca < NR, rb = cb >= 0 && cb < NR;
+                    if (ra != rb && !g.cz) table = false;
+                }
+            if (table) {
+                std::vector<DEnt> tl[2];           // TILE, LOCAL entries
+                std::vector<DEnt> mixcz;
+                std::vector<TabEnt> tphi, tpsi;   // register entries: Phi (forward: U), Psi
+                bool separate = false;
+                for (int pos : run) {
+                    const PGate &g = G[order[pos]];
+                    const int rf = E.reverse ? g.rec_i : g.rec_f, ra_ = E.reverse ? g.rec_a : g.rec_f;
+                    DEnt d{};
+                    d.k = (int8_t)g.k;
+                    d.ca = (int8_t)code_of(g.q[0]);
+                    d.cb = (int8_t)(g.k == 2 ? code_of(g.q[1]) : 0);
+                    d.slot = -1;
+                    const bool ra = d.ca >= 0 && d.ca < NR, rb = g.k == 2 && d.cb >= 0 && d.cb < NR;
+                    if (ra || rb) {
+                        if (g.k == 2 && ra != rb) {   // mixed CZ: no matrix
+                            d.cls = DC_REG;
+                            d.mat = d.mat2 = -1;
+                            mixcz.push_back(d);
+                            continue;
+                        }
+                        tphi.push_back(TabEnt{rf, (int8_t)g.k, d.ca, d.cb, 0});
+                        tpsi.push_back(TabEnt{ra_, (int8_t)g.k, d.ca, d.cb, 0});
+                        if (ra_ != rf) separate = true;
+                        continue;
+                    }
+                    d.mat = (int16_t)E.unit(rf, g.k);
+                    d.mat2 = (int16_t)E.unit(ra_, g.k);
+                    if (d.mat2 != d.mat) separate = true;
+                    const bool tile = d.ca < 0 && (g.k == 1 || d.cb < 0);
+                    d.cls = tile ? DC_TILE : DC_LOCAL;
+                    tl[tile ? 0 : 1].push_back(d);
+                }
+                for (const DEnt &d : tl[0]) E.ents.push_back(d);
+                for (const DEnt &d : tl[1]) E.ents.push_back(d);
+                for (const DEnt &d : mixcz) E.ents.push_back(d);
+                if (tl[0].size() > 255 || tl[1].size() > 255 || mixcz.size() > 255) E.overflow = true;
+                f.perm = (int)tl[0].size() | ((int)tl[1].size() << 8) | ((int)mixcz.size() << 16);
+                f.mat = (int16_t)E.table(tphi);
+                f.mat2 = separate ? (int16_t)E.table(tpsi) : f.mat;
+                f.flags = (int8_t)((separate ? FLAG_SEPARATE : 0) | FLAG_TABLE);
+                f.n_ent = (int16_t)((int)E.ents.size() - E.ent_base - f.ent);
+                // one complex product per amplitude and state
+                E.flops += (separate ? 2.0 : 1.0) * 6 + st * 6;
+                E.gates.push_back(f);
+                continue;
+            }
             // phase entries, grouped by class
             std::vector<DEnt> cls_ents[6];
             bool separate = false;
@@ -419,7 +491,7 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
                 E.overflow = true;
             }
             f.perm = cnt[DC_TILE] | (cnt[DC_LOCAL] << 8) | (cnt[DC_REG] << 16) | (np << 24);
-            f.flags = separate ? 1 : 0;
+            f.flags = separate ? FLAG_SEPARATE : 0;
             f.n_ent = (int16_t)((int)E.ents.size() - E.ent_base - f.ent);
             // per thread: the block's local factors, register pairs, two half tables and one
             // product per amplitude and state; PAIR entries add a controlled phase on a quarter
@@ -606,6 +678,7 @@ bool build_fused_plan(const std::vector<PGate> &G, int n, const PlanOptions &opt
                       rev ? slot_counter : dummy_counter, rev ? out.slot_param : dummy_params,
                       rev ? out.rsubs : out.fsubs, rev ? out.rgates : out.fgates,
                       rev ? out.rents : out.fents, rev ? out.runits : out.funits,
+                      rev ? out.rtabs : out.ftabs, rev ? out.rtabents : out.ftabents, opt.phase_tables,
                       0, 0, 0, {}, 0.0, 0, false, false};
             E.gate_base = (int)E.gates.size();
             E.ent_base = (int)E.ents.size();

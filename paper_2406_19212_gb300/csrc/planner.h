@@ -36,6 +36,7 @@ struct PlanOptions {
     int max_slots = 128;   // gradient slots per pass
     int elem_bytes = 4;    // real element size (4: complex64, 8: complex128)
     int gate_smem = 24 * 1024;  // shared-memory budget of a pass's gate data
+    bool phase_tables = false;  // table-mode phase blocks (needs the per-step matrix image)
 };
 
 struct FusedPlan {
@@ -45,6 +46,9 @@ struct FusedPlan {
     std::vector<FGate> fgates, rgates;
     std::vector<DEnt> fents, rents;
     std::vector<MatUnit> funits, runits;
+    // register phase tables of table-mode blocks (computed per step into the images)
+    std::vector<TabDesc> ftabs, rtabs;
+    std::vector<TabEnt> ftabents, rtabents;
     int n_slots = 0;                // gradient slots over all passes
     std::vector<int> slot_param;    // parameter of each slot
     int max_pass_slots = 0;

@@ -317,3 +317,22 @@ def test_wrappers_reject_host_tensors(lib):
     expect_status(1, gb.sv_wrap, np.zeros(16, np.complex64), 4)
     expect_status(1, gb.expect_noalloc, psi, 4, [(1.0, ((0, "Z"),))], out)
     expect_status(1, gb.sv_wrap, psi, 0)
+
+
+def test_specialised_sources_compile_host(lib, tmp_path, monkeypatch):
+    """The generated CUDA of every record kind compiles with NVRTC for sm_103a without a
+    GPU (one-qubit layers and gates, table and factor-pair phase blocks, two-qubit gates,
+    FSIM probes, density circuits with barrier passes), and a second call finds every
+    kernel in the cache."""
+    from tests.test_gpu_parity import _noisy_two_qubit_channels
+    monkeypatch.setenv("GBVQC_JIT_CACHE", str(tmp_path))
+    circs = [I.random_circuit(9, 120, 4).circuit, I.fsim_grid_vqe(3, 3, 2, 7, pmask=0b11111).circuit,
+             _noisy_two_qubit_channels(5, 3)[0]]
+    for circ in circs:
+        c = gb.circuit_create(circ)
+        c.set_tiling(7, 2)
+        for dtype in (gb.C64, gb.C128):
+            for for_grad in (True, False):
+                info = c.specialize(dtype, for_grad)
+                assert info["kernels"] >= 1
+                assert c.specialize(dtype, for_grad)["cached"] == info["kernels"]
