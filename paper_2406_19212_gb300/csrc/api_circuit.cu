@@ -153,6 +153,12 @@ static void free_plan(DevPlan *p)
     dev_free(p->d_ftabs); dev_free(p->d_rtabs); dev_free(p->d_ftabents); dev_free(p->d_rtabents);
     if (p->jit) jit_free(*p->jit);
     p->jit.reset();
+    for (cudaStream_t st : p->pf_streams) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : p->pf_done) cudaEventDestroy(ev);
+    if (p->pf_fork) cudaEventDestroy(p->pf_fork);
+    p->pf_streams.clear();
+    p->pf_done.clear();
+    p->pf_fork = nullptr;
 }
 
 void free_graphs(gbvqc_circuit *c)

@@ -73,6 +73,58 @@ static gbvqc_status ensure_jit(DevPlan *p, int dtype, bool with_rev)
         p->jit.reset();
         return fail(GBVQC_ERR_CUDA, "specialising the tile passes: %s", err.c_str());
     }
+    if (with_rev) {  // side streams of the gradient's code prefetch (made outside any capture)
+        size_t n = 0;
+        for (size_t i = 0; i < p->p.fwd.size(); i++) n += p->p.barrier[i] >= 0 ? 0 : 2;
+        CUDA_TRY(cudaEventCreateWithFlags(&p->pf_fork, cudaEventDisableTiming));
+        for (size_t i = 0; i < n; i++) {
+            cudaStream_t st = nullptr;
+            cudaEvent_t ev = nullptr;
+            CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            p->pf_streams.push_back(st);
+            CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            p->pf_done.push_back(ev);
+        }
+    }
+    return GBVQC_OK;
+}
+
+// Code prefetch of the specialised passes of a gradient evaluation.  Straight-line passes
+// are hundreds of kilobytes of instructions each; when the caches are cold (another
+// workload ran in between) every SM would stream them from HBM at the pace of its
+// instruction fetch.  At the start of the evaluation a dry launch of every pass (one CTA
+// per sub-run, each walking its own sub-run's code on tile 0, no global stores) is forked
+// onto its own side stream: they pull all passes' code into L2 concurrently, in a few
+// microseconds, before the real launches reach it.  join = false forks, join = true makes
+// s wait for the prefetch launches.
+static gbvqc_status jit_prefetch(gbvqc_circuit *c, DevPlan *p, bool join, cudaStream_t s)
+{
+    if (g_prof || !p->jit || p->pf_streams.empty()) return GBVQC_OK;  // profiles time the passes alone
+    if (join) {
+        for (cudaEvent_t ev : p->pf_done) CUDA_TRY(cudaStreamWaitEvent(s, ev, 0));
+        return GBVQC_OK;
+    }
+    CUDA_TRY(cudaEventRecord(p->pf_fork, s));
+    Workspace &w = c->ws;
+    const int tiles = 1 << (c->n_phys - p->p.t);
+    size_t k = 0;
+    for (int dir = 0; dir < 2; dir++)
+        for (size_t i = 0; i < p->p.fwd.size(); i++) {
+            if (p->p.barrier[i] >= 0) continue;
+            cudaStream_t st = p->pf_streams[k];
+            CUDA_TRY(cudaStreamWaitEvent(st, p->pf_fork, 0));
+            const bool rev = dir == 1;
+            const PassDesc &d = rev ? p->p.rev[i] : p->p.fwd[i];
+            const FusedArgs args = rev ? FusedArgs{p->d_rev + i, p->d_rsubs, p->d_rgates, p->d_rents, p->d_runits,
+                                                   c->d_recs, p->d_rimg, w.d_slot_partials, tiles}
+                                       : FusedArgs{p->d_fwd + i, p->d_fsubs, p->d_fgates, p->d_fents, p->d_funits,
+                                                   c->d_recs, p->d_fimg, nullptr, 0};
+            CUDA_TRY(jit_launch(rev ? p->jit->rev[i] : p->jit->fwd[i], w.phi, w.psi, args, (unsigned)d.n_sub,
+                                1 << (d.t - (rev ? p->p.nr_r : p->p.nr_f)), rev ? p->rev_smem[i] : p->fwd_smem[i],
+                                st, true));
+            CUDA_TRY(cudaEventRecord(p->pf_done[k], st));
+            k++;
+        }
     return GBVQC_OK;
 }
 
@@ -161,6 +213,7 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
     RedScratch red{w.d_red, w.d_counter};
     const bool fused = mode != GBVQC_MODE_PLAIN && p, jit = mode == GBVQC_MODE_JIT && p;
     const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
+    if (jit) ST_TRY(jit_prefetch(c, p, false, s));  // first: overlaps the whole sequence
     ST_TRY(run_k("materialize", 0, 0, s, [&] {
         return launch_materialize(c->d_dyn, (int)c->dyn.size(), w.d_theta, c->d_recs, s);
     }));
@@ -215,6 +268,7 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
         ST_TRY(run_k("accumulate", 0, 0, s, [&] {
             return launch_accumulate(w.d_slot_grad, p->d_csr_ptr, p->d_csr_slots, c->n_params, w.d_grad, s);
         }));
+        if (jit) ST_TRY(jit_prefetch(c, p, true, s));
     } else {
         // Algorithm 2: Phi <- Q^-1 Phi; g = scale Re <Psi|dQ|Phi>; Psi <- Q^-1 Psi (Q^dag for channels)
         for (int j = (int)c->plain.size() - 1; j >= 0; j--) {

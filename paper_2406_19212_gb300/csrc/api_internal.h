@@ -189,6 +189,11 @@ struct DevPlan {  // a FusedPlan and its device copies (uploaded on first launch
     TabEnt *d_ftabents = nullptr, *d_rtabents = nullptr;
     int *d_csr_ptr = nullptr, *d_csr_slots = nullptr;
     std::unique_ptr<JitPlan> jit;  // specialised passes (GBVQC_MODE_JIT), built on first use
+    // code prefetch of the specialised passes: one side stream and completion event per
+    // kernel, forked from the gradient sequence's stream at its start and joined at its end
+    std::vector<cudaStream_t> pf_streams;
+    std::vector<cudaEvent_t> pf_done;
+    cudaEvent_t pf_fork = nullptr;
 };
 
 struct gbvqc_circuit {

@@ -1036,6 +1036,7 @@ __device__ __forceinline__ void tile_end(typename CT<R>::T *__restrict__ phi, ty
 {
     typedef typename CT<R>::T T;
     constexpr int CNT = sizeof(T) == 8 ? (1 << (NR - 1)) : (1 << NR);
+    if (args.dry) return;  // a code-prefetch launch writes nothing
     tile_store<R, CNT>(phi, c.sphi, c.low, c.tilebase, c.hitab);
     if (REV) {
         tile_store<R, CNT>(psi, c.spsi, c.low, c.tilebase, c.hitab);

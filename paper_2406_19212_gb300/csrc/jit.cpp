@@ -244,19 +244,21 @@ std::string jit_source(const FusedPlan &P, int p, bool rev, int dtype)
       << fused_min_blocks(rev) << ") " << jit_kernel_name(p, rev)
       << "(Tt *__restrict__ phi, Tt *__restrict__ psi, const FusedArgs args)\n{\n"
       << "  constexpr int NR = " << NR << ";\n  constexpr bool REV = " << (rev ? "true" : "false") << ";\n"
-      << "  TileCtx<Rt, NR, REV> c;\n  tile_begin<Rt, NR, REV>(phi, psi, args, blockIdx.x, c);\n"
+      << "  // a code-prefetch launch (args.dry) runs tile 0 and CTA s walks sub-run s only\n"
+      << "  const int64_t tile = args.dry ? 0 : blockIdx.x;\n"
+      << "  TileCtx<Rt, NR, REV> c;\n  tile_begin<Rt, NR, REV>(phi, psi, args, tile, c);\n"
       << "  Tt a[1 << NR], b[REV ? (1 << NR) : 1];\n"
       << "  const Rt *smat = c.smat;\n  const DEnt *sents = c.sents;\n  const RedCtx<Rt> &rc = c.rc;\n"
       << "  const int64_t tilebase = c.tilebase;\n  (void)sents; (void)rc; (void)tilebase; (void)b;\n";
     for (int s = 0; s < d.n_sub; s++) {
         const SubRun &sr = subs[d.sub_begin + s];
-        o << "  {  // sub-run " << s << "\n    const int Rp[NR] = {";
+        o << "  if (!args.dry || blockIdx.x == " << s << ") {  // sub-run " << s << "\n    const int Rp[NR] = {";
         for (int k = 0; k < NR; k++) o << (k ? ", " : "") << (int)sr.R[k];
         o << "};\n    int off[NR];\n    const int base = subrun_load<Rt, NR, REV>(c, Rp, off, a, b);\n    (void)base;\n";
         for (int gi = sr.g_begin; gi < sr.g_end; gi++) emit_gate(o, P, d, gates[d.gate_begin + gi], rev, NR);
         o << "    subrun_store<Rt, NR, REV>(c, base, off, a, b);\n  }\n";
     }
-    o << "  tile_end<Rt, NR, REV>(phi, psi, args, blockIdx.x, c);\n}\n";
+    o << "  tile_end<Rt, NR, REV>(phi, psi, args, tile, c);\n}\n";
     return o.str();
 }
 
@@ -384,9 +386,10 @@ void jit_free(JitPlan &jp)
 }
 
 cudaError_t jit_launch(const JitPass &jp, void *phi, void *psi, const FusedArgs &args, unsigned tiles, int threads,
-                       size_t smem, cudaStream_t s)
+                       size_t smem, cudaStream_t s, bool dry)
 {
     FusedArgs a = args;
+    a.dry = dry ? 1 : 0;
     void *params[] = {&phi, &psi, &a};
     return cudaLaunchKernel((const void *)jp.kern, dim3(tiles), dim3(threads), params, smem, s);
 }

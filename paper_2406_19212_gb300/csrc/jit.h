@@ -56,8 +56,11 @@ bool jit_build(const FusedPlan &plan, int dtype, bool want_rev, JitPlan &out, st
 void jit_free(JitPlan &jp);
 
 // Launch a specialised pass: 2^(n-t) tiles of 2^(t-NR) threads with smem bytes of dynamic
-// shared memory, the same arguments as the interpreter's kernel.
+// shared memory, the same arguments as the interpreter's kernel.  dry: a code-prefetch
+// launch with args.dry = 1 and one CTA per sub-run of the pass (tiles = its sub-run
+// count): CTA s runs tile 0 through sub-run s's code only, pulling it into L2, and writes
+// nothing to global memory.
 cudaError_t jit_launch(const JitPass &jp, void *phi, void *psi, const FusedArgs &args, unsigned tiles, int threads,
-                       size_t smem, cudaStream_t s);
+                       size_t smem, cudaStream_t s, bool dry = false);
 
 }  // namespace gbvqc

@@ -121,6 +121,9 @@ struct FusedArgs {
                       // are one contiguous run), or null to gather them through units/recs
     double *slot_partials;
     int tiles_stride;
+    int dry;  // 1: a code-prefetch launch (specialised passes): runs tile 0 of the pass and
+              // writes nothing to global memory; it only pulls the kernel's instructions
+              // into L2 ahead of the pass's real launch
 };
 // img_f / img_r [8 u + e] = element e of unit u of the forward / reverse unit list, in the
 // state's precision (after the step's matrices are materialised).

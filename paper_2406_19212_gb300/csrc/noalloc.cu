@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <algorithm>
 #include <cstdio>
 #include <map>
 #include <mutex>
@@ -29,7 +30,8 @@ void gbvqc_internal_set_error(const char *msg);
 namespace {
 
 constexpr int kNaMaxTerms = 64;      // Pauli terms accepted (kernel-parameter space)
-constexpr int kNaMaxBlocks = 608;    // reduction blocks (4 per SM on 152 SMs)
+constexpr int kNaMaxBlocks = 608;    // reduction blocks at most: 4 per SM up to 152 SMs (the launch
+                                     // takes 4 per SM of the device, capped here)
 constexpr int kNaThreads = 256;
 
 // Scratch: [0, 256) arrival counter, [256, 256 + 8 * kNaMaxBlocks) block partials.
@@ -138,27 +140,31 @@ gbvqc_status na_fail(gbvqc_status st, const char *msg)
     return st;
 }
 
-// Device address of the scratch array, looked up once per device with that device
-// current (the host-side symbol is only a stand-in, not a device address).
-gbvqc_status na_scratch_address(unsigned char **ptr)
+// Device address of the scratch array and the device's SM count, looked up once per
+// device with that device current (the host-side symbol is only a stand-in, not a device
+// address).
+gbvqc_status na_scratch_address(unsigned char **ptr, int *sms)
 {
     static std::mutex mu;
-    static std::map<int, unsigned char *> addr;
+    static std::map<int, std::pair<unsigned char *, int>> addr;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return na_fail(GBVQC_ERR_CUDA, "expect_noalloc: no CUDA device");
     std::lock_guard<std::mutex> lk(mu);
     auto it = addr.find(dev);
     if (it == addr.end()) {
         void *p = nullptr;
+        int n_sm = 0;
         cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess || !p) {
             char msg[200];
-            snprintf(msg, sizeof msg, "expect_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            snprintf(msg, sizeof msg, "expect_noalloc: device set-up failed: %s", cudaGetErrorString(e));
             return na_fail(GBVQC_ERR_CUDA, msg);
         }
-        it = addr.emplace(dev, static_cast<unsigned char *>(p)).first;
+        it = addr.emplace(dev, std::make_pair(static_cast<unsigned char *>(p), n_sm)).first;
     }
-    *ptr = it->second;
+    *ptr = it->second.first;
+    *sms = it->second.second;
     return GBVQC_OK;
 }
 
@@ -197,14 +203,16 @@ extern "C" gbvqc_status expect_noalloc(const void *psi_device, int n_qubits, int
         g.t_end = nt;
     }
     unsigned char *scratch = nullptr;
-    gbvqc_status st = na_scratch_address(&scratch);
+    int sms = 0;
+    gbvqc_status st = na_scratch_address(&scratch, &sms);
     if (st != GBVQC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned), s);  // arrival counter starts at zero
     if (e != cudaSuccess) return na_fail(GBVQC_ERR_CUDA, cudaGetErrorString(e));
     const int64_t len = int64_t(1) << n_qubits;
     int64_t blocks = (len + kNaThreads - 1) / kNaThreads;
-    if (blocks > kNaMaxBlocks) blocks = kNaMaxBlocks;
+    const int max_blocks = std::max(1, std::min(kNaMaxBlocks, 4 * sms));
+    if (blocks > max_blocks) blocks = max_blocks;
     if (dtype == GBVQC_C64)
         k_expect_noalloc<float><<<(int)blocks, kNaThreads, 0, s>>>((const float2 *)psi_device, len, obs, scratch,
                                                                    energy_device);
