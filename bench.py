@@ -263,7 +263,10 @@ def run_ours(args, world, rank, local):
 
     # kernel-level profile of one evaluation (CUDA events on the launching stream)
     prof = gb.grad_profile(circ, w.theta, obs, gb.C64, MODE, stream=stream)
-    launches_per_step = sum(v[0] for v in prof.values())
+    # the profile times the passes alone; a step also forks one code-prefetch launch per
+    # specialised pass (two directions, no barrier passes in this circuit)
+    prefetch_launches = 2 * circ.plan_stats(gb.C64, True)["passes"] if MODE == gb.JIT else 0
+    launches_per_step = sum(v[0] for v in prof.values()) + prefetch_launches
 
     # timed region: per-step events, L2 flushed between steps outside the events
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]

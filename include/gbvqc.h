@@ -18,8 +18,8 @@
  *
  * Errors: every call returns a gbvqc_status; no call throws or aborts.  On failure
  * gbvqc_last_error() returns a message for the calling thread.  A CUDA error inside a
- * call is reported as GBVQC_ERR_CUDA; bounded device-side waits that run out return
- * GBVQC_ERR_TIMEOUT and leave the CUDA context usable.
+ * call is reported as GBVQC_ERR_CUDA.  No kernel of the library waits on another, so no
+ * call has a bounded device wait: GBVQC_ERR_TIMEOUT is reserved and no call returns it.
  *
  * Streams: `stream` arguments are cudaStream_t values passed as void* (NULL = the
  * legacy default stream).  Calls enqueue work on that stream; calls that return a
@@ -40,7 +40,7 @@ typedef enum {
     GBVQC_ERR_ARG = 1,          /* bad handle, size, qubit index or option          */
     GBVQC_ERR_OOM = 2,          /* device allocation failed                         */
     GBVQC_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed      */
-    GBVQC_ERR_TIMEOUT = 4,      /* a bounded device wait ran out                    */
+    GBVQC_ERR_TIMEOUT = 4,      /* reserved: a bounded device wait ran out (unused)  */
     GBVQC_ERR_NOT_DENSITY = 5,  /* channel applied to a pure state                  */
     GBVQC_ERR_UNSUPPORTED = 6   /* valid request the library does not implement     */
 } gbvqc_status;
