@@ -471,22 +471,34 @@ def batch_rate(gb, I, torch):
     th = torch.tensor(np.concatenate([w.theta for w in ws]), dtype=torch.float64, device="cuda")
     e = torch.empty(len(ws), dtype=torch.float64, device="cuda")
     g = torch.empty(th.numel(), dtype=torch.float64, device="cuda")
-    for _ in range(2):
-        b.grad(th, out=(e, g))
-    torch.cuda.synchronize()
-    reps = 5
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record()
-    for _ in range(reps):
-        b.grad(th, out=(e, g))
-    t1.record()
-    torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1) / reps
+
+    def time_batch():
+        for _ in range(2):
+            b.grad(th, out=(e, g))
+        torch.cuda.synchronize()
+        reps = 5
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(reps):
+            b.grad(th, out=(e, g))
+        t1.record()
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / reps
+
+    ms_default = time_batch()                      # every member at the default 12-qubit tile
+    t_setup = time.perf_counter()
+    tiles, _ = b.autotune(np.concatenate([w.theta for w in ws]))
+    tune_s = time.perf_counter() - t_setup
+    ms = time_batch()
     b.free()
+    hist = {}
+    for t in tiles:
+        hist[str(t)] = hist.get(str(t), 0) + 1
     return {"workload": "batch_512: 512 VQE instances, n ~ U{12..20}, depth ~ U{4..16}, Ry.Rz + CNOT ladder, "
                         "random-field Ising H; complex64, FP64 reductions; one CUDA-graph replay per batch",
             "ms_per_batch": ms, "gradient_evals_per_s": len(ws) * 1e3 / ms,
+            "ms_per_batch_default_tiles": ms_default, "autotuned_tiles": hist, "autotune_s": tune_s,
             "amplitudes": int(sum(1 << w.circuit.n_qubits for w in ws))}
 
 

@@ -331,6 +331,16 @@ gbvqc_status batch_free(batch_handle b);
 gbvqc_status batch_grad(batch_handle b, const double *theta_all, int n_theta_total, int ptr_loc,
                         void *stream, double *energies, double *grads);
 
+/* Autotuner of a batch: times batch_grad (theta_all on the host, n_theta_total values)
+ * with every member's tile size set to T = 8 .. 12 (clamped to the member's qubit count),
+ * then, for the four qubit-count classes holding the most amplitudes, each T for that
+ * class alone; keeps the fastest assignment (set on the member circuits, as
+ * circuit_set_tiling would, and the batch rebuilt) and returns the members' tile sizes in
+ * tiles[0 .. n_circuits) (may be NULL) and its time per batch_grad in *best_ms.  Takes
+ * up to about 25 batch rebuilds and four timed calls each.  Errors: those of batch_grad. */
+gbvqc_status batch_autotune(batch_handle b, const double *theta_all, int n_theta_total, void *stream, int *tiles,
+                            double *best_ms);
+
 /* One-shot convenience: batch_create (complex64), batch_grad with host pointers,
  * batch_free. */
 gbvqc_status grad_batch(const circuit_handle *circuits, const obs_handle *observables,

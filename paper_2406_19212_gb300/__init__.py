@@ -433,6 +433,21 @@ class BatchHandle:
             off += k
         return e, out_g
 
+    def autotune(self, thetas, stream=None):
+        """Batch autotuner (batch_autotune): returns (tile size of every member, ms per
+        batch_grad of the chosen assignment)."""
+        if isinstance(thetas, np.ndarray) and thetas.ndim == 1:
+            th = np.ascontiguousarray(thetas, dtype=np.float64)
+        else:
+            th = np.ascontiguousarray(np.concatenate([np.asarray(t, dtype=np.float64).reshape(-1)
+                                                      for t in thetas]))
+        n = len(self.n_params)
+        tiles = (ctypes.c_int * max(1, n))()
+        ms = ctypes.c_double()
+        _abi.check(_abi.lib().batch_autotune(self.handle, th.ctypes.data_as(_abi.dp) if th.size else None,
+                                             th.size, _stream_ptr(stream), tiles, ctypes.byref(ms)))
+        return [tiles[i] for i in range(n)], ms.value
+
     def free(self):
         if self.handle:
             _abi.lib().batch_free(self.handle)

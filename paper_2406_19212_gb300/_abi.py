@@ -106,6 +106,7 @@ def lib() -> ctypes.CDLL:
         "batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)],
         "batch_free": [vp],
         "batch_grad": [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp],
+        "batch_autotune": [vp, dp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)],
         "gbvqc_mem_info": [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     }
     for name, args in sig.items():
@@ -126,7 +127,7 @@ def exported_symbols() -> List[str]:
             "sv_set", "sv_get", "sv_info", "circuit_create", "circuit_free", "circuit_set_tiling",
             "circuit_plan_info", "circuit_plan_stats", "circuit_autotune", "apply_circuit", "apply_channel", "obs_create", "obs_free",
             "expect", "grad", "grad_profile", "grad_batch", "batch_create", "batch_free",
-            "batch_grad", "expect_noalloc", "measure", "sample", "gate_shape", "gbvqc_mem_info", "circuit_specialize"]
+            "batch_grad", "expect_noalloc", "measure", "sample", "gate_shape", "gbvqc_mem_info", "circuit_specialize", "batch_autotune"]
 
 
 # ------------------------------------------------------------------ marshalling

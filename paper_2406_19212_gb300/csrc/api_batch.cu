@@ -36,9 +36,9 @@ struct gbvqc_batch {
     cudaGraphExec_t graph = nullptr;
 };
 
-extern "C" gbvqc_status batch_free(batch_handle b)
+// Device resources of a batch (everything batch_build makes); the member lists stay.
+static void batch_release(gbvqc_batch *b)
 {
-    if (!b) return GBVQC_OK;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     for (auto *L : {&b->fwd, &b->rev})
@@ -47,6 +47,20 @@ extern "C" gbvqc_status batch_free(batch_handle b)
     dev_free(b->d_theta); dev_free(b->d_energies); dev_free(b->d_grads); dev_free(b->d_slot_grad);
     dev_free(b->d_slot_partials); dev_free(b->d_pauli_partials); dev_free(b->d_pauli);
     dev_free(b->d_slots); dev_free(b->d_csr_ptr); dev_free(b->d_csr_slots);
+    gbvqc_batch fresh;
+    fresh.circs = std::move(b->circs);
+    fresh.obs = std::move(b->obs);
+    fresh.dtype = b->dtype;
+    fresh.n = b->n;
+    fresh.total_params = b->total_params;
+    fresh.param_off = std::move(b->param_off);
+    *b = std::move(fresh);
+}
+
+extern "C" gbvqc_status batch_free(batch_handle b)
+{
+    if (!b) return GBVQC_OK;
+    batch_release(b);
     delete b;
     return GBVQC_OK;
 }
@@ -252,4 +266,85 @@ extern "C" gbvqc_status grad_batch(const circuit_handle *circuits, const obs_han
     gbvqc_status st = batch_grad(b, theta_all, b->total_params, GBVQC_PTR_HOST, stream, energies, grads);
     batch_free(b);
     return st;
+}
+
+// Rebuild the batch after its members' tilings changed.
+static gbvqc_status batch_rebuild(gbvqc_batch *b)
+{
+    batch_release(b);
+    return batch_build(b);
+}
+
+extern "C" gbvqc_status batch_autotune(batch_handle b, const double *theta_all, int n_theta_total, void *stream,
+                                       int *tiles, double *best_ms)
+{
+    if (!b || !best_ms || (n_theta_total > 0 && !theta_all)) return fail(GBVQC_ERR_ARG, "NULL argument");
+    if (n_theta_total != b->total_params)
+        return fail(GBVQC_ERR_ARG, "expected %d parameters, got %d", b->total_params, n_theta_total);
+    const int n = b->n, tmax = max_tile(b->dtype);
+    std::vector<double> e(n), g(std::max(1, b->total_params));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    // member i's tile for a requested size: within [8, 12] and the member's qubits
+    auto clamp_tile = [&](int i, int t) { return std::max(6, std::min({t, tmax, b->circs[i]->n_phys})); };
+    auto evaluate = [&](const std::vector<int> &t, double *ms) -> gbvqc_status {
+        for (int i = 0; i < n; i++)
+            if (b->circs[i]->tile_qubits != t[i]) ST_TRY(circuit_set_tiling(b->circs[i], t[i], b->circs[i]->low_qubits));
+        ST_TRY(batch_rebuild(b));
+        // one call captures the graph; then the median of three timed calls
+        ST_TRY(batch_grad(b, theta_all, n_theta_total, GBVQC_PTR_HOST, stream, e.data(), g.data()));
+        std::vector<double> runs;
+        for (int r = 0; r < 3; r++) {
+            CUDA_TRY(cudaEventRecord(e0, (cudaStream_t)stream));
+            ST_TRY(batch_grad(b, theta_all, n_theta_total, GBVQC_PTR_HOST, stream, e.data(), g.data()));
+            CUDA_TRY(cudaEventRecord(e1, (cudaStream_t)stream));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float f = 0;
+            CUDA_TRY(cudaEventElapsedTime(&f, e0, e1));
+            runs.push_back(f);
+        }
+        std::sort(runs.begin(), runs.end());
+        *ms = runs[1];
+        return GBVQC_OK;
+    };
+    gbvqc_status st = GBVQC_OK;
+    std::vector<int> best(n), cur(n);
+    double best_t = 1e30;
+    // one tile size for every member (clamped to its qubits) ...
+    for (int T = 8; T <= 12 && st == GBVQC_OK; T++) {
+        for (int i = 0; i < n; i++) cur[i] = clamp_tile(i, T);
+        double ms = 0;
+        st = evaluate(cur, &ms);
+        if (st == GBVQC_OK && ms < best_t) best_t = ms, best = cur;
+    }
+    // ... then per qubit-count class, the classes with the most amplitudes first
+    std::map<int, double> weight;
+    for (int i = 0; i < n; i++) weight[b->circs[i]->n_phys] += std::ldexp(1.0, b->circs[i]->n_phys);
+    std::vector<std::pair<double, int>> classes;
+    for (auto &kv : weight) classes.push_back({-kv.second, kv.first});
+    std::sort(classes.begin(), classes.end());
+    for (size_t ci = 0; ci < classes.size() && ci < 4 && st == GBVQC_OK; ci++) {
+        const int nq = classes[ci].second;
+        for (int T = 8; T <= 12 && st == GBVQC_OK; T++) {
+            cur = best;
+            bool changed = false;
+            for (int i = 0; i < n; i++)
+                if (b->circs[i]->n_phys == nq && cur[i] != clamp_tile(i, T)) cur[i] = clamp_tile(i, T), changed = true;
+            if (!changed) continue;
+            double ms = 0;
+            st = evaluate(cur, &ms);
+            if (st == GBVQC_OK && ms < best_t) best_t = ms, best = cur;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != GBVQC_OK) return st;
+    for (int i = 0; i < n; i++)
+        if (b->circs[i]->tile_qubits != best[i]) ST_TRY(circuit_set_tiling(b->circs[i], best[i], b->circs[i]->low_qubits));
+    ST_TRY(batch_rebuild(b));
+    if (tiles)
+        for (int i = 0; i < n; i++) tiles[i] = best[i];
+    *best_ms = best_t;
+    return GBVQC_OK;
 }

@@ -67,6 +67,38 @@ def test_batch512_full_sample():
         assert abs(e[i] - e1) <= 1e-5 * max(1.0, abs(e1))
         assert np.abs(gs[i] - g1).max() <= 1e-4 * np.abs(g1).max()
     assert np.all(np.isfinite(e)) and np.all(np.abs(e) <= [sum(abs(c) for c, _ in w.observable) for w in ws])
+    # full-size members against the oracle directly: the largest 20-qubit member, the
+    # deepest member and a 12-qubit one
+    n20 = [i for i, w in enumerate(ws) if w.circuit.n_qubits == 20]
+    big = max(n20, key=lambda i: ws[i].circuit.n_params)
+    deep = max(range(len(ws)), key=lambda i: len(ws[i].circuit.ops))
+    small = min(range(len(ws)), key=lambda i: ws[i].circuit.n_qubits)
+    for i in sorted({big, deep, small}):
+        e_ref, g_ref = O.adjoint_grad(ws[i].circuit, ws[i].theta, ws[i].observable)
+        assert abs(e[i] - e_ref) <= 1e-5 * max(1.0, abs(e_ref))
+        assert np.abs(gs[i] - g_ref).max() <= 1e-4 * np.abs(g_ref).max()
+    b.free()
+
+
+def test_batch_autotune_keeps_results():
+    """batch_autotune picks member tile sizes in [8, 12] (within each member's qubits)
+    and the rebuilt batch still matches the oracle."""
+    ws = small_batch(seed=11, count=10, n_lo=8, n_hi=14)
+    circs = [gb.circuit_create(w.circuit) for w in ws]
+    obss = [gb.obs_create(w.observable, w.circuit.n_qubits) for w in ws]
+    b = gb.batch_create(circs, obss)
+    thetas = [w.theta for w in ws]
+    tiles, ms = b.autotune(thetas)
+    assert ms > 0 and len(tiles) == len(ws)
+    for t, w in zip(tiles, ws):
+        assert min(8, w.circuit.n_qubits) <= t <= min(12, w.circuit.n_qubits)
+    for i, c in enumerate(circs):
+        assert c.plan_stats(gb.C64, True)["tile_qubits"] == tiles[i]
+    e, gs = b.grad(thetas)
+    for i in (0, 3, len(ws) - 1):
+        e_ref, g_ref = O.adjoint_grad(ws[i].circuit, thetas[i], ws[i].observable)
+        assert abs(e[i] - e_ref) <= 1e-5 * max(1.0, abs(e_ref))
+        assert np.abs(gs[i] - g_ref).max() <= 1e-4 * np.abs(g_ref).max()
     b.free()
 
 
