@@ -347,6 +347,54 @@ gbvqc_status grad_batch(const circuit_handle *circuits, const obs_handle *observ
                         int n_circuits, const double *theta_all, void *stream,
                         double *energies, double *grads);
 
+/* ------------------------------------------- sharded states with qubit-swap exchange */
+
+/* A pure state of n_qubits split into 2^n_global shards by its n_global global qubits
+ * (the standard partition of a state over devices, each shard holding 2^(n - n_global)
+ * amplitudes; the paper simulates beyond one device with distributed simulators,
+ * Introduction).  Gates on local qubits act on every shard alone; diagonal gates on
+ * global qubits become per-shard phases or one-qubit diagonals on the local partner;
+ * any other gate on a global qubit is preceded by a qubit swap that trades its position
+ * with a local qubit's, exchanging half of every shard with its partner shard.  In this
+ * library the shards are buffers on the calling thread's current GPU and the exchange a
+ * swap kernel between them (one GPU per process); the schedule is the one a multi-device
+ * run would execute. */
+typedef struct gbvqc_sharded *sharded_handle;
+
+/* The exchange schedule of a pure circuit for n_global global qubits (host only, no GPU):
+ * steps[3 i .. 3 i + 2] = {0, op_begin, op_end} (apply ops [op_begin, op_end) of the
+ * circuit on every shard) or {1, j, l} (swap global qubit position j with local qubit
+ * position l).  Positions start as the identity (qubit q at position q; positions
+ * >= n - n_global are global, bit position - (n - n_global) of the shard index).  The
+ * local qubit given up is the one whose next non-diagonal use is farthest away.  Fills
+ * min(max_steps, total) steps, sets *n_steps = total and *n_swaps (may be NULL).
+ * Errors: ERR_ARG (NULL, n_global outside [1, n - 2]), ERR_UNSUPPORTED (density circuit). */
+gbvqc_status shard_plan(circuit_handle c, int n_global, int32_t *steps, int max_steps, int *n_steps, int *n_swaps);
+
+/* A sharded state |0...0> of n_qubits (3 .. 34) with n_global (1 .. 10, leaving at least
+ * two local qubits) global qubits, dtype GBVQC_C64 / GBVQC_C128.  Errors: ERR_ARG,
+ * ERR_OOM, ERR_CUDA. */
+gbvqc_status sharded_alloc(int n_qubits, int n_global, int dtype, sharded_handle *out);
+gbvqc_status sharded_free(sharded_handle h);
+
+/* Copy the full state (2^n amplitudes in the logical order, index bit q = qubit q, host
+ * memory) into / out of the shards, through the state's current qubit positions.
+ * Synchronous. */
+gbvqc_status sharded_set(sharded_handle h, const void *host_src);
+gbvqc_status sharded_get(sharded_handle h, void *host_dst);
+
+/* psi <- C(theta) psi for a pure circuit of the same qubit count (theta on the host): the
+ * exchange schedule from the state's current positions, local segments run as tile passes
+ * on every shard (per-gate kernels below 6 local qubits), exchanges between the shard
+ * pairs.  The positions the schedule leaves are kept (sharded_get reads through them).
+ * Synchronous.  Errors: ERR_ARG, ERR_UNSUPPORTED (density circuit), ERR_OOM, ERR_CUDA. */
+gbvqc_status sharded_apply(sharded_handle h, circuit_handle c, const double *theta, int n_theta);
+
+/* The current position of every qubit (n_qubits entries), and the exchanges made so far
+ * (shard-pair swaps) with their bytes moved (each pair swaps half of both shards); any
+ * pointer may be NULL. */
+gbvqc_status sharded_info(sharded_handle h, int32_t *positions, int64_t *exchanges, int64_t *bytes);
+
 /* ------------------------------------------------------ allocation-free expectation */
 
 /* <psi|H|psi> of a pure state for callers that cannot allocate device memory.  The

@@ -25,7 +25,8 @@ from ._abi import C64, C128, FUSED, JIT, PLAIN, GbvqcError
 __all__ = ["C64", "C128", "PLAIN", "FUSED", "JIT", "GbvqcError", "StateVector", "CircuitHandle",
            "Observable", "sv_alloc", "sv_wrap", "sv_set", "sv_get", "sv_reset",
            "circuit_create", "apply_circuit", "apply_channel", "obs_create", "expect", "grad",
-           "grad_profile", "grad_batch", "batch_create", "BatchHandle", "expect_noalloc", "mem_info", "measure", "sample",
+           "grad_profile", "grad_batch", "batch_create", "BatchHandle", "expect_noalloc", "mem_info", "measure", "sample", "shard_plan", "ShardedState",
+           "sharded_alloc",
            "gate_shape",
            "VQEEnergy",
            "load"]
@@ -144,6 +145,7 @@ class CircuitHandle:
         self.n_qubits = circuit.n_qubits
         self.n_params = circuit.n_params
         self.density = circuit.density
+        self.n_ops = len(circuit.ops)
 
     def set_tiling(self, tile_qubits: int = 0, low_qubits: int = 0) -> None:
         _abi.check(_abi.lib().circuit_set_tiling(self.handle, tile_qubits, low_qubits))
@@ -385,6 +387,60 @@ def grad_profile(circ: CircuitHandle, theta, obs: Observable, dtype: int = C64,
     del keep
     return {stats[i].name.decode(): (stats[i].launches, stats[i].ms, stats[i].alg_flops,
                                      stats[i].alg_bytes) for i in range(n.value)}
+
+
+def shard_plan(circ: CircuitHandle, n_global: int):
+    """Exchange schedule for n_global global qubits: [("ops", begin, end) | ("swap", j, l)]."""
+    cap = 2 * circ.n_ops + 16
+    buf = (ctypes.c_int32 * (3 * cap))()
+    n, sw = ctypes.c_int(), ctypes.c_int()
+    _abi.check(_abi.lib().shard_plan(circ.handle, n_global, buf, cap, ctypes.byref(n), ctypes.byref(sw)))
+    return [("ops" if buf[3 * i] == 0 else "swap", buf[3 * i + 1], buf[3 * i + 2]) for i in range(n.value)]
+
+
+class ShardedState:
+    """A pure state split into 2^n_global shards by its global qubits (sharded_alloc)."""
+
+    def __init__(self, n_qubits: int, n_global: int, dtype: int = C64):
+        h = ctypes.c_void_p()
+        _abi.check(_abi.lib().sharded_alloc(n_qubits, n_global, dtype, ctypes.byref(h)))
+        self.handle, self.n_qubits, self.n_global, self.dtype = h.value, n_qubits, n_global, dtype
+
+    def set(self, amps) -> None:
+        a = np.ascontiguousarray(np.asarray(amps), dtype=_np_dtype(self.dtype))
+        assert a.size == 1 << self.n_qubits
+        _abi.check(_abi.lib().sharded_set(self.handle, a.ctypes.data))
+
+    def get(self) -> np.ndarray:
+        out = np.empty(1 << self.n_qubits, dtype=_np_dtype(self.dtype))
+        _abi.check(_abi.lib().sharded_get(self.handle, out.ctypes.data))
+        return out
+
+    def apply(self, circ: CircuitHandle, theta=()) -> None:
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1))
+        _abi.check(_abi.lib().sharded_apply(self.handle, circ.handle,
+                                            th.ctypes.data_as(_abi.dp) if th.size else None, th.size))
+
+    def info(self):
+        pos = (ctypes.c_int32 * self.n_qubits)()
+        ex, by = ctypes.c_int64(), ctypes.c_int64()
+        _abi.check(_abi.lib().sharded_info(self.handle, pos, ctypes.byref(ex), ctypes.byref(by)))
+        return list(pos), ex.value, by.value
+
+    def free(self):
+        if self.handle:
+            _abi.lib().sharded_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sharded_alloc(n_qubits: int, n_global: int, dtype: int = C64) -> ShardedState:
+    return ShardedState(n_qubits, n_global, dtype)
 
 
 class BatchHandle:

@@ -108,6 +108,15 @@ def lib() -> ctypes.CDLL:
         "batch_grad": [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp],
         "batch_autotune": [vp, dp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)],
         "gbvqc_mem_info": [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+        "shard_plan": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                       ctypes.POINTER(ctypes.c_int)],
+        "sharded_alloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)],
+        "sharded_free": [vp],
+        "sharded_set": [vp, vp],
+        "sharded_get": [vp, vp],
+        "sharded_apply": [vp, vp, dp, ctypes.c_int],
+        "sharded_info": [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                         ctypes.POINTER(ctypes.c_int64)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -127,7 +136,8 @@ def exported_symbols() -> List[str]:
             "sv_set", "sv_get", "sv_info", "circuit_create", "circuit_free", "circuit_set_tiling",
             "circuit_plan_info", "circuit_plan_stats", "circuit_autotune", "apply_circuit", "apply_channel", "obs_create", "obs_free",
             "expect", "grad", "grad_profile", "grad_batch", "batch_create", "batch_free",
-            "batch_grad", "expect_noalloc", "measure", "sample", "gate_shape", "gbvqc_mem_info", "circuit_specialize", "batch_autotune"]
+            "batch_grad", "expect_noalloc", "measure", "sample", "gate_shape", "gbvqc_mem_info", "circuit_specialize", "batch_autotune", "shard_plan", "sharded_alloc",
+            "sharded_free", "sharded_set", "sharded_get", "sharded_apply", "sharded_info"]
 
 
 # ------------------------------------------------------------------ marshalling

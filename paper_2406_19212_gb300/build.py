@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbvqc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api_state.cu", "api_matrices.cu", "api_circuit.cu", "api_grad.cu", "api_tune.cu",
-           "api_batch.cu", "planner.cpp", "jit.cpp", "kernels_plain.cu", "kernels_reduce.cu",
+           "api_batch.cu", "api_shard.cu", "planner.cpp", "jit.cpp", "kernels_plain.cu", "kernels_reduce.cu",
            "kernels_fused.cu", "kernels_batch.cu", "noalloc.cu"]
 # device headers the specialised tile passes are compiled from at run time (NVRTC), embedded
 # into the library as strings

@@ -57,6 +57,8 @@ constexpr int kMaxRedBlocks = 1024;
 cudaError_t launch_gate(int dtype, void *psi, int n, int shape, int q0, int q1,
                         const MatRec *rec, cudaStream_t s);
 cudaError_t launch_zero_state(int dtype, void *psi, int n, cudaStream_t s);
+// Qubit-swap exchange between two shards of 2^local_qubits amplitudes (see k_shard_swap).
+cudaError_t launch_shard_swap(int dtype, void *a, void *b, int local_qubits, int l, cudaStream_t s);
 // Four-qubit gate: psi <- M psi on physical qubits q0..q3 (matrix bits 0..3), M = 16 x 16
 // complex in 16 consecutive records (record r = row r).
 cudaError_t launch_gate4(int dtype, void *psi, int n, int q0, int q1, int q2, int q3, const MatRec *rows,

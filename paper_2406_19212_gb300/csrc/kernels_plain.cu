@@ -316,6 +316,32 @@ cudaError_t launch_zero_state(int dtype, void *psi, int n, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Qubit-swap exchange of a sharded state: shard a (global bit j = 0) and shard b (its
+// partner, bit j = 1) of 2^L amplitudes each exchange the amplitudes whose local bit l is
+// 1 in a with those whose local bit l is 0 in b, at equal other bits; afterwards the
+// global qubit and the local qubit have traded positions.  2^(L-1) swaps per pair.
+template <typename T>
+__global__ void __launch_bounds__(256) k_shard_swap(T *__restrict__ a, T *__restrict__ b, int64_t half, int l)
+{
+    const int64_t lowmask = (int64_t(1) << l) - 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < half; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x0 = ((i & ~lowmask) << 1) | (i & lowmask);  // local bit l = 0
+        const int64_t x1 = x0 | (int64_t(1) << l);
+        const T u = a[x1];
+        a[x1] = b[x0];
+        b[x0] = u;
+    }
+}
+
+cudaError_t launch_shard_swap(int dtype, void *a, void *b, int local_qubits, int l, cudaStream_t s)
+{
+    const int64_t half = int64_t(1) << (local_qubits - 1);
+    const int gr = grid_for(half, 256);
+    if (dtype == 0) k_shard_swap<float2><<<gr, 256, 0, s>>>((float2 *)a, (float2 *)b, half, l);
+    else k_shard_swap<double2><<<gr, 256, 0, s>>>((double2 *)a, (double2 *)b, half, l);
+    return cudaGetLastError();
+}
+
 // Gate materialisation on the device: theta -> rotation matrices (record by record).
 __global__ void k_materialize(const DynRec *__restrict__ dyn, int n_dyn,
                               const double *__restrict__ theta, MatRec *recs)
