@@ -680,9 +680,9 @@ constexpr int kTwoCtaSmem = 110 * 1024;
 // batch: the plan a batch member runs with (launches shared by all members take the
 // largest member's shared memory, so its passes keep the smaller slot budget that leaves
 // two CTAs per SM; a single circuit takes larger passes, fewer tile loads and stores).
-gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out, bool batch)
+gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out, bool batch, bool jit)
 {
-    int key = dtype * 2 + (grad_layout ? 1 : 0) + (batch ? 4 : 0);
+    int key = dtype * 2 + (grad_layout ? 1 : 0) + (batch ? 4 : 0) + (jit ? 8 : 0);
     auto it = c->plans.find(key);
     if (it != c->plans.end()) {
         *out = it->second.get();
@@ -692,8 +692,9 @@ gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPla
     PlanOptions opt;
     opt.t = c->tile_qubits ? c->tile_qubits : default_tile(dtype);
     opt.low = c->low_qubits ? c->low_qubits : default_low(dtype);
-    opt.nr_f = fused_nr(dtype, false);
-    opt.nr_r = fused_nr(dtype, true);
+    const int64_t tiles = int64_t(1) << (c->n_phys - std::min(std::min(opt.t, max_tile(dtype)), c->n_phys));
+    opt.nr_f = jit ? jit_nr(dtype, false, tiles) : fused_nr(dtype, false);
+    opt.nr_r = jit ? jit_nr(dtype, true, tiles) : fused_nr(dtype, true);
     opt.t = std::min(opt.t, max_tile(dtype));
     opt.elem_bytes = dtype == GBVQC_C64 ? 4 : 8;
     opt.max_slots = batch ? 128 : 512;
@@ -742,10 +743,10 @@ gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPla
 }
 
 // Fused plan with its device copies.
-gbvqc_status get_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out, bool batch)
+gbvqc_status get_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out, bool batch, bool jit)
 {
     DevPlan *dp = nullptr;
-    ST_TRY(get_host_plan(c, dtype, grad_layout, &dp, batch));
+    ST_TRY(get_host_plan(c, dtype, grad_layout, &dp, batch, jit));
     if (!dp->uploaded) {
         CUDA_TRY(fused_prepare());
         ST_TRY(upload(&dp->d_fwd, dp->p.fwd));
@@ -854,7 +855,7 @@ extern "C" gbvqc_status circuit_specialize(circuit_handle c, int dtype, int for_
     std::lock_guard<std::mutex> lk(c->mu);
     if (!fused_supported(c, dtype)) return fail(GBVQC_ERR_UNSUPPORTED, "too few qubits for tiles");
     DevPlan *p = nullptr;
-    ST_TRY(get_host_plan(c, dtype, for_grad != 0, &p));
+    ST_TRY(get_host_plan(c, dtype, for_grad != 0, &p, false, true));
     std::vector<JitModule> mods;
     double secs = 0;
     std::string err;

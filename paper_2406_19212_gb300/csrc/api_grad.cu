@@ -172,7 +172,7 @@ extern "C" gbvqc_status apply_circuit(sv_handle sv, circuit_handle c, const doub
     CUDA_TRY(launch_materialize(c->d_dyn, (int)c->dyn.size(), c->ws.d_theta, c->d_recs, s));
     if (mode != GBVQC_MODE_PLAIN && fused_supported(c, sv->dtype)) {
         DevPlan *p = nullptr;
-        ST_TRY(get_plan(c, sv->dtype, false, &p));
+        ST_TRY(get_plan(c, sv->dtype, false, &p, false, mode == GBVQC_MODE_JIT));
         if (mode == GBVQC_MODE_JIT) ST_TRY(ensure_jit(p, sv->dtype, false));
         ST_TRY(gather_images(c, p, sv->dtype, false, s));
         return run_fused_forward(c, p, sv->dtype, sv->data, s, mode == GBVQC_MODE_JIT);
@@ -309,7 +309,7 @@ extern "C" gbvqc_status grad(circuit_handle c, const double *theta, int n_theta,
     ST_TRY(ensure_obs(h));
     DevPlan *p = nullptr;
     if (mode != GBVQC_MODE_PLAIN && fused_supported(c, dtype)) {
-        ST_TRY(get_plan(c, dtype, true, &p));
+        ST_TRY(get_plan(c, dtype, true, &p, false, mode == GBVQC_MODE_JIT));
         if (mode == GBVQC_MODE_JIT) ST_TRY(ensure_jit(p, dtype, true));
     } else {
         mode = GBVQC_MODE_PLAIN;

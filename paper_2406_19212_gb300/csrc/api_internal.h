@@ -242,9 +242,11 @@ gbvqc_status ensure_device(gbvqc_circuit *c);
 // Largest tile the fused kernels take for dtype.
 int max_tile(int dtype);
 // Fused plan for (dtype, layout), host side only (no GPU needed); batch: the plan of a
-// batch member.
-gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out, bool batch = false);
+// batch member; jit: the plan of the specialised passes (its own register-qubit counts).
+gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out, bool batch = false,
+                           bool jit = false);
 // The same with its device copies.
-gbvqc_status get_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out, bool batch = false);
+gbvqc_status get_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPlan **out, bool batch = false,
+                      bool jit = false);
 bool fused_supported(const gbvqc_circuit *c, int dtype);
 double state_bytes(const gbvqc_circuit *c, int dtype);

@@ -546,6 +546,47 @@ __device__ __forceinline__ void emit_partials(const RedCtx<R> &c, const int (&lo
         for (int k = 0; k < N; k++) c.sgrad[local_slot[k] * c.nwarps + c.warp] = v[k];
 }
 
+// N per-thread partials (N <= 32) summed over the warp by a transpose reduction, for the
+// pass-local slots first_slot .. first_slot + N - 1: each of the first log2(N') steps
+// (N' = N rounded up to a power of two) halves the values a lane holds, exchanging the
+// half it gives up with its partner, so N values cost about 2 N' shuffles and adds
+// instead of 5 N; the remaining steps are a plain butterfly.  Lane l then holds the sum
+// of value index (its high lane bits), and the lanes whose low bits are zero store it.
+// Blocks narrower than a warp take the plain form.
+template <typename R, int N>
+__device__ __forceinline__ void emit_partials_seq(const RedCtx<R> &c, int first_slot, R (&v)[N])
+{
+    constexpr int S = N <= 1 ? 0 : N <= 2 ? 1 : N <= 4 ? 2 : N <= 8 ? 3 : N <= 16 ? 4 : 5;
+    if (c.lanes < 32) {
+        int ls[N];
+#pragma unroll
+        for (int k = 0; k < N; k++) ls[k] = first_slot + k;
+        emit_partials<R, N>(c, ls, v);
+        return;
+    }
+    R w[1 << S];
+#pragma unroll
+    for (int k = 0; k < (1 << S); k++) w[k] = k < N ? v[k] : R(0);
+#pragma unroll
+    for (int t = 0; t < S; t++) {
+        const int o = 16 >> t, half = 1 << (S - t - 1);
+        const bool hi = (c.lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; i++) {
+            const R send = hi ? w[i] : w[i + half];
+            const R keep = hi ? w[i + half] : w[i];
+            w[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+#pragma unroll
+    for (int o = 16 >> S; o > 0; o >>= 1) w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
+    int idx = 0;
+#pragma unroll
+    for (int t = 0; t < S; t++)
+        if (c.lane & (16 >> t)) idx |= 1 << (S - t - 1);
+    if ((c.lane & ((1 << (5 - S)) - 1)) == 0 && idx < N) c.sgrad[(first_slot + idx) * c.nwarps + c.warp] = w[0];
+}
+
 // A 2x2 matrix unit (8 reals) from shared memory as 16-byte vector loads.
 template <typename R>
 __device__ __forceinline__ void load_unit(const R *p, R (&m)[8])
@@ -936,20 +977,26 @@ __device__ __forceinline__ void subrun_store(const TileCtx<R, NR, REV> &c, int b
 }
 
 // Z-generator reads of a phase block (reverse): per register bit k the sum of
-// Im(conj(Psi) Phi) with sign (-1)^(bit k), and the total.
+// Im(conj(Psi) Phi) with sign (-1)^(bit k), and the total.  A halving tree: level k
+// holds the sums of v over the lowest k bits, and dk[k] is the alternating sum of level
+// k's entries (2^(NR+1) + 2^NR - NR - 3 adds instead of (NR + 1) 2^NR).
 template <typename R, int NR>
 __device__ __forceinline__ void z_sums(const typename CT<R>::T *a, const typename CT<R>::T *b, R &tot, R (&dk)[NR])
 {
-    tot = 0;
+    R s[1 << NR];
 #pragma unroll
-    for (int k = 0; k < NR; k++) dk[k] = 0;
+    for (int j = 0; j < (1 << NR); j++) s[j] = b[j].x * a[j].y - b[j].y * a[j].x;  // Im(conj(Psi) Phi)
 #pragma unroll
-    for (int j = 0; j < (1 << NR); j++) {
-        const R v = b[j].x * a[j].y - b[j].y * a[j].x;  // Im(conj(Psi) Phi)
-        tot += v;
+    for (int k = 0; k < NR; k++) {
+        const int m = 1 << (NR - k - 1);  // pairs at this level
+        R d = s[0] - s[1];
 #pragma unroll
-        for (int k = 0; k < NR; k++) dk[k] += ((j >> k) & 1) ? -v : v;
+        for (int i = 1; i < m; i++) d += s[2 * i] - s[2 * i + 1];
+        dk[k] = d;
+#pragma unroll
+        for (int i = 0; i < m; i++) s[i] = s[2 * i] + s[2 * i + 1];
     }
+    tot = s[0];
 }
 
 // The record interpreter: gates [g_begin, g_end) of the pass on the register amplitudes.

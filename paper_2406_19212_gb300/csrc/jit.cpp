@@ -167,11 +167,17 @@ void emit_gate(std::ostringstream &o, const FusedPlan &P, const PassDesc &d, con
             if (rev) o << ind << "rg1<Rt, NR, " << K << ", " << SH << ">(b, smat + " << 8 * e.mat2 << ");\n";
         }
         if (!reads.empty()) {
-            o << ind << "{ const int ls[" << reads.size() << "] = {";
-            for (size_t i = 0; i < reads.size(); i++) o << (i ? ", " : "") << reads[i].first;
-            o << "}; Rt lv[" << reads.size() << "] = {";
+            bool seq = true;  // the planner numbers a record's gradient slots consecutively
+            for (size_t i = 0; i < reads.size(); i++) seq = seq && reads[i].first == reads[0].first + (int)i;
+            o << ind << "{ Rt lv[" << reads.size() << "] = {";
             for (size_t i = 0; i < reads.size(); i++) o << (i ? ", " : "") << reads[i].second;
-            o << "}; emit_partials<Rt, " << reads.size() << ">(rc, ls, lv); }\n";
+            if (seq) {
+                o << "}; emit_partials_seq<Rt, " << reads.size() << ">(rc, " << reads[0].first << ", lv); }\n";
+            } else {
+                o << "}; const int ls[" << reads.size() << "] = {";
+                for (size_t i = 0; i < reads.size(); i++) o << (i ? ", " : "") << reads[i].first;
+                o << "}; emit_partials<Rt, " << reads.size() << ">(rc, ls, lv); }\n";
+            }
         }
         o << ind << "}\n";
         return;
@@ -179,17 +185,24 @@ void emit_gate(std::ostringstream &o, const FusedPlan &P, const PassDesc &d, con
     if (g.type == FT_DIAGB) {
         const int off = g.ent + (rev ? g.nz : 0);
         if (rev && g.nz > 0) {
+            bool seq = true;
+            for (int i = 0; i < g.nz; i++)
+                seq = seq && E[d.ent_begin + g.ent + i].slot == E[d.ent_begin + g.ent].slot + i;
             o << ind << "{ Rt tot, dk[NR]; z_sums<Rt, NR>(a, b, tot, dk);\n" << ind << "  const int ls[" << (int)g.nz
               << "] = {";
             for (int i = 0; i < g.nz; i++) o << (i ? ", " : "") << E[d.ent_begin + g.ent + i].slot - d.slot_begin;
-            o << "};\n" << ind << "  Rt lv[" << (int)g.nz << "] = {";
+            o << "};\n" << ind << "  (void)ls;\n" << ind << "  Rt lv[" << (int)g.nz << "] = {";
             for (int i = 0; i < g.nz; i++) {
                 const DEnt &z = E[d.ent_begin + g.ent + i];
                 if (i) o << ", ";
                 if (z.ca >= 0 && z.ca < NR) o << "dk[" << (int)z.ca << "] * " << flit(z.coef);
                 else o << "(const_bit<NR>(" << (int)z.ca << ", base, tilebase) ? -tot : tot) * " << flit(z.coef);
             }
-            o << "};\n" << ind << "  emit_partials<Rt, " << (int)g.nz << ">(rc, ls, lv); }\n";
+            if (seq)
+                o << "};\n" << ind << "  emit_partials_seq<Rt, " << (int)g.nz << ">(rc, "
+                  << E[d.ent_begin + g.ent].slot - d.slot_begin << ", lv); }\n";
+            else
+                o << "};\n" << ind << "  emit_partials<Rt, " << (int)g.nz << ">(rc, ls, lv); }\n";
         }
         const bool table = g.flags & FLAG_TABLE, sep = rev && (g.flags & FLAG_SEPARATE);
         const int cs = 4 * g.slot;
@@ -228,6 +241,18 @@ void emit_gate(std::ostringstream &o, const FusedPlan &P, const PassDesc &d, con
 
 }  // namespace
 
+int jit_nr(int dtype, bool reverse, int64_t tiles)
+{
+    if (dtype != 0) return reverse ? 3 : 4;
+    // measured: a 20-qubit state (256 tiles) forward 5 -> 4 takes the gradient step from
+    // 0.767 to 0.663 ms (twice the warps); a 28-qubit one (65536 tiles) is 73.5 -> 79.0 ms
+    // slower with 4 (warps to spare, fewer sub-runs with 5)
+    if (reverse) return 4;
+    return tiles < 1024 ? 4 : 5;
+}
+
+int jit_min_blocks(int threads) { return threads >= 256 ? 2 : 3; }
+
 std::string jit_kernel_name(int p, bool rev) { return std::string(rev ? "gbvqc_jit_r" : "gbvqc_jit_f") + std::to_string(p); }
 
 std::string jit_source(const FusedPlan &P, int p, bool rev, int dtype)
@@ -240,8 +265,8 @@ std::string jit_source(const FusedPlan &P, int p, bool rev, int dtype)
     o << "// specialised " << (rev ? "reverse" : "forward") << " tile pass " << p << " (generated)\n"
       << "#include \"fused_tile.cuh\"\nusing namespace gbvqc;\n"
       << "typedef " << (dtype == 0 ? "float" : "double") << " Rt;\ntypedef CT<Rt>::T Tt;\n"
-      << "extern \"C\" __global__ void __launch_bounds__(" << fused_max_threads(NR, rev) << ", "
-      << fused_min_blocks(rev) << ") " << jit_kernel_name(p, rev)
+      << "extern \"C\" __global__ void __launch_bounds__(" << (1 << (d.t - NR)) << ", "
+      << jit_min_blocks(1 << (d.t - NR)) << ") " << jit_kernel_name(p, rev)
       << "(Tt *__restrict__ phi, Tt *__restrict__ psi, const FusedArgs args)\n{\n"
       << "  constexpr int NR = " << NR << ";\n  constexpr bool REV = " << (rev ? "true" : "false") << ";\n"
       << "  // a code-prefetch launch (args.dry) runs tile 0 and CTA s walks sub-run s only\n"

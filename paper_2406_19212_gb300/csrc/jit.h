@@ -30,6 +30,14 @@ struct JitPlan {
     int compiled = 0, cached = 0;   // passes compiled now / loaded from the on-disk cache
 };
 
+// Register qubits of the specialised passes' sub-runs (their plans are built with these),
+// for a state of `tiles` tiles: complex64 4 in reverse, and forward 4 below 1024 tiles
+// (few CTAs per SM: straight-line code gains from twice the warps and half the code per
+// gate) else 5 (the interpreter's choice); complex128 as the interpreter.
+int jit_nr(int dtype, bool reverse, int64_t tiles);
+// CTAs per SM the specialised kernels are compiled for (launch bounds), by CTA size.
+int jit_min_blocks(int threads);
+
 // CUDA source of the specialised kernel of pass p of the plan (rev: the reverse sweep).
 std::string jit_source(const FusedPlan &plan, int p, bool rev, int dtype);
 std::string jit_kernel_name(int p, bool rev);
