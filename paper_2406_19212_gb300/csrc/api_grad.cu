@@ -92,15 +92,17 @@ static gbvqc_status ensure_jit(DevPlan *p, int dtype, bool with_rev)
 // Code prefetch of the specialised passes of a gradient evaluation.  Straight-line passes
 // are hundreds of kilobytes of instructions each; when the caches are cold (another
 // workload ran in between) every SM would stream them from HBM at the pace of its
-// instruction fetch.  At the start of the evaluation a dry launch of every pass (one CTA
-// per sub-run, each walking its own sub-run's code on tile 0, no global stores) is forked
-// onto its own side stream: they pull all passes' code into L2 concurrently, in a few
-// microseconds, before the real launches reach it.  join = false forks, join = true makes
-// s wait for the prefetch launches.
-static gbvqc_status jit_prefetch(gbvqc_circuit *c, DevPlan *p, bool join, cudaStream_t s)
+// instruction fetch.  A dry launch of every pass (one CTA per sub-run, each walking its
+// own sub-run's code on tile 0, no global stores) is forked onto its own side stream:
+// they pull the passes' code into L2 concurrently, in a few microseconds, before the real
+// launches reach it.  Phase 0 forks the forward passes' prefetch at the start of the
+// evaluation, phase 1 the reverse passes' after the forward sweep (so that their CTAs do
+// not take SM slots from the forward passes; the expectation kernel between the sweeps
+// gives them time), phase 2 makes s wait for all of them.
+static gbvqc_status jit_prefetch(gbvqc_circuit *c, DevPlan *p, int phase, cudaStream_t s)
 {
     if (g_prof || !p->jit || p->pf_streams.empty()) return GBVQC_OK;  // profiles time the passes alone
-    if (join) {
+    if (phase == 2) {
         for (cudaEvent_t ev : p->pf_done) CUDA_TRY(cudaStreamWaitEvent(s, ev, 0));
         return GBVQC_OK;
     }
@@ -111,6 +113,10 @@ static gbvqc_status jit_prefetch(gbvqc_circuit *c, DevPlan *p, bool join, cudaSt
     for (int dir = 0; dir < 2; dir++)
         for (size_t i = 0; i < p->p.fwd.size(); i++) {
             if (p->p.barrier[i] >= 0) continue;
+            if (dir != phase) {  // the other sweep's stream and event, left alone
+                k++;
+                continue;
+            }
             cudaStream_t st = p->pf_streams[k];
             CUDA_TRY(cudaStreamWaitEvent(st, p->pf_fork, 0));
             const bool rev = dir == 1;
@@ -213,13 +219,14 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
     RedScratch red{w.d_red, w.d_counter};
     const bool fused = mode != GBVQC_MODE_PLAIN && p, jit = mode == GBVQC_MODE_JIT && p;
     const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
-    if (jit) ST_TRY(jit_prefetch(c, p, false, s));  // first: overlaps the whole sequence
+    if (jit) ST_TRY(jit_prefetch(c, p, 0, s));  // first: overlaps the whole sequence
     ST_TRY(run_k("materialize", 0, 0, s, [&] {
         return launch_materialize(c->d_dyn, (int)c->dyn.size(), w.d_theta, c->d_recs, s);
     }));
     if (fused) ST_TRY(gather_images(c, p, dtype, true, s));
     ST_TRY(run_k("zero_state", 0, sb, s, [&] { return launch_zero_state(dtype, w.phi, c->n_phys, s); }));
     if (fused) ST_TRY(run_fused_forward(c, p, dtype, w.phi, s, jit));
+    if (jit) ST_TRY(jit_prefetch(c, p, 1, s));
     else ST_TRY(run_plain_forward(c, dtype, w.phi, s));
     // energy and adjoint seed
     if (c->density) {
@@ -268,7 +275,7 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
         ST_TRY(run_k("accumulate", 0, 0, s, [&] {
             return launch_accumulate(w.d_slot_grad, p->d_csr_ptr, p->d_csr_slots, c->n_params, w.d_grad, s);
         }));
-        if (jit) ST_TRY(jit_prefetch(c, p, true, s));
+        if (jit) ST_TRY(jit_prefetch(c, p, 2, s));
     } else {
         // Algorithm 2: Phi <- Q^-1 Phi; g = scale Re <Psi|dQ|Phi>; Psi <- Q^-1 Psi (Q^dag for channels)
         for (int j = (int)c->plain.size() - 1; j >= 0; j--) {
