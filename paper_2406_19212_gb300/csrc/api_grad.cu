@@ -225,9 +225,12 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
     }));
     if (fused) ST_TRY(gather_images(c, p, dtype, true, s));
     ST_TRY(run_k("zero_state", 0, sb, s, [&] { return launch_zero_state(dtype, w.phi, c->n_phys, s); }));
-    if (fused) ST_TRY(run_fused_forward(c, p, dtype, w.phi, s, jit));
-    if (jit) ST_TRY(jit_prefetch(c, p, 1, s));
-    else ST_TRY(run_plain_forward(c, dtype, w.phi, s));
+    if (fused) {
+        ST_TRY(run_fused_forward(c, p, dtype, w.phi, s, jit));
+        if (jit) ST_TRY(jit_prefetch(c, p, 1, s));
+    } else {
+        ST_TRY(run_plain_forward(c, dtype, w.phi, s));
+    }
     // energy and adjoint seed
     if (c->density) {
         const DensMap &m = fused ? c->map_grad : c->map_std;
