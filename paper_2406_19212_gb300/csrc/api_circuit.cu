@@ -272,6 +272,23 @@ static Mat mat_scaled(const Mat &M, cd z)
 // phases cancel between the ket (U) and bra (conj U) sides; on a pure state their sum is
 // multiplied into one fixed gate whose shape is kept by a complex scale, or, if there is
 // none, undone on the first normalised gate, so the fused sweeps give the exact state.
+// Plan-time variant of a fixed SH_BLOCK2 record, for the specialised passes (FGate.perm of
+// an FT_BLOCK2 gate): BLOCK2_VARIANT | the shape of the 2x2 on {|01>, |10>} (0 general,
+// 1 real diagonal and imaginary off-diagonal, 2 real) | BLOCK2_P00_ONE / BLOCK2_P11_ONE
+// when the phase on |00> / |11> is exactly 1 in both precisions.  Exact comparisons: a
+// variant only drops terms that are exactly zero, so results are unchanged.
+static int block2_variant(const MatRec &r)
+{
+    auto zero = [&](int i) { return r.d[i] == 0.0 && r.f[i] == 0.0f; };
+    auto one = [&](int i) { return r.d[i] == 1.0 && r.f[i] == 1.0f; };
+    int v = BLOCK2_VARIANT;
+    if (zero(11) && zero(13) && zero(19) && zero(21)) v |= 2;
+    else if (zero(11) && zero(21) && zero(12) && zero(18)) v |= 1;
+    if (one(0) && zero(1)) v |= BLOCK2_P00_ONE;
+    if (one(30) && zero(31)) v |= BLOCK2_P11_ONE;
+    return v;
+}
+
 static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGate> &out)
 {
     out.clear();
@@ -415,10 +432,11 @@ static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGa
             }
         }
     }
+    if (c->density) return;
     const double ph = std::remainder(phase, 2.0 * M_PI);
-    if (c->density || ph == 0.0) return;
     const cd z = std::polar(1.0, ph);
-    if (fold >= 0) {  // shape kept: same ftype and permutation bits
+    if (ph == 0.0) {
+    } else if (fold >= 0) {  // shape kept: same ftype and permutation bits
         out[fold].rec_f = add_rec(c, mat_scaled(fold_f, z));
         out[fold].rec_i = out[fold].rec_a = add_rec(c, mat_scaled(fold_i, std::conj(z)));
     } else if (first_norm >= 0) {  // back to a general 2x2 on the first normalised gate
@@ -427,6 +445,14 @@ static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGa
         out[first_norm].rec_i = out[first_norm].rec_a = add_rec(c, mat_dagger(W, 2));
         out[first_norm].ftype = FT_DENSE1;
     }
+    // fixed block gates (FSIM with constant angles): the structure of their final matrices
+    std::vector<char> dynamic(c->recs.size(), 0);
+    for (const DynRec &d : c->dyn) dynamic[d.rec] = 1;
+    for (PGate &g : out)
+        if (g.ftype == FT_BLOCK2 && !dynamic[g.rec_f] && !dynamic[g.rec_i] && g.rec_a == g.rec_i) {
+            g.perm_f = block2_variant(c->recs[g.rec_f]);
+            g.perm_r = block2_variant(c->recs[g.rec_i]);
+        }
 }
 
 extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qubits, int n_params,

@@ -134,8 +134,12 @@ static gbvqc_status jit_prefetch(gbvqc_circuit *c, DevPlan *p, int phase, cudaSt
     return GBVQC_OK;
 }
 
+// Forward tile passes of plan p on psi.  init: psi is not read, the sweep starts from
+// |0...0> (the first pass must be a tile pass: init_in_first_pass).
+static bool init_in_first_pass(const DevPlan *p) { return !p->p.fwd.empty() && p->p.barrier[0] < 0; }
+
 static gbvqc_status run_fused_forward(gbvqc_circuit *c, DevPlan *p, int dtype, void *psi, cudaStream_t s,
-                                      bool jit = false)
+                                      bool jit = false, bool init = false)
 {
     const double amps = double(size_t(1) << c->n_phys), sb = state_bytes(c, dtype);
     const FusedDev fd{p->d_fwd, p->d_fsubs, p->d_fgates, p->d_fents, p->d_funits, c->d_recs, p->d_fimg};
@@ -147,8 +151,9 @@ static gbvqc_status run_fused_forward(gbvqc_circuit *c, DevPlan *p, int dtype, v
         }
         if (jit) {
             const PassDesc &d = p->p.fwd[i];
-            const FusedArgs args{p->d_fwd + i, p->d_fsubs, p->d_fgates, p->d_fents, p->d_funits, c->d_recs,
-                                 p->d_fimg, nullptr, 0};
+            FusedArgs args{p->d_fwd + i, p->d_fsubs, p->d_fgates, p->d_fents, p->d_funits, c->d_recs,
+                           p->d_fimg, nullptr, 0};
+            args.init = init && i == 0;
             ST_TRY(run_k("fused_forward", p->p.fwd_flops[i] * amps, 2 * sb, s, [&] {
                 return jit_launch(p->jit->fwd[i], psi, nullptr, args, 1u << (d.n - d.t), 1 << (d.t - p->p.nr_f),
                                   p->fwd_smem[i], s);
@@ -156,7 +161,7 @@ static gbvqc_status run_fused_forward(gbvqc_circuit *c, DevPlan *p, int dtype, v
             continue;
         }
         ST_TRY(run_k("fused_forward", p->p.fwd_flops[i] * amps, 2 * sb, s, [&] {
-            return launch_fused_forward(dtype, psi, fd, (int)i, p->p.fwd[i], p->fwd_smem[i], s);
+            return launch_fused_forward(dtype, psi, fd, (int)i, p->p.fwd[i], p->fwd_smem[i], s, init && i == 0);
         }));
     }
     return GBVQC_OK;
@@ -224,9 +229,11 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
         return launch_materialize(c->d_dyn, (int)c->dyn.size(), w.d_theta, c->d_recs, s);
     }));
     if (fused) ST_TRY(gather_images(c, p, dtype, true, s));
-    ST_TRY(run_k("zero_state", 0, sb, s, [&] { return launch_zero_state(dtype, w.phi, c->n_phys, s); }));
+    // Phi starts as |0...0>: written by the first tile pass where the plan starts with one
+    const bool init = fused && init_in_first_pass(p);
+    if (!init) ST_TRY(run_k("zero_state", 0, sb, s, [&] { return launch_zero_state(dtype, w.phi, c->n_phys, s); }));
     if (fused) {
-        ST_TRY(run_fused_forward(c, p, dtype, w.phi, s, jit));
+        ST_TRY(run_fused_forward(c, p, dtype, w.phi, s, jit, init));
         if (jit) ST_TRY(jit_prefetch(c, p, 1, s));
     } else {
         ST_TRY(run_plain_forward(c, dtype, w.phi, s));
@@ -272,11 +279,9 @@ static gbvqc_status enqueue_grad(gbvqc_circuit *c, obs_handle h, int dtype, int 
                                             w.d_slot_partials, tiles, s);
             }));
         }
-        ST_TRY(run_k("reduce_slots", 0, 0, s, [&] {
-            return launch_reduce_slots(w.d_slot_partials, p->p.n_slots, tiles, tiles, w.d_slot_grad, s);
-        }));
-        ST_TRY(run_k("accumulate", 0, 0, s, [&] {
-            return launch_accumulate(w.d_slot_grad, p->d_csr_ptr, p->d_csr_slots, c->n_params, w.d_grad, s);
+        ST_TRY(run_k("reduce_grad", 0, 0, s, [&] {
+            return launch_reduce_grad(w.d_slot_partials, tiles, tiles, p->d_csr_ptr, p->d_csr_slots, c->n_params,
+                                      w.d_grad, s);
         }));
         if (jit) ST_TRY(jit_prefetch(c, p, 2, s));
     } else {

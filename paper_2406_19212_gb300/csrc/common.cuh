@@ -289,6 +289,10 @@ enum FType : int32_t {
     FT_PAR2 = 14,    // SH_PAR2 on two register slots
     FT_RPAR2 = 15    // SH_RPAR2 on two register slots
 };
+// FGate.perm of an FT_BLOCK2 gate with a fixed matrix (set at plan time, read by the
+// specialised passes only): BLOCK2_VARIANT | inner shape (bits 0-1: 0 general, 1 real
+// diagonal with imaginary off-diagonal, 2 real) | P00 / P11 = 1 flags.
+enum : int32_t { BLOCK2_VARIANT = 0x100, BLOCK2_P00_ONE = 4, BLOCK2_P11_ONE = 8 };
 // Generator of a variational gate for the fused reverse sweep: the gradient term is
 // coef * Im <Psi| P |Phi> with both states taken right after the gate.
 enum GenType : int32_t { GEN_NONE = 0, GEN_X = 1, GEN_Y = 2, GEN_Z = 3, GEN_M2 = 4 /* FT_PROBE2 */ };

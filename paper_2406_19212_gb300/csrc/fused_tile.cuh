@@ -122,6 +122,24 @@ __device__ __forceinline__ void rg2(typename CT<R>::T *a, const R *m, int perm)
     }
 }
 
+// SH_BLOCK2 with a plan-time variant (a fixed matrix): the 2x2 on {|01>, |10>} applied
+// in its INNER shape, the |00> / |11> phases skipped where they are exactly 1 (P00 /
+// P11 false).  The skipped terms are exact zeros or unit factors.
+template <typename R, int NR, int K0, int K1, int INNER, bool P00, bool P11>
+__device__ __forceinline__ void rg2_block2v(typename CT<R>::T *a, const R *m)
+{
+    typedef typename CT<R>::T T;
+    const R u[8] = GBVQC_BLOCK2_U(m);
+#pragma unroll
+    for (int j = 0; j < (1 << NR); j++) {
+        if (j & ((1 << K0) | (1 << K1))) continue;
+        const int i1 = j | (1 << K0), i2 = j | (1 << K1), i3 = i1 | i2;
+        apply2<R, INNER>(u, a[i1], a[i2]);
+        if (P00) cmul_ip<T, R>(m[0], m[1], a[j]);
+        if (P11) cmul_ip<T, R>(m[30], m[31], a[i3]);
+    }
+}
+
 template <typename R, int NR, int SH>
 __device__ __forceinline__ void rg2_dispatch(int k0, int k1, typename CT<R>::T *a, const R *m, int perm)
 {
@@ -767,6 +785,20 @@ __device__ __forceinline__ void tile_store(typename CT<R>::T *gmem, const typena
     }
 }
 
+// Zeros to every amplitude of the tile (the words tile_store would write).
+template <typename R, int CNT>
+__device__ __forceinline__ void tile_zero(typename CT<R>::T *gmem, int low, int64_t tilebase, const int64_t *hitab)
+{
+    constexpr int AW = sizeof(typename CT<R>::T) == 8 ? 2 : 1;
+    const int lowmask = (1 << low) - 1;
+#pragma unroll
+    for (int c = 0; c < CNT; c++) {
+        const int l = (int)(threadIdx.x + c * blockDim.x) * AW;
+        const int64_t g = tilebase | hitab[l >> low] | (l & lowmask);
+        *reinterpret_cast<float4 *>(gmem + g) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // Shared-memory layout and per-CTA state of one tile pass, built by tile_begin and used
@@ -788,9 +820,11 @@ struct TileCtx {
 // Prologue of a tile pass: the tile's base offset and strided address table, the tile's
 // global loads (issued first), the staging of the pass's gate records, diagonal entries
 // and matrices, the tile into shared memory, and the tile-constant products of every
-// phase block.  Ends with the block synchronised.
+// phase block.  Ends with the block synchronised.  Returns false, with nothing staged,
+// for a tile of a pass started from |0...0> (args.init) that is not tile 0: the tile's
+// amplitudes are written as zeros and the CTA has nothing more to do.
 template <typename R, int NR, bool REV>
-__device__ __forceinline__ void tile_begin(const typename CT<R>::T *__restrict__ phi,
+__device__ __forceinline__ bool tile_begin(const typename CT<R>::T *__restrict__ phi,
                                            const typename CT<R>::T *__restrict__ psi, const FusedArgs &args,
                                            const int64_t tile, TileCtx<R, NR, REV> &c)
 {
@@ -867,7 +901,17 @@ __device__ __forceinline__ void tile_begin(const typename CT<R>::T *__restrict__
     // words of 16 bytes per thread: 2^t amplitudes over 2^(t - NR) threads
     constexpr int CNT = sizeof(T) == 8 ? (1 << (NR - 1)) : (1 << NR);
     float4 wphi[CNT], wpsi[REV ? CNT : 1];
-    tile_fetch<R, CNT>(phi, wphi, low, tilebase, hitab);
+    if (!REV && args.init) {
+#pragma unroll
+        for (int k = 0; k < CNT; k++) wphi[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tile != 0) {  // uniform over the CTA; a prefetch launch runs tile 0 only
+            tile_zero<R, CNT>(const_cast<T *>(phi), low, tilebase, hitab);
+            return false;
+        }
+        if (threadIdx.x == 0) *reinterpret_cast<T *>(&wphi[0]) = T{R(1), R(0)};  // local 0 = global 0
+    } else {
+        tile_fetch<R, CNT>(phi, wphi, low, tilebase, hitab);
+    }
     if constexpr (REV) tile_fetch<R, CNT>(psi, wpsi, low, tilebase, hitab);
     // stage the pass's gates, diagonal entries and matrices while the tile loads are in flight
     {
@@ -927,6 +971,7 @@ __device__ __forceinline__ void tile_begin(const typename CT<R>::T *__restrict__
     c.n_slots = pd.n_slots;
     c.slot_begin = pd.slot_begin;
     c.rc = RedCtx<R>{sgrad, pd.slot_begin, nwarps, warp, lane, lanes, lanemask};
+    return true;
 }
 
 // Gather a sub-run's register amplitudes: tile positions Rp[0..NR-1] are the register
@@ -947,14 +992,19 @@ __device__ __forceinline__ int subrun_load(const TileCtx<R, NR, REV> &c, const i
     }
 #pragma unroll
     for (int k = 0; k < NR; k++) off[k] = 1 << Rp[k];
+    // base and the register offsets occupy disjoint bits, so base | C = base ^ C, and the
+    // swizzle is linear over XOR: slot(base | C_j) = swz(base) ^ swz(C_j) with swz(C_j) a
+    // constant of the sub-run (a literal in the specialised passes)
+    const int sb = swz<R>(base);
 #pragma unroll
     for (int j = 0; j < (1 << NR); j++) {
-        int l = base;
+        int cj = 0;
 #pragma unroll
         for (int k = 0; k < NR; k++)
-            if ((j >> k) & 1) l |= off[k];
-        a[j] = c.sphi[swz<R>(l)];
-        if constexpr (REV) b[j] = c.spsi[swz<R>(l)];
+            if ((j >> k) & 1) cj |= off[k];
+        const int l = sb ^ swz<R>(cj);
+        a[j] = c.sphi[l];
+        if constexpr (REV) b[j] = c.spsi[l];
     }
     return base;
 }
@@ -964,14 +1014,16 @@ template <typename R, int NR, bool REV>
 __device__ __forceinline__ void subrun_store(const TileCtx<R, NR, REV> &c, int base, const int (&off)[NR],
                                              const typename CT<R>::T *a, const typename CT<R>::T *b)
 {
+    const int sb = swz<R>(base);  // as in subrun_load
 #pragma unroll
     for (int j = 0; j < (1 << NR); j++) {
-        int l = base;
+        int cj = 0;
 #pragma unroll
         for (int k = 0; k < NR; k++)
-            if ((j >> k) & 1) l |= off[k];
-        c.sphi[swz<R>(l)] = a[j];
-        if constexpr (REV) c.spsi[swz<R>(l)] = b[j];
+            if ((j >> k) & 1) cj |= off[k];
+        const int l = sb ^ swz<R>(cj);
+        c.sphi[l] = a[j];
+        if constexpr (REV) c.spsi[l] = b[j];
     }
     __syncthreads();
 }
@@ -1104,7 +1156,7 @@ __device__ __forceinline__ void fused_tile(typename CT<R>::T *__restrict__ phi, 
 {
     typedef typename CT<R>::T T;
     TileCtx<R, NR, REV> c;
-    tile_begin<R, NR, REV>(phi, psi, args, tile, c);
+    if (!tile_begin<R, NR, REV>(phi, psi, args, tile, c)) return;
     const int n_sub = args.pd->n_sub, sub_begin = args.pd->sub_begin;
     T a[1 << NR], b[REV ? (1 << NR) : 1];
     for (int s = 0; s < n_sub; s++) {

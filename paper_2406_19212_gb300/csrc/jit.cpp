@@ -231,6 +231,16 @@ void emit_gate(std::ostringstream &o, const FusedPlan &P, const PassDesc &d, con
     if (rev && (g.gen == GEN_X || g.gen == GEN_Y))
         o << ind << "emit_partial<Rt>(rc, " << g.slot << ", gen_xy<Rt, NR, " << (int)g.gpos << ", " << gen_name(g.gen)
           << ">(a, b) * " << flit(g.coef) << ");\n";
+    if (g.type == FT_BLOCK2 && (g.perm & BLOCK2_VARIANT)) {  // fixed matrix: its own structure
+        const int inner = (g.perm & 3) == 1 ? SH_IMAG1 : (g.perm & 3) == 2 ? SH_REAL1 : SH_DENSE1;
+        std::ostringstream t;
+        t << "rg2_block2v<Rt, NR, " << (int)g.a << ", " << (int)g.b << ", " << inner << ", "
+          << ((g.perm & BLOCK2_P00_ONE) ? "false" : "true") << ", " << ((g.perm & BLOCK2_P11_ONE) ? "false" : "true")
+          << ">";
+        o << ind << t.str() << "(a, smat + " << 8 * g.mat << ");\n";
+        if (rev) o << ind << t.str() << "(b, smat + " << 8 * g.mat2 << ");\n";
+        return;
+    }
     const char *twoq = d.has_2q ? "true" : "false";
     o << ind << "apply_fgate<Rt, NR, " << twoq << ">(" << (int)g.type << ", " << (int)g.a << ", " << (int)g.b << ", "
       << g.perm << ", smat + " << 8 * g.mat << ", a);\n";
@@ -271,7 +281,7 @@ std::string jit_source(const FusedPlan &P, int p, bool rev, int dtype)
       << "  constexpr int NR = " << NR << ";\n  constexpr bool REV = " << (rev ? "true" : "false") << ";\n"
       << "  // a code-prefetch launch (args.dry) runs tile 0 and CTA s walks sub-run s only\n"
       << "  const int64_t tile = args.dry ? 0 : blockIdx.x;\n"
-      << "  TileCtx<Rt, NR, REV> c;\n  tile_begin<Rt, NR, REV>(phi, psi, args, tile, c);\n"
+      << "  TileCtx<Rt, NR, REV> c;\n  if (!tile_begin<Rt, NR, REV>(phi, psi, args, tile, c)) return;\n"
       << "  Tt a[1 << NR], b[REV ? (1 << NR) : 1];\n"
       << "  const Rt *smat = c.smat;\n  const DEnt *sents = c.sents;\n  const RedCtx<Rt> &rc = c.rc;\n"
       << "  const int64_t tilebase = c.tilebase;\n  (void)sents; (void)rc; (void)tilebase; (void)b;\n";

@@ -126,6 +126,10 @@ struct FusedArgs {
     int dry;  // 1: a code-prefetch launch (specialised passes): runs tile 0 of the pass and
               // writes nothing to global memory; it only pulls the kernel's instructions
               // into L2 ahead of the pass's real launch
+    int init;  // 1 (first forward pass of a gradient): the pass starts from |0...0> instead of
+               // reading phi.  Tile 0 holds the one nonzero amplitude and runs the gates;
+               // every other tile stays zero under the pass's linear maps and is written as
+               // zeros without running them.
 };
 // img_f / img_r [8 u + e] = element e of unit u of the forward / reverse unit list, in the
 // state's precision (after the step's matrices are materialised).
@@ -147,14 +151,16 @@ int fused_nr(int dtype, bool reverse);           // register qubits per sub-run
 constexpr int fused_max_threads(int nr, bool reverse) { return reverse && nr < 5 ? 256 : 128; }
 constexpr int fused_min_blocks(bool reverse) { return reverse ? 2 : 3; }
 cudaError_t fused_prepare();                     // shared-memory opt-in, outside capture
+// init: the pass starts from |0...0> and writes psi without reading it (FusedArgs::init).
 cudaError_t launch_fused_forward(int dtype, void *psi, const FusedDev &fd, int pass,
-                                 const PassDesc &pass_host, size_t smem, cudaStream_t s);
+                                 const PassDesc &pass_host, size_t smem, cudaStream_t s, bool init = false);
 cudaError_t launch_fused_reverse(int dtype, void *phi, void *psi, const FusedDev &fd, int pass,
                                  const PassDesc &pass_host, size_t smem, double *slot_partials,
                                  int n_tiles_stride, cudaStream_t s);
-// slot_grad[s] = sum_tile slot_partials[s * stride + tile], tiles in index order.
-cudaError_t launch_reduce_slots(const double *slot_partials, int n_slots, int n_tiles,
-                                int stride, double *slot_grad, cudaStream_t s);
+// grad[p] = sum over slots[ptr[p] .. ptr[p+1]) of sum_tile slot_partials[slot * stride + tile]
+// (tiles and slots in index order, one fixed reduction tree per slot).
+cudaError_t launch_reduce_grad(const double *slot_partials, int n_tiles, int stride, const int *csr_ptr,
+                               const int *csr_slots, int n_params, double *grad, cudaStream_t s);
 
 // ---- batched kernels (kernels_batch.cu): one launch covers many circuits; CTA c
 // belongs to the last entry whose `begin` is <= c.

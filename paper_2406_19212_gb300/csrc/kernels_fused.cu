@@ -105,9 +105,10 @@ static cudaError_t fused_launch(void *phi, void *psi, const PassDesc &ph, size_t
 }
 
 cudaError_t launch_fused_forward(int dtype, void *psi, const FusedDev &fd, int pass, const PassDesc &ph,
-                                 size_t smem, cudaStream_t s)
+                                 size_t smem, cudaStream_t s, bool init)
 {
     FusedArgs args{fd.passes + pass, fd.subs, fd.gates, fd.ents, fd.units, fd.recs, fd.img, nullptr, 0};
+    args.init = init ? 1 : 0;
     if (dtype == 0) return fused_launch<float, 5, false>(psi, nullptr, ph, smem, args, s);
     return fused_launch<double, 4, false>(psi, nullptr, ph, smem, args, s);
 }
@@ -174,27 +175,36 @@ cudaError_t launch_gather_units(int dtype, const GatherArgs &g, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// slot_grad[s] = sum over tiles, in tile order within each thread, then a fixed tree.
-__global__ void k_reduce_slots(const double *__restrict__ part, int n_tiles, int stride, double *out)
+// grad[p] = sum over the slots of parameter p (slot order) of the slot's sum over tiles;
+// a slot's sum takes the tiles in order within each thread, then a fixed tree, so the
+// result does not depend on timing.
+__global__ void k_reduce_grad(const double *__restrict__ part, int n_tiles, int stride, const int *__restrict__ ptr,
+                              const int *__restrict__ slots, double *grad)
 {
     __shared__ double sh[256];
-    const int s = blockIdx.x;
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < n_tiles; i += blockDim.x) acc += part[(int64_t)s * stride + i];
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    const int p = blockIdx.x;
+    double total = 0.0;
+    for (int i = ptr[p]; i < ptr[p + 1]; i++) {
+        const int64_t s = slots[i];
+        double acc = 0.0;
+        for (int k = threadIdx.x; k < n_tiles; k += blockDim.x) acc += part[s * stride + k];
+        sh[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        total += sh[0];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[s] = sh[0];
+    if (threadIdx.x == 0) grad[p] = total;
 }
 
-cudaError_t launch_reduce_slots(const double *slot_partials, int n_slots, int n_tiles, int stride,
-                                double *slot_grad, cudaStream_t s)
+cudaError_t launch_reduce_grad(const double *slot_partials, int n_tiles, int stride, const int *csr_ptr,
+                               const int *csr_slots, int n_params, double *grad, cudaStream_t s)
 {
-    if (n_slots == 0) return cudaSuccess;
-    k_reduce_slots<<<n_slots, 256, 0, s>>>(slot_partials, n_tiles, stride, slot_grad);
+    if (n_params == 0) return cudaSuccess;
+    k_reduce_grad<<<n_params, 256, 0, s>>>(slot_partials, n_tiles, stride, csr_ptr, csr_slots, grad);
     return cudaGetLastError();
 }
 

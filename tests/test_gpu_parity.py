@@ -133,6 +133,56 @@ def test_expect_matches_oracle(n, seed, dtype):
     check_energy(e, O.expect(terms, psi, n), dtype)
 
 
+def rich_observable(n, seed, count=16):
+    """Pauli strings on random qubits (the highest ones included), each with two companions
+    on the same X mask: its X and Y factors exchanged, and an extra Z factor.  Groups of
+    equal X mask then hold several terms whose Z masks and Y counts differ, so a group's
+    coefficient is complex and depends on the amplitude index."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    terms = []
+    for _ in range(count):
+        k = int(rng.integers(1, 5))
+        qs = [int(q) for q in sorted(rng.choice(n, size=k, replace=False))]
+        ps = ["XYZ"[int(rng.integers(0, 3))] for _ in qs]
+        if all(p == "Z" for p in ps):
+            ps[0] = "X"
+        c = float(rng.normal())
+        terms.append((c, tuple(zip(qs, ps))))
+        swapped = ["Y" if p == "X" else "X" if p == "Y" else p for p in ps]
+        terms.append((0.5 * c, tuple(zip(qs, swapped))))
+        free = [q for q in range(n) if q not in qs]
+        z = int(rng.choice(free))
+        terms.append((-0.25 * c, tuple(sorted(list(zip(qs, ps)) + [(z, "Z")]))))
+    return terms
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,seed", [(10, 21), (11, 22), (15, 23)])
+def test_expect_rich_observable(n, seed, dtype):
+    """Groups flipping qubits inside and outside a 2^10-amplitude chunk, complex group
+    coefficients, Z masks on every qubit."""
+    psi = I.random_state(n, seed)
+    terms = rich_observable(n, seed)
+    sv = gb.sv_alloc(n, dtype)
+    gb.sv_set(sv, psi)
+    check_energy(gb.expect(sv, gb.obs_create(terms, n)), O.expect(terms, psi, n), dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", MODES + [gb.JIT])
+@pytest.mark.parametrize("n,seed", [(12, 31), (14, 32)])
+def test_grad_rich_observable(n, seed, dtype, mode):
+    """The adjoint seed lambda = H Phi of an observable with complex, index-dependent group
+    coefficients and flips of high qubits: every gradient entry is a linear functional of
+    lambda, compared with the oracle's."""
+    w = I.random_circuit(n, 90, seed)
+    terms = rich_observable(n, seed)
+    e_ref, g_ref = O.adjoint_grad(w.circuit, w.theta, terms)
+    e, g = gb.grad(gb.circuit_create(w.circuit), w.theta, gb.obs_create(terms, n), dtype, mode)
+    check_energy(e, e_ref, dtype)
+    check_grad(g, g_ref, dtype)
+
+
 # --------------------------------------------------------------------- gradients
 
 @pytest.mark.parametrize("dtype", DTYPES)
