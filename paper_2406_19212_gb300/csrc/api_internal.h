@@ -144,10 +144,18 @@ struct gbvqc_obs {
     std::vector<ObsTerm> terms;
     ObsGroup *d_groups = nullptr;
     ObsTerm *d_terms = nullptr;
-    ObsDev dev() const { return ObsDev{d_groups, d_terms, (int)groups.size(), (int)terms.size()}; }
+    unsigned char *d_chunk = nullptr;  // chunked kernels' staging image (chunk_image)
+    ObsDev dev() const { return ObsDev{d_groups, d_terms, (int)groups.size(), (int)terms.size(), d_chunk}; }
     // device copies with the X/Z masks permuted to a gradient layout (key: the layout)
-    std::map<std::vector<int8_t>, std::pair<ObsGroup *, ObsTerm *>> perm_dev;
+    struct PermDev {
+        ObsGroup *groups;
+        ObsTerm *terms;
+        unsigned char *chunk;
+    };
+    std::map<std::vector<int8_t>, PermDev> perm_dev;
 };
+// Staging image of the chunked Pauli kernels for a grouped observable (layout in kernels.h).
+std::vector<unsigned char> chunk_image(const std::vector<ObsGroup> &groups, const std::vector<ObsTerm> &terms);
 
 // One gate of the per-gate schedule.
 struct PlainGate {

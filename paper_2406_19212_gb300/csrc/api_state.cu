@@ -268,12 +268,49 @@ extern "C" gbvqc_status obs_create(const gbvqc_pauli *terms, int n_terms, int n_
     return GBVQC_OK;
 }
 
+std::vector<unsigned char> chunk_image(const std::vector<ObsGroup> &groups, const std::vector<ObsTerm> &terms)
+{
+    const int G = (int)groups.size(), T = (int)terms.size();
+    std::vector<unsigned char> img(chunk_image_bytes(G, T), 0);
+    ChunkGroup *cg = reinterpret_cast<ChunkGroup *>(img.data());
+    ChunkTermF *tf = reinterpret_cast<ChunkTermF *>(img.data() + chunk_terms_f_offset(G));
+    ChunkTermD *td = reinterpret_cast<ChunkTermD *>(img.data() + chunk_terms_d_offset(G, T));
+    for (int g = 0; g < G; g++) {
+        const uint64_t x = groups[g].x;
+        uint32_t flags = 0, real = 1, zany = 0;
+        for (int k = groups[g].t_begin; k < groups[g].t_end; k++) {
+            const ObsTerm &t = terms[k];
+            real &= (t.ph & 1) == 0;
+            zany |= t.z != 0;
+            // i^{ph} (-1)^{popcount(x & z)}: the coefficient as seen from amplitude a
+            const int ph = (t.ph + 2 * (__builtin_popcountll(x & t.z) & 1)) & 3;
+            uint32_t rpat = 0;
+            const uint32_t zr = (uint32_t)(t.z >> kPauliTB) & (kPauliPV - 1);
+            for (int r = 0; r < kPauliPV; r++) rpat |= (uint32_t)(__builtin_popcount(r & zr) & 1) << r;
+            const double c = t.coeff;
+            const float cf = t.coeff_f;
+            tf[k] = ChunkTermF{(uint32_t)t.z, (uint32_t)(t.z >> 32), rpat, ph == 0 ? cf : ph == 2 ? -cf : 0.0f,
+                               ph == 1 ? cf : ph == 3 ? -cf : 0.0f, 0u};
+            td[k] = ChunkTermD{(uint32_t)t.z, (uint32_t)(t.z >> 32), rpat, 0u, ph == 0 ? c : ph == 2 ? -c : 0.0,
+                               ph == 1 ? c : ph == 3 ? -c : 0.0};
+        }
+        if (real) flags |= CG_REAL;
+        if (x == 0) flags |= CG_SELF;
+        if ((x >> kPauliC) == 0) flags |= CG_CHUNK;
+        if (!zany) flags |= CG_CONST;
+        cg[g] = ChunkGroup{(uint32_t)x, (uint32_t)(x >> 32), (uint16_t)groups[g].t_begin, (uint16_t)groups[g].t_end,
+                           flags};
+    }
+    return img;
+}
+
 gbvqc_status ensure_obs(gbvqc_obs *h)
 {
     if (h->d_groups) return GBVQC_OK;
     CUDA_TRY(pauli_prepare());
     ST_TRY(upload(&h->d_terms, h->terms));
     ST_TRY(upload(&h->d_groups, h->groups));
+    if (h->terms.size() < 65536) ST_TRY(upload(&h->d_chunk, chunk_image(h->groups, h->terms)));
     return GBVQC_OK;
 }
 
@@ -299,12 +336,13 @@ gbvqc_status obs_dev_perm(gbvqc_obs *h, const std::vector<int8_t> &perm, ObsDev 
         std::vector<ObsTerm> t = h->terms;
         for (ObsGroup &x : g) x.x = permute_mask(x.x, perm);
         for (ObsTerm &x : t) x.z = permute_mask(x.z, perm);
-        std::pair<ObsGroup *, ObsTerm *> d{nullptr, nullptr};
-        ST_TRY(upload(&d.first, g));
-        ST_TRY(upload(&d.second, t));
+        gbvqc_obs::PermDev d{nullptr, nullptr, nullptr};
+        ST_TRY(upload(&d.groups, g));
+        ST_TRY(upload(&d.terms, t));
+        if (t.size() < 65536) ST_TRY(upload(&d.chunk, chunk_image(g, t)));
         it = h->perm_dev.emplace(perm, d).first;
     }
-    *out = ObsDev{it->second.first, it->second.second, (int)h->groups.size(), (int)h->terms.size()};
+    *out = ObsDev{it->second.groups, it->second.terms, (int)h->groups.size(), (int)h->terms.size(), it->second.chunk};
     return GBVQC_OK;
 }
 
@@ -313,9 +351,11 @@ extern "C" gbvqc_status obs_free(obs_handle h)
     if (!h) return GBVQC_OK;
     if (h->d_groups) dev_free(h->d_groups);
     if (h->d_terms) dev_free(h->d_terms);
+    if (h->d_chunk) dev_free(h->d_chunk);
     for (auto &kv : h->perm_dev) {
-        dev_free(kv.second.first);
-        dev_free(kv.second.second);
+        dev_free(kv.second.groups);
+        dev_free(kv.second.terms);
+        dev_free(kv.second.chunk);
     }
     delete h;
     return GBVQC_OK;

@@ -28,7 +28,41 @@ struct ObsDev {
     const ObsTerm *terms;
     int n_groups;
     int n_terms;
+    const unsigned char *chunk = nullptr;  // staging image of the chunked kernels (chunk_image)
 };
+
+// Chunked Pauli-sum kernels (k_pauli_chunk): a CTA of 2^kPauliTB threads stages 2^kPauliC
+// amplitudes, kPauliPV per thread (a = hi | r << kPauliTB | thread).  The observable is
+// staged from a host-built image: the groups, then the terms in the sweep's precision
+// with the group's sign (-1)^{x_g . z} folded into the coefficient (the sign of a term at
+// amplitude a ^ x_g is then read from a itself) and rpat = bit r set where the term's
+// Z mask has odd overlap with r << kPauliTB.
+constexpr int kPauliPV = 4, kPauliTB = 8, kPauliC = 10;
+enum : uint32_t { CG_REAL = 1, CG_SELF = 2, CG_CHUNK = 4, CG_CONST = 8 };
+struct ChunkGroup {
+    uint32_t xlo, xhi;
+    uint16_t t_begin, t_end;
+    uint32_t flags;  // CG_*: real coefficients, X mask 0, X mask inside the chunk, every Z mask 0
+};
+struct ChunkTermF {
+    uint32_t zlo, zhi, rpat;
+    float cr, ci;
+    uint32_t pad;
+};
+struct ChunkTermD {
+    uint32_t zlo, zhi, rpat, pad;
+    double cr, ci;
+};
+// Byte offsets in the image: groups (16 * even count), complex64 terms, complex128 terms.
+__host__ __device__ inline size_t chunk_terms_f_offset(int n_groups) { return 16 * (size_t)((n_groups + 1) & ~1); }
+__host__ __device__ inline size_t chunk_terms_d_offset(int n_groups, int n_terms)
+{
+    return chunk_terms_f_offset(n_groups) + ((sizeof(ChunkTermF) * (size_t)n_terms + 15) & ~size_t(15));
+}
+inline size_t chunk_image_bytes(int n_groups, int n_terms)
+{
+    return chunk_terms_d_offset(n_groups, n_terms) + sizeof(ChunkTermD) * (size_t)n_terms;
+}
 
 // Shared memory of the staged observable in the expectation kernels; observables
 // larger than kObsStageMax (or with 65536 terms or more) are read from global memory.

@@ -235,105 +235,74 @@ __global__ void __launch_bounds__(256) k_pauli_expect(const typename CTr<R>::T *
 
 // ----------------------------------------------------- chunked Pauli sums (n >= 10)
 //
-// The same lambda = H psi and Re <psi|H psi> with the state read in chunks of 2^10
+// The same lambda = H psi and Re <psi|H psi> with the state read in chunks of 2^kPauliC
 // amplitudes: a CTA stages its chunk in shared memory, so the partner psi_{a ^ x_g} of a
 // group whose X mask stays inside the chunk's bits is a shared-memory read (only groups
 // that flip a higher bit read the partner chunk from global memory / L2).  A thread owns
-// the PV amplitudes a = hi | r << 8 | tid (r < PV).  Since popcount((a ^ x) & z) =
-// popcount(a & z) + popcount(x & z) mod 2, each term's sign (-1)^{x_g . z} is folded
-// into its coefficient when it is staged, and the sign of amplitude r is the thread's
-// parity of (hi | tid) & z flipped by bit r of a staged pattern over r; terms whose Z
-// mask avoids the register bits (pattern 0) cost one add per amplitude, and groups
-// whose every Z mask is empty take their coefficient as a constant.
-constexpr int PV = 4, PTB = 8, PC = 10;  // amplitudes per thread, log2 threads, chunk bits
-
-template <typename R>
-struct CTerm {
-    uint32_t zlo, zhi, rpat, pad;
-    R cr, ci;  // coeff * i^{ph} * (-1)^{x_g . z}
-};
-struct CGroup {
-    uint32_t xlo, xhi;
-    uint16_t t_begin, t_end;
-    uint32_t flags;
-};
-enum : uint32_t { CG_REAL = 1, CG_SELF = 2, CG_CHUNK = 4, CG_CONST = 8 };
+// the kPauliPV amplitudes a = hi | r << kPauliTB | tid.  Since popcount((a ^ x) & z) =
+// popcount(a & z) + popcount(x & z) mod 2, each term's group sign (-1)^{x_g . z} is folded
+// into its staged coefficient, and the sign of amplitude r is the thread's parity of
+// (hi | tid) & z flipped by bit r of the term's rpat: terms with rpat 0 add one per-thread
+// constant, groups whose every Z mask is empty take one constant coefficient.
+template <typename R> struct ChunkTerm;
+template <> struct ChunkTerm<float> { typedef ChunkTermF T; };
+template <> struct ChunkTerm<double> { typedef ChunkTermD T; };
 
 inline size_t chunk_smem_bytes(const ObsDev &obs, int dtype)
 {
-    const size_t amp = dtype == 0 ? 8 : 16, term = dtype == 0 ? 24 : 32;
-    return (amp << PC) + 16 * (size_t)((obs.n_groups + 1) & ~1) + term * (size_t)obs.n_terms;
+    const size_t amp = dtype == 0 ? 8 : 16, term = dtype == 0 ? sizeof(ChunkTermF) : sizeof(ChunkTermD);
+    return (amp << kPauliC) + chunk_terms_f_offset(obs.n_groups) + ((term * (size_t)obs.n_terms + 15) & ~size_t(15));
 }
 
 template <typename R>
-__global__ void __launch_bounds__(1 << PTB) k_pauli_chunk(const typename CTr<R>::T *__restrict__ psi,
-                                                          typename CTr<R>::T *__restrict__ lam, int64_t n_chunks,
-                                                          ObsDev obs, RedScratch red, double *out)
+__global__ void __launch_bounds__(1 << kPauliTB) k_pauli_chunk(const typename CTr<R>::T *__restrict__ psi,
+                                                               typename CTr<R>::T *__restrict__ lam,
+                                                               int64_t n_chunks, ObsDev obs, RedScratch red,
+                                                               double *out)
 {
     typedef typename CTr<R>::T T;
+    typedef typename ChunkTerm<R>::T CT_;
+    constexpr int PV = kPauliPV, TB = kPauliTB, PC = kPauliC;
     extern __shared__ __align__(16) unsigned char psm[];
     T *sx = reinterpret_cast<T *>(psm);
-    CGroup *sg = reinterpret_cast<CGroup *>(psm + (sizeof(T) << PC));
-    CTerm<R> *st = reinterpret_cast<CTerm<R> *>(reinterpret_cast<unsigned char *>(sg) +
-                                                16 * (size_t)((obs.n_groups + 1) & ~1));
+    unsigned char *sobs = psm + (sizeof(T) << PC);
     const int tid = threadIdx.x, G = obs.n_groups;
-    for (int g = tid; g < G; g += blockDim.x) {
-        const ObsGroup gr = obs.groups[g];
-        uint32_t f = 0, real = 1, zany = 0;
-        for (int k = gr.t_begin; k < gr.t_end; k++) {
-            real &= (obs.terms[k].ph & 1) == 0;
-            zany |= obs.terms[k].z != 0;
-        }
-        if (real) f |= CG_REAL;
-        if (gr.x == 0) f |= CG_SELF;
-        if ((gr.x >> PC) == 0) f |= CG_CHUNK;
-        if (!zany) f |= CG_CONST;
-        sg[g] = CGroup{(uint32_t)gr.x, (uint32_t)(gr.x >> 32), (uint16_t)gr.t_begin, (uint16_t)gr.t_end, f};
+    const size_t goff = chunk_terms_f_offset(G);
+    const ChunkGroup *sg = reinterpret_cast<const ChunkGroup *>(sobs);
+    const CT_ *st = reinterpret_cast<const CT_ *>(sobs + goff);
+
+    // the first chunk's own amplitudes are requested before the observable is staged
+    int64_t chunk = blockIdx.x;
+    T pa[PV];
+#pragma unroll
+    for (int r = 0; r < PV; r++) pa[r] = psi[(chunk << PC) | (r << TB) | tid];
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(obs.chunk);
+        int4 *dst = reinterpret_cast<int4 *>(sobs);
+        for (int i = tid; i < (int)(goff / 16); i += blockDim.x) dst[i] = src[i];
+        const size_t toff = sizeof(R) == 4 ? goff : chunk_terms_d_offset(G, obs.n_terms);
+        const int tw = (int)((sizeof(CT_) * (size_t)obs.n_terms + 15) / 16);
+        const int4 *tsrc = reinterpret_cast<const int4 *>(obs.chunk + toff);
+        int4 *tdst = reinterpret_cast<int4 *>(sobs + goff);
+        for (int i = tid; i < tw; i += blockDim.x) tdst[i] = tsrc[i];
     }
-    __syncthreads();
-    for (int k = tid; k < obs.n_terms; k += blockDim.x) {
-        int lo = 0, hi = G - 1;  // the group holding term k (groups cover the terms in order)
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (sg[mid].t_begin <= k) lo = mid;
-            else hi = mid - 1;
-        }
-        const uint64_t x = (uint64_t)sg[lo].xlo | ((uint64_t)sg[lo].xhi << 32);
-        const ObsTerm t = obs.terms[k];
-        R c;
-        if constexpr (sizeof(R) == 4) c = t.coeff_f;
-        else c = t.coeff;
-        const int ph = (t.ph + 2 * (__popcll(x & t.z) & 1)) & 3;
-        const uint32_t zr = (uint32_t)(t.z >> PTB) & (PV - 1);
-        uint32_t rpat = 0;
-        for (int r = 0; r < PV; r++) rpat |= (uint32_t)(__popc(r & zr) & 1) << r;
-        CTerm<R> ct;
-        ct.zlo = (uint32_t)t.z;
-        ct.zhi = (uint32_t)(t.z >> 32);
-        ct.rpat = rpat;
-        ct.pad = 0;
-        ct.cr = ph == 0 ? c : ph == 2 ? -c : R(0);
-        ct.ci = ph == 1 ? c : ph == 3 ? -c : R(0);
-        st[k] = ct;
-    }
-    __syncthreads();
     double acc = 0.0;
-    for (int64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
+    for (; chunk < n_chunks; chunk += gridDim.x) {
         const int64_t hi = chunk << PC;
+        if (chunk != (int64_t)blockIdx.x) {
+#pragma unroll
+            for (int r = 0; r < PV; r++) pa[r] = psi[hi | (r << TB) | tid];
+        }
+#pragma unroll
+        for (int r = 0; r < PV; r++) sx[(r << TB) | tid] = pa[r];
+        __syncthreads();
         const uint64_t a0 = (uint64_t)(hi | tid);
         const uint32_t a0lo = (uint32_t)a0, a0hi = (uint32_t)(a0 >> 32);
-        T pa[PV];
-#pragma unroll
-        for (int r = 0; r < PV; r++) {
-            pa[r] = psi[hi | (r << PTB) | tid];
-            sx[(r << PTB) | tid] = pa[r];
-        }
-        __syncthreads();
         R lr[PV], li[PV];
 #pragma unroll
         for (int r = 0; r < PV; r++) lr[r] = li[r] = R(0);
         for (int g = 0; g < G; g++) {
-            const CGroup gr = sg[g];
+            const ChunkGroup gr = sg[g];
             T pb[PV];
             if (gr.flags & CG_SELF) {
 #pragma unroll
@@ -342,59 +311,56 @@ __global__ void __launch_bounds__(1 << PTB) k_pauli_chunk(const typename CTr<R>:
                 const uint32_t xl = gr.xlo & ((1u << PC) - 1);
                 if (gr.flags & CG_CHUNK) {
 #pragma unroll
-                    for (int r = 0; r < PV; r++) pb[r] = sx[((uint32_t)(r << PTB) | tid) ^ xl];
+                    for (int r = 0; r < PV; r++) pb[r] = sx[((uint32_t)(r << TB) | tid) ^ xl];
                 } else {
-                    const int64_t ph_ = (hi ^ (int64_t)(((uint64_t)gr.xlo | ((uint64_t)gr.xhi << 32)) & ~uint64_t((1u << PC) - 1)));
+                    const uint64_t x = (uint64_t)gr.xlo | ((uint64_t)gr.xhi << 32);
+                    const int64_t ph = hi ^ (int64_t)(x & ~uint64_t((1u << PC) - 1));
 #pragma unroll
-                    for (int r = 0; r < PV; r++) pb[r] = psi[ph_ | (int64_t)(((uint32_t)(r << PTB) | tid) ^ xl)];
+                    for (int r = 0; r < PV; r++) pb[r] = psi[ph | (int64_t)(((uint32_t)(r << TB) | tid) ^ xl)];
                 }
             }
-            R cr[PV], ci[PV];
-            if (gr.flags & CG_CONST) {  // every term has Z mask 0: one constant coefficient
-                R c0 = 0, c1 = 0;
-                for (int k = gr.t_begin; k < gr.t_end; k++) {
-                    c0 += st[k].cr;
-                    c1 += st[k].ci;
-                }
+            // per-amplitude coefficient: a per-thread constant part (c0) plus the terms
+            // whose sign depends on the register index (cr / ci)
+            R c0r = 0, c0i = 0, cr[PV], ci[PV];
 #pragma unroll
-                for (int r = 0; r < PV; r++) {
-                    cr[r] = c0;
-                    ci[r] = c1;
+            for (int r = 0; r < PV; r++) cr[r] = ci[r] = R(0);
+            const bool real = (gr.flags & CG_REAL) != 0;
+            if (gr.flags & CG_CONST) {
+                for (int k = gr.t_begin; k < gr.t_end; k++) {
+                    c0r += st[k].cr;
+                    c0i += st[k].ci;
                 }
             } else {
-#pragma unroll
-                for (int r = 0; r < PV; r++) cr[r] = ci[r] = R(0);
                 for (int k = gr.t_begin; k < gr.t_end; k++) {
-                    const CTerm<R> t = st[k];
+                    const CT_ t = st[k];
                     const uint32_t par = (__popc(a0lo & t.zlo) ^ __popc(a0hi & t.zhi)) & 1;
                     const R sr = sign_flip(t.cr, par), si = sign_flip(t.ci, par);
                     if (t.rpat == 0) {
-#pragma unroll
-                        for (int r = 0; r < PV; r++) {
-                            cr[r] += sr;
-                            ci[r] += si;
-                        }
+                        c0r += sr;
+                        c0i += si;
                     } else {
 #pragma unroll
                         for (int r = 0; r < PV; r++) {
                             const uint32_t f = (t.rpat >> r) & 1;
                             cr[r] += sign_flip(sr, f);
-                            ci[r] += sign_flip(si, f);
+                            if (!real) ci[r] += sign_flip(si, f);
                         }
                     }
                 }
             }
-            if (gr.flags & CG_REAL) {
+            if (real) {
 #pragma unroll
                 for (int r = 0; r < PV; r++) {
-                    lr[r] = fma(cr[r], pb[r].x, lr[r]);
-                    li[r] = fma(cr[r], pb[r].y, li[r]);
+                    const R c = cr[r] + c0r;
+                    lr[r] = fma(c, pb[r].x, lr[r]);
+                    li[r] = fma(c, pb[r].y, li[r]);
                 }
             } else {
 #pragma unroll
                 for (int r = 0; r < PV; r++) {
-                    lr[r] = fma(cr[r], pb[r].x, fma(-ci[r], pb[r].y, lr[r]));
-                    li[r] = fma(cr[r], pb[r].y, fma(ci[r], pb[r].x, li[r]));
+                    const R c = cr[r] + c0r, d = ci[r] + c0i;
+                    lr[r] = fma(c, pb[r].x, fma(-d, pb[r].y, lr[r]));
+                    li[r] = fma(c, pb[r].y, fma(d, pb[r].x, li[r]));
                 }
             }
         }
@@ -405,7 +371,7 @@ __global__ void __launch_bounds__(1 << PTB) k_pauli_chunk(const typename CTr<R>:
                 T l;
                 l.x = lr[r];
                 l.y = li[r];
-                lam[hi | (r << PTB) | tid] = l;
+                lam[hi | (r << TB) | tid] = l;
             }
             e += pa[r].x * lr[r] + pa[r].y * li[r];
         }
@@ -437,15 +403,17 @@ cudaError_t launch_pauli_expect(int dtype, const void *psi, void *lam, int n, Ob
                                 RedScratch red, double *out, cudaStream_t s)
 {
     int64_t len = int64_t(1) << n;
-    if (n >= PC && obs.n_groups > 0 && obs.n_terms < 65536 && chunk_smem_bytes(obs, dtype) <= kObsStageMax) {
-        const int64_t chunks = int64_t(1) << (n - PC);
+    if (n >= kPauliC && obs.chunk && obs.n_groups > 0 && obs.n_terms < 65536 &&
+        chunk_smem_bytes(obs, dtype) <= kObsStageMax) {
+        const int64_t chunks = int64_t(1) << (n - kPauliC);
         const int gr = (int)(chunks > kMaxRedBlocks ? kMaxRedBlocks : chunks);
         const size_t smem = chunk_smem_bytes(obs, dtype);
         if (dtype == 0)
-            k_pauli_chunk<float><<<gr, 1 << PTB, smem, s>>>((const float2 *)psi, (float2 *)lam, chunks, obs, red, out);
+            k_pauli_chunk<float><<<gr, 1 << kPauliTB, smem, s>>>((const float2 *)psi, (float2 *)lam, chunks, obs, red,
+                                                                 out);
         else
-            k_pauli_chunk<double><<<gr, 1 << PTB, smem, s>>>((const double2 *)psi, (double2 *)lam, chunks, obs, red,
-                                                            out);
+            k_pauli_chunk<double><<<gr, 1 << kPauliTB, smem, s>>>((const double2 *)psi, (double2 *)lam, chunks, obs,
+                                                                  red, out);
         return cudaGetLastError();
     }
     // up to the reduction scratch's 1024 blocks: about 54 warps per SM at 2^20 amplitudes
