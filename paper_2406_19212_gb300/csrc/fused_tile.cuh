@@ -732,17 +732,46 @@ __device__ __forceinline__ void apply_layer(const FGate &g, const DEnt *le, cons
 // complex128 amplitude each): tile_fetch issues all of its global loads into registers
 // (so their latencies overlap with each other and with the gate staging), tile_put
 // writes them to shared memory.  The block has exactly 2^t * size(T) / 16 / CNT threads.
+//
+// Word c of a thread starts at tile position l = A | B_c, A = AW * thread and B_c = AW * c *
+// blockDim on disjoint bits.  Its global offset tilebase | hitab[l >> low] | (l & lowmask)
+// and its swizzled slot are both linear over such a split (OR of disjoint deposits, XOR),
+// so the thread part is computed once and the part of word c is a block-uniform value.
+template <typename R>
+struct TileAddr {
+    int64_t g;  // global offset of the thread part (tilebase included)
+    int s;      // swizzled slot of the thread part
+};
+
+template <typename R>
+__device__ __forceinline__ TileAddr<R> tile_addr(int low, int64_t tilebase, const int64_t *hitab)
+{
+    constexpr int AW = sizeof(typename CT<R>::T) == 8 ? 2 : 1;
+    const int A = (int)threadIdx.x * AW;
+    return TileAddr<R>{tilebase | hitab[A >> low] | (A & ((1 << low) - 1)), swz<R>(A)};
+}
+
+// Word c's part: global offset (B's deposit) and slot (swz(B)).
+template <typename R>
+__device__ __forceinline__ void tile_word(int c, int low, const int64_t *hitab, int64_t &g, int &sl)
+{
+    constexpr int AW = sizeof(typename CT<R>::T) == 8 ? 2 : 1;
+    const int B = c * (int)blockDim.x * AW;
+    g = c ? (hitab[B >> low] | (B & ((1 << low) - 1))) : 0;
+    sl = swz<R>(B);
+}
+
 template <typename R, int CNT>
 __device__ __forceinline__ void tile_fetch(const typename CT<R>::T *gmem, float4 (&w)[CNT], int low, int64_t tilebase,
                                            const int64_t *hitab)
 {
-    constexpr int AW = sizeof(typename CT<R>::T) == 8 ? 2 : 1;  // amplitudes per word
-    const int lowmask = (1 << low) - 1;
+    const TileAddr<R> ta = tile_addr<R>(low, tilebase, hitab);
 #pragma unroll
     for (int c = 0; c < CNT; c++) {
-        const int l = (int)(threadIdx.x + c * blockDim.x) * AW;
-        const int64_t g = tilebase | hitab[l >> low] | (l & lowmask);
-        w[c] = *reinterpret_cast<const float4 *>(gmem + g);
+        int64_t g;
+        int sl;
+        tile_word<R>(c, low, hitab, g, sl);
+        w[c] = *reinterpret_cast<const float4 *>(gmem + (ta.g | g));
     }
 }
 
@@ -750,15 +779,16 @@ template <typename R, int CNT>
 __device__ __forceinline__ void tile_put(typename CT<R>::T *sm, const float4 (&w)[CNT])
 {
     constexpr int AW = sizeof(typename CT<R>::T) == 8 ? 2 : 1;
+    const int sA = swz<R>((int)threadIdx.x * AW);
 #pragma unroll
     for (int c = 0; c < CNT; c++) {
-        const int l = (int)(threadIdx.x + c * blockDim.x) * AW;
-        if constexpr (AW == 2) {
+        const int l = sA ^ swz<R>(c * (int)blockDim.x * AW);
+        if constexpr (AW == 2) {  // l ^ 1 = slot of the odd amplitude (swz(1) = 1)
             float2 *s2 = reinterpret_cast<float2 *>(sm);
-            s2[swz<R>(l)] = make_float2(w[c].x, w[c].y);
-            s2[swz<R>(l + 1)] = make_float2(w[c].z, w[c].w);
+            s2[l] = make_float2(w[c].x, w[c].y);
+            s2[l ^ 1] = make_float2(w[c].z, w[c].w);
         } else {
-            reinterpret_cast<float4 *>(sm)[swz<R>(l)] = w[c];
+            reinterpret_cast<float4 *>(sm)[l] = w[c];
         }
     }
 }
@@ -768,20 +798,22 @@ __device__ __forceinline__ void tile_store(typename CT<R>::T *gmem, const typena
                                            int64_t tilebase, const int64_t *hitab)
 {
     constexpr int AW = sizeof(typename CT<R>::T) == 8 ? 2 : 1;
-    const int lowmask = (1 << low) - 1;
+    const TileAddr<R> ta = tile_addr<R>(low, tilebase, hitab);
 #pragma unroll
     for (int c = 0; c < CNT; c++) {
-        const int l = (int)(threadIdx.x + c * blockDim.x) * AW;
-        const int64_t g = tilebase | hitab[l >> low] | (l & lowmask);
+        int64_t g;
+        int sl;
+        tile_word<R>(c, low, hitab, g, sl);
+        const int l = ta.s ^ sl;
         float4 w;
         if constexpr (AW == 2) {
             const float2 *s2 = reinterpret_cast<const float2 *>(sm);
-            const float2 a = s2[swz<R>(l)], b = s2[swz<R>(l + 1)];
+            const float2 a = s2[l], b = s2[l ^ 1];
             w = make_float4(a.x, a.y, b.x, b.y);
         } else {
-            w = reinterpret_cast<const float4 *>(sm)[swz<R>(l)];
+            w = reinterpret_cast<const float4 *>(sm)[l];
         }
-        *reinterpret_cast<float4 *>(gmem + g) = w;
+        *reinterpret_cast<float4 *>(gmem + (ta.g | g)) = w;
     }
 }
 
@@ -789,13 +821,13 @@ __device__ __forceinline__ void tile_store(typename CT<R>::T *gmem, const typena
 template <typename R, int CNT>
 __device__ __forceinline__ void tile_zero(typename CT<R>::T *gmem, int low, int64_t tilebase, const int64_t *hitab)
 {
-    constexpr int AW = sizeof(typename CT<R>::T) == 8 ? 2 : 1;
-    const int lowmask = (1 << low) - 1;
+    const TileAddr<R> ta = tile_addr<R>(low, tilebase, hitab);
 #pragma unroll
     for (int c = 0; c < CNT; c++) {
-        const int l = (int)(threadIdx.x + c * blockDim.x) * AW;
-        const int64_t g = tilebase | hitab[l >> low] | (l & lowmask);
-        *reinterpret_cast<float4 *>(gmem + g) = make_float4(0.f, 0.f, 0.f, 0.f);
+        int64_t g;
+        int sl;
+        tile_word<R>(c, low, hitab, g, sl);
+        *reinterpret_cast<float4 *>(gmem + (ta.g | g)) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
