@@ -48,15 +48,16 @@ __device__ __forceinline__ void apply2(const R *m, typename CT<R>::T &a, typenam
 {
     if (SH == SH_DENSE1) {
         if constexpr (sizeof(R) == 4) {
-            // packed FP32x2: z x = (zr, zr) * x + (-zi, zi) * swap(x) for complex z, so each
-            // output takes one packed multiply and three packed fmas
-            const float2 sa = make_float2(a.y, a.x), sb = make_float2(b.y, b.x);
-            const float2 na = __ffma2_rn(make_float2(m[0], m[0]), a,
-                                         __fmul2_rn(make_float2(-m[1], m[1]), sa));
-            const float2 nb = __ffma2_rn(make_float2(m[4], m[4]), a,
-                                         __fmul2_rn(make_float2(-m[5], m[5]), sa));
-            a = __ffma2_rn(make_float2(-m[3], m[3]), sb, __ffma2_rn(make_float2(m[2], m[2]), b, na));
-            b = __ffma2_rn(make_float2(-m[7], m[7]), sb, __ffma2_rn(make_float2(m[6], m[6]), b, nb));
+            // packed FP32x2 without swapped operands: for an output row (u, v) the packed
+            // P = Re(u) a + Re(v) b and Q = Im(u) a + Im(v) b give the output as
+            // (P.x - Q.y, P.y + Q.x): four packed operations and two adds per output, none
+            // of them a register move
+            const float2 pa = __ffma2_rn(make_float2(m[2], m[2]), b, __fmul2_rn(make_float2(m[0], m[0]), a));
+            const float2 qa = __ffma2_rn(make_float2(m[3], m[3]), b, __fmul2_rn(make_float2(m[1], m[1]), a));
+            const float2 pb = __ffma2_rn(make_float2(m[6], m[6]), b, __fmul2_rn(make_float2(m[4], m[4]), a));
+            const float2 qb = __ffma2_rn(make_float2(m[7], m[7]), b, __fmul2_rn(make_float2(m[5], m[5]), a));
+            a = make_float2(pa.x - qa.y, pa.y + qa.x);
+            b = make_float2(pb.x - qb.y, pb.y + qb.x);
         } else {
             // contributions of the old a to a' and b'
             const R a1x = fma(m[0], a.x, -m[1] * a.y), a1y = fma(m[0], a.y, m[1] * a.x);

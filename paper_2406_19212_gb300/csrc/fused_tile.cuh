@@ -855,7 +855,17 @@ struct TileCtx {
 // phase block.  Ends with the block synchronised.  Returns false, with nothing staged,
 // for a tile of a pass started from |0...0> (args.init) that is not tile 0: the tile's
 // amplitudes are written as zeros and the CTA has nothing more to do.
-template <typename R, int NR, bool REV>
+// Geometry of a pass read from its descriptor at run time (the interpreter).  The
+// specialised passes pass their own provider with kStatic = true and the pass's tile
+// positions compiled in: tilebase(tile) deposits the tile index on the physical qubits
+// outside the tile, hi(h) the high local bits h on the tile's qubits low..t-1.
+struct RuntimeGeom {
+    static constexpr bool kStatic = false;
+    __device__ static int64_t tilebase(int64_t) { return 0; }
+    __device__ static int64_t hi(int) { return 0; }
+};
+
+template <typename R, int NR, bool REV, class Geom = RuntimeGeom>
 __device__ __forceinline__ bool tile_begin(const typename CT<R>::T *__restrict__ phi,
                                            const typename CT<R>::T *__restrict__ psi, const FusedArgs &args,
                                            const int64_t tile, TileCtx<R, NR, REV> &c)
@@ -892,7 +902,10 @@ __device__ __forceinline__ bool tile_begin(const typename CT<R>::T *__restrict__
     R *smat = reinterpret_cast<R *>(p);
 
     int64_t tilebase = 0;
-    {
+    if constexpr (Geom::kStatic) {
+        tilebase = Geom::tilebase(tile);
+        for (int h = threadIdx.x; h < nhi; h += blockDim.x) hitab[h] = Geom::hi(h);
+    } else {
         // S as two 64-bit words: byte j = physical qubit of tile position j (j < t <= 16)
         const int4 sw = *reinterpret_cast<const int4 *>(pdg.S);
         const uint64_t s_lo = (uint64_t)(uint32_t)sw.x | ((uint64_t)(uint32_t)sw.y << 32);
@@ -1006,27 +1019,31 @@ __device__ __forceinline__ bool tile_begin(const typename CT<R>::T *__restrict__
     return true;
 }
 
-// Gather a sub-run's register amplitudes: tile positions Rp[0..NR-1] are the register
-// bits, the thread index spells the other positions in ascending order (returned: the
-// thread's base position, off[k] = 1 << Rp[k]).
-template <typename R, int NR, bool REV>
-__device__ __forceinline__ int subrun_load(const TileCtx<R, NR, REV> &c, const int (&Rp)[NR], int (&off)[NR],
-                                           typename CT<R>::T *a, typename CT<R>::T *b)
+// A sub-run's thread base position: tile positions Rp[0..NR-1] are the register bits,
+// the thread index spells the other positions (below t) in ascending order.
+template <int NR>
+__device__ __forceinline__ int subrun_base(int t, const int (&Rp)[NR])
 {
     int rmask = 0;
 #pragma unroll
     for (int k = 0; k < NR; k++) rmask |= 1 << Rp[k];
     int base = 0;
-    for (int q = 0, i = 0; q < c.t; q++) {
+    for (int q = 0, i = 0; q < t; q++) {
         if ((rmask >> q) & 1) continue;
         if ((threadIdx.x >> i) & 1) base |= 1 << q;
         i++;
     }
-#pragma unroll
-    for (int k = 0; k < NR; k++) off[k] = 1 << Rp[k];
-    // base and the register offsets occupy disjoint bits, so base | C = base ^ C, and the
-    // swizzle is linear over XOR: slot(base | C_j) = swz(base) ^ swz(C_j) with swz(C_j) a
-    // constant of the sub-run (a literal in the specialised passes)
+    return base;
+}
+
+// Gather the register amplitudes of the thread at base with register offsets off[k] =
+// 1 << Rp[k].  base and the register offsets occupy disjoint bits, so base | C = base ^ C,
+// and the swizzle is linear over XOR: slot(base | C_j) = swz(base) ^ swz(C_j) with swz(C_j)
+// a constant of the sub-run (a literal in the specialised passes).
+template <typename R, int NR, bool REV>
+__device__ __forceinline__ void subrun_gather(const TileCtx<R, NR, REV> &c, int base, const int (&off)[NR],
+                                              typename CT<R>::T *a, typename CT<R>::T *b)
+{
     const int sb = swz<R>(base);
 #pragma unroll
     for (int j = 0; j < (1 << NR); j++) {
@@ -1038,6 +1055,17 @@ __device__ __forceinline__ int subrun_load(const TileCtx<R, NR, REV> &c, const i
         a[j] = c.sphi[l];
         if constexpr (REV) b[j] = c.spsi[l];
     }
+}
+
+// Base position, register offsets and gather of a sub-run (returns the base).
+template <typename R, int NR, bool REV>
+__device__ __forceinline__ int subrun_load(const TileCtx<R, NR, REV> &c, const int (&Rp)[NR], int (&off)[NR],
+                                           typename CT<R>::T *a, typename CT<R>::T *b)
+{
+#pragma unroll
+    for (int k = 0; k < NR; k++) off[k] = 1 << Rp[k];
+    const int base = subrun_base<NR>(c.t, Rp);
+    subrun_gather<R, NR, REV>(c, base, off, a, b);
     return base;
 }
 

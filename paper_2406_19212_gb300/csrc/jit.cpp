@@ -147,6 +147,25 @@ std::string flit(float v)  // exact literal of a float coefficient
 
 const char *gen_name(int g) { return g == GEN_X ? "GEN_X" : "GEN_Y"; }
 
+// Bit deposit as shifts and masks: bit i of var goes to position pos[i]; runs of
+// consecutive bits landing on consecutive positions are one term.
+std::string deposit_expr(const char *var, const std::vector<int> &pos, const char *type)
+{
+    std::ostringstream o;
+    bool first = true;
+    for (size_t i = 0; i < pos.size();) {
+        size_t j = i + 1;
+        while (j < pos.size() && pos[j] == pos[j - 1] + 1) j++;
+        const unsigned long long mask = (j - i) >= 64 ? ~0ull : ((1ull << (j - i)) - 1);
+        o << (first ? "" : " | ") << "(((" << type << ")(" << var << ") >> " << i << ") & (" << type << ")0x" << std::hex
+          << mask << std::dec << "ull) << " << pos[i];
+        first = false;
+        i = j;
+    }
+    if (first) o << "(" << type << ")0";
+    return o.str();
+}
+
 void emit_gate(std::ostringstream &o, const FusedPlan &P, const PassDesc &d, const FGate &g, bool rev, int NR)
 {
     const std::vector<DEnt> &E = rev ? P.rents : P.fents;
@@ -274,25 +293,43 @@ std::string jit_source(const FusedPlan &P, int p, bool rev, int dtype)
     const std::vector<SubRun> &subs = rev ? P.rsubs : P.fsubs;
     const std::vector<FGate> &gates = rev ? P.rgates : P.fgates;
     const int NR = rev ? P.nr_r : P.nr_f;
+    // the pass's tile geometry as literals: tile index -> qubits outside the tile (ascending),
+    // high local bits -> tile qubits low..t-1
+    std::vector<int> ns, hs;
+    for (int i = 0; i < d.n - d.t; i++) ns.push_back(d.NS[i]);
+    for (int i = d.low; i < d.t; i++) hs.push_back(d.S[i]);
+    const std::string geom = "struct Geom {\n  static constexpr bool kStatic = true;\n"
+                             "  __device__ static int64_t tilebase(int64_t tile) { return " +
+                             deposit_expr("tile", ns, "int64_t") +
+                             "; }\n  __device__ static int64_t hi(int h) { return " + deposit_expr("h", hs, "int64_t") +
+                             "; }\n};\n";
     std::ostringstream o;
     o << "// specialised " << (rev ? "reverse" : "forward") << " tile pass " << p << " (generated)\n"
       << "#include \"fused_tile.cuh\"\nusing namespace gbvqc;\n"
       << "typedef " << (dtype == 0 ? "float" : "double") << " Rt;\ntypedef CT<Rt>::T Tt;\n"
-      << "extern \"C\" __global__ void __launch_bounds__(" << (1 << (d.t - NR)) << ", "
+      << geom << "extern \"C\" __global__ void __launch_bounds__(" << (1 << (d.t - NR)) << ", "
       << jit_min_blocks(1 << (d.t - NR)) << ") " << jit_kernel_name(p, rev)
       << "(Tt *__restrict__ phi, Tt *__restrict__ psi, const FusedArgs args)\n{\n"
       << "  constexpr int NR = " << NR << ";\n  constexpr bool REV = " << (rev ? "true" : "false") << ";\n"
       << "  // a code-prefetch launch (args.dry) runs tile 0 and CTA s walks sub-run s only\n"
       << "  const int64_t tile = args.dry ? 0 : blockIdx.x;\n"
-      << "  TileCtx<Rt, NR, REV> c;\n  if (!tile_begin<Rt, NR, REV>(phi, psi, args, tile, c)) return;\n"
+      << "  TileCtx<Rt, NR, REV> c;\n  if (!tile_begin<Rt, NR, REV, Geom>(phi, psi, args, tile, c)) return;\n"
       << "  Tt a[1 << NR], b[REV ? (1 << NR) : 1];\n"
       << "  const Rt *smat = c.smat;\n  const DEnt *sents = c.sents;\n  const RedCtx<Rt> &rc = c.rc;\n"
       << "  const int64_t tilebase = c.tilebase;\n  (void)sents; (void)rc; (void)tilebase; (void)b;\n";
     for (int s = 0; s < d.n_sub; s++) {
         const SubRun &sr = subs[d.sub_begin + s];
-        o << "  if (!args.dry || blockIdx.x == " << s << ") {  // sub-run " << s << "\n    const int Rp[NR] = {";
-        for (int k = 0; k < NR; k++) o << (k ? ", " : "") << (int)sr.R[k];
-        o << "};\n    int off[NR];\n    const int base = subrun_load<Rt, NR, REV>(c, Rp, off, a, b);\n    (void)base;\n";
+        // thread bit i -> i-th lowest tile position outside the sub-run's registers
+        std::vector<int> bpos;
+        for (int q = 0; q < d.t; q++) {
+            bool reg = false;
+            for (int k = 0; k < NR; k++) reg = reg || sr.R[k] == q;
+            if (!reg) bpos.push_back(q);
+        }
+        o << "  if (!args.dry || blockIdx.x == " << s << ") {  // sub-run " << s << "\n    const int off[NR] = {";
+        for (int k = 0; k < NR; k++) o << (k ? ", " : "") << (1 << (int)sr.R[k]);
+        o << "};\n    const int base = " << deposit_expr("threadIdx.x", bpos, "int")
+          << ";\n    subrun_gather<Rt, NR, REV>(c, base, off, a, b);\n";
         for (int gi = sr.g_begin; gi < sr.g_end; gi++) emit_gate(o, P, d, gates[d.gate_begin + gi], rev, NR);
         o << "    subrun_store<Rt, NR, REV>(c, base, off, a, b);\n  }\n";
     }
