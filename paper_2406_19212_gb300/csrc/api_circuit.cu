@@ -201,9 +201,11 @@ gbvqc_status csr_upload(const std::vector<int> &slot_param, int n_params, int **
     return GBVQC_OK;
 }
 
-// A general one-qubit unitary U = e^{i alpha} V with V real (SH_REAL1) or with a real
-// diagonal and an imaginary off-diagonal (SH_IMAG1): sqrt(Y) and sqrt(X) are of this
-// kind up to the phase e^{i pi/4}, and V costs 6 instead of 14 flops per amplitude.
+// A general one-qubit unitary U = e^{i alpha} V with V real (SH_REAL1), with a real
+// diagonal and an imaginary off-diagonal (SH_IMAG1), or with a real diagonal only (kept
+// SH_DENSE1; the specialised passes apply it as SH_RDIAG1): sqrt(Y), sqrt(X) and sqrt(W)
+// are of these kinds up to the phase e^{i pi/4}, and V costs 6 or 10 instead of 14 flops
+// per amplitude.
 // Components that the pattern makes zero are set to exactly zero (they are below
 // 1e-13 of the largest entry).
 static bool phase_normalize(const Mat &U, Mat &V, double &alpha)
@@ -214,10 +216,10 @@ static bool phase_normalize(const Mat &U, Mat &V, double &alpha)
         if (std::abs(U[k]) > mx) mx = std::abs(U[k]), kmax = k;
     if (mx == 0.0) return false;
     const double tol = 1e-13 * mx;
-    for (int pattern = 0; pattern < 2; pattern++) {
+    for (int pattern = 0; pattern < 3; pattern++) {
         double a;
         if (pattern == 0) a = std::arg(U[kmax]);  // real: any largest entry sets the phase
-        else {                                    // imaginary off-diagonal: the diagonal does
+        else {  // imaginary off-diagonal, or (2) a real diagonal only: the diagonal does
             const int kd = std::abs(U[0]) >= std::abs(U[3]) ? 0 : 3;
             if (std::abs(U[kd]) <= tol) continue;
             a = std::arg(U[kd]);
@@ -231,7 +233,7 @@ static bool phase_normalize(const Mat &U, Mat &V, double &alpha)
             if (pattern == 0 || diag) {
                 ok = ok && std::abs(W[k].imag()) <= tol;
                 W[k] = cd(W[k].real(), 0.0);
-            } else {
+            } else if (pattern == 1) {
                 ok = ok && std::abs(W[k].real()) <= tol;
                 W[k] = cd(0.0, W[k].imag());
             }
@@ -267,11 +269,6 @@ static Mat mat_scaled(const Mat &M, cd z)
     return D;
 }
 
-// Physical gate list of the fused engine for a density layout `map` (or pure, map unused).
-// Fixed one-qubit gates are phase-normalised (normalize_fixed).  On a density matrix the
-// phases cancel between the ket (U) and bra (conj U) sides; on a pure state their sum is
-// multiplied into one fixed gate whose shape is kept by a complex scale, or, if there is
-// none, undone on the first normalised gate, so the fused sweeps give the exact state.
 // Plan-time variant of a fixed SH_BLOCK2 record, for the specialised passes (FGate.perm of
 // an FT_BLOCK2 gate): BLOCK2_VARIANT | the shape of the 2x2 on {|01>, |10>} (0 general,
 // 1 real diagonal and imaginary off-diagonal, 2 real) | BLOCK2_P00_ONE / BLOCK2_P11_ONE
@@ -289,6 +286,11 @@ static int block2_variant(const MatRec &r)
     return v;
 }
 
+// Physical gate list of the fused engine for a density layout `map` (or pure, map unused).
+// Fixed one-qubit gates are phase-normalised (normalize_fixed).  On a density matrix the
+// phases cancel between the ket (U) and bra (conj U) sides; on a pure state their sum is
+// multiplied into one fixed gate whose shape is kept by a complex scale, or, if there is
+// none, undone on the first normalised gate, so the fused sweeps give the exact state.
 static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGate> &out)
 {
     out.clear();
@@ -445,14 +447,23 @@ static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGa
         out[first_norm].rec_i = out[first_norm].rec_a = add_rec(c, mat_dagger(W, 2));
         out[first_norm].ftype = FT_DENSE1;
     }
-    // fixed block gates (FSIM with constant angles): the structure of their final matrices
+    // fixed block gates (FSIM with constant angles) and dense one-qubit gates: the
+    // structure of their final matrices
     std::vector<char> dynamic(c->recs.size(), 0);
     for (const DynRec &d : c->dyn) dynamic[d.rec] = 1;
-    for (PGate &g : out)
-        if (g.ftype == FT_BLOCK2 && !dynamic[g.rec_f] && !dynamic[g.rec_i] && g.rec_a == g.rec_i) {
+    auto real_diag = [&](int rec) {
+        const MatRec &r = c->recs[rec];
+        return r.d[1] == 0.0 && r.d[7] == 0.0 && r.f[1] == 0.0f && r.f[7] == 0.0f;
+    };
+    for (PGate &g : out) {
+        if (dynamic[g.rec_f] || dynamic[g.rec_i] || g.rec_a != g.rec_i) continue;
+        if (g.ftype == FT_BLOCK2) {
             g.perm_f = block2_variant(c->recs[g.rec_f]);
             g.perm_r = block2_variant(c->recs[g.rec_i]);
+        } else if (g.ftype == FT_DENSE1 && g.k == 1) {
+            g.rdiag = real_diag(g.rec_f) && real_diag(g.rec_i);
         }
+    }
 }
 
 extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qubits, int n_params,

@@ -45,7 +45,9 @@ enum Shape : int32_t {
                     // (superoperator of a phase-covariant one-qubit channel on (ket, bra))
     SH_RPAR2 = 12,  // SH_PAR2 with real entries (depolarising, amplitude and phase damping)
     SH_CX = 13,     // exactly CNOT (control = first qubit): a swap, no arithmetic
-    SH_CZ = 14      // exactly CZ: the sign of |11>, no arithmetic
+    SH_CZ = 14,     // exactly CZ: the sign of |11>, no arithmetic
+    SH_RDIAG1 = 15  // real diagonal, general off-diagonal 2x2 (a fixed gate such as sqrt(W)
+                    // after phase normalisation); one-qubit layer entries only
 };
 
 inline __host__ __device__ bool shape_is_diag(int sh) { return sh == SH_DIAG1 || sh == SH_DIAG2 || sh == SH_CZ; }

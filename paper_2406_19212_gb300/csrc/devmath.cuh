@@ -70,6 +70,24 @@ __device__ __forceinline__ void apply2(const R *m, typename CT<R>::T &a, typenam
             b.x = fma(m[6], b.x, bx);
             b.y = fma(m[6], b.y, by);
         }
+    } else if (SH == SH_RDIAG1) {
+        // real diagonal (m[1] = m[7] = 0): the diagonal term of each output is one packed
+        // multiply (complex64) or two multiplies
+        if constexpr (sizeof(R) == 4) {
+            const float2 pa = __ffma2_rn(make_float2(m[2], m[2]), b, __fmul2_rn(make_float2(m[0], m[0]), a));
+            const float2 qa = __fmul2_rn(make_float2(m[3], m[3]), b);
+            const float2 pb = __ffma2_rn(make_float2(m[4], m[4]), a, __fmul2_rn(make_float2(m[6], m[6]), b));
+            const float2 qb = __fmul2_rn(make_float2(m[5], m[5]), a);
+            a = make_float2(pa.x - qa.y, pa.y + qa.x);
+            b = make_float2(pb.x - qb.y, pb.y + qb.x);
+        } else {
+            const R ax = fma(m[2], b.x, fma(-m[3], b.y, m[0] * a.x)), ay = fma(m[2], b.y, fma(m[3], b.x, m[0] * a.y));
+            const R bx = fma(m[4], a.x, fma(-m[5], a.y, m[6] * b.x)), by = fma(m[4], a.y, fma(m[5], a.x, m[6] * b.y));
+            a.x = ax;
+            a.y = ay;
+            b.x = bx;
+            b.y = by;
+        }
     } else if (SH == SH_DIAG1) {
         cmul_ip(m[0], m[1], a);
         cmul_ip(m[6], m[7], b);

@@ -657,7 +657,7 @@ __device__ __forceinline__ void layer_slot_ent(int mask, const DEnt *le, int &id
             } else if (d.k == SH_IMAG1) {
                 rg1<R, NR, K, SH_IMAG1>(a, m);
                 if constexpr (REV) rg1<R, NR, K, SH_IMAG1>(b, m2);
-            } else if (d.k == SH_DENSE1) {
+            } else if (d.k == SH_DENSE1 || d.k == SH_RDIAG1) {  // (general form for both)
                 rg1<R, NR, K, SH_DENSE1>(a, m);
                 if constexpr (REV) rg1<R, NR, K, SH_DENSE1>(b, m2);
             } else {

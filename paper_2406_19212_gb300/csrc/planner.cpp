@@ -317,6 +317,7 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
                         d.k = (int8_t)(g.ftype == FT_REAL1   ? SH_REAL1
                                        : g.ftype == FT_ANTI1 ? SH_ANTI1
                                        : g.ftype == FT_IMAG1 ? SH_IMAG1
+                                       : g.rdiag             ? SH_RDIAG1
                                                              : SH_DENSE1);
                         codes |= (g.ftype == FT_REAL1 ? 1 : g.ftype == FT_IMAG1 ? 2 : g.ftype == FT_ANTI1 ? 3 : 0) << (2 * k);
                         d.ca = (int8_t)k;

@@ -27,6 +27,7 @@ struct PGate {
     float coef;       // gradient weight
     int param;        // parameter index or -1
     bool cz = false;  // exactly diag(1, 1, 1, -1) in every direction (CZ)
+    bool rdiag = false;  // FT_DENSE1 whose matrices (every direction) have an exactly real diagonal
 };
 
 struct PlanOptions {
