@@ -743,7 +743,15 @@ struct TileAddr {
     int s;      // swizzled slot of the thread part
 };
 
+// The swizzle only touches bits below 2B (SwzBits): slot(X ^ H) = swz(X) + H for H on bits
+// >= 2B that X does not use, so such a part of an index is an address offset.
 template <typename R>
+__device__ __forceinline__ int swz_lo_mask() { return (1 << (2 * SwzBits<R>::B)) - 1; }
+
+template <int THREADS>
+__device__ __forceinline__ int tile_threads() { return THREADS ? THREADS : (int)blockDim.x; }
+
+template <typename R, int THREADS>
 __device__ __forceinline__ TileAddr<R> tile_addr(int low, int64_t tilebase, const int64_t *hitab)
 {
     constexpr int AW = sizeof(typename CT<R>::T) == 8 ? 2 : 1;
@@ -751,38 +759,42 @@ __device__ __forceinline__ TileAddr<R> tile_addr(int low, int64_t tilebase, cons
     return TileAddr<R>{tilebase | hitab[A >> low] | (A & ((1 << low) - 1)), swz<R>(A)};
 }
 
-// Word c's part: global offset (B's deposit) and slot (swz(B)).
-template <typename R>
-__device__ __forceinline__ void tile_word(int c, int low, const int64_t *hitab, int64_t &g, int &sl)
+// Word c's part B = AW * c * threads: its global offset (B's deposit) and its slot split
+// into swz(B's bits below 2B) (XORed with the thread part) and B's higher bits (added:
+// the thread part A < AW * threads never holds them).
+template <typename R, int THREADS>
+__device__ __forceinline__ void tile_word(int c, int low, const int64_t *hitab, int64_t &g, int &slo, int &shi)
 {
     constexpr int AW = sizeof(typename CT<R>::T) == 8 ? 2 : 1;
-    const int B = c * (int)blockDim.x * AW;
+    const int B = c * tile_threads<THREADS>() * AW;
     g = c ? (hitab[B >> low] | (B & ((1 << low) - 1))) : 0;
-    sl = swz<R>(B);
+    slo = swz<R>(B & swz_lo_mask<R>());
+    shi = B & ~swz_lo_mask<R>();
 }
 
-template <typename R, int CNT>
+template <typename R, int CNT, int THREADS = 0>
 __device__ __forceinline__ void tile_fetch(const typename CT<R>::T *gmem, float4 (&w)[CNT], int low, int64_t tilebase,
                                            const int64_t *hitab)
 {
-    const TileAddr<R> ta = tile_addr<R>(low, tilebase, hitab);
+    const TileAddr<R> ta = tile_addr<R, THREADS>(low, tilebase, hitab);
 #pragma unroll
     for (int c = 0; c < CNT; c++) {
         int64_t g;
-        int sl;
-        tile_word<R>(c, low, hitab, g, sl);
+        int slo, shi;
+        tile_word<R, THREADS>(c, low, hitab, g, slo, shi);
         w[c] = *reinterpret_cast<const float4 *>(gmem + (ta.g | g));
     }
 }
 
-template <typename R, int CNT>
+template <typename R, int CNT, int THREADS = 0>
 __device__ __forceinline__ void tile_put(typename CT<R>::T *sm, const float4 (&w)[CNT])
 {
     constexpr int AW = sizeof(typename CT<R>::T) == 8 ? 2 : 1;
     const int sA = swz<R>((int)threadIdx.x * AW);
 #pragma unroll
     for (int c = 0; c < CNT; c++) {
-        const int l = sA ^ swz<R>(c * (int)blockDim.x * AW);
+        const int B = c * tile_threads<THREADS>() * AW;
+        const int l = (sA ^ swz<R>(B & swz_lo_mask<R>())) + (B & ~swz_lo_mask<R>());
         if constexpr (AW == 2) {  // l ^ 1 = slot of the odd amplitude (swz(1) = 1)
             float2 *s2 = reinterpret_cast<float2 *>(sm);
             s2[l] = make_float2(w[c].x, w[c].y);
@@ -793,18 +805,18 @@ __device__ __forceinline__ void tile_put(typename CT<R>::T *sm, const float4 (&w
     }
 }
 
-template <typename R, int CNT>
+template <typename R, int CNT, int THREADS = 0>
 __device__ __forceinline__ void tile_store(typename CT<R>::T *gmem, const typename CT<R>::T *sm, int low,
                                            int64_t tilebase, const int64_t *hitab)
 {
     constexpr int AW = sizeof(typename CT<R>::T) == 8 ? 2 : 1;
-    const TileAddr<R> ta = tile_addr<R>(low, tilebase, hitab);
+    const TileAddr<R> ta = tile_addr<R, THREADS>(low, tilebase, hitab);
 #pragma unroll
     for (int c = 0; c < CNT; c++) {
         int64_t g;
-        int sl;
-        tile_word<R>(c, low, hitab, g, sl);
-        const int l = ta.s ^ sl;
+        int slo, shi;
+        tile_word<R, THREADS>(c, low, hitab, g, slo, shi);
+        const int l = (ta.s ^ slo) + shi;
         float4 w;
         if constexpr (AW == 2) {
             const float2 *s2 = reinterpret_cast<const float2 *>(sm);
@@ -818,15 +830,15 @@ __device__ __forceinline__ void tile_store(typename CT<R>::T *gmem, const typena
 }
 
 // Zeros to every amplitude of the tile (the words tile_store would write).
-template <typename R, int CNT>
+template <typename R, int CNT, int THREADS = 0>
 __device__ __forceinline__ void tile_zero(typename CT<R>::T *gmem, int low, int64_t tilebase, const int64_t *hitab)
 {
-    const TileAddr<R> ta = tile_addr<R>(low, tilebase, hitab);
+    const TileAddr<R> ta = tile_addr<R, THREADS>(low, tilebase, hitab);
 #pragma unroll
     for (int c = 0; c < CNT; c++) {
         int64_t g;
-        int sl;
-        tile_word<R>(c, low, hitab, g, sl);
+        int slo, shi;
+        tile_word<R, THREADS>(c, low, hitab, g, slo, shi);
         *reinterpret_cast<float4 *>(gmem + (ta.g | g)) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
@@ -861,6 +873,7 @@ struct TileCtx {
 // outside the tile, hi(h) the high local bits h on the tile's qubits low..t-1.
 struct RuntimeGeom {
     static constexpr bool kStatic = false;
+    static constexpr int kThreads = 0;  // block size (0: read blockDim.x)
     __device__ static int64_t tilebase(int64_t) { return 0; }
     __device__ static int64_t hi(int) { return 0; }
 };
@@ -950,14 +963,14 @@ __device__ __forceinline__ bool tile_begin(const typename CT<R>::T *__restrict__
 #pragma unroll
         for (int k = 0; k < CNT; k++) wphi[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (tile != 0) {  // uniform over the CTA; a prefetch launch runs tile 0 only
-            tile_zero<R, CNT>(const_cast<T *>(phi), low, tilebase, hitab);
+            tile_zero<R, CNT, Geom::kThreads>(const_cast<T *>(phi), low, tilebase, hitab);
             return false;
         }
         if (threadIdx.x == 0) *reinterpret_cast<T *>(&wphi[0]) = T{R(1), R(0)};  // local 0 = global 0
     } else {
-        tile_fetch<R, CNT>(phi, wphi, low, tilebase, hitab);
+        tile_fetch<R, CNT, Geom::kThreads>(phi, wphi, low, tilebase, hitab);
     }
-    if constexpr (REV) tile_fetch<R, CNT>(psi, wpsi, low, tilebase, hitab);
+    if constexpr (REV) tile_fetch<R, CNT, Geom::kThreads>(psi, wpsi, low, tilebase, hitab);
     // stage the pass's gates, diagonal entries and matrices while the tile loads are in flight
     {
         const int4 *src = reinterpret_cast<const int4 *>(args.gates + pd.gate_begin);
@@ -979,8 +992,8 @@ __device__ __forceinline__ bool tile_begin(const typename CT<R>::T *__restrict__
             }
         }
     }
-    tile_put<R, CNT>(sphi, wphi);
-    if constexpr (REV) tile_put<R, CNT>(spsi, wpsi);
+    tile_put<R, CNT, Geom::kThreads>(sphi, wphi);
+    if constexpr (REV) tile_put<R, CNT, Geom::kThreads>(spsi, wpsi);
     __syncthreads();
     // tile-constant phase products of every phase block (bits fixed by the tile index)
     for (int gi = threadIdx.x; gi < pd.n_gates; gi += blockDim.x) {
@@ -1051,7 +1064,8 @@ __device__ __forceinline__ void subrun_gather(const TileCtx<R, NR, REV> &c, int 
 #pragma unroll
         for (int k = 0; k < NR; k++)
             if ((j >> k) & 1) cj |= off[k];
-        const int l = sb ^ swz<R>(cj);
+        // register bits at or above 2B are an offset (base never holds them)
+        const int l = (sb ^ swz<R>(cj & swz_lo_mask<R>())) + (cj & ~swz_lo_mask<R>());
         a[j] = c.sphi[l];
         if constexpr (REV) b[j] = c.spsi[l];
     }
@@ -1074,14 +1088,14 @@ template <typename R, int NR, bool REV>
 __device__ __forceinline__ void subrun_store(const TileCtx<R, NR, REV> &c, int base, const int (&off)[NR],
                                              const typename CT<R>::T *a, const typename CT<R>::T *b)
 {
-    const int sb = swz<R>(base);  // as in subrun_load
+    const int sb = swz<R>(base);  // as in subrun_gather
 #pragma unroll
     for (int j = 0; j < (1 << NR); j++) {
         int cj = 0;
 #pragma unroll
         for (int k = 0; k < NR; k++)
             if ((j >> k) & 1) cj |= off[k];
-        const int l = sb ^ swz<R>(cj);
+        const int l = (sb ^ swz<R>(cj & swz_lo_mask<R>())) + (cj & ~swz_lo_mask<R>());
         c.sphi[l] = a[j];
         if constexpr (REV) c.spsi[l] = b[j];
     }
@@ -1189,16 +1203,16 @@ __device__ __forceinline__ void run_records(const TileCtx<R, NR, REV> &c, int g_
 
 // Epilogue: the tile back to global memory and (reverse) the tile's FP64 partial of every
 // gradient slot of the pass, summed over the warps in fixed order.
-template <typename R, int NR, bool REV>
+template <typename R, int NR, bool REV, class Geom = RuntimeGeom>
 __device__ __forceinline__ void tile_end(typename CT<R>::T *__restrict__ phi, typename CT<R>::T *__restrict__ psi,
                                          const FusedArgs &args, const int64_t tile, const TileCtx<R, NR, REV> &c)
 {
     typedef typename CT<R>::T T;
     constexpr int CNT = sizeof(T) == 8 ? (1 << (NR - 1)) : (1 << NR);
     if (args.dry) return;  // a code-prefetch launch writes nothing
-    tile_store<R, CNT>(phi, c.sphi, c.low, c.tilebase, c.hitab);
+    tile_store<R, CNT, Geom::kThreads>(phi, c.sphi, c.low, c.tilebase, c.hitab);
     if (REV) {
-        tile_store<R, CNT>(psi, c.spsi, c.low, c.tilebase, c.hitab);
+        tile_store<R, CNT, Geom::kThreads>(psi, c.spsi, c.low, c.tilebase, c.hitab);
         const int nwarps = c.rc.nwarps;
         for (int sl = threadIdx.x; sl < c.n_slots; sl += blockDim.x) {
             double acc = 0.0;

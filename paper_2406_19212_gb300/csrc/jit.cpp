@@ -298,7 +298,8 @@ std::string jit_source(const FusedPlan &P, int p, bool rev, int dtype)
     std::vector<int> ns, hs;
     for (int i = 0; i < d.n - d.t; i++) ns.push_back(d.NS[i]);
     for (int i = d.low; i < d.t; i++) hs.push_back(d.S[i]);
-    const std::string geom = "struct Geom {\n  static constexpr bool kStatic = true;\n"
+    const std::string geom = "struct Geom {\n  static constexpr bool kStatic = true;\n  static constexpr int kThreads = " +
+                             std::to_string(1 << (d.t - NR)) + ";\n"
                              "  __device__ static int64_t tilebase(int64_t tile) { return " +
                              deposit_expr("tile", ns, "int64_t") +
                              "; }\n  __device__ static int64_t hi(int h) { return " + deposit_expr("h", hs, "int64_t") +
@@ -333,7 +334,7 @@ std::string jit_source(const FusedPlan &P, int p, bool rev, int dtype)
         for (int gi = sr.g_begin; gi < sr.g_end; gi++) emit_gate(o, P, d, gates[d.gate_begin + gi], rev, NR);
         o << "    subrun_store<Rt, NR, REV>(c, base, off, a, b);\n  }\n";
     }
-    o << "  tile_end<Rt, NR, REV>(phi, psi, args, tile, c);\n}\n";
+    o << "  tile_end<Rt, NR, REV, Geom>(phi, psi, args, tile, c);\n}\n";
     return o.str();
 }
 
