@@ -464,6 +464,16 @@ static void fused_gates_of(gbvqc_circuit *c, const DensMap &map, std::vector<PGa
             g.rdiag = real_diag(g.rec_f) && real_diag(g.rec_i);
         }
     }
+    // rotations [[c, -s], [s, c]] (Ry, fixed or variational) in every direction
+    auto rotation = [&](int rec) {
+        const MatRec &r = c->recs[rec];
+        for (int i = 1; i < 8; i += 2)
+            if (r.d[i] != 0.0) return false;
+        return r.d[0] == r.d[6] && r.d[2] == -r.d[4];
+    };
+    for (PGate &g : out)
+        if (g.ftype == FT_REAL1 && g.k == 1 && g.rec_a == g.rec_i)
+            g.rot = g.param >= 0 || (!dynamic[g.rec_f] && !dynamic[g.rec_i] && rotation(g.rec_f) && rotation(g.rec_i));
 }
 
 extern "C" gbvqc_status circuit_create(const gbvqc_op *ops, int n_ops, int n_qubits, int n_params,
@@ -737,6 +747,8 @@ gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPla
     opt.max_slots = batch ? 128 : 512;
     opt.gate_smem = batch ? 40 * 1024 : 64 * 1024;
     opt.phase_tables = !batch;  // batch members stage matrices without a per-step image
+    // a gradient through the specialised passes ignores global phases: rotations as shears
+    opt.rot_shears = grad_layout && jit && !batch && !c->density;
     std::vector<int8_t> perm;
     std::vector<PGate> permuted;
     if (grad_layout && !c->density) perm = choose_grad_layout(pg0, c->n_phys, opt);

@@ -46,8 +46,10 @@ enum Shape : int32_t {
     SH_RPAR2 = 12,  // SH_PAR2 with real entries (depolarising, amplitude and phase damping)
     SH_CX = 13,     // exactly CNOT (control = first qubit): a swap, no arithmetic
     SH_CZ = 14,     // exactly CZ: the sign of |11>, no arithmetic
-    SH_RDIAG1 = 15  // real diagonal, general off-diagonal 2x2 (a fixed gate such as sqrt(W)
+    SH_RDIAG1 = 15, // real diagonal, general off-diagonal 2x2 (a fixed gate such as sqrt(W)
                     // after phase normalisation); one-qubit layer entries only
+    SH_ROT1 = 16    // a rotation [[c, -s], [s, c]] applied as three shears (unit entries:
+                    // alpha, beta; kUnitShear); up to a global sign, so gradient plans only
 };
 
 inline __host__ __device__ bool shape_is_diag(int sh) { return sh == SH_DIAG1 || sh == SH_DIAG2 || sh == SH_CZ; }
@@ -304,6 +306,10 @@ enum GenType : int32_t { GEN_NONE = 0, GEN_X = 1, GEN_Y = 2, GEN_Z = 3, GEN_M2 =
 struct MatUnit {
     int32_t rec, part;
 };
+// MatUnit.part of a unit holding a rotation record's shear parameters (alpha, beta, 0...):
+// for c >= 0, alpha = -s / (1 + c), beta = s; for c < 0 the shears of -R, alpha = s / (1 - c),
+// beta = -s (|alpha| <= 1 both ways; the dropped sign is a global phase).
+constexpr int32_t kUnitShear = 8;
 
 struct FGate {               // 32 bytes, staged in shared memory
     int8_t type;             // FType

@@ -70,6 +70,22 @@ __device__ __forceinline__ void apply2(const R *m, typename CT<R>::T &a, typenam
             b.x = fma(m[6], b.x, bx);
             b.y = fma(m[6], b.y, by);
         }
+    } else if (SH == SH_ROT1) {
+        // R(phi) = [[1, alpha], [0, 1]] [[1, 0], [beta, 1]] [[1, alpha], [0, 1]] with
+        // alpha = -tan(phi / 2), beta = sin(phi): three fmas per component pair
+        if constexpr (sizeof(R) == 4) {
+            const float2 al = make_float2(m[0], m[0]), be = make_float2(m[1], m[1]);
+            a = __ffma2_rn(al, b, a);
+            b = __ffma2_rn(be, a, b);
+            a = __ffma2_rn(al, b, a);
+        } else {
+            a.x = fma(m[0], b.x, a.x);
+            a.y = fma(m[0], b.y, a.y);
+            b.x = fma(m[1], a.x, b.x);
+            b.y = fma(m[1], a.y, b.y);
+            a.x = fma(m[0], b.x, a.x);
+            a.y = fma(m[0], b.y, a.y);
+        }
     } else if (SH == SH_RDIAG1) {
         // real diagonal (m[1] = m[7] = 0): the diagonal term of each output is one packed
         // multiply (complex64) or two multiplies

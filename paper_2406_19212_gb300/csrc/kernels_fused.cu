@@ -142,6 +142,18 @@ __device__ __forceinline__ void phase_table_entry(const TabDesc &tab, int j, con
     img[tab.off + 2 * j + 1] = (R)pi;
 }
 
+// Element e of unit m: a record part, or the shear parameters of a rotation record
+// (kUnitShear), computed from its FP64 entries c = m[0], s = m[4].
+template <typename R>
+__device__ __forceinline__ R unit_elem(const MatUnit &m, int e, const MatRec *__restrict__ recs)
+{
+    if (m.part != kUnitShear) return mat_of<R>(&recs[m.rec])[8 * m.part + e];
+    if (e > 1) return R(0);
+    const double c = recs[m.rec].d[0], s = recs[m.rec].d[4];
+    if (e == 0) return (R)(c >= 0.0 ? -s / (1.0 + c) : s / (1.0 - c));
+    return (R)(c >= 0.0 ? s : -s);
+}
+
 template <typename R>
 __global__ void k_gather_units(GatherArgs g)
 {
@@ -150,10 +162,10 @@ __global__ void k_gather_units(GatherArgs g)
     R *img_f = (R *)g.img_f, *img_r = (R *)g.img_r;
     if (u < g.nf) {
         const MatUnit m = g.fu[u];
-        if (m.rec >= 0) img_f[i] = mat_of<R>(&g.recs[m.rec])[8 * m.part + e];  // rec < 0: a table's units
+        if (m.rec >= 0) img_f[i] = unit_elem<R>(m, e, g.recs);  // rec < 0: a table's units
     } else if (u < g.nf + g.nr) {
         const MatUnit m = g.ru[u - g.nf];
-        if (m.rec >= 0) img_r[i - 8 * g.nf] = mat_of<R>(&g.recs[m.rec])[8 * m.part + e];
+        if (m.rec >= 0) img_r[i - 8 * g.nf] = unit_elem<R>(m, e, g.recs);
     } else {
         const int k = i - 8 * (g.nf + g.nr);
         const int nfe = g.n_ftabs << g.fbits;

@@ -100,11 +100,22 @@ struct Emitter {
     bool overflow = false;   // a phase block class with more than 255 entries
 
     // a unit of its own (no sharing): layers take runs of consecutive units
-    int fresh_unit(int rec)
+    int fresh_unit(int rec, int part = 0)
     {
-        units.push_back(MatUnit{rec, 0});
+        units.push_back(MatUnit{rec, part});
         return (int)units.size() - 1 - unit_base;
     }
+
+    // the shear parameters of a rotation record (shared)
+    std::map<int, int> shear_of_rec;
+    int shear_unit(int rec)
+    {
+        auto it = shear_of_rec.find(rec);
+        if (it != shear_of_rec.end()) return it->second;
+        units.push_back(MatUnit{rec, kUnitShear});
+        return shear_of_rec[rec] = (int)units.size() - 1 - unit_base;
+    }
+    bool rot_shears = false;  // PlanOptions::rot_shears
 
     // a register phase table over 2^NR indices from the given entries: reserves its units
     // (placeholders the gather skips) and returns the first, pass-local
@@ -302,9 +313,11 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
                     f.slot = -1;
                     f.ent = (int16_t)((int)E.ents.size() - E.ent_base);
                     int first = -1;
+                    auto shear = [&](const PGate &g) { return E.rot_shears && g.rot && g.ftype == FT_REAL1; };
                     if (!E.reverse)
                         for (int pos : layer) {
-                            const int u = E.fresh_unit(G[order[pos]].rec_f);
+                            const PGate &g = G[order[pos]];
+                            const int u = E.fresh_unit(g.rec_f, shear(g) ? kUnitShear : 0);
                             if (first < 0) first = u;
                         }
                     f.mat = f.mat2 = (int16_t)first;
@@ -314,15 +327,21 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
                         DEnt d{};
                         const int k = slot_of(E.local_of[g.q[0]]);
                         mask |= 1 << k;
-                        d.k = (int8_t)(g.ftype == FT_REAL1   ? SH_REAL1
+                        d.k = (int8_t)(shear(g)              ? SH_ROT1
+                                       : g.ftype == FT_REAL1 ? SH_REAL1
                                        : g.ftype == FT_ANTI1 ? SH_ANTI1
                                        : g.ftype == FT_IMAG1 ? SH_IMAG1
                                        : g.rdiag             ? SH_RDIAG1
                                                              : SH_DENSE1);
                         codes |= (g.ftype == FT_REAL1 ? 1 : g.ftype == FT_IMAG1 ? 2 : g.ftype == FT_ANTI1 ? 3 : 0) << (2 * k);
                         d.ca = (int8_t)k;
-                        d.mat = (int16_t)(E.reverse ? E.unit(g.rec_i, 1) : first + i_ent);
-                        d.mat2 = (int16_t)(E.reverse ? E.unit(g.rec_a, 1) : d.mat);
+                        if (E.reverse && shear(g)) {
+                            d.mat = (int16_t)E.shear_unit(g.rec_i);
+                            d.mat2 = (int16_t)E.shear_unit(g.rec_a);
+                        } else {
+                            d.mat = (int16_t)(E.reverse ? E.unit(g.rec_i, 1) : first + i_ent);
+                            d.mat2 = (int16_t)(E.reverse ? E.unit(g.rec_a, 1) : d.mat);
+                        }
                         i_ent++;
                         d.cls = GEN_NONE;
                         d.slot = -1;
@@ -681,6 +700,7 @@ bool build_fused_plan(const std::vector<PGate> &G, int n, const PlanOptions &opt
                       rev ? out.rents : out.fents, rev ? out.runits : out.funits,
                       rev ? out.rtabs : out.ftabs, rev ? out.rtabents : out.ftabents, opt.phase_tables,
                       0, 0, 0, {}, 0.0, 0, false, false};
+            E.rot_shears = opt.rot_shears;
             E.gate_base = (int)E.gates.size();
             E.ent_base = (int)E.ents.size();
             E.unit_base = (int)E.units.size();

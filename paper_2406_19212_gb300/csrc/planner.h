@@ -28,6 +28,7 @@ struct PGate {
     int param;        // parameter index or -1
     bool cz = false;  // exactly diag(1, 1, 1, -1) in every direction (CZ)
     bool rdiag = false;  // FT_DENSE1 whose matrices (every direction) have an exactly real diagonal
+    bool rot = false;    // FT_REAL1 whose matrices are rotations [[c, -s], [s, c]] (Ry)
 };
 
 struct PlanOptions {
@@ -38,6 +39,8 @@ struct PlanOptions {
     int elem_bytes = 4;    // real element size (4: complex64, 8: complex128)
     int gate_smem = 24 * 1024;  // shared-memory budget of a pass's gate data
     bool phase_tables = false;  // table-mode phase blocks (needs the per-step matrix image)
+    bool rot_shears = false;    // rotations as SH_ROT1 layer entries (gradient plans of the
+                                // specialised passes: a global sign per gate is allowed)
 };
 
 struct FusedPlan {
