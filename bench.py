@@ -141,7 +141,8 @@ def max_over_ranks(world, x: float) -> float:
     return float(t.item())
 
 
-KERNEL_SOURCES = ("fused_tile.cuh", "devmath.cuh", "common.cuh", "kernels_fused.cu", "jit.cpp")
+KERNEL_SOURCES = ("fused_tile.cuh", "devmath.cuh", "common.cuh", "kernels_fused.cu", "jit.cpp", "planner.cpp",
+                  "api_circuit.cu")
 
 
 def kernel_src_sha() -> str:
