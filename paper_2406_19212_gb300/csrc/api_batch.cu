@@ -34,6 +34,7 @@ struct gbvqc_batch {
     int *d_csr_ptr = nullptr, *d_csr_slots = nullptr;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
+    bool init_in_pass = false;  // every member's first forward pass writes its |0...0> start
 };
 
 // Device resources of a batch (everything batch_build makes); the member lists stay.
@@ -111,6 +112,8 @@ static gbvqc_status batch_build(gbvqc_batch *b)
     auto state_ptr = [&](void *base, int i) { return (void *)((unsigned char *)base + amp_off[i] * amp); };
     // fused launches: pass p of every circuit that has one, grouped by tile size
     CUDA_TRY(fused_batch_prepare());
+    b->init_in_pass = true;
+    for (int i = 0; i < n; i++) b->init_in_pass = b->init_in_pass && !plans[i]->p.fwd.empty();
     for (int dir = 0; dir < 2; dir++) {
         const bool rev = dir == 1;
         for (int r = 0; r < max_passes; r++) {
@@ -138,6 +141,9 @@ static gbvqc_status batch_build(gbvqc_batch *b)
                     else
                         e.args = FusedArgs{dp->d_fwd + p, dp->d_fsubs, dp->d_fgates, dp->d_fents, dp->d_funits,
                                            b->circs[i]->d_recs, nullptr, nullptr, 0};
+                    // the first forward pass starts from |0...0>: only the member's tile 0
+                    // runs its gates, the others are written as zeros (FusedArgs::init)
+                    if (!rev && p == 0 && b->init_in_pass) e.args.init = 1;
                     e.phi = state_ptr(b->phi_all, i);
                     e.psi = rev ? state_ptr(b->psi_all, i) : nullptr;
                     e.begin = L.tiles;
@@ -183,7 +189,7 @@ static gbvqc_status batch_build(gbvqc_batch *b)
 static gbvqc_status batch_enqueue(gbvqc_batch *b, cudaStream_t s)
 {
     CUDA_TRY(launch_batch_init(b->d_dyn, b->n_dyn, b->d_theta, b->dtype, b->phi_all, b->state_bytes, b->d_amp_off,
-                               b->n, s));
+                               b->n, s, !b->init_in_pass));
     for (const BatchLaunch &L : b->fwd)
         CUDA_TRY(launch_fused_batch(b->dtype, false, L.twoq, L.t, L.d_entries, L.n_entries, L.tiles, L.smem, s));
     CUDA_TRY(launch_pauli_batch(b->dtype, b->d_pauli, b->n, b->pauli_chunks, b->pauli_smem, b->d_energies, s));

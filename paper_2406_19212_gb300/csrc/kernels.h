@@ -234,7 +234,10 @@ cudaError_t launch_pauli_batch(int dtype, const PauliBatchEntry *entries, int n_
                                size_t smem, double *energies, cudaStream_t s);
 cudaError_t launch_slots_batch(const SlotBatchEntry *entries, int n_entries, int64_t total_slots,
                                double *slot_grad, cudaStream_t s);
+// Materialise the batch's rotation records and, with zero_states, set every instance to
+// |0...0> (without it the first forward passes write the initial states: FusedArgs::init).
 cudaError_t launch_batch_init(const BatchDyn *dyn, int n_dyn, const double *theta, int dtype, void *phi_all,
-                              size_t phi_bytes, const int64_t *offsets, int n_inst, cudaStream_t s);
+                              size_t phi_bytes, const int64_t *offsets, int n_inst, cudaStream_t s,
+                              bool zero_states = true);
 
 }  // namespace gbvqc

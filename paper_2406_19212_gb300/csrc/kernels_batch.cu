@@ -294,13 +294,14 @@ __global__ void k_zero_ones(void *base, const int64_t *offsets, int n, int dtype
 }
 
 cudaError_t launch_batch_init(const BatchDyn *dyn, int n_dyn, const double *theta, int dtype, void *phi_all,
-                              size_t phi_bytes, const int64_t *offsets, int n_inst, cudaStream_t s)
+                              size_t phi_bytes, const int64_t *offsets, int n_inst, cudaStream_t s, bool zero_states)
 {
     if (n_dyn > 0) {
         k_materialize_batch<<<(n_dyn + 127) / 128, 128, 0, s>>>(dyn, n_dyn, theta);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (!zero_states) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(phi_all, 0, phi_bytes, s);
     if (e != cudaSuccess) return e;
     k_zero_ones<<<(n_inst + 127) / 128, 128, 0, s>>>(phi_all, offsets, n_inst, dtype);
