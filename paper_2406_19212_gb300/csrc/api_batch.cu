@@ -35,6 +35,9 @@ struct gbvqc_batch {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool init_in_pass = false;  // every member's first forward pass writes its |0...0> start
+    GatherArgs *d_gather = nullptr;  // per member: its plan's per-step image (phase tables)
+    int64_t *d_gather_off = nullptr;
+    int64_t gather_total = 0;
 };
 
 // Device resources of a batch (everything batch_build makes); the member lists stay.
@@ -48,6 +51,7 @@ static void batch_release(gbvqc_batch *b)
     dev_free(b->d_theta); dev_free(b->d_energies); dev_free(b->d_grads); dev_free(b->d_slot_grad);
     dev_free(b->d_slot_partials); dev_free(b->d_pauli_partials); dev_free(b->d_pauli);
     dev_free(b->d_slots); dev_free(b->d_csr_ptr); dev_free(b->d_csr_slots);
+    dev_free(b->d_gather); dev_free(b->d_gather_off);
     gbvqc_batch fresh;
     fresh.circs = std::move(b->circs);
     fresh.obs = std::move(b->obs);
@@ -136,11 +140,11 @@ static gbvqc_status batch_build(gbvqc_batch *b)
                     FusedBatchEntry e{};
                     if (rev)
                         e.args = FusedArgs{dp->d_rev + p, dp->d_rsubs, dp->d_rgates, dp->d_rents, dp->d_runits,
-                                           b->circs[i]->d_recs, nullptr, b->d_slot_partials + part_off[i],
+                                           b->circs[i]->d_recs, dp->d_rimg, b->d_slot_partials + part_off[i],
                                            1 << (b->circs[i]->n_phys - dp->p.t)};
                     else
                         e.args = FusedArgs{dp->d_fwd + p, dp->d_fsubs, dp->d_fgates, dp->d_fents, dp->d_funits,
-                                           b->circs[i]->d_recs, nullptr, nullptr, 0};
+                                           b->circs[i]->d_recs, dp->d_fimg, nullptr, 0};
                     // the first forward pass starts from |0...0>: only the member's tile 0
                     // runs its gates, the others are written as zeros (FusedArgs::init)
                     if (!rev && p == 0 && b->init_in_pass) e.args.init = 1;
@@ -179,6 +183,19 @@ static gbvqc_status batch_build(gbvqc_batch *b)
         b->pauli_smem = std::max(b->pauli_smem, obs_smem_bytes(od, b->dtype));
     }
     if (!staged) b->pauli_smem = 0;
+    // per-step matrix images of every member (their phase tables), one launch
+    std::vector<GatherArgs> ga(n);
+    std::vector<int64_t> goff(n + 1, 0);
+    for (int i = 0; i < n; i++) {
+        DevPlan *p = plans[i];
+        ga[i] = GatherArgs{p->d_funits, (int)p->p.funits.size(), p->d_runits, (int)p->p.runits.size(), p->d_fimg,
+                           p->d_rimg, b->circs[i]->d_recs, p->d_ftabs, p->d_rtabs, p->d_ftabents, p->d_rtabents,
+                           (int)p->p.ftabs.size(), (int)p->p.rtabs.size(), p->p.nr_f, p->p.nr_r};
+        goff[i + 1] = goff[i] + gather_items(ga[i]);
+    }
+    b->gather_total = goff[n];
+    ST_TRY(upload(&b->d_gather, ga));
+    ST_TRY(upload(&b->d_gather_off, goff));
     ST_TRY(upload(&b->d_pauli, pe));
     ST_TRY(upload(&b->d_slots, se));
     ST_TRY(csr_upload(gslot_param, b->total_params, &b->d_csr_ptr, &b->d_csr_slots));
@@ -190,6 +207,7 @@ static gbvqc_status batch_enqueue(gbvqc_batch *b, cudaStream_t s)
 {
     CUDA_TRY(launch_batch_init(b->d_dyn, b->n_dyn, b->d_theta, b->dtype, b->phi_all, b->state_bytes, b->d_amp_off,
                                b->n, s, !b->init_in_pass));
+    CUDA_TRY(launch_gather_batch(b->dtype, b->d_gather, b->d_gather_off, b->n, b->gather_total, s));
     for (const BatchLaunch &L : b->fwd)
         CUDA_TRY(launch_fused_batch(b->dtype, false, L.twoq, L.t, L.d_entries, L.n_entries, L.tiles, L.smem, s));
     CUDA_TRY(launch_pauli_batch(b->dtype, b->d_pauli, b->n, b->pauli_chunks, b->pauli_smem, b->d_energies, s));

@@ -746,7 +746,7 @@ gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPla
     opt.elem_bytes = dtype == GBVQC_C64 ? 4 : 8;
     opt.max_slots = batch ? 128 : 512;
     opt.gate_smem = batch ? 40 * 1024 : 64 * 1024;
-    opt.phase_tables = !batch;  // batch members stage matrices without a per-step image
+    opt.phase_tables = true;  // (batch members' images: one batched gather per step)
     // a gradient through the specialised passes ignores global phases: rotations as shears
     opt.rot_shears = grad_layout && jit && !batch && !c->density;
     std::vector<int8_t> perm;

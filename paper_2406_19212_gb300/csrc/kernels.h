@@ -178,7 +178,16 @@ struct GatherArgs {
     const TabEnt *ftabents, *rtabents;
     int n_ftabs, n_rtabs, fbits, rbits;
 };
+// Items of a plan's image (one thread each).
+inline __host__ __device__ int64_t gather_items(const GatherArgs &g)
+{
+    return 8 * (int64_t)(g.nf + g.nr) + ((int64_t)g.n_ftabs << g.fbits) + ((int64_t)g.n_rtabs << g.rbits);
+}
 cudaError_t launch_gather_units(int dtype, const GatherArgs &g, cudaStream_t s);
+// The same for n plans at once (batched gradients): args[k] of plan k, item_off[k] its
+// first item (8 per unit, one per table entry), item_off[n] = total items.
+cudaError_t launch_gather_batch(int dtype, const GatherArgs *args, const int64_t *item_off, int n, int64_t total,
+                                cudaStream_t s);
 int fused_nr(int dtype, bool reverse);           // register qubits per sub-run
 // Threads per CTA the fused kernels are compiled for (launch bounds): 2^(t - NR) must
 // not exceed it.  Two CTAs per SM for the reverse kernels, three for the forward ones.

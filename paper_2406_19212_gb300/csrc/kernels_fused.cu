@@ -154,10 +154,11 @@ __device__ __forceinline__ R unit_elem(const MatUnit &m, int e, const MatRec *__
     return (R)(c >= 0.0 ? s : -s);
 }
 
+// Item i of a plan's per-step image: element i & 7 of unit i >> 3 (forward units, then
+// reverse units), then the entries of the forward and reverse phase tables.
 template <typename R>
-__global__ void k_gather_units(GatherArgs g)
+__device__ __forceinline__ void gather_item(const GatherArgs &g, int i)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int u = i >> 3, e = i & 7;
     R *img_f = (R *)g.img_f, *img_r = (R *)g.img_r;
     if (u < g.nf) {
@@ -177,9 +178,41 @@ __global__ void k_gather_units(GatherArgs g)
     }
 }
 
+template <typename R>
+__global__ void k_gather_units(GatherArgs g)
+{
+    gather_item<R>(g, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// The images of many plans in one launch: item i belongs to the plan k with
+// item_off[k] <= i < item_off[k + 1] (binary search; item_off[n] = total).
+template <typename R>
+__global__ void k_gather_batch(const GatherArgs *__restrict__ args, const int64_t *__restrict__ item_off, int n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= item_off[n]) return;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    gather_item<R>(args[lo], (int)(i - item_off[lo]));
+}
+
+cudaError_t launch_gather_batch(int dtype, const GatherArgs *args, const int64_t *item_off, int n, int64_t total,
+                                cudaStream_t s)
+{
+    if (total == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    if (dtype == 0) k_gather_batch<float><<<blocks, 256, 0, s>>>(args, item_off, n);
+    else k_gather_batch<double><<<blocks, 256, 0, s>>>(args, item_off, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather_units(int dtype, const GatherArgs &g, cudaStream_t s)
 {
-    const int64_t total = 8 * (int64_t)(g.nf + g.nr) + ((int64_t)g.n_ftabs << g.fbits) + ((int64_t)g.n_rtabs << g.rbits);
+    const int64_t total = gather_items(g);
     if (total == 0) return cudaSuccess;
     const int blocks = (int)((total + 255) / 256);
     if (dtype == 0) k_gather_units<float><<<blocks, 256, 0, s>>>(g);
