@@ -747,8 +747,8 @@ gbvqc_status get_host_plan(gbvqc_circuit *c, int dtype, bool grad_layout, DevPla
     opt.max_slots = batch ? 128 : 512;
     opt.gate_smem = batch ? 40 * 1024 : 64 * 1024;
     opt.phase_tables = true;  // (batch members' images: one batched gather per step)
-    // a gradient through the specialised passes ignores global phases: rotations as shears
-    opt.rot_shears = grad_layout && jit && !batch && !c->density;
+    // a gradient ignores global phases: rotations as shears in every pure-state gradient plan
+    opt.rot_shears = grad_layout && !c->density;
     std::vector<int8_t> perm;
     std::vector<PGate> permuted;
     if (grad_layout && !c->density) perm = choose_grad_layout(pg0, c->n_phys, opt);

@@ -630,6 +630,7 @@ __device__ __forceinline__ void layer_gate(int sh, const R *m, typename CT<R>::T
     if (sh == 1) rg1<R, NR, K, SH_REAL1>(a, m);
     else if (sh == 2) rg1<R, NR, K, SH_IMAG1>(a, m);
     else if (sh == 0) rg1<R, NR, K, SH_DENSE1>(a, m);
+    else if (sh == 4) rg1<R, NR, K, SH_ROT1>(a, m);
     else rg1<R, NR, K, SH_ANTI1>(a, m);
 }
 
@@ -657,6 +658,9 @@ __device__ __forceinline__ void layer_slot_ent(int mask, const DEnt *le, int &id
             } else if (d.k == SH_IMAG1) {
                 rg1<R, NR, K, SH_IMAG1>(a, m);
                 if constexpr (REV) rg1<R, NR, K, SH_IMAG1>(b, m2);
+            } else if (d.k == SH_ROT1) {
+                rg1<R, NR, K, SH_ROT1>(a, m);
+                if constexpr (REV) rg1<R, NR, K, SH_ROT1>(b, m2);
             } else if (d.k == SH_DENSE1 || d.k == SH_RDIAG1) {  // (general form for both)
                 rg1<R, NR, K, SH_DENSE1>(a, m);
                 if constexpr (REV) rg1<R, NR, K, SH_DENSE1>(b, m2);
@@ -670,7 +674,7 @@ __device__ __forceinline__ void layer_slot_ent(int mask, const DEnt *le, int &id
 }
 
 // Forward form for kernels without two-qubit gates: the record carries each slot's shape
-// (codes, 2 bits per slot) and the first of the layer's consecutive matrix units, so no
+// (codes, 3 bits per slot) and the first of the layer's consecutive matrix units, so no
 // matrix address waits for an entry load, and the next entry's matrix is loaded into
 // registers while the current one is applied.
 template <typename R, int NR, int K>
@@ -681,7 +685,7 @@ __device__ __forceinline__ void layer_slot_pf(int mask, int codes, const R *mp, 
         if ((mask >> K) & 1) {
             R nxt[8];
             load_unit<R>(mp + 8 * (idx + 1 < last ? idx + 1 : last), nxt);
-            layer_gate<R, NR, K>((codes >> (2 * K)) & 3, cur, a);
+            layer_gate<R, NR, K>((codes >> (3 * K)) & 7, cur, a);
 #pragma unroll
             for (int i = 0; i < 8; i++) cur[i] = nxt[i];
             idx++;
@@ -845,6 +849,18 @@ __device__ __forceinline__ void tile_zero(typename CT<R>::T *gmem, int low, int6
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// Element e of matrix unit m: a record part, or the shear parameters of a rotation record
+// (kUnitShear), computed from its FP64 entries c = m[0], s = m[4].
+template <typename R>
+__device__ __forceinline__ R unit_elem(const MatUnit &m, int e, const MatRec *__restrict__ recs)
+{
+    if (m.part != kUnitShear) return mat_of<R>(&recs[m.rec])[8 * m.part + e];
+    if (e > 1) return R(0);
+    const double c = recs[m.rec].d[0], s = recs[m.rec].d[4];
+    if (e == 0) return (R)(c >= 0.0 ? -s / (1.0 + c) : s / (1.0 - c));
+    return (R)(c >= 0.0 ? s : -s);
+}
+
 // Shared-memory layout and per-CTA state of one tile pass, built by tile_begin and used
 // by the sub-runs (interpreted from the pass's records, or specialised code) and tile_end.
 template <typename R, int NR, bool REV>
@@ -988,7 +1004,7 @@ __device__ __forceinline__ bool tile_begin(const typename CT<R>::T *__restrict__
         } else {
             for (int i = threadIdx.x; i < pd.n_units * 8; i += blockDim.x) {
                 const MatUnit u = args.units[pd.unit_begin + (i >> 3)];
-                smat[i] = u.rec >= 0 ? mat_of<R>(&args.recs[u.rec])[8 * u.part + (i & 7)] : R(0);
+                smat[i] = u.rec >= 0 ? unit_elem<R>(u, i & 7, args.recs) : R(0);
             }
         }
     }

@@ -142,18 +142,6 @@ __device__ __forceinline__ void phase_table_entry(const TabDesc &tab, int j, con
     img[tab.off + 2 * j + 1] = (R)pi;
 }
 
-// Element e of unit m: a record part, or the shear parameters of a rotation record
-// (kUnitShear), computed from its FP64 entries c = m[0], s = m[4].
-template <typename R>
-__device__ __forceinline__ R unit_elem(const MatUnit &m, int e, const MatRec *__restrict__ recs)
-{
-    if (m.part != kUnitShear) return mat_of<R>(&recs[m.rec])[8 * m.part + e];
-    if (e > 1) return R(0);
-    const double c = recs[m.rec].d[0], s = recs[m.rec].d[4];
-    if (e == 0) return (R)(c >= 0.0 ? -s / (1.0 + c) : s / (1.0 - c));
-    return (R)(c >= 0.0 ? s : -s);
-}
-
 // Item i of a plan's per-step image: element i & 7 of unit i >> 3 (forward units, then
 // reverse units), then the entries of the forward and reverse phase tables.
 template <typename R>

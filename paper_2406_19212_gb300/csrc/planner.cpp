@@ -333,7 +333,11 @@ void build_subruns(const std::vector<int> &order, Emitter &E)
                                        : g.ftype == FT_IMAG1 ? SH_IMAG1
                                        : g.rdiag             ? SH_RDIAG1
                                                              : SH_DENSE1);
-                        codes |= (g.ftype == FT_REAL1 ? 1 : g.ftype == FT_IMAG1 ? 2 : g.ftype == FT_ANTI1 ? 3 : 0) << (2 * k);
+                        codes |= (shear(g)               ? 4
+                                  : g.ftype == FT_REAL1 ? 1
+                                  : g.ftype == FT_IMAG1 ? 2
+                                  : g.ftype == FT_ANTI1 ? 3
+                                                        : 0) << (3 * k);
                         d.ca = (int8_t)k;
                         if (E.reverse && shear(g)) {
                             d.mat = (int16_t)E.shear_unit(g.rec_i);

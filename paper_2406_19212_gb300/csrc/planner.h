@@ -39,8 +39,8 @@ struct PlanOptions {
     int elem_bytes = 4;    // real element size (4: complex64, 8: complex128)
     int gate_smem = 24 * 1024;  // shared-memory budget of a pass's gate data
     bool phase_tables = false;  // table-mode phase blocks (needs the per-step matrix image)
-    bool rot_shears = false;    // rotations as SH_ROT1 layer entries (gradient plans of the
-                                // specialised passes: a global sign per gate is allowed)
+    bool rot_shears = false;    // rotations as SH_ROT1 layer entries (gradient plans: a
+                                // global sign per gate is allowed)
 };
 
 struct FusedPlan {
