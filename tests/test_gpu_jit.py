@@ -114,3 +114,29 @@ def test_jit_rqc24_matches_oracle():
         got = gb.sv_get(sv).astype(np.complex128)
         sv.free()
         check_amps(got, ref, dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", [gb.FUSED, gb.JIT])
+def test_grad_rotation_angles_at_the_shear_branches(dtype, mode):
+    """Gradient plans apply Ry as three shears, with the shears of -R where cos(theta/2) < 0
+    (a global sign that Phi and Psi share).  Angles on and around the branch point
+    (theta = pi), near 0 and 2 pi, and beyond [0, 2 pi): energy and gradient against the
+    oracle, which applies the rotation matrices directly."""
+    n = 11
+    angles = [0.0, np.pi, np.pi - 1e-7, np.pi + 1e-7, 2 * np.pi - 1e-9, 3 * np.pi, -np.pi / 2, 0.5, 2.5, 4.0, 5.9]
+    ops, p = [], 0
+    for layer in range(3):
+        for q in range(n):
+            ops.append(I.Op("RY", (q,), param=p))
+            p += 1
+        for q in range(layer % 2, n - 1, 2):
+            ops.append(I.Op("CZ", (q, q + 1)))
+        ops.append(I.Op("RY", ((layer * 5) % n,), fixed=(angles[layer * 3 % len(angles)],)))
+    theta = np.array([angles[i % len(angles)] for i in range(p)])
+    circuit = I.Circuit(n, ops, p)
+    obs = [(0.7, ((q, "X"),)) for q in range(n)] + [(1.0, ((q, "Z"), (q + 1, "Z"))) for q in range(n - 1)]
+    e_ref, g_ref = O.adjoint_grad(circuit, theta, obs)
+    e, g = gb.grad(gb.circuit_create(circuit), theta, gb.obs_create(obs, n), dtype, mode)
+    check_energy(e, e_ref, dtype)
+    check_grad(g, g_ref, dtype)
